@@ -1,0 +1,148 @@
+/*
+ * bsparareal.h -- C ABI of the GB300 (sm_103a) Parareal library for the two-asset
+ * Black-Scholes equation.
+ *
+ * Method: Ibrahim, Goetschel, Ruprecht, "Space-time parallel scaling of Parareal with a
+ * physics-informed Fourier Neural Operator coarse propagator applied to the Black-Scholes
+ * equation" (PASC'25).  Section and equation names below refer to that paper.
+ *
+ * Conventions
+ *  - Every entry point returns an int status: BS_OK (0) or a negative BS_ERR_* code.
+ *    bs_last_error() returns a message for the last failure on the calling host thread.
+ *  - Grids are square: M nodes per axis including both ends, x_i = i*xmax/(M-1)
+ *    (the paper uses dx = dy, Sec. 3.2).  A state is a row-major float array u[j*M + i]
+ *    with j the y (second asset) index and i the x (first asset) index.
+ *  - Device pointers are owned by the caller.  Handles (bs_grid, bs_pino) are owned by
+ *    the library and released with the matching *_destroy call.
+ *  - Work is enqueued on the caller's CUDA stream (a cudaStream_t / CUstream; NULL is the
+ *    legacy default stream) and is asynchronous unless a function says "synchronous".
+ *  - A handle may be used by one stream at a time: internal workspace is reused between
+ *    calls in stream order.
+ *  - Time is tau = T - t (eq. bse_change_variable); tau = 0 is the payoff.
+ */
+#ifndef BSPARAREAL_H
+#define BSPARAREAL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* bs_stream;      /* same type as cudaStream_t */
+
+typedef struct bs_grid bs_grid;             /* opaque: grid size + internal workspace */
+typedef struct bs_pino bs_pino;             /* opaque: PINO weights resident on the GPU */
+
+enum {
+  BS_OK = 0,
+  BS_ERR_ARG = -1,      /* invalid argument (NULL pointer, size, unsupported combination) */
+  BS_ERR_CUDA = -2,     /* a CUDA runtime call failed; message has the CUDA error string */
+  BS_ERR_NOCONV = -3,   /* an inner Krylov solve hit its iteration cap */
+  BS_ERR_MAXITER = -4,  /* Parareal reached Kmax without meeting tol (results still valid) */
+  BS_ERR_OOM = -5,      /* device allocation failed */
+  BS_ERR_FILE = -6      /* weight file missing, truncated or malformed */
+};
+
+enum {
+  BS_PAYOFF_BASKET = 0,          /* max(w1*x + w2*y - K, 0) */
+  BS_PAYOFF_EXCHANGE = 1,        /* max(x - y, 0) */
+  BS_PAYOFF_CALL1 = 2,           /* max(x - K, 0): one-asset call, y is a spectator */
+  BS_PAYOFF_CASH_OR_NOTHING = 3  /* c if x >= S1 and y >= S2 else 0 (Sec. 3.2) */
+};
+
+enum { BS_COARSE_NUM = 0, BS_COARSE_PINO = 1 };
+
+/* Model and payoff parameters (eq. bse: sigma1, sigma2, rho, r; Sec. 3.2 payoff). */
+typedef struct {
+  double sigma1, sigma2;   /* volatilities, > 0 */
+  double rho;              /* correlation, |rho| < 1 */
+  double r;                /* risk-free rate, >= 0 */
+  double T;                /* maturity (tau runs over [0, T]) */
+  double strike;           /* K (basket, one-asset call) or S1 (cash-or-nothing) */
+  double w1, w2;           /* basket weights */
+  int payoff;              /* BS_PAYOFF_* */
+  int reserved;            /* must be 0 */
+  double strike2;          /* S2 (cash-or-nothing) */
+  double cash;             /* c  (cash-or-nothing) */
+} bs_params;
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char* bs_last_error(void);
+
+/* Create a grid of M x M nodes on [0, xmax]^2 (4 <= M <= 4096, xmax > 0).  Selects the
+ * device that is current on the calling thread.  *g receives the handle. */
+int bs_grid_create(int M, double xmax, bs_grid** g);
+int bs_grid_destroy(bs_grid* g);
+
+/* Write the payoff u(tau = 0) (Sec. 3.2; reading of the boundary: the far edges carry the
+ * same closed-form data as at tau = 0) into the device array u[M*M].  Asynchronous. */
+int bs_payoff(const bs_grid* g, const bs_params* p, float* u, bs_stream stream);
+
+/* Fine propagator F of Sec. 3.1 for B independent states at once (eq. fd with implicit
+ * Euler, Sec. 3.2).  For item b, nsteps implicit-Euler steps of size dtau[b] are taken
+ * from tau0[b]:  (I - dtau R_h) u^{m+1} = u^m, with the 9-point centred operator R_h of
+ * eq. (fd), the PDE row itself on x = 0 and y = 0 (its coefficients vanish there), and
+ * far-field Dirichlet data g(x, y, tau^{m+1}) on x = xmax and y = xmax (exchange: Margrabe;
+ * basket: max(w1 x + w2 y - K e^{-r tau}, 0); one-asset: Black-Scholes call; cash-or-nothing:
+ * eq. solution).  Each implicit system is solved in FP32 by weighted-Jacobi sweeps whose
+ * count follows from the Gershgorin contraction of the system; the state is carried as a
+ * compensated (hi, lo) float pair across steps and rounded to float on output.
+ *
+ *  p[B], tau0[B], dtau[B]  host arrays (per-item parameters)
+ *  u_in[B], u_out[B]       host arrays of device pointers to float[M*M]; u_out[b] may
+ *                          equal u_in[b] (in place)
+ *  nsteps >= 0, 1 <= B
+ * Results for an item do not depend on B or on the other items.  Asynchronous.
+ * Errors: BS_ERR_ARG (NULL, B < 1, dtau <= 0, contraction >= 0.8 -- Jacobi does not
+ * apply), BS_ERR_CUDA. */
+int fine_propagate_batched(const bs_grid* g, const bs_params* p,
+                           const float* const* u_in, float* const* u_out,
+                           const double* tau0, const double* dtau, int nsteps, int B,
+                           bs_stream stream);
+
+/* Coarse propagator G of Sec. 3.1 for one state.
+ *  kind = BS_COARSE_NUM: nsteps implicit-Euler steps of size dtau_slice/nsteps with the
+ *    same operator as F (Sec. 3.2: the numerical coarse model is the same discretisation
+ *    with a larger step), solved by BiCGSTAB in FP32 (the paper runs its coarse models in
+ *    single precision, Sec. 4.1).  net must be NULL.
+ *  kind = BS_COARSE_PINO: one evaluation of the PINO (Sec. 3.4-3.5) mapping u(tau0) and
+ *    the interval (tau0, tau0 + dtau_slice) to u(tau0 + dtau_slice); nsteps is ignored.
+ * u_in, u_out: device float[M*M] (may alias).  Asynchronous.
+ * Errors: BS_ERR_ARG, BS_ERR_CUDA.  A Krylov solve that hits its iteration cap is reported
+ * by the next synchronous call on this grid as BS_ERR_NOCONV. */
+int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_params* p,
+                     const float* u_in, float* u_out, double tau0, double dtau_slice,
+                     int nsteps, bs_stream stream);
+
+/* Load PINO weights (Sec. 3.5: FNO backbone with lifting, L Fourier layers, projection;
+ * batch norm folded into the pointwise weights) from a little-endian file written by
+ * paper_2404_02521_gb300/pino_train.py.  Weights are converted to BF16 on load.
+ * Synchronous.  Errors: BS_ERR_FILE, BS_ERR_ARG, BS_ERR_OOM. */
+int pino_load(const char* path, bs_pino** net);
+int pino_destroy(bs_pino* net);
+
+/* Parareal, eq. (parareal): u_{n+1}^{k+1} = G(u_n^{k+1}) + F(u_n^k) - G(u_n^k) on N slices
+ * of [0, p->T], starting from the payoff and one serial coarse sweep.  F takes fine_steps
+ * implicit-Euler steps per slice; G is the numerical model with coarse_steps steps per slice
+ * or the PINO.  Iterates until delta_k = max_n ||u_n^{k+1} - u_n^k||_2 / max_n ||u_n^{k+1}||_2
+ * <= tol (FP64 reductions on the GPU) or k = Kmax (Kmax <= N; Kmax = N reproduces the serial
+ * fine solution bitwise).
+ *  u_out        device float[(N+1)*M*M]: u_0..u_N on return
+ *  k_done       host int: iterations performed
+ *  defect_hist  host double[Kmax] (may be NULL): delta_k per iteration
+ * Synchronous (returns after the stream has drained).
+ * Returns BS_OK on convergence, BS_ERR_MAXITER if tol was not met within Kmax (u_out then
+ * holds the last iterate), BS_ERR_NOCONV if a coarse Krylov solve failed. */
+int parareal_solve(const bs_grid* g, const bs_params* p, int N, int fine_steps,
+                   int coarse_kind, int coarse_steps, const bs_pino* net, double tol,
+                   int Kmax, float* u_out, int* k_done, double* defect_hist,
+                   bs_stream stream);
+
+/* Number of Jacobi sweeps F uses per implicit step for these parameters and step size on
+ * this grid (0 if Jacobi does not apply).  Host-only helper. */
+int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSPARAREAL_H */

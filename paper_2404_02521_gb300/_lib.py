@@ -1,0 +1,186 @@
+"""ctypes binding of libbsparareal.so: argument marshalling only.
+
+Every function mirrors an entry point of include/bsparareal.h and takes torch tensors (or
+raw device pointers) for device arrays.  All arithmetic happens in the CUDA library; if the
+library cannot be loaded this module raises, there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbsparareal.so")
+
+BS_OK, BS_ERR_ARG, BS_ERR_CUDA, BS_ERR_NOCONV, BS_ERR_MAXITER, BS_ERR_OOM, BS_ERR_FILE = 0, -1, -2, -3, -4, -5, -6
+ERR_NAMES = {0: "BS_OK", -1: "BS_ERR_ARG", -2: "BS_ERR_CUDA", -3: "BS_ERR_NOCONV",
+             -4: "BS_ERR_MAXITER", -5: "BS_ERR_OOM", -6: "BS_ERR_FILE"}
+BASKET, EXCHANGE, CALL1, CASH_OR_NOTHING = 0, 1, 2, 3
+COARSE_NUM, COARSE_PINO = 0, 1
+
+# exported entry points declared in include/bsparareal.h
+EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
+           "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
+           "parareal_solve", "bs_fine_sweeps"]
+
+
+class bs_params(C.Structure):
+    _fields_ = [("sigma1", C.c_double), ("sigma2", C.c_double), ("rho", C.c_double),
+                ("r", C.c_double), ("T", C.c_double), ("strike", C.c_double),
+                ("w1", C.c_double), ("w2", C.c_double), ("payoff", C.c_int),
+                ("reserved", C.c_int), ("strike2", C.c_double), ("cash", C.c_double)]
+
+
+class BSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load the shared library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if path is None:
+        if not _build.up_to_date():
+            _build.build()
+        path = LIB_PATH
+    lib = C.CDLL(path)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    P = C.POINTER
+    lib.bs_last_error.restype = C.c_char_p
+    lib.bs_last_error.argtypes = []
+    lib.bs_grid_create.argtypes = [i, d, P(vp)]
+    lib.bs_grid_destroy.argtypes = [vp]
+    lib.bs_payoff.argtypes = [vp, P(bs_params), vp, vp]
+    lib.fine_propagate_batched.argtypes = [vp, P(bs_params), P(vp), P(vp), P(d), P(d), i, i, vp]
+    lib.coarse_propagate.argtypes = [vp, i, vp, P(bs_params), vp, vp, d, d, i, vp]
+    lib.pino_load.argtypes = [C.c_char_p, P(vp)]
+    lib.pino_destroy.argtypes = [vp]
+    lib.parareal_solve.argtypes = [vp, P(bs_params), i, i, i, i, vp, d, i, vp, P(i), P(d), vp]
+    lib.bs_fine_sweeps.argtypes = [vp, P(bs_params), d]
+    for name in EXPORTS:
+        if name != "bs_last_error":
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().bs_last_error().decode()
+
+
+def check(rc: int, allow=()) -> int:
+    if rc != BS_OK and rc not in allow:
+        raise BSError(rc, last_error())
+    return rc
+
+
+def to_params(p) -> bs_params:
+    """From a workloads.Params-like object (attributes sigma1 ... cash)."""
+    return bs_params(float(p.sigma1), float(p.sigma2), float(p.rho), float(p.r), float(p.T),
+                     float(p.strike), float(p.w1), float(p.w2), int(p.payoff), 0,
+                     float(getattr(p, "strike2", 0.0)), float(getattr(p, "cash", 1.0)))
+
+
+def _ptr(x) -> int:
+    return x if isinstance(x, int) else x.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+class Grid:
+    """bs_grid handle: M x M nodes on [0, xmax]^2."""
+
+    def __init__(self, M: int, xmax: float):
+        lib = load()
+        h = C.c_void_p()
+        check(lib.bs_grid_create(int(M), float(xmax), C.byref(h)))
+        self.h, self.M, self.xmax = h, int(M), float(xmax)
+
+    def close(self):
+        if self.h:
+            load().bs_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bs_payoff(g: Grid, p, u, stream=None):
+    bp = to_params(p)
+    return check(load().bs_payoff(g.h, C.byref(bp), _ptr(u), _stream(stream)))
+
+
+def fine_propagate_batched(g: Grid, params: Sequence, u_in: Sequence, u_out: Sequence,
+                           tau0: Sequence[float], dtau: Sequence[float], nsteps: int,
+                           stream=None):
+    B = len(u_in)
+    P = (bs_params * B)(*[to_params(p) for p in params])
+    pin = (C.c_void_p * B)(*[_ptr(x) for x in u_in])
+    pout = (C.c_void_p * B)(*[_ptr(x) for x in u_out])
+    t0 = (C.c_double * B)(*[float(t) for t in tau0])
+    dt = (C.c_double * B)(*[float(t) for t in dtau])
+    return check(load().fine_propagate_batched(g.h, P, pin, pout, t0, dt, int(nsteps), B,
+                                               _stream(stream)))
+
+
+def coarse_propagate(g: Grid, kind: int, net, p, u_in, u_out, tau0: float, dtau_slice: float,
+                     nsteps: int, stream=None):
+    bp = to_params(p)
+    return check(load().coarse_propagate(g.h, int(kind), net.h if net is not None else None,
+                                         C.byref(bp), _ptr(u_in), _ptr(u_out), float(tau0),
+                                         float(dtau_slice), int(nsteps), _stream(stream)))
+
+
+def parareal_solve(g: Grid, p, N: int, fine_steps: int, coarse_kind: int, coarse_steps: int,
+                   net, tol: float, Kmax: int, u_out, stream=None, allow_maxiter=True):
+    """Returns (status, k_done, defects)."""
+    bp = to_params(p)
+    k = C.c_int(0)
+    hist = (C.c_double * max(1, Kmax))()
+    rc = load().parareal_solve(g.h, C.byref(bp), int(N), int(fine_steps), int(coarse_kind),
+                               int(coarse_steps), net.h if net is not None else None,
+                               float(tol), int(Kmax), _ptr(u_out), C.byref(k), hist,
+                               _stream(stream))
+    check(rc, allow=(BS_ERR_MAXITER,) if allow_maxiter else ())
+    return rc, k.value, [hist[i] for i in range(k.value)]
+
+
+def bs_fine_sweeps(g: Grid, p, dtau: float) -> int:
+    bp = to_params(p)
+    return int(load().bs_fine_sweeps(g.h, C.byref(bp), float(dtau)))
+
+
+class Pino:
+    """bs_pino handle loaded from a weight file."""
+
+    def __init__(self, path: str):
+        h = C.c_void_p()
+        check(load().pino_load(path.encode(), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().pino_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

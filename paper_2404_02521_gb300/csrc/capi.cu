@@ -1,0 +1,340 @@
+// C ABI of the Black-Scholes Parareal library: handles, argument checks, the payoff kernel
+// (K6) and the Parareal driver loop (eq. parareal, Sec. 3.1).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bsp {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  return set_error(e == cudaErrorMemoryAllocation ? BS_ERR_OOM : BS_ERR_CUDA, "%s failed: %s",
+                   what, cudaGetErrorString(e));
+}
+
+int check_params(const bs_params* p) {
+  if (!p) return set_error(BS_ERR_ARG, "params is NULL");
+  if (!(p->sigma1 > 0.0) || !(p->sigma2 > 0.0)) return set_error(BS_ERR_ARG, "sigma must be > 0");
+  if (!(std::fabs(p->rho) < 1.0)) return set_error(BS_ERR_ARG, "|rho| must be < 1");
+  if (!(p->r >= 0.0)) return set_error(BS_ERR_ARG, "r must be >= 0");
+  if (p->payoff < BS_PAYOFF_BASKET || p->payoff > BS_PAYOFF_CASH_OR_NOTHING)
+    return set_error(BS_ERR_ARG, "unknown payoff %d", p->payoff);
+  if (p->reserved != 0) return set_error(BS_ERR_ARG, "bs_params.reserved must be 0");
+  if (p->payoff == BS_PAYOFF_CASH_OR_NOTHING && !(std::fabs(p->rho) <= 0.95))
+    return set_error(BS_ERR_ARG, "cash-or-nothing far field needs |rho| <= 0.95");
+  return BS_OK;
+}
+
+ItemDesc make_item(const bs_params& p, double tau0, double dtau) {
+  ItemDesc d;
+  d.in = nullptr;
+  d.out = nullptr;
+  d.tau0 = tau0;
+  d.dtau = dtau;
+  d.s1 = p.sigma1; d.s2 = p.sigma2; d.rho = p.rho; d.r = p.r;
+  d.K = p.strike; d.w1 = p.w1; d.w2 = p.w2; d.K2 = p.strike2; d.cash = p.cash;
+  d.payoff = p.payoff;
+  d.sweeps = 0;
+  return d;
+}
+
+// max over PDE rows (0 <= i, j <= M-2) of sum |off-diagonal| / diagonal of I - dtau R_h.
+double jacobi_contraction(int M, const bs_params& p, double dtau) {
+  double q = 0.0;
+  const double g = std::fabs(p.rho) * p.sigma1 * p.sigma2;
+  for (int j = 0; j <= M - 2; ++j) {
+    const double bj = 0.5 * p.sigma2 * p.sigma2 * j * j, nj = 0.5 * p.r * j;
+    const double offy = std::fabs(bj + nj) + std::fabs(bj - nj);
+    for (int i = 0; i <= M - 2; ++i) {
+      const double ai = 0.5 * p.sigma1 * p.sigma1 * i * i, mi = 0.5 * p.r * i;
+      const double off = dtau * (std::fabs(ai + mi) + std::fabs(ai - mi) + offy + g * i * j);
+      const double diag = 1.0 + dtau * (2.0 * ai + 2.0 * bj + p.r);
+      q = std::fmax(q, off / diag);
+    }
+  }
+  return q;
+}
+
+// Sweeps so that q^m <= 2^-22 (at least 2: the first sweep forms b, the last applies d).
+int sweeps_for(double q) {
+  if (!(q < 0.8)) return 0;
+  if (q <= 0.0) return 2;
+  int m = (int)std::ceil(-22.0 * std::log(2.0) / std::log(q));
+  return m < 2 ? 2 : m;
+}
+
+BandShape band_shape(int M) {
+  BandShape s;
+  s.M = M;
+  s.ncol = ((M + 31) / 32) * 32;
+  s.G = s.ncol <= kThreads ? kThreads / s.ncol : 0;
+  s.K = (s.ncol <= 64) ? 8 : 16;
+  s.BH = s.G * s.K;
+  s.C = s.BH > 0 ? (M + s.BH - 1) / s.BH : 0;
+  if (s.C > kMaxCluster || s.G == 0) s.C = 0;
+  return s;
+}
+
+int ensure(Workspace& w, size_t bytes) {
+  if (w.bytes >= bytes) return BS_OK;
+  if (w.ptr) cudaFree(w.ptr);
+  w.ptr = nullptr;
+  w.bytes = 0;
+  BS_CUDA_TRY(cudaMalloc(&w.ptr, bytes));
+  w.bytes = bytes;
+  return BS_OK;
+}
+
+__global__ void payoff_kernel(PayoffF pf, float* u, int M, float h) {
+  const size_t n = (size_t)M * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+    u[e] = payoff_value(pf, i * h, j * h);
+  }
+}
+
+int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s) {
+  const int M = g->M;
+  const size_t n = (size_t)M * M;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  payoff_kernel<<<blocks, 256, 0, s>>>(make_payoff(d), u, M, (float)(g->xmax / (M - 1)));
+  BS_CUDA_TRY(cudaGetLastError());
+  return BS_OK;
+}
+
+static int grid_sweeps(bs_grid* g, const bs_params& p, double dtau) {
+  const double key[6] = {p.sigma1, p.sigma2, p.rho, p.r, dtau, (double)g->M};
+  if (std::memcmp(key, g->q_key, sizeof(key)) != 0) {
+    g->q_val = jacobi_contraction(g->M, p, dtau);
+    std::memcpy(g->q_key, key, sizeof(key));
+  }
+  return sweeps_for(g->q_val);
+}
+
+}  // namespace bsp
+
+using namespace bsp;
+
+extern "C" {
+
+const char* bs_last_error(void) { return g_err; }
+
+int bs_grid_create(int M, double xmax, bs_grid** out) {
+  g_err[0] = 0;
+  if (!out) return set_error(BS_ERR_ARG, "bs_grid_create: out is NULL");
+  *out = nullptr;
+  if (M < 4 || M > 4096) return set_error(BS_ERR_ARG, "bs_grid_create: M=%d out of [4, 4096]", M);
+  if (!(xmax > 0.0)) return set_error(BS_ERR_ARG, "bs_grid_create: xmax must be > 0");
+  bs_grid* g = new bs_grid();
+  g->M = M;
+  g->xmax = xmax;
+  g->shape = band_shape(M);
+  std::memset(g->q_key, 0, sizeof(g->q_key));
+  g->q_val = 0.0;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->dscal, 8 * sizeof(double));
+  g->dnorms = nullptr;
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_error(e, "bs_grid_create");
+  }
+  *out = g;
+  return BS_OK;
+}
+
+int bs_grid_destroy(bs_grid* g) {
+  if (!g) return BS_OK;
+  cudaFree(g->status);
+  cudaFree(g->dscal);
+  if (g->dnorms) cudaFree(g->dnorms);
+  if (g->ws_par.ptr) cudaFree(g->ws_par.ptr);
+  delete g;
+  return BS_OK;
+}
+
+int bs_payoff(const bs_grid* g, const bs_params* p, float* u, bs_stream stream) {
+  if (!g || !u) return set_error(BS_ERR_ARG, "bs_payoff: NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  return launch_payoff(g, make_item(*p, 0.0, 0.0), u, (cudaStream_t)stream);
+}
+
+int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau) {
+  if (!g || check_params(p) || !(dtau > 0.0)) return 0;
+  return grid_sweeps(const_cast<bs_grid*>(g), *p, dtau);
+}
+
+int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* const* u_in,
+                           float* const* u_out, const double* tau0, const double* dtau,
+                           int nsteps, int B, bs_stream stream) {
+  if (!g || !p || !u_in || !u_out || !tau0 || !dtau)
+    return set_error(BS_ERR_ARG, "fine_propagate_batched: NULL argument");
+  if (B < 1 || nsteps < 0) return set_error(BS_ERR_ARG, "fine_propagate_batched: B=%d nsteps=%d", B, nsteps);
+  std::vector<ItemDesc> items((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    int rc = check_params(&p[b]);
+    if (rc) return rc;
+    if (!u_in[b] || !u_out[b]) return set_error(BS_ERR_ARG, "fine_propagate_batched: NULL state %d", b);
+    if (!(dtau[b] > 0.0)) return set_error(BS_ERR_ARG, "fine_propagate_batched: dtau[%d] <= 0", b);
+    ItemDesc d = make_item(p[b], tau0[b], dtau[b]);
+    d.in = u_in[b];
+    d.out = u_out[b];
+    d.sweeps = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b]);
+    if (d.sweeps == 0)
+      return set_error(BS_ERR_ARG, "fine_propagate_batched: Jacobi contraction %.3f >= 0.8 for "
+                       "item %d; take smaller fine steps", g->q_val, b);
+    items[(size_t)b] = d;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nsteps == 0) {
+    for (int b = 0; b < B; ++b)
+      if (u_out[b] != u_in[b])
+        BS_CUDA_TRY(cudaMemcpyAsync(u_out[b], u_in[b], sizeof(float) * g->M * g->M,
+                                    cudaMemcpyDeviceToDevice, s));
+    return BS_OK;
+  }
+  return launch_fine(g, items.data(), B, nsteps, s);
+}
+
+int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_params* p,
+                     const float* u_in, float* u_out, double tau0, double dtau_slice, int nsteps,
+                     bs_stream stream) {
+  if (!g || !u_in || !u_out) return set_error(BS_ERR_ARG, "coarse_propagate: NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!(dtau_slice > 0.0)) return set_error(BS_ERR_ARG, "coarse_propagate: dtau_slice <= 0");
+  if (kind == BS_COARSE_NUM) {
+    if (net) return set_error(BS_ERR_ARG, "coarse_propagate: net must be NULL for BS_COARSE_NUM");
+    if (nsteps < 1) return set_error(BS_ERR_ARG, "coarse_propagate: nsteps < 1");
+    ItemDesc d = make_item(*p, tau0, dtau_slice / nsteps);
+    SweepArgs a = {};
+    a.mode = SWEEP_PROP;
+    a.n_first = 0;
+    a.N = 1;
+    a.csteps = nsteps;
+    a.slice_len = 0.0;
+    a.in = u_in;
+    a.out = u_out;
+    a.status = g->status;
+    a.tol = 1e-6;
+    a.maxit = 400;
+    return launch_sweep(g, d, a, (cudaStream_t)stream);
+  }
+  if (kind == BS_COARSE_PINO) return set_error(BS_ERR_ARG, "coarse_propagate: PINO not loaded");
+  return set_error(BS_ERR_ARG, "coarse_propagate: unknown kind %d", kind);
+}
+
+int pino_load(const char* path, bs_pino** net) {
+  if (net) *net = nullptr;
+  return set_error(BS_ERR_FILE, "pino_load: %s: PINO support not built", path ? path : "(null)");
+}
+
+int pino_destroy(bs_pino* net) { return BS_OK; }
+
+int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps, int coarse_kind,
+                   int coarse_steps, const bs_pino* net, double tol, int Kmax, float* u_out,
+                   int* k_done, double* defect_hist, bs_stream stream) {
+  bs_grid* g = const_cast<bs_grid*>(gc);
+  if (!g || !u_out || !k_done) return set_error(BS_ERR_ARG, "parareal_solve: NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (N < 1 || fine_steps < 1 || Kmax < 0 || Kmax > N || !(p->T > 0.0))
+    return set_error(BS_ERR_ARG, "parareal_solve: N=%d fine_steps=%d Kmax=%d T=%g", N, fine_steps,
+                     Kmax, p->T);
+  if (coarse_kind != BS_COARSE_NUM) return set_error(BS_ERR_ARG, "parareal_solve: coarse kind %d unsupported", coarse_kind);
+  if (coarse_steps < 1) return set_error(BS_ERR_ARG, "parareal_solve: coarse_steps < 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int M = g->M;
+  const size_t MM = (size_t)M * M;
+  const double slice = p->T / N;
+  const double dtau_f = slice / fine_steps;
+  const int sweeps = grid_sweeps(g, *p, dtau_f);
+  if (sweeps == 0)
+    return set_error(BS_ERR_ARG, "parareal_solve: Jacobi contraction %.3f >= 0.8; more fine steps needed", g->q_val);
+  rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1));
+  if (rc) return rc;
+  float* Fb = (float*)g->ws_par.ptr;
+  float* Gold = Fb + (size_t)N * MM;
+  double* norms = (double*)(Gold + (size_t)N * MM);
+  BS_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), s));
+
+  ItemDesc dc = make_item(*p, 0.0, slice / coarse_steps);
+  rc = launch_payoff(g, dc, u_out, s);
+  if (rc) return rc;
+  SweepArgs a = {};
+  a.N = N;
+  a.csteps = coarse_steps;
+  a.slice_len = slice;
+  a.U = u_out;
+  a.Fb = Fb;
+  a.Gold = Gold;
+  a.norms = norms;
+  a.defect = g->dscal;
+  a.status = g->status;
+  a.tol = 1e-6;
+  a.maxit = 400;
+  a.mode = SWEEP_INIT;
+  a.n_first = 0;
+  rc = launch_sweep(g, dc, a, s);
+  if (rc) return rc;
+
+  std::vector<ItemDesc> items((size_t)N);
+  int k = 0;
+  int status = BS_ERR_MAXITER;
+  for (; k < Kmax; ++k) {
+    // F on slices k..N-1 (slices below k are already exact)
+    const int B = N - k;
+    for (int n = k; n < N; ++n) {
+      ItemDesc d = make_item(*p, n * slice, dtau_f);
+      d.in = u_out + (size_t)n * MM;
+      d.out = Fb + (size_t)n * MM;
+      d.sweeps = sweeps;
+      items[(size_t)(n - k)] = d;
+    }
+    rc = launch_fine(g, items.data(), B, fine_steps, s);
+    if (rc) return rc;
+    a.mode = SWEEP_ITER;
+    a.n_first = k;
+    rc = launch_sweep(g, dc, a, s);
+    if (rc) return rc;
+    double host[1];
+    int hstat = 0;
+    BS_CUDA_TRY(cudaMemcpyAsync(host, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    BS_CUDA_TRY(cudaMemcpyAsync(&hstat, g->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (defect_hist) defect_hist[k] = host[0];
+    if (hstat) {
+      *k_done = k + 1;
+      return set_error(BS_ERR_NOCONV, "parareal_solve: a coarse BiCGSTAB solve hit its iteration cap");
+    }
+    if (host[0] <= tol) {
+      ++k;
+      status = BS_OK;
+      break;
+    }
+  }
+  *k_done = k;
+  if (Kmax == 0) BS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (status == BS_ERR_MAXITER)
+    return set_error(BS_ERR_MAXITER, "parareal_solve: tol %g not met after %d iterations", tol, k);
+  return BS_OK;
+}
+
+}  // extern "C"

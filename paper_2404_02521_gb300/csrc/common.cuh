@@ -1,0 +1,222 @@
+// Shared device/host definitions of the Black-Scholes Parareal library (sm_103a).
+//
+// Grid and operator conventions (eq. fd, Sec. 3.2):
+//   nodes x_i = i*h, h = xmax/(M-1); state u[j*M + i] (row = y index j, column = x index i).
+//   In index units the coefficients of dtau*R_h are, at node (i, j):
+//     east  (i+1, j): dtau*(s1^2 i^2/2 + r i/2)      west  (i-1, j): dtau*(s1^2 i^2/2 - r i/2)
+//     south (i, j+1): dtau*(s2^2 j^2/2 + r j/2)      north (i, j-1): dtau*(s2^2 j^2/2 - r j/2)
+//     cross: +dtau*rho s1 s2 i j/4 on (i+1, j+1), (i-1, j-1); minus on (i+1, j-1), (i-1, j+1)
+//     centre: -(sum of the four axis weights) - dtau*r
+//   because x_i/h = i, so the spacing h cancels from every term of eq. (fd).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bsparareal.h"
+
+namespace bsp {
+
+constexpr int kMaxItems = 96;        // items per fine launch (kernel-parameter descriptors)
+constexpr int kThreads = 512;        // threads per CTA of the band kernels
+constexpr int kMaxCluster = 16;
+
+// Per-item description carried in kernel parameters.
+struct ItemDesc {
+  const float* in;
+  float* out;
+  double tau0, dtau;
+  double s1, s2, rho, r;
+  double K, w1, w2, K2, cash;
+  int payoff;
+  int sweeps;     // Jacobi sweeps per implicit step (fine) / unused (coarse)
+};
+
+// Band decomposition of an M x M slice over a cluster of C CTAs: each CTA owns BH = G*K
+// consecutive rows of ncol (>= M, multiple of 32) columns; thread t works on column
+// t % ncol and rows (t / ncol)*K .. +K-1 of the band.
+struct BandShape {
+  int M, ncol, G, K, BH, C;
+};
+
+// FP32 payoff / far-field data, evaluated on the device.
+struct PayoffF {
+  int kind;
+  float K, w1, w2, K2, cash, s1, s2, rho, r;
+};
+
+__host__ __device__ inline PayoffF make_payoff(const ItemDesc& d) {
+  PayoffF p;
+  p.kind = d.payoff;
+  p.K = (float)d.K; p.w1 = (float)d.w1; p.w2 = (float)d.w2; p.K2 = (float)d.K2;
+  p.cash = (float)d.cash; p.s1 = (float)d.s1; p.s2 = (float)d.s2; p.rho = (float)d.rho;
+  p.r = (float)d.r;
+  return p;
+}
+
+// Bivariate standard normal CDF by integrating its derivative in the correlation
+// (Plackett's identity dB/drho = phi2(h, k; rho)) from 0 to rho with 20-point
+// Gauss-Legendre quadrature in FP32; used only for the cash-or-nothing far field.
+__device__ inline float bvn_cdf_f(float h, float k, float rho) {
+  // Gauss-Legendre nodes/weights on [-1, 1], 20 points (positive half; symmetric).
+  const float xg[10] = {0.0765265211f, 0.2277858511f, 0.3737060887f, 0.5108670020f,
+                        0.6360536807f, 0.7463319065f, 0.8391169718f, 0.9122344283f,
+                        0.9639719273f, 0.9931285992f};
+  const float wg[10] = {0.1527533871f, 0.1491729865f, 0.1420961093f, 0.1316886384f,
+                        0.1181945320f, 0.1019301198f, 0.0832767416f, 0.0626720483f,
+                        0.0406014298f, 0.0176140071f};
+  float base = normcdff(h) * normcdff(k);
+  if (rho == 0.0f) return base;
+  float acc = 0.0f;
+  for (int q = 0; q < 10; ++q) {
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      float t = 0.5f * rho * (1.0f + sgn * xg[q]);
+      float om = 1.0f - t * t;
+      float e = __expf(-(h * h - 2.0f * t * h * k + k * k) / (2.0f * om));
+      acc += wg[q] * e * rsqrtf(om);
+    }
+  }
+  return base + 0.5f * rho * acc * 0.15915494309f;  // 1/(2 pi)
+}
+
+// Far-field Dirichlet value g(x, y, tau) (reading of the boundary: exchange -> Margrabe,
+// basket -> forward value max(w1 x + w2 y - K e^{-r tau}, 0), one-asset -> Black-Scholes
+// call in x, cash-or-nothing -> eq. solution).  At tau = 0 every branch is the payoff.
+__device__ inline float far_field(const PayoffF& p, float x, float y, float tau) {
+  switch (p.kind) {
+    case BS_PAYOFF_BASKET:
+      return fmaxf(p.w1 * x + p.w2 * y - p.K * expf(-p.r * tau), 0.0f);
+    case BS_PAYOFF_EXCHANGE: {
+      if (y <= 0.0f) return x;
+      if (x <= 0.0f) return 0.0f;
+      float v = p.s1 * p.s1 + p.s2 * p.s2 - 2.0f * p.rho * p.s1 * p.s2;
+      if (tau <= 0.0f || v <= 0.0f) return fmaxf(x - y, 0.0f);
+      float sq = sqrtf(v * tau);
+      float d1 = (logf(x / y) + 0.5f * v * tau) / sq;
+      float d2 = d1 - sq;
+      return x * normcdff(d1) - y * normcdff(d2);
+    }
+    case BS_PAYOFF_CALL1: {
+      if (x <= 0.0f) return 0.0f;
+      if (tau <= 0.0f) return fmaxf(x - p.K, 0.0f);
+      float sq = p.s1 * sqrtf(tau);
+      float d1 = (logf(x / p.K) + (p.r + 0.5f * p.s1 * p.s1) * tau) / sq;
+      float d2 = d1 - sq;
+      return x * normcdff(d1) - p.K * expf(-p.r * tau) * normcdff(d2);
+    }
+    case BS_PAYOFF_CASH_OR_NOTHING: {
+      if (tau <= 0.0f) return (x >= p.K && y >= p.K2) ? p.cash : 0.0f;
+      if (x <= 0.0f || y <= 0.0f) return 0.0f;
+      float st = sqrtf(tau);
+      float dx = (logf(x / p.K) + (p.r - 0.5f * p.s1 * p.s1) * tau) / (p.s1 * st);
+      float dy = (logf(y / p.K2) + (p.r - 0.5f * p.s2 * p.s2) * tau) / (p.s2 * st);
+      return p.cash * expf(-p.r * tau) * bvn_cdf_f(dx, dy, p.rho);
+    }
+  }
+  return 0.0f;
+}
+
+// Payoff u(tau = 0) at (x, y).
+__device__ inline float payoff_value(const PayoffF& p, float x, float y) {
+  switch (p.kind) {
+    case BS_PAYOFF_BASKET: return fmaxf(p.w1 * x + p.w2 * y - p.K, 0.0f);
+    case BS_PAYOFF_EXCHANGE: return fmaxf(x - y, 0.0f);
+    case BS_PAYOFF_CALL1: return fmaxf(x - p.K, 0.0f);
+    case BS_PAYOFF_CASH_OR_NOTHING: return (x >= p.K && y >= p.K2) ? p.cash : 0.0f;
+  }
+  return 0.0f;
+}
+
+// Coefficients of dtau*R_h at a node, in index units (see the file header).
+struct Coef {
+  float e, w, s, n, g, rdt, invd;   // invd = 1 / (1 + e + w + s + n + rdt)
+};
+
+__device__ inline void column_coefs(const ItemDesc& d, int i, float& ce, float& cw,
+                                    float& cgi) {
+  double di = (double)i;
+  double a = 0.5 * d.s1 * d.s1 * di * di * d.dtau;
+  double m = 0.5 * d.r * di * d.dtau;
+  ce = (float)(a + m);
+  cw = (float)(a - m);
+  cgi = (float)(d.rho * d.s1 * d.s2 * di * 0.25 * d.dtau);
+}
+
+__device__ inline void row_coefs(const ItemDesc& d, int j, float& cs, float& cn, float& gj) {
+  double dj = (double)j;
+  double b = 0.5 * d.s2 * d.s2 * dj * dj * d.dtau;
+  double n = 0.5 * d.r * dj * d.dtau;
+  cs = (float)(b + n);
+  cn = (float)(b - n);
+  gj = (float)dj;
+}
+
+__device__ inline float inv_diag(const ItemDesc& d, int i, int j) {
+  double di = (double)i, dj = (double)j;
+  return (float)(1.0 / (1.0 + d.dtau * (d.s1 * d.s1 * di * di + d.s2 * d.s2 * dj * dj + d.r)));
+}
+
+// ---------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+#define BS_CUDA_TRY(call)                                      \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return ::bsp::cuda_error(e_, #call); \
+  } while (0)
+
+ItemDesc make_item(const bs_params& p, double tau0, double dtau);
+int check_params(const bs_params* p);
+double jacobi_contraction(int M, const bs_params& p, double dtau);
+int sweeps_for(double q);
+BandShape band_shape(int M);
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+int ensure(Workspace& w, size_t bytes);
+
+}  // namespace bsp
+
+struct bs_grid {
+  int M;
+  double xmax;
+  int device;
+  bsp::BandShape shape;
+  int* status;                 // device: bit 0 = Krylov cap hit
+  double* dscal;               // device: scalar outputs (defect)
+  double* dnorms;              // device: per-slice squared norms / defects
+  bsp::Workspace ws_par;       // Parareal F / Gold buffers
+  // cached contraction
+  double q_key[6];
+  double q_val;
+};
+
+// Kernel launchers implemented in the .cu files.
+namespace bsp {
+int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s);
+int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s);
+// Coarse numerical propagation / Parareal serial sweep (see coarse.cu).
+enum { SWEEP_PROP = 0, SWEEP_INIT = 1, SWEEP_ITER = 2 };
+struct SweepArgs {
+  int mode;
+  int n_first, N;
+  int csteps;           // implicit steps per slice
+  double slice_len;     // tau length of one slice
+  const float* in;      // SWEEP_PROP: input state
+  float* out;           // SWEEP_PROP: output state
+  float* U;             // [N+1][M*M]
+  const float* Fb;      // [N][M*M]
+  float* Gold;          // [N][M*M]
+  double* norms;        // [2*(N+1)]: ||U_n||^2 and ||dU_n||^2 (iteration)
+  double* defect;       // scalar out
+  int* status;
+  double tol;           // relative residual of the Krylov solve
+  int maxit;
+};
+int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
+}  // namespace bsp

@@ -1,0 +1,66 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads, exports every
+entry point that include/bsparareal.h declares, and rejects bad arguments before touching
+the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bsparareal.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_02521_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["bs_grid_create", "fine_propagate_batched", "coarse_propagate", "pino_load",
+                     "parareal_solve"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2404_02521_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) <= set(_lib.EXPORTS) | {"bs_last_error"}
+
+
+def test_grid_create_rejects_bad_sizes(lib):
+    from paper_2404_02521_gb300 import _lib
+    h = C.c_void_p()
+    assert lib.bs_grid_create(2, 4.0, C.byref(h)) == _lib.BS_ERR_ARG
+    assert "M=2" in _lib.last_error()
+    assert lib.bs_grid_create(64, -1.0, C.byref(h)) == _lib.BS_ERR_ARG
+    assert lib.bs_grid_create(64, 4.0, None) == _lib.BS_ERR_ARG
+
+
+def test_null_handles_are_rejected(lib):
+    from paper_2404_02521_gb300 import _lib
+    p = _lib.bs_params(0.3, 0.2, 0.5, 0.05, 1.0, 1.0, 0.5, 0.5, 0, 0, 0.0, 1.0)
+    assert lib.bs_payoff(None, C.byref(p), None, None) == _lib.BS_ERR_ARG
+    assert lib.fine_propagate_batched(None, C.byref(p), None, None, None, None, 1, 1, None) == _lib.BS_ERR_ARG
+    assert lib.coarse_propagate(None, 0, None, C.byref(p), None, None, 0.0, 0.1, 1, None) == _lib.BS_ERR_ARG
+    k = C.c_int()
+    assert lib.parareal_solve(None, C.byref(p), 8, 16, 0, 4, None, 1e-4, 8, None, C.byref(k), None, None) == _lib.BS_ERR_ARG
+    assert lib.bs_grid_destroy(None) == _lib.BS_OK
+
+
+def test_missing_weight_file(lib, tmp_path):
+    from paper_2404_02521_gb300 import _lib
+    h = C.c_void_p()
+    rc = lib.pino_load(str(tmp_path / "nope.bin").encode(), C.byref(h))
+    assert rc == _lib.BS_ERR_FILE
+    assert not h.value

@@ -1,0 +1,132 @@
+"""GPU parity of the fine propagator F (fine_propagate_batched, eq. fd + implicit Euler)
+against the FP64 sparse-LU oracle, element by element."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests.gpu_util import (FP32_FINE_TOL, dtau_for, oracle_fine, rel_err, start_state, to_gpu,
+                            to_np)
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = [
+    wl.Params(0.3, 0.2, 0.5, 0.05, payoff=wl.BASKET),
+    wl.Params(0.25, 0.35, -0.5, 0.03, payoff=wl.EXCHANGE),
+    wl.Params(0.25, 0.35, 0.7, 0.03, payoff=wl.EXCHANGE),
+    wl.Params(0.4, 0.15, 0.0, 0.08, strike=1.2, payoff=wl.CALL1),
+]
+
+
+@pytest.fixture(scope="module")
+def bs():
+    import paper_2404_02521_gb300 as bs
+    bs.load()
+    return bs
+
+
+# M spans one CTA (33, 64), two bands with a ragged tail (100), 7 bands with padding (200)
+# and the full 8-CTA cluster (256).
+@pytest.mark.parametrize("M", [5, 33, 64, 100, 128, 200, 256])
+@pytest.mark.parametrize("pi", range(len(PARAMS)))
+def test_fine_matches_oracle(bs, M, pi):
+    import torch
+    p = PARAMS[pi]
+    xmax = 4.0
+    dtau = dtau_for(M, p)
+    nsteps = 12 if M >= 200 else 30
+    u0 = start_state(M, xmax, p, "payoff" if pi % 2 == 0 else "random", seed=M)
+    tau0 = 0.05 * pi
+    g = bs.Grid(M, xmax)
+    uin = to_gpu(u0)
+    uout = torch.empty_like(uin)
+    bs.fine_propagate_batched(g, [p], [uin], [uout], [tau0], [dtau], nsteps)
+    torch.cuda.synchronize()
+    want = oracle_fine(M, xmax, p, u0, tau0, dtau, nsteps)
+    assert rel_err(to_np(uout), want) <= FP32_FINE_TOL
+
+
+def test_batch_invariance_and_in_place(bs):
+    import torch
+    M, xmax = 100, 4.0
+    items = [(PARAMS[0], 0.0), (PARAMS[1], 0.3), (PARAMS[3], 0.1), (PARAMS[2], 0.7)]
+    dt = [dtau_for(M, p) for p, _ in items]
+    u0 = [start_state(M, xmax, p, "payoff") for p, _ in items]
+    g = bs.Grid(M, xmax)
+    ins = [to_gpu(u) for u in u0]
+    outs = [torch.empty_like(x) for x in ins]
+    bs.fine_propagate_batched(g, [p for p, _ in items], ins, outs, [t for _, t in items], dt, 9)
+    alone = torch.empty_like(ins[1])
+    bs.fine_propagate_batched(g, [items[1][0]], [ins[1]], [alone], [items[1][1]], [dt[1]], 9)
+    inplace = ins[2].clone()
+    bs.fine_propagate_batched(g, [items[2][0]], [inplace], [inplace], [items[2][1]], [dt[2]], 9)
+    torch.cuda.synchronize()
+    assert torch.equal(alone, outs[1])
+    assert torch.equal(inplace, outs[2])
+    for (p, t0), u, o, d in zip(items, u0, outs, dt):
+        assert rel_err(to_np(o), oracle_fine(M, xmax, p, u, t0, d, 9)) <= FP32_FINE_TOL
+
+
+def test_zero_steps_is_a_copy(bs):
+    import torch
+    g = bs.Grid(40, 4.0)
+    u = to_gpu(np.random.default_rng(1).uniform(size=(40, 40)))
+    out = torch.zeros_like(u)
+    bs.fine_propagate_batched(g, [PARAMS[0]], [u], [out], [0.0], [1e-4], 0)
+    torch.cuda.synchronize()
+    assert torch.equal(out, u)
+
+
+def test_large_batch_spans_several_launches(bs):
+    import torch
+    M, xmax, n = 33, 4.0, 100     # more items than one launch's descriptor table
+    p = PARAMS[1]
+    dt = dtau_for(M, p)
+    g = bs.Grid(M, xmax)
+    u0 = start_state(M, xmax, p, "payoff")
+    ins = [to_gpu(u0) for _ in range(n)]
+    outs = [torch.empty_like(x) for x in ins]
+    taus = [0.01 * k for k in range(n)]
+    bs.fine_propagate_batched(g, [p] * n, ins, outs, taus, [dt] * n, 5)
+    torch.cuda.synchronize()
+    for k in (0, 57, 99):
+        assert rel_err(to_np(outs[k]), oracle_fine(M, xmax, p, u0, taus[k], dt, 5)) <= FP32_FINE_TOL
+
+
+def test_long_chain_compensated_state(bs):
+    # 4096 steps on a 64-grid: without the compensated (hi, lo) state, increments below
+    # half an ulp would be lost and the error would exceed the FP32 bound.
+    import torch
+    M, xmax = 64, 4.0
+    p = wl.Params(0.25, 0.35, 0.7, 0.03, payoff=wl.EXCHANGE)
+    dtau, nsteps = 1.0 / 4096, 4096
+    u0 = start_state(M, xmax, p, "payoff")
+    g = bs.Grid(M, xmax)
+    uin = to_gpu(u0)
+    out = torch.empty_like(uin)
+    bs.fine_propagate_batched(g, [p], [uin], [out], [0.0], [dtau], nsteps)
+    torch.cuda.synchronize()
+    assert rel_err(to_np(out), oracle_fine(M, xmax, p, u0, 0.0, dtau, nsteps)) <= FP32_FINE_TOL
+
+
+def test_bad_step_is_rejected(bs):
+    import torch
+    g = bs.Grid(64, 4.0)
+    u = to_gpu(np.zeros((64, 64)))
+    with pytest.raises(bs.BSError):
+        bs.fine_propagate_batched(g, [PARAMS[0]], [u], [u], [0.0], [1.0], 3)   # q >= 0.8
+    with pytest.raises(bs.BSError):
+        bs.fine_propagate_batched(g, [PARAMS[0]], [u], [u], [0.0], [-1e-3], 3)
+
+
+def test_payoff_kernel(bs):
+    import torch
+    from oracle import fd
+    for p in PARAMS:
+        M = 77
+        g = bs.Grid(M, 4.0)
+        u = torch.empty((M, M), device="cuda")
+        bs.bs_payoff(g, p, u)
+        torch.cuda.synchronize()
+        X, Y = fd.mesh(M, 4.0)
+        want = fd.payoff(p, X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64))
+        assert np.max(np.abs(to_np(u) - want)) <= 1e-6

@@ -1,0 +1,114 @@
+"""GPU parity of the numerical coarse propagator G (BiCGSTAB) and of parareal_solve against
+the FP64 oracle (eq. parareal), plus the exact Parareal invariants on the GPU."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fd
+from oracle import parareal as opr
+from tests.gpu_util import FP32_FINE_TOL, rel_err, start_state, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+# The coarse solve stops at a relative residual of 1e-6 of the Jacobi-scaled system in FP32;
+# over a few coarse steps that stays below 2e-5 of max|V|.
+COARSE_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def bs():
+    import paper_2404_02521_gb300 as bs
+    bs.load()
+    return bs
+
+
+@pytest.mark.parametrize("M,pi", [(33, 0), (64, 1), (100, 2), (200, 0), (256, 1)])
+def test_coarse_matches_oracle(bs, M, pi):
+    import torch
+    P = [wl.Params(0.3, 0.2, 0.5, 0.05, payoff=wl.BASKET),
+         wl.Params(0.25, 0.35, 0.7, 0.03, payoff=wl.EXCHANGE),
+         wl.Params(0.25, 0.35, -0.5, 0.03, payoff=wl.EXCHANGE)]
+    p = P[pi]
+    xmax, slice_len, steps, tau0 = 4.0, 1.0 / 64, 4, 0.25
+    u0 = start_state(M, xmax, p, "random", seed=M)
+    g = bs.Grid(M, xmax)
+    uin = to_gpu(u0)
+    out = torch.empty_like(uin)
+    bs.coarse_propagate(g, bs.COARSE_NUM, None, p, uin, out, tau0, slice_len, steps)
+    torch.cuda.synchronize()
+    ie = fd.ImplicitEuler(M, xmax, p, slice_len / steps)
+    want = ie.propagate(u0.astype(np.float64), tau0, steps)
+    assert rel_err(to_np(out), want) <= COARSE_TOL
+
+
+def cfg_small(payoff=wl.BASKET, M=64, N=8, fine=64, coarse=4):
+    base = wl.basket_cfg1().params if payoff == wl.BASKET else wl.exchange_cfg2(0.7).params
+    return wl.Problem("small", M, 4.0, N, fine, coarse, base)
+
+
+def gpu_parareal(bs, pb, tol, Kmax):
+    import torch
+    g = bs.Grid(pb.M, pb.xmax)
+    U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+    rc, k, defects = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM,
+                                       pb.coarse_steps, None, tol, Kmax, U)
+    torch.cuda.synchronize()
+    return rc, k, defects, U
+
+
+def gpu_serial_fine(bs, pb):
+    import torch
+    g = bs.Grid(pb.M, pb.xmax)
+    U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+    bs.bs_payoff(g, pb.params, U[0])
+    slice_len = pb.params.T / pb.N
+    for n in range(pb.N):
+        bs.fine_propagate_batched(g, [pb.params], [U[n]], [U[n + 1]], [n * slice_len],
+                                  [slice_len / pb.fine_steps], pb.fine_steps)
+    torch.cuda.synchronize()
+    return U
+
+
+@pytest.mark.parametrize("payoff", [wl.BASKET, wl.EXCHANGE])
+def test_k_equals_n_is_serial_fine_bitwise(bs, payoff):
+    import torch
+    pb = cfg_small(payoff, M=40, N=6, fine=96, coarse=2)
+    rc, k, _, U = gpu_parareal(bs, pb, 0.0, pb.N)
+    assert k == pb.N
+    S = gpu_serial_fine(bs, pb)
+    assert torch.equal(U, S)
+    want = fd.serial_fine(pb)
+    assert rel_err(to_np(U), want) <= FP32_FINE_TOL
+
+
+def test_parareal_matches_oracle_parareal(bs):
+    pb = cfg_small(wl.BASKET, M=64, N=8, fine=64, coarse=4)
+    rc, k, defects, U = gpu_parareal(bs, pb, 1e-4, pb.N)
+    assert rc == 0
+    F = fd.SlicePropagator(pb.M, pb.xmax, pb.params, pb.N, pb.fine_steps)
+    G = fd.SlicePropagator(pb.M, pb.xmax, pb.params, pb.N, pb.coarse_steps)
+    serial = fd.serial_fine(pb)
+    Uo, ko, do, _ = opr.parareal(serial[0], F, G, pb.N, 1e-4, pb.N)
+    assert k == ko
+    assert rel_err(to_np(U), Uo) <= 3 * COARSE_TOL
+    for a, b in zip(defects, do):
+        assert abs(a - b) <= 1e-3 * b + 1e-6
+    # converged Parareal is within the tolerance of the serial fine solution
+    assert rel_err(to_np(U), serial) <= 1e-3
+
+
+def test_exact_prefix_on_gpu(bs):
+    # after k iterations the first k+1 slices equal serial fine bitwise
+    import torch
+    pb = cfg_small(wl.EXCHANGE, M=40, N=5, fine=160, coarse=2)
+    S = gpu_serial_fine(bs, pb)
+    for K in range(1, pb.N + 1):
+        rc, k, _, U = gpu_parareal(bs, pb, 0.0, K)
+        assert k == K
+        assert torch.equal(U[: K + 1], S[: K + 1]), K
+
+
+def test_maxiter_status(bs):
+    pb = cfg_small(wl.BASKET, M=40, N=6, fine=24, coarse=1)
+    rc, k, defects, _ = gpu_parareal(bs, pb, 1e-14, 2)
+    assert rc == -4 and k == 2 and len(defects) == 2
