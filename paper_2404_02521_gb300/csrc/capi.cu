@@ -76,15 +76,18 @@ int sweeps_for(double q) {
   return m < 2 ? 2 : m;
 }
 
+// Band shapes of the cluster-resident kernels (NCOL columns, NT threads, K rows per thread,
+// band height BH = (NT / NCOL) * K, cluster size C = ceil(M / BH)).
 BandShape band_shape(int M) {
-  BandShape s;
+  BandShape s = {};
   s.M = M;
-  s.ncol = ((M + 31) / 32) * 32;
-  s.G = s.ncol <= kThreads ? kThreads / s.ncol : 0;
-  s.K = (s.ncol <= 64) ? 8 : 16;
+  if (M <= 32) { s.ncol = 32; s.G = 8; s.K = 4; }
+  else if (M <= 64) { s.ncol = 64; s.G = 8; s.K = 8; }
+  else if (M <= 128) { s.ncol = 128; s.G = 4; s.K = 16; }
+  else if (M <= 256) { s.ncol = 256; s.G = 2; s.K = 16; }
+  else { s.C = 0; return s; }
   s.BH = s.G * s.K;
-  s.C = s.BH > 0 ? (M + s.BH - 1) / s.BH : 0;
-  if (s.C > kMaxCluster || s.G == 0) s.C = 0;
+  s.C = (M + s.BH - 1) / s.BH;
   return s;
 }
 
@@ -147,8 +150,8 @@ int bs_grid_create(int M, double xmax, bs_grid** out) {
   std::memset(g->q_key, 0, sizeof(g->q_key));
   g->q_val = 0.0;
   cudaError_t e = cudaGetDevice(&g->device);
-  if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->status, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->status, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->dscal, 8 * sizeof(double));
   g->dnorms = nullptr;
   if (e != cudaSuccess) {
@@ -273,7 +276,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   float* Fb = (float*)g->ws_par.ptr;
   float* Gold = Fb + (size_t)N * MM;
   double* norms = (double*)(Gold + (size_t)N * MM);
-  BS_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), s));
+  BS_CUDA_TRY(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), s));
 
   ItemDesc dc = make_item(*p, 0.0, slice / coarse_steps);
   rc = launch_payoff(g, dc, u_out, s);

@@ -32,49 +32,48 @@ struct SweepParams {
   float h;
 };
 
-struct Band {
-  int M, ncol, BH, C, rank, col, r0, jbase;
-  bool active;
+template <int NCOL, int NT, int K>
+struct CBand {
+  static constexpr int G = NT / NCOL;
+  static constexpr int BH = G * K;
+  static constexpr int NW = NT / 32;
 };
 
-// Jacobi-scaled operator A^ y = y - invd * (off-diagonal part of dtau R_h) y at interior
-// nodes; zero elsewhere.  y lives in shared memory (band) with halo rows in the
-// neighbouring CTAs.
-template <int K>
-__device__ __forceinline__ void scaled_matvec(const Band& bd, const float* y, const float* y_prev,
-                                              const float* y_next, const float4* rowt,
-                                              const float* invd, float ce, float cw, float cgi,
-                                              float* out) {
-  const int ncol = bd.ncol, col = bd.col, r0 = bd.r0, BH = bd.BH;
-  const int il = col > 0 ? col - 1 : 0;
-  const int ir = col + 1 < ncol ? col + 1 : col;
-  const float* up = (r0 == 0) ? (y_prev ? y_prev + (BH - 1) * ncol : y) : y + (r0 - 1) * ncol;
-  float uW = up[il], uC = up[col], uE = up[ir];
-  float cW = y[r0 * ncol + il], cC = y[r0 * ncol + col], cE = y[r0 * ncol + ir];
-  const bool last_group = (r0 + K >= BH);
+// Jacobi-scaled operator A^ y = y - invd * (off-diagonal part of dtau R_h) y on the thread's
+// column strip; zero on non-interior nodes (invd = 0 there and y = 0 there).
+template <int NCOL, int K>
+__device__ __forceinline__ void scaled_matvec(const float* __restrict__ y, const float* upr,
+                                              const float* dnr, const float2* __restrict__ rowc,
+                                              const float* __restrict__ ID, int col, int il,
+                                              int ir, int r0, float ce, float cw, float cg0,
+                                              float cgi, float (&out)[K]) {
+  float nW = upr[il], nC = upr[col], nE = upr[ir];
+  const float sDW = dnr[il], sDC = dnr[col], sDE = dnr[ir];
+  float cW = y[r0 * NCOL + il], cC = y[r0 * NCOL + col], cE = y[r0 * NCOL + ir];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int r = r0 + k, j = bd.jbase + r;
-    const float* dn = (k < K - 1 || !last_group) ? y + (r + 1) * ncol
-                                                 : (y_next ? y_next : y + (BH - 1) * ncol);
-    const float dW = dn[il], dC = dn[col], dE = dn[ir];
-    float o = 0.f;
-    if (j < bd.M - 1 && col < bd.M - 1) {
-      const float4 rc = rowt[r];
-      const float cg = cgi * rc.z;
-      o = cC - invd[r * ncol + col] * (ce * cE + cw * cW + rc.x * dC + rc.y * uC +
-                                       cg * ((dE - uE) - (dW - uW)));
+    const int r = r0 + k;
+    float sW, sC, sE;
+    if (k < K - 1) {
+      sW = y[(r + 1) * NCOL + il]; sC = y[(r + 1) * NCOL + col]; sE = y[(r + 1) * NCOL + ir];
+    } else {
+      sW = sDW; sC = sDC; sE = sDE;
     }
-    out[k] = o;
-    uW = cW; uC = cC; uE = cE;
-    cW = dW; cC = dC; cE = dE;
+    const float2 rc = rowc[r];
+    const float cg = fmaf((float)k, cgi, cg0);
+    out[k] = cC - ID[r * NCOL + col] *
+                      (ce * cE + cw * cW + rc.x * sC + rc.y * nC + cg * ((sE - nE) - (sW - nW)));
+    nW = cW; nC = cC; nE = cE;
+    cW = sW; cC = sC; cE = sE;
   }
 }
 
-// Deterministic sum of NV per-thread values over the cluster.  Every thread returns the
-// same totals.  `slot` alternates so that a fast CTA never overwrites partials that a
-// slow CTA is still reading.
-template <int NV>
+// Deterministic cluster-wide sum of NV values: butterfly within each warp, butterfly of
+// the warp partials in warp 0, then one lane per CTA of the cluster reads that CTA's
+// partial and warp 0 sums them by butterfly.  A butterfly gives every lane the same bits
+// (each level adds the same two operands), so every CTA obtains identical totals.
+// `round` alternates the slot so a fast CTA never overwrites partials still being read.
+template <int NV, int NW>
 __device__ __forceinline__ void cluster_sum(cg::cluster_group& cluster, double (&v)[NV],
                                             double* wpart, double* slots, double* bcast,
                                             int& round, int C) {
@@ -88,22 +87,30 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cluster, double (
   }
   __syncthreads();
   double* slot = slots + (round & 1) * NV;
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
+#pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += wpart[w * NV + q];
-      slot[q] = s;
+      double x = lane < NW ? wpart[lane * NV + q] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if (C == 1) {
+        if (lane == 0) bcast[q] = x;
+      } else if (lane == 0) {
+        slot[q] = x;
+      }
     }
   }
-  cluster.sync();
-  if (threadIdx.x == 0) {
-    double tot[NV];
-    for (int q = 0; q < NV; ++q) tot[q] = 0.0;
-    for (int c = 0; c < C; ++c) {
-      const double* rs = cluster.map_shared_rank(slot, c);
-      for (int q = 0; q < NV; ++q) tot[q] += rs[q];
+  if (C > 1) {
+    cluster.sync();
+    if (warp == 0) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        double x = lane < C ? cluster.map_shared_rank(slot, lane)[q] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) bcast[q] = x;
+      }
     }
-    for (int q = 0; q < NV; ++q) bcast[q] = tot[q];
   }
   __syncthreads();
 #pragma unroll
@@ -111,80 +118,91 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cluster, double (
   ++round;
 }
 
+template <int NCOL, int NT, int BH>
 __device__ __forceinline__ void set_far_field_c(float* u, const PayoffF& pf, float tau, float h,
-                                                const Band& bd, int tid) {
-  const int M = bd.M, BH = bd.BH, jbase = bd.jbase, ncol = bd.ncol;
+                                                int M, int jbase, int tid) {
   const bool has_last_row = (jbase <= M - 1) && (M - 1 < jbase + BH);
   const int n_entries = BH + (has_last_row ? (M - 1) : 0);
-  for (int e = tid; e < n_entries; e += kThreads) {
+  for (int e = tid; e < n_entries; e += NT) {
     int r, c;
     if (e < BH) { r = e; c = M - 1; if (jbase + r > M - 1) continue; }
     else { r = M - 1 - jbase; c = e - BH; }
-    u[r * ncol + c] = far_field(pf, c * h, (jbase + r) * h, tau);
+    u[r * NCOL + c] = far_field(pf, c * h, (jbase + r) * h, tau);
   }
 }
 
-template <int K>
-__global__ void __launch_bounds__(kThreads, 1) sweep_band_kernel(const __grid_constant__ SweepParams sp) {
+template <int NCOL, int NT, int K>
+__global__ void __launch_bounds__(NT, 1) sweep_band_kernel(const __grid_constant__ SweepParams sp) {
+  using CB = CBand<NCOL, NT, K>;
+  constexpr int G = CB::G, BH = CB::BH, NW = CB::NW;
   cg::cluster_group cluster = cg::this_cluster();
   const ItemDesc& d = sp.d;
   const SweepArgs& a = sp.a;
-  Band bd;
-  bd.M = sp.sh.M; bd.ncol = sp.sh.ncol; bd.BH = sp.sh.BH; bd.C = sp.sh.C;
-  bd.rank = (int)cluster.block_rank();
+  const int M = sp.sh.M, C = sp.sh.C;
+  const int rank = C > 1 ? (int)cluster.block_rank() : 0;
   const int tid = threadIdx.x;
-  bd.col = tid % bd.ncol;
-  const int grp = tid / bd.ncol;
-  bd.active = (grp < sp.sh.G) && (bd.col < bd.M);
-  bd.r0 = grp * K;
-  bd.jbase = bd.rank * bd.BH;
-  const int M = bd.M, ncol = bd.ncol, BH = bd.BH, C = bd.C;
+  const int col = tid % NCOL, grp = tid / NCOL;
+  const int r0 = grp * K;
+  const int jbase = rank * BH;
   const size_t MM = (size_t)M * M;
   const float h = sp.h;
   const PayoffF pf = make_payoff(d);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* u = reinterpret_cast<float*>(smem_raw);   // state
-  float* P = u + BH * ncol;                        // search direction p
-  float* S = P + BH * ncol;                        // s
-  float* RH = S + BH * ncol;                       // shadow residual r^
-  float* ID = RH + BH * ncol;                      // inverse diagonal
-  float4* rowt = reinterpret_cast<float4*>(ID + BH * ncol);
-  double* wpart = reinterpret_cast<double*>(rowt + BH);   // [16 warps][4]
-  double* slots = wpart + (kThreads / 32) * 4;            // [2][4]
+  float* u = reinterpret_cast<float*>(smem_raw);   // state w / u
+  float* P = u + BH * NCOL;                        // search direction p
+  float* S = P + BH * NCOL;                        // s
+  float* RH = S + BH * NCOL;                       // shadow residual r^
+  float* ID = RH + BH * NCOL;                      // inverse diagonal (0 off the PDE rows)
+  float2* rowc = reinterpret_cast<float2*>(ID + BH * NCOL);
+  double* wpart = reinterpret_cast<double*>(rowc + BH);   // [NW][4]
+  double* slots = wpart + NW * 4;                         // [2][4]
   double* bcast = slots + 8;                              // [4]
 
-  float* u_prev = bd.rank > 0 ? cluster.map_shared_rank(u, bd.rank - 1) : nullptr;
-  float* u_next = bd.rank < C - 1 ? cluster.map_shared_rank(u, bd.rank + 1) : nullptr;
-  float* P_prev = bd.rank > 0 ? cluster.map_shared_rank(P, bd.rank - 1) : nullptr;
-  float* P_next = bd.rank < C - 1 ? cluster.map_shared_rank(P, bd.rank + 1) : nullptr;
-  float* S_prev = bd.rank > 0 ? cluster.map_shared_rank(S, bd.rank - 1) : nullptr;
-  float* S_next = bd.rank < C - 1 ? cluster.map_shared_rank(S, bd.rank + 1) : nullptr;
+  const bool has_prev = rank > 0, has_next = rank < C - 1;
+  auto up_row = [&](float* buf) -> const float* {
+    if (grp > 0) return buf + (r0 - 1) * NCOL;
+    return has_prev ? cluster.map_shared_rank(buf, rank - 1) + (BH - 1) * NCOL : buf;
+  };
+  auto dn_row = [&](float* buf) -> const float* {
+    if (grp < G - 1) return buf + (r0 + K) * NCOL;
+    return has_next ? cluster.map_shared_rank(buf, rank + 1) : buf + (BH - 1) * NCOL;
+  };
+  const float* u_up = up_row(u);
+  const float* u_dn = dn_row(u);
+  const float* P_up = up_row(P);
+  const float* P_dn = dn_row(P);
+  const float* S_up = up_row(S);
+  const float* S_dn = dn_row(S);
 
-  for (int e = tid; e < BH * ncol; e += kThreads) {
-    const int r = e / ncol, c = e - r * ncol;
-    const int j = bd.jbase + r;
+  for (int e = tid; e < BH * NCOL; e += NT) {
+    const int r = e / NCOL, c = e % NCOL;
+    const int j = jbase + r;
     ID[e] = (j < M - 1 && c < M - 1) ? inv_diag(d, c, j) : 0.f;
     P[e] = 0.f; S[e] = 0.f; RH[e] = 0.f;
   }
-  for (int r = tid; r < BH; r += kThreads) {
+  for (int r = tid; r < BH; r += NT) {
     float cs, cn, gj;
-    row_coefs(d, bd.jbase + r, cs, cn, gj);
-    rowt[r] = make_float4(cs, cn, gj, 0.f);
+    row_coefs(d, jbase + r, cs, cn, gj);
+    rowc[r] = make_float2(cs, cn);
   }
   float ce = 0.f, cw = 0.f, cgi = 0.f;
-  if (bd.active) column_coefs(d, bd.col, ce, cw, cgi);
+  column_coefs(d, col, ce, cw, cgi);
+  const float cg0 = cgi * (float)(jbase + r0);
+  const int il = col > 0 ? col - 1 : 0;
+  const int ir = col + 1 < NCOL ? col + 1 : col;
   const float rdt = (float)(d.r * d.dtau);
   int round = 0;
+  int iters_max = 0;
 
   // initial state of the first slice
   const float* src;
   if (a.mode == SWEEP_PROP) src = a.in;
   else if (a.mode == SWEEP_INIT) src = a.U;
   else src = a.Gold + (size_t)a.n_first * MM;   // ITER: G(u_k) is unchanged -> reuse G_old_k
-  for (int e = tid; e < BH * ncol; e += kThreads) {
-    const int r = e / ncol, c = e - r * ncol;
-    const int j = bd.jbase + r;
+  for (int e = tid; e < BH * NCOL; e += NT) {
+    const int r = e / NCOL, c = e % NCOL;
+    const int j = jbase + r;
     u[e] = (j < M && c < M) ? src[(size_t)j * M + c] : 0.f;
   }
   __syncthreads();
@@ -196,54 +214,44 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_band_kernel(const __grid_co
     if (!skip_g) {
       for (int cstep = 0; cstep < a.csteps; ++cstep) {
         const double tau_new = d.tau0 + a.slice_len * n + (cstep + 1) * d.dtau;
-        set_far_field_c(u, pf, (float)tau_new, h, bd, tid);
-        cluster.sync();
-        // b^ = D^{-1} dtau R_h w ; x = 0 ; r = r^ = p = b^
+        set_far_field_c<NCOL, NT, BH>(u, pf, (float)tau_new, h, M, jbase, tid);
+        if (C > 1) cluster.sync(); else __syncthreads();
+        // b^ = D^{-1} dtau R_h w ;  x = 0 ;  r = r^ = p = b^
         float x[K], rr[K], vv[K], tt[K];
-        double acc[1] = {0.0};
-        if (bd.active) {
-          const int col = bd.col, r0 = bd.r0;
-          const int il = col > 0 ? col - 1 : 0, ir = col + 1 < ncol ? col + 1 : col;
-          const float* up = (r0 == 0) ? (u_prev ? u_prev + (BH - 1) * ncol : u) : u + (r0 - 1) * ncol;
-          float uW = up[il], uC = up[col], uE = up[ir];
-          float cW = u[r0 * ncol + il], cC = u[r0 * ncol + col], cE = u[r0 * ncol + ir];
-          const bool last_group = (r0 + K >= BH);
+        double acc[1];
+        {
+          float nW = u_up[il], nC = u_up[col], nE = u_up[ir];
+          float cW = u[r0 * NCOL + il], cC = u[r0 * NCOL + col], cE = u[r0 * NCOL + ir];
           float part = 0.f;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const int r = r0 + k, j = bd.jbase + r;
-            const float* dn = (k < K - 1 || !last_group) ? u + (r + 1) * ncol
-                                                         : (u_next ? u_next : u + (BH - 1) * ncol);
-            const float dW = dn[il], dC = dn[col], dE = dn[ir];
-            float bh = 0.f;
-            if (j < M - 1 && col < M - 1) {
-              const float4 rc = rowt[r];
-              const float cg = cgi * rc.z;
-              const float b = ce * (cE - cC) - cw * (cC - cW) + rc.x * (dC - cC) - rc.y * (cC - uC) +
-                              cg * ((dE - uE) - (dW - uW)) - rdt * cC;
-              bh = b * ID[r * ncol + col];
+            const int r = r0 + k;
+            float sW, sC, sE;
+            if (k < K - 1) {
+              sW = u[(r + 1) * NCOL + il]; sC = u[(r + 1) * NCOL + col]; sE = u[(r + 1) * NCOL + ir];
+            } else {
+              sW = u_dn[il]; sC = u_dn[col]; sE = u_dn[ir];
             }
+            const float2 rc = rowc[r];
+            const float cg = fmaf((float)k, cgi, cg0);
+            const float b = ce * (cE - cC) - cw * (cC - cW) + rc.x * (sC - cC) - rc.y * (cC - nC) +
+                            cg * ((sE - nE) - (sW - nW)) - rdt * cC;
+            const float bh = b * ID[r * NCOL + col];
             x[k] = 0.f; rr[k] = bh; vv[k] = 0.f; tt[k] = 0.f;
-            part += bh * bh;
-            uW = cW; uC = cC; uE = cE;
-            cW = dW; cC = dC; cE = dE;
+            part = fmaf(bh, bh, part);
+            nW = cW; nC = cC; nE = cE;
+            cW = sW; cC = sC; cE = sE;
           }
           acc[0] = (double)part;
-        } else {
-#pragma unroll
-          for (int k = 0; k < K; ++k) { x[k] = rr[k] = vv[k] = tt[k] = 0.f; }
         }
-        // P and RH may still be read by neighbours of the previous solve: the cluster.sync
-        // above ordered those reads before these writes.
-        if (bd.active) {
+        // P and RH are not read by anyone between the barrier above and the next one.
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int idx = (bd.r0 + k) * ncol + bd.col;
-            P[idx] = rr[k];
-            RH[idx] = rr[k];
-          }
+        for (int k = 0; k < K; ++k) {
+          const int idx = (r0 + k) * NCOL + col;
+          P[idx] = rr[k];
+          RH[idx] = rr[k];
         }
-        cluster_sum<1>(cluster, acc, wpart, slots, bcast, round, C);   // publishes P
+        cluster_sum<1, NW>(cluster, acc, wpart, slots, bcast, round, C);   // also publishes P
         const double bnorm2 = acc[0];
         double rho = bnorm2;
         double alpha = 1.0, omega = 1.0;
@@ -252,135 +260,134 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_band_kernel(const __grid_co
         bool conv = (bnorm2 <= 1e-60);
         while (!conv && it < a.maxit) {
           ++it;
-          // v = A^ p ; alpha = rho / (r^, v)
-          double red1[1] = {0.0};
-          if (bd.active) {
-            scaled_matvec<K>(bd, P, P_prev, P_next, rowt, ID, ce, cw, cgi, vv);
+          // v = A^ p ;  alpha = rho / (r^, v)
+          scaled_matvec<NCOL, K>(P, P_up, P_dn, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
+          double red1[1];
+          {
             float part = 0.f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) part += RH[(bd.r0 + k) * ncol + bd.col] * vv[k];
+            for (int k = 0; k < K; ++k) part = fmaf(RH[(r0 + k) * NCOL + col], vv[k], part);
             red1[0] = (double)part;
           }
-          cluster_sum<1>(cluster, red1, wpart, slots, bcast, round, C);
+          cluster_sum<1, NW>(cluster, red1, wpart, slots, bcast, round, C);
           if (red1[0] == 0.0) { failed = true; break; }
           alpha = rho / red1[0];
+          const float af = (float)alpha;
           // s = r - alpha v
-          if (bd.active) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) S[(bd.r0 + k) * ncol + bd.col] = rr[k] - (float)alpha * vv[k];
-          }
-          cluster.sync();
-          // t = A^ s ; omega = (t, s) / (t, t)
-          double red2[2] = {0.0, 0.0};
-          if (bd.active) {
-            scaled_matvec<K>(bd, S, S_prev, S_next, rowt, ID, ce, cw, cgi, tt);
+          for (int k = 0; k < K; ++k) S[(r0 + k) * NCOL + col] = fmaf(-af, vv[k], rr[k]);
+          if (C > 1) cluster.sync(); else __syncthreads();
+          // t = A^ s ;  omega = (t, s) / (t, t)
+          scaled_matvec<NCOL, K>(S, S_up, S_dn, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, tt);
+          double red2[2];
+          {
             float p0 = 0.f, p1 = 0.f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const float sv = S[(bd.r0 + k) * ncol + bd.col];
-              p0 += tt[k] * sv;
-              p1 += tt[k] * tt[k];
+              const float sv = S[(r0 + k) * NCOL + col];
+              p0 = fmaf(tt[k], sv, p0);
+              p1 = fmaf(tt[k], tt[k], p1);
             }
             red2[0] = (double)p0; red2[1] = (double)p1;
           }
-          cluster_sum<2>(cluster, red2, wpart, slots, bcast, round, C);
+          cluster_sum<2, NW>(cluster, red2, wpart, slots, bcast, round, C);
           omega = (red2[1] > 0.0) ? red2[0] / red2[1] : 0.0;
-          // x += alpha p + omega s ; r = s - omega t
-          double red3[2] = {0.0, 0.0};
-          if (bd.active) {
+          const float of = (float)omega;
+          // x += alpha p + omega s ;  r = s - omega t
+          double red3[2];
+          {
             float p0 = 0.f, p1 = 0.f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const int idx = (bd.r0 + k) * ncol + bd.col;
+              const int idx = (r0 + k) * NCOL + col;
               const float sv = S[idx];
-              x[k] += (float)alpha * P[idx] + (float)omega * sv;
-              rr[k] = sv - (float)omega * tt[k];
-              p0 += RH[idx] * rr[k];
-              p1 += rr[k] * rr[k];
+              x[k] += af * P[idx] + of * sv;
+              rr[k] = fmaf(-of, tt[k], sv);
+              p0 = fmaf(RH[idx], rr[k], p0);
+              p1 = fmaf(rr[k], rr[k], p1);
             }
             red3[0] = (double)p0; red3[1] = (double)p1;
           }
-          cluster_sum<2>(cluster, red3, wpart, slots, bcast, round, C);
+          cluster_sum<2, NW>(cluster, red3, wpart, slots, bcast, round, C);
           if (red3[1] <= stop2) { conv = true; break; }
           if (omega == 0.0 || rho == 0.0) { failed = true; break; }
           const double beta = (red3[0] / rho) * (alpha / omega);
           rho = red3[0];
-          if (bd.active) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-              const int idx = (bd.r0 + k) * ncol + bd.col;
-              P[idx] = rr[k] + (float)beta * (P[idx] - (float)omega * vv[k]);
-            }
-          }
-          cluster.sync();
-        }
-        if (!conv) failed = true;
-        // u^{m+1} = w + d on interior nodes (far-field nodes already hold g(tau_new))
-        if (bd.active) {
+          const float bf = (float)beta;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const int r = bd.r0 + k, j = bd.jbase + r;
-            if (j < M - 1 && bd.col < M - 1) u[r * ncol + bd.col] += x[k];
+            const int idx = (r0 + k) * NCOL + col;
+            P[idx] = rr[k] + bf * (P[idx] - of * vv[k]);
           }
+          if (C > 1) cluster.sync(); else __syncthreads();
         }
-        cluster.sync();
+        if (!conv) failed = true;
+        iters_max = it > iters_max ? it : iters_max;
+        // u^{m+1} = w + d (x = 0 off the PDE rows, whose values already hold g(tau_new))
+#pragma unroll
+        for (int k = 0; k < K; ++k) u[(r0 + k) * NCOL + col] += x[k];
+        if (C > 1) cluster.sync(); else __syncthreads();
       }
     }
 
     if (a.mode == SWEEP_PROP) {
-      if (bd.active) {
+      if (col < M) {
+#pragma unroll
         for (int k = 0; k < K; ++k) {
-          const int j = bd.jbase + bd.r0 + k;
-          if (j < M) a.out[(size_t)j * M + bd.col] = u[(bd.r0 + k) * ncol + bd.col];
+          const int j = jbase + r0 + k;
+          if (j < M) a.out[(size_t)j * M + col] = u[(r0 + k) * NCOL + col];
         }
       }
     } else if (a.mode == SWEEP_INIT) {
       double nr[1] = {0.0};
-      if (bd.active) {
+      if (col < M) {
         float* Un = a.U + (size_t)(n + 1) * MM;
         float* Gn = a.Gold + (size_t)n * MM;
+#pragma unroll
         for (int k = 0; k < K; ++k) {
-          const int j = bd.jbase + bd.r0 + k;
+          const int j = jbase + r0 + k;
           if (j < M) {
-            const float g = u[(bd.r0 + k) * ncol + bd.col];
-            Un[(size_t)j * M + bd.col] = g;
-            Gn[(size_t)j * M + bd.col] = g;
+            const float g = u[(r0 + k) * NCOL + col];
+            Un[(size_t)j * M + col] = g;
+            Gn[(size_t)j * M + col] = g;
             nr[0] += (double)g * (double)g;
           }
         }
       }
-      cluster_sum<1>(cluster, nr, wpart, slots, bcast, round, C);
-      if (bd.rank == 0 && tid == 0) { a.norms[2 * (n + 1)] = nr[0]; a.norms[2 * (n + 1) + 1] = 0.0; }
+      cluster_sum<1, NW>(cluster, nr, wpart, slots, bcast, round, C);
+      if (rank == 0 && tid == 0) { a.norms[2 * (n + 1)] = nr[0]; a.norms[2 * (n + 1) + 1] = 0.0; }
     } else {
-      // correction u_{n+1} = F_n + (G_new - G_old_n), defect partials
+      // correction u_{n+1} = F_n + (G_new - G_old_n) and defect partials
       double nr[2] = {0.0, 0.0};
-      if (bd.active) {
+      if (col < M) {
         float* Un = a.U + (size_t)(n + 1) * MM;
         const float* Fn = a.Fb + (size_t)n * MM;
         float* Gn = a.Gold + (size_t)n * MM;
+#pragma unroll
         for (int k = 0; k < K; ++k) {
-          const int r = bd.r0 + k, j = bd.jbase + r;
+          const int r = r0 + k, j = jbase + r;
           if (j < M) {
-            const size_t gi = (size_t)j * M + bd.col;
-            const float gnew = u[r * ncol + bd.col];
+            const size_t gi = (size_t)j * M + col;
+            const float gnew = u[r * NCOL + col];
             const float unew = Fn[gi] + (gnew - Gn[gi]);
             const float uold = Un[gi];
             Un[gi] = unew;
             Gn[gi] = gnew;
-            u[r * ncol + bd.col] = unew;
+            u[r * NCOL + col] = unew;
             const double du = (double)unew - (double)uold;
             nr[0] += (double)unew * (double)unew;
             nr[1] += du * du;
           }
         }
       }
-      cluster_sum<2>(cluster, nr, wpart, slots, bcast, round, C);
-      if (bd.rank == 0 && tid == 0) { a.norms[2 * (n + 1)] = nr[0]; a.norms[2 * (n + 1) + 1] = nr[1]; }
+      cluster_sum<2, NW>(cluster, nr, wpart, slots, bcast, round, C);
+      if (rank == 0 && tid == 0) { a.norms[2 * (n + 1)] = nr[0]; a.norms[2 * (n + 1) + 1] = nr[1]; }
     }
   }
 
-  if (bd.rank == 0 && tid == 0) {
+  if (rank == 0 && tid == 0) {
     if (failed) atomicOr(a.status, 1);
+    atomicMax(a.status + 1, iters_max);
     if (a.mode == SWEEP_ITER) {
       double num = 0.0, den = 0.0;
       for (int n = 1; n <= a.N; ++n) {
@@ -392,22 +399,22 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_band_kernel(const __grid_co
   }
 }
 
-template <int K>
+template <int NCOL, int NT, int K>
 static int launch_sweep_k(const bs_grid* g, const SweepParams& sp, cudaStream_t s) {
-  const BandShape& sh = sp.sh;
-  const size_t smem = (size_t)5 * sh.BH * sh.ncol * sizeof(float) + (size_t)sh.BH * sizeof(float4) +
-                      ((kThreads / 32) * 4 + 8 + 4) * sizeof(double);
-  auto kern = sweep_band_kernel<K>;
+  using CB = CBand<NCOL, NT, K>;
+  const size_t smem = (size_t)5 * CB::BH * NCOL * sizeof(float) + (size_t)CB::BH * sizeof(float2) +
+                      (CB::NW * 4 + 8 + 4) * sizeof(double);
+  auto kern = sweep_band_kernel<NCOL, NT, K>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  if (sp.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(sh.C, 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.gridDim = dim3(sp.sh.C, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = sh.C;
+  attr[0].val.clusterDim.x = sp.sh.C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -424,7 +431,13 @@ int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaSt
   sp.h = (float)(g->xmax / (g->M - 1));
   if (sp.sh.C < 1 || sp.sh.C > kMaxCluster)
     return set_error(BS_ERR_ARG, "coarse propagator: grid M=%d not supported", g->M);
-  return (sp.sh.K == 8) ? launch_sweep_k<8>(g, sp, s) : launch_sweep_k<16>(g, sp, s);
+  switch (sp.sh.ncol) {
+    case 32: return launch_sweep_k<32, 256, 4>(g, sp, s);
+    case 64: return launch_sweep_k<64, 512, 8>(g, sp, s);
+    case 128: return launch_sweep_k<128, 512, 16>(g, sp, s);
+    case 256: return launch_sweep_k<256, 512, 16>(g, sp, s);
+  }
+  return set_error(BS_ERR_ARG, "coarse propagator: no band shape for M=%d", g->M);
 }
 
 }  // namespace bsp
