@@ -1,0 +1,433 @@
+"""Benchmark: Parareal time-to-tolerance vs serial fine stepping on one GB300.
+
+One step = Parareal (eq. parareal, numerical coarse model) to tol 1e-4 on the exchange
+option workload: 256x256 nodes on [0,4]^2, sigma1=0.25, sigma2=0.35, r=0.03, T=1, N=64 slices
+of 512 implicit-Euler fine steps and 4 coarse steps, for each rho in {-0.5, 0, 0.7}.
+
+  value   serial-fine-equivalent grid-point updates per second delivered by Parareal
+          (sum over the step's solves of M*M*N*fine_steps / device time of the step)
+  e2e     the same through parareal_solve with host buffers: the initial state is copied
+          from pinned host memory and the price surface u_N read back inside the timed region
+  roofline, cpu_baseline, clocks, gpu_launches: see the README of the output keys below.
+
+--impl reference times the FP64 CPU oracle (oracle/) on the host cores on a bounded sample
+of the same workload, in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "Parareal time-to-tol vs serial fine (1 GB300); fine pt-updates/s; p99 latency"
+UNIT = "pt-updates/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 issue peak of the fine stepper's bound: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA)
+# x the maximum SM clock.
+def fp32_peak_tflops(sm_mhz):
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# Algorithmic FLOPs of one fine point-step with m Jacobi sweeps: each sweep is the 9-point
+# update (5 FMA + 3 add + 1 multiply = 14 FLOP), plus b = dtau R_h w (16 FLOP) and the
+# compensated update (8 FLOP) once per step.  A launch of s steps takes m0 sweeps in its
+# first (cold-started) step and m in the others.
+def fine_flops_per_point_step(m):
+    return 14 * m + 24
+
+
+def fine_flops_per_point_launch(m, m0, steps):
+    return (steps - 1) * fine_flops_per_point_step(m) + fine_flops_per_point_step(m0)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def traffic_for(kernel, source_files):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for s in source_files:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    if ent.get("source_sha256") != h.hexdigest():
+        return None
+    return ent.get("dram_bytes_per_launch_full")
+
+
+def gpu_arm(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2404_02521_gb300 as bs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    bs.load()
+    problems = [wl.exchange_cfg2(rho) for rho in wl.EXCHANGE_RHOS]
+    pb0 = problems[0]
+    M, N = pb0.M, pb0.N
+    g = bs.Grid(M, pb0.xmax)
+    U = torch.empty((N + 1, M, M), device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    bs.bs_set_option(bs.OPT_PHASE_TIMING, 1)
+
+    def solve(pb):
+        rc, k, d = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM,
+                                     pb.coarse_steps, None, pb.tol, pb.N, U, stream)
+        return k
+
+    def step():
+        return [solve(pb) for pb in problems]
+
+    # warm-up
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    bs.bs_phase_stats(g)
+
+    # timed region: device events per step, L2 flushed between steps (outside the events)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    ks = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ks.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    phases = bs.bs_phase_stats(g)
+    t_max_ms = barrier_max(total_ms, world)
+    pts_per_step = sum(pb.M * pb.M * pb.N * pb.fine_steps for pb in problems)
+    value = world * args.steps * pts_per_step / (t_max_ms / 1e3)
+
+    # fine stepper alone: every slice of every rho in one batched launch per rho
+    m_sweeps = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine)
+    m_cold = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, first_step=True)
+    Fb = torch.empty((N, M, M), device=dev)
+    for pb in problems:
+        bs.bs_payoff(g, pb.params, U[0])
+    sl = pb0.params.T / N
+    fine_ms = []
+    for pb in problems:
+        for n in range(1, N + 1):
+            U[n].copy_(U[0])
+        args_f = ([pb.params] * N, [U[n] for n in range(N)], [Fb[n] for n in range(N)],
+                  [n * sl for n in range(N)], [pb.dtau_fine] * N, pb.fine_steps)
+        bs.fine_propagate_batched(g, *args_f, stream=stream)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bs.fine_propagate_batched(g, *args_f, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fine_ms.append(e0.elapsed_time(e1))
+    fine_rate = N * M * M * pb0.fine_steps / (statistics.mean(fine_ms) / 1e3)
+
+    # serial fine on the same GPU: one slice after another (what Parareal replaces)
+    serial_ms = []
+    for pb in problems:
+        bs.bs_payoff(g, pb.params, U[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for n in range(N):
+            bs.fine_propagate_batched(g, [pb.params], [U[n]], [U[n + 1]], [n * sl],
+                                      [pb.dtau_fine], pb.fine_steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        serial_ms.append(e0.elapsed_time(e1))
+    bs.bs_phase_stats(g)
+
+    # end-to-end through the C ABI with host buffers
+    u0_host = torch.empty((len(problems), M, M), dtype=torch.float32).pin_memory()
+    for q, pb in enumerate(problems):
+        bs.bs_payoff(g, pb.params, U[0])
+        torch.cuda.synchronize()
+        u0_host[q].copy_(U[0].cpu())
+    out_host = torch.empty((len(problems), M, M), dtype=torch.float32).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q, pb in enumerate(problems):
+            U[0].copy_(u0_host[q], non_blocking=True)
+            bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps,
+                              bs.COARSE_NUM | bs.PARAREAL_USER_U0, pb.coarse_steps, None, pb.tol,
+                              pb.N, U, stream)
+            out_host[q].copy_(U[N], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+    e2e_max = barrier_max(e2e_ms, world)
+    e2e_value = world * args.steps * pts_per_step / (e2e_max / 1e3)
+
+    # roofline of the dominant kernel by event-timed share
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fine_launch_ms = phases["fine_ms"] / max(1, phases["fine_launches"])
+    coarse_launch_ms = phases["coarse_ms"] / max(1, phases["coarse_launches"])
+    k_tot = sum(sum(k) for k in ks)
+    # fine launches in the timed region: iteration k covers slices k..N-1
+    fine_pt_launches = 0
+    for kl in ks:
+        for k in kl:
+            fine_pt_launches += sum((N - kk) for kk in range(k)) * M * M
+    fine_flops = fine_pt_launches * fine_flops_per_point_launch(m_sweeps, m_cold, pb0.fine_steps)
+    peak_fp32 = fp32_peak_tflops(sm_max)
+    fine_tflops = fine_flops / (phases["fine_ms"] / 1e3) / 1e12 if phases["fine_ms"] > 0 else 0.0
+    kernels = {
+        "fine_band_kernel": {"ms_total": phases["fine_ms"], "launches": phases["fine_launches"],
+                             "ms_per_launch": fine_launch_ms, "bound": "alu",
+                             "achieved_tflops": fine_tflops,
+                             "peak_tflops": peak_fp32,
+                             "frac": fine_tflops / peak_fp32},
+        "sweep_band_kernel": {"ms_total": phases["coarse_ms"], "launches": phases["coarse_launches"],
+                              "ms_per_launch": coarse_launch_ms,
+                              "note": "serial coarse sweep: BiCGSTAB latency-bound (cluster barriers)"},
+    }
+    dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    if dominant == "fine_band_kernel":
+        roof = {"kernel": dominant, "bound": "alu", "achieved": fine_tflops, "peak": peak_fp32,
+                "unit": "TFLOP/s", "frac": fine_tflops / peak_fp32,
+                "traffic": traffic_for("fine_band_kernel", ["paper_2404_02521_gb300/csrc/fine.cu"]),
+                "peak_source": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({pk_kind} max clock)"}
+    else:
+        # algorithmic FLOPs of the coarse sweep: per BiCGSTAB iteration and node, two
+        # matrix-vector products (2 x 14) and the dot/axpy work (22)
+        roof = {"kernel": dominant, "bound": "alu", "achieved": None, "peak": peak_fp32,
+                "unit": "TFLOP/s", "frac": None,
+                "traffic": traffic_for("sweep_band_kernel", ["paper_2404_02521_gb300/csrc/coarse.cu"]),
+                "peak_source": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({pk_kind} max clock)",
+                "note": "latency-bound serial coarse solve; see kernels"}
+    launches = phases["fine_launches"] + phases["coarse_launches"] + phases["other_launches"]
+    return {
+        "value": value, "t_ms": t_max_ms, "ks": ks, "fine_rate": fine_rate, "fine_ms": fine_ms,
+        "serial_ms": serial_ms, "e2e": e2e_value, "roof": roof, "kernels": kernels, "clocks": clk,
+        "launches": launches, "sweeps": m_sweeps, "sweeps_cold": m_cold, "pts_per_step": pts_per_step,
+        "h2d": len(problems) * M * M * 4, "d2h": len(problems) * M * M * 4,
+    }
+
+
+def oracle_sample(seconds_budget=15.0):
+    """Oracle serial fine on the first rho of the workload, as many steps as fit the budget."""
+    from oracle import fd
+    pb = wl.exchange_cfg2(wl.EXCHANGE_RHOS[0])
+    t0 = time.perf_counter()
+    ie = fd.ImplicitEuler(pb.M, pb.xmax, pb.params, pb.dtau_fine)
+    u = fd.initial_state(pb.M, pb.xmax, pb.params)
+    steps = 0
+    while time.perf_counter() - t0 < seconds_budget and steps < pb.N * pb.fine_steps:
+        u = ie.step(u, (steps + 1) * pb.dtau_fine)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return pb.M * pb.M * steps / dt, steps, dt
+
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    try:
+        from threadpoolctl import threadpool_limits
+        ctx = threadpool_limits(1)
+    except Exception:
+        ctx = None
+    budget = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(budget / 4)
+    vals, total_steps, total_s = [], 0, 0.0
+    for _ in range(args.steps):
+        v, st, dt = oracle_sample(budget)
+        vals.append(v)
+        total_steps += st
+        total_s += dt
+    value = sum(vals) / len(vals)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "exchange256_N64_fine512_coarse4", "rho": list(wl.EXCHANGE_RHOS),
+                   "l2": "oracle runs on the CPU"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 sparse-LU serial fine stepping, rho={wl.EXCHANGE_RHOS[0]}, "
+                                   f"{total_steps} implicit steps of the 256x256 grid over "
+                                   f"{args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    world, rank, local = dist_setup()
+    r = gpu_arm(args, world, rank, local)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            from threadpoolctl import threadpool_limits
+            ctx = threadpool_limits(1)
+        except Exception:
+            ctx = None
+        v, st, dt = oracle_sample(15.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 sparse-LU serial fine stepping of the 256x256 exchange workload "
+                         f"(rho={wl.EXCHANGE_RHOS[0]}), first {st} of 32768 implicit steps, {dt:.1f} s"}
+    ks = r["ks"]
+    mean_serial = statistics.mean(r["serial_ms"])
+    per_solve = r["t_ms"] / (args.steps * len(wl.EXCHANGE_RHOS))
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["t_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "exchange256_N64_fine512_coarse4",
+                   "grid": 256, "slices": 64, "fine_steps": 512, "coarse_steps": 4,
+                   "coarse": "numerical (BiCGSTAB)", "rho": list(wl.EXCHANGE_RHOS), "tol": 1e-4,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "flushed between timed steps (2x L2 buffer write)"},
+        "time_to_tol_ms_per_solve": per_solve,
+        "serial_fine_ms_per_solve": mean_serial,
+        "speedup_vs_serial_fine": mean_serial / per_solve,
+        "parareal_iterations": ks[-1],
+        "fine_pt_updates_per_s": r["fine_rate"],
+        "fine_sweeps_per_step": r["sweeps"],
+        "fine_sweeps_first_step": r["sweeps_cold"],
+        "roofline": r["roof"],
+        "kernels": r["kernels"],
+        "cpu_baseline": cpu,
+        "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -51,6 +51,10 @@ enum {
 };
 
 enum { BS_COARSE_NUM = 0, BS_COARSE_PINO = 1 };
+/* Flag or-ed into parareal_solve's coarse_kind: u_out[0..M*M) already holds the initial state
+ * u(tau = 0) on entry (for example a tabulated payoff uploaded by the caller); without it the
+ * payoff of p is written there.  The far-field data still follow p->payoff. */
+enum { BS_PARAREAL_USER_U0 = 0x100 };
 
 /* Model and payoff parameters (eq. bse: sigma1, sigma2, rho, r; Sec. 3.2 payoff). */
 typedef struct {
@@ -139,8 +143,39 @@ int parareal_solve(const bs_grid* g, const bs_params* p, int N, int fine_steps,
                    bs_stream stream);
 
 /* Number of Jacobi sweeps F uses per implicit step for these parameters and step size on
- * this grid (0 if Jacobi does not apply).  Host-only helper. */
-int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau);
+ * this grid: for the first step of a launch (first_step != 0, started from a zero increment)
+ * or for the warm-started steps after it.  0 if Jacobi does not apply.  Host-only helper. */
+int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_step);
+
+/* Solver options (process-wide; set them before launching work, not concurrently with it).
+ *  BS_OPT_FINE_SWEEPS    Jacobi sweeps per fine step, >= 3; 0 = derive from the contraction
+ *                        bound (default)
+ *  BS_OPT_JACOBI_TARGET  the derived sweep count of a warm-started step (each step starts
+ *                        from the previous step's increment) makes q^sweeps <= this
+ *                        (default 2^-10)
+ *  BS_OPT_JACOBI_TARGET_COLD  the same for the first step of a launch, which starts from a
+ *                        zero increment (default 2^-22)
+ *  BS_OPT_KRYLOV_TOL     relative residual at which a coarse BiCGSTAB solve stops (1e-6)
+ *  BS_OPT_KRYLOV_MAXIT   iteration cap of a coarse BiCGSTAB solve (default 400)
+ *  BS_OPT_PHASE_TIMING   1: parareal_solve brackets its fine and coarse launches with CUDA
+ *                        events on the caller's stream (read back by bs_phase_stats); 0: off
+ * Returns BS_OK or BS_ERR_ARG for an unknown option or an out-of-range value. */
+enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
+       BS_OPT_KRYLOV_MAXIT = 3, BS_OPT_PHASE_TIMING = 4, BS_OPT_JACOBI_TARGET_COLD = 5 };
+int bs_set_option(int option, double value);
+
+/* Diagnostics of the coarse solves enqueued on this grid since the last parareal_solve or
+ * bs_grid_stats call: the largest BiCGSTAB iteration count and whether any solve hit its
+ * cap.  Synchronous (waits for the device), then resets the counters. */
+int bs_grid_stats(bs_grid* g, int* krylov_iters_max, int* krylov_failed);
+
+/* Per-phase accounting on this grid since the last call: kernel launches of the fine
+ * propagator, of the coarse propagator / serial Parareal sweep, and of everything else
+ * (payoff), and -- when BS_OPT_PHASE_TIMING is on -- the summed CUDA-event durations of the
+ * fine and coarse launches made by parareal_solve.  Host-only (the event times were read
+ * when parareal_solve synchronised); resets the counters.  Any pointer may be NULL. */
+int bs_phase_stats(bs_grid* g, double* fine_ms, int* fine_launches, double* coarse_ms,
+                   int* coarse_launches, int* other_launches);
 
 #ifdef __cplusplus
 }

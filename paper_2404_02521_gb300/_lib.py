@@ -22,7 +22,10 @@ COARSE_NUM, COARSE_PINO = 0, 1
 # exported entry points declared in include/bsparareal.h
 EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
-           "parareal_solve", "bs_fine_sweeps"]
+           "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats"]
+OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
+OPT_JACOBI_TARGET_COLD = 5
+PARAREAL_USER_U0 = 0x100
 
 
 class bs_params(C.Structure):
@@ -64,7 +67,10 @@ def load(path: Optional[str] = None):
     lib.pino_load.argtypes = [C.c_char_p, P(vp)]
     lib.pino_destroy.argtypes = [vp]
     lib.parareal_solve.argtypes = [vp, P(bs_params), i, i, i, i, vp, d, i, vp, P(i), P(d), vp]
-    lib.bs_fine_sweeps.argtypes = [vp, P(bs_params), d]
+    lib.bs_fine_sweeps.argtypes = [vp, P(bs_params), d, i]
+    lib.bs_set_option.argtypes = [i, d]
+    lib.bs_grid_stats.argtypes = [vp, P(i), P(i)]
+    lib.bs_phase_stats.argtypes = [vp, P(d), P(i), P(d), P(i), P(i)]
     for name in EXPORTS:
         if name != "bs_last_error":
             getattr(lib, name).restype = C.c_int
@@ -161,9 +167,29 @@ def parareal_solve(g: Grid, p, N: int, fine_steps: int, coarse_kind: int, coarse
     return rc, k.value, [hist[i] for i in range(k.value)]
 
 
-def bs_fine_sweeps(g: Grid, p, dtau: float) -> int:
+def bs_fine_sweeps(g: Grid, p, dtau: float, first_step: bool = False) -> int:
     bp = to_params(p)
-    return int(load().bs_fine_sweeps(g.h, C.byref(bp), float(dtau)))
+    return int(load().bs_fine_sweeps(g.h, C.byref(bp), float(dtau), int(bool(first_step))))
+
+
+def bs_set_option(option: int, value: float):
+    return check(load().bs_set_option(int(option), float(value)))
+
+
+def bs_grid_stats(g: Grid):
+    """(max BiCGSTAB iterations, any solve hit its cap) since the last reset."""
+    it, fail = C.c_int(0), C.c_int(0)
+    check(load().bs_grid_stats(g.h, C.byref(it), C.byref(fail)))
+    return it.value, bool(fail.value)
+
+
+def bs_phase_stats(g: Grid) -> dict:
+    """Launch counts and (with OPT_PHASE_TIMING) event-timed ms per phase; resets them."""
+    fm, cm = C.c_double(0), C.c_double(0)
+    fl, cl, ol = C.c_int(0), C.c_int(0), C.c_int(0)
+    check(load().bs_phase_stats(g.h, C.byref(fm), C.byref(fl), C.byref(cm), C.byref(cl), C.byref(ol)))
+    return {"fine_ms": fm.value, "fine_launches": fl.value, "coarse_ms": cm.value,
+            "coarse_launches": cl.value, "other_launches": ol.value}
 
 
 class Pino:

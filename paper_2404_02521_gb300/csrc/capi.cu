@@ -48,6 +48,8 @@ ItemDesc make_item(const bs_params& p, double tau0, double dtau) {
   d.K = p.strike; d.w1 = p.w1; d.w2 = p.w2; d.K2 = p.strike2; d.cash = p.cash;
   d.payoff = p.payoff;
   d.sweeps = 0;
+  d.sweeps0 = 0;
+  d.pad = 0;
   return d;
 }
 
@@ -68,12 +70,17 @@ double jacobi_contraction(int M, const bs_params& p, double dtau) {
   return q;
 }
 
-// Sweeps so that q^m <= 2^-22 (at least 2: the first sweep forms b, the last applies d).
-int sweeps_for(double q) {
+Options g_opt;
+
+// Sweeps so that q^m <= target (at least 3: the first sweep forms b, the last applies d, and
+// the far-field update sits between them).
+int sweeps_for(double q, bool cold) {
   if (!(q < 0.8)) return 0;
-  if (q <= 0.0) return 2;
-  int m = (int)std::ceil(-22.0 * std::log(2.0) / std::log(q));
-  return m < 2 ? 2 : m;
+  if (g_opt.fine_sweeps > 0) return g_opt.fine_sweeps;
+  if (q <= 0.0) return 3;
+  const double target = cold ? g_opt.jacobi_target_cold : g_opt.jacobi_target;
+  int m = (int)std::ceil(std::log(target) / std::log(q));
+  return m < 3 ? 3 : m;
 }
 
 // Band shapes of the cluster-resident kernels (NCOL columns, NT threads, K rows per thread,
@@ -120,13 +127,13 @@ int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s)
   return BS_OK;
 }
 
-static int grid_sweeps(bs_grid* g, const bs_params& p, double dtau) {
+static int grid_sweeps(bs_grid* g, const bs_params& p, double dtau, bool cold = false) {
   const double key[6] = {p.sigma1, p.sigma2, p.rho, p.r, dtau, (double)g->M};
   if (std::memcmp(key, g->q_key, sizeof(key)) != 0) {
     g->q_val = jacobi_contraction(g->M, p, dtau);
     std::memcpy(g->q_key, key, sizeof(key));
   }
-  return sweeps_for(g->q_val);
+  return sweeps_for(g->q_val, cold);
 }
 
 }  // namespace bsp
@@ -176,12 +183,13 @@ int bs_payoff(const bs_grid* g, const bs_params* p, float* u, bs_stream stream) 
   if (!g || !u) return set_error(BS_ERR_ARG, "bs_payoff: NULL argument");
   int rc = check_params(p);
   if (rc) return rc;
+  const_cast<bs_grid*>(g)->n_other += 1;
   return launch_payoff(g, make_item(*p, 0.0, 0.0), u, (cudaStream_t)stream);
 }
 
-int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau) {
+int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_step) {
   if (!g || check_params(p) || !(dtau > 0.0)) return 0;
-  return grid_sweeps(const_cast<bs_grid*>(g), *p, dtau);
+  return grid_sweeps(const_cast<bs_grid*>(g), *p, dtau, first_step != 0);
 }
 
 int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* const* u_in,
@@ -200,6 +208,7 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* co
     d.in = u_in[b];
     d.out = u_out[b];
     d.sweeps = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b]);
+    d.sweeps0 = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], true);
     if (d.sweeps == 0)
       return set_error(BS_ERR_ARG, "fine_propagate_batched: Jacobi contraction %.3f >= 0.8 for "
                        "item %d; take smaller fine steps", g->q_val, b);
@@ -213,6 +222,7 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* co
                                     cudaMemcpyDeviceToDevice, s));
     return BS_OK;
   }
+  const_cast<bs_grid*>(g)->n_fine += (B + kMaxItems - 1) / kMaxItems;
   return launch_fine(g, items.data(), B, nsteps, s);
 }
 
@@ -236,12 +246,66 @@ int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_pa
     a.in = u_in;
     a.out = u_out;
     a.status = g->status;
-    a.tol = 1e-6;
-    a.maxit = 400;
+    a.tol = g_opt.krylov_tol;
+    a.maxit = g_opt.krylov_maxit;
+    const_cast<bs_grid*>(g)->n_coarse += 1;
     return launch_sweep(g, d, a, (cudaStream_t)stream);
   }
   if (kind == BS_COARSE_PINO) return set_error(BS_ERR_ARG, "coarse_propagate: PINO not loaded");
   return set_error(BS_ERR_ARG, "coarse_propagate: unknown kind %d", kind);
+}
+
+int bs_set_option(int option, double value) {
+  switch (option) {
+    case BS_OPT_FINE_SWEEPS:
+      if (!(value == 0.0 || (value >= 3.0 && value <= 256.0)))
+        return set_error(BS_ERR_ARG, "BS_OPT_FINE_SWEEPS must be 0 or in [3, 256]");
+      g_opt.fine_sweeps = (int)value;
+      return BS_OK;
+    case BS_OPT_JACOBI_TARGET:
+      if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_JACOBI_TARGET must be in (0, 1)");
+      g_opt.jacobi_target = value;
+      return BS_OK;
+    case BS_OPT_JACOBI_TARGET_COLD:
+      if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_JACOBI_TARGET_COLD must be in (0, 1)");
+      g_opt.jacobi_target_cold = value;
+      return BS_OK;
+    case BS_OPT_KRYLOV_TOL:
+      if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_KRYLOV_TOL must be in (0, 1)");
+      g_opt.krylov_tol = value;
+      return BS_OK;
+    case BS_OPT_PHASE_TIMING:
+      g_opt.phase_timing = value != 0.0;
+      return BS_OK;
+    case BS_OPT_KRYLOV_MAXIT:
+      if (!(value >= 1.0 && value <= 100000.0)) return set_error(BS_ERR_ARG, "BS_OPT_KRYLOV_MAXIT must be in [1, 1e5]");
+      g_opt.krylov_maxit = (int)value;
+      return BS_OK;
+  }
+  return set_error(BS_ERR_ARG, "bs_set_option: unknown option %d", option);
+}
+
+int bs_grid_stats(bs_grid* g, int* krylov_iters_max, int* krylov_failed) {
+  if (!g) return set_error(BS_ERR_ARG, "bs_grid_stats: NULL grid");
+  int h[2] = {0, 0};
+  BS_CUDA_TRY(cudaMemcpy(h, g->status, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  BS_CUDA_TRY(cudaMemset(g->status, 0, 2 * sizeof(int)));
+  if (krylov_iters_max) *krylov_iters_max = h[1];
+  if (krylov_failed) *krylov_failed = h[0] & 1;
+  return BS_OK;
+}
+
+int bs_phase_stats(bs_grid* g, double* fine_ms, int* fine_launches, double* coarse_ms,
+                   int* coarse_launches, int* other_launches) {
+  if (!g) return set_error(BS_ERR_ARG, "bs_phase_stats: NULL grid");
+  if (fine_ms) *fine_ms = g->ms_fine;
+  if (coarse_ms) *coarse_ms = g->ms_coarse;
+  if (fine_launches) *fine_launches = g->n_fine;
+  if (coarse_launches) *coarse_launches = g->n_coarse;
+  if (other_launches) *other_launches = g->n_other;
+  g->ms_fine = g->ms_coarse = 0.0;
+  g->n_fine = g->n_coarse = g->n_other = 0;
+  return BS_OK;
 }
 
 int pino_load(const char* path, bs_pino** net) {
@@ -251,6 +315,35 @@ int pino_load(const char* path, bs_pino** net) {
 
 int pino_destroy(bs_pino* net) { return BS_OK; }
 
+// CUDA events bracketing one launch group on the caller's stream (BS_OPT_PHASE_TIMING).
+struct PhaseTimer {
+  cudaEvent_t e[2] = {nullptr, nullptr};
+  bool on = false;
+  int begin(cudaStream_t s) {
+    if (!on) return BS_OK;
+    if (!e[0]) {
+      BS_CUDA_TRY(cudaEventCreate(&e[0]));
+      BS_CUDA_TRY(cudaEventCreate(&e[1]));
+    }
+    BS_CUDA_TRY(cudaEventRecord(e[0], s));
+    return BS_OK;
+  }
+  int end(cudaStream_t s) {
+    if (on) BS_CUDA_TRY(cudaEventRecord(e[1], s));
+    return BS_OK;
+  }
+  // after the stream has been synchronised
+  double elapsed() const {
+    float ms = 0.f;
+    if (on && e[0]) cudaEventElapsedTime(&ms, e[0], e[1]);
+    return (double)ms;
+  }
+  ~PhaseTimer() {
+    if (e[0]) cudaEventDestroy(e[0]);
+    if (e[1]) cudaEventDestroy(e[1]);
+  }
+};
+
 int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps, int coarse_kind,
                    int coarse_steps, const bs_pino* net, double tol, int Kmax, float* u_out,
                    int* k_done, double* defect_hist, bs_stream stream) {
@@ -258,6 +351,8 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   if (!g || !u_out || !k_done) return set_error(BS_ERR_ARG, "parareal_solve: NULL argument");
   int rc = check_params(p);
   if (rc) return rc;
+  const bool user_u0 = (coarse_kind & BS_PARAREAL_USER_U0) != 0;
+  coarse_kind &= ~BS_PARAREAL_USER_U0;
   if (N < 1 || fine_steps < 1 || Kmax < 0 || Kmax > N || !(p->T > 0.0))
     return set_error(BS_ERR_ARG, "parareal_solve: N=%d fine_steps=%d Kmax=%d T=%g", N, fine_steps,
                      Kmax, p->T);
@@ -269,6 +364,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   const double slice = p->T / N;
   const double dtau_f = slice / fine_steps;
   const int sweeps = grid_sweeps(g, *p, dtau_f);
+  const int sweeps0 = grid_sweeps(g, *p, dtau_f, true);
   if (sweeps == 0)
     return set_error(BS_ERR_ARG, "parareal_solve: Jacobi contraction %.3f >= 0.8; more fine steps needed", g->q_val);
   rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1));
@@ -277,10 +373,15 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   float* Gold = Fb + (size_t)N * MM;
   double* norms = (double*)(Gold + (size_t)N * MM);
   BS_CUDA_TRY(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), s));
+  PhaseTimer tf, tc;
+  tf.on = tc.on = g_opt.phase_timing != 0;
 
   ItemDesc dc = make_item(*p, 0.0, slice / coarse_steps);
-  rc = launch_payoff(g, dc, u_out, s);
-  if (rc) return rc;
+  if (!user_u0) {
+    rc = launch_payoff(g, dc, u_out, s);
+    if (rc) return rc;
+    g->n_other += 1;
+  }
   SweepArgs a = {};
   a.N = N;
   a.csteps = coarse_steps;
@@ -291,12 +392,20 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   a.norms = norms;
   a.defect = g->dscal;
   a.status = g->status;
-  a.tol = 1e-6;
-  a.maxit = 400;
+  a.tol = g_opt.krylov_tol;
+  a.maxit = g_opt.krylov_maxit;
   a.mode = SWEEP_INIT;
   a.n_first = 0;
+  if ((rc = tc.begin(s))) return rc;
   rc = launch_sweep(g, dc, a, s);
   if (rc) return rc;
+  if ((rc = tc.end(s))) return rc;
+  g->n_coarse += 1;
+  double ms_c = 0.0, ms_f = 0.0;
+  if (tc.on) {
+    BS_CUDA_TRY(cudaStreamSynchronize(s));
+    ms_c += tc.elapsed();
+  }
 
   std::vector<ItemDesc> items((size_t)N);
   int k = 0;
@@ -309,22 +418,33 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
       d.in = u_out + (size_t)n * MM;
       d.out = Fb + (size_t)n * MM;
       d.sweeps = sweeps;
+      d.sweeps0 = sweeps0;
       items[(size_t)(n - k)] = d;
     }
+    if ((rc = tf.begin(s))) return rc;
     rc = launch_fine(g, items.data(), B, fine_steps, s);
     if (rc) return rc;
+    if ((rc = tf.end(s))) return rc;
+    g->n_fine += (B + kMaxItems - 1) / kMaxItems;
     a.mode = SWEEP_ITER;
     a.n_first = k;
+    if ((rc = tc.begin(s))) return rc;
     rc = launch_sweep(g, dc, a, s);
     if (rc) return rc;
+    if ((rc = tc.end(s))) return rc;
+    g->n_coarse += 1;
     double host[1];
     int hstat = 0;
     BS_CUDA_TRY(cudaMemcpyAsync(host, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
     BS_CUDA_TRY(cudaMemcpyAsync(&hstat, g->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     BS_CUDA_TRY(cudaStreamSynchronize(s));
+    ms_f += tf.elapsed();
+    ms_c += tc.elapsed();
     if (defect_hist) defect_hist[k] = host[0];
     if (hstat) {
       *k_done = k + 1;
+      g->ms_fine += ms_f;
+      g->ms_coarse += ms_c;
       return set_error(BS_ERR_NOCONV, "parareal_solve: a coarse BiCGSTAB solve hit its iteration cap");
     }
     if (host[0] <= tol) {
@@ -334,6 +454,8 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
     }
   }
   *k_done = k;
+  g->ms_fine += ms_f;
+  g->ms_coarse += ms_c;
   if (Kmax == 0) BS_CUDA_TRY(cudaStreamSynchronize(s));
   if (status == BS_ERR_MAXITER)
     return set_error(BS_ERR_MAXITER, "parareal_solve: tol %g not met after %d iterations", tol, k);

@@ -5,23 +5,24 @@
 // dominant, so each step is solved by BiCGSTAB (van der Vorst 1992) on the Jacobi-scaled
 // system  D^{-1}(I - dtau R_h) d = D^{-1} dtau R_h w  in FP32 (the paper runs its coarse
 // models in single precision, Sec. 4.1).  One thread-block cluster holds the whole state and
-// the two matrix-vector operands in shared memory (same band layout as the fine stepper);
-// dot products are reduced warp -> CTA -> cluster in a fixed order, so every CTA obtains
-// bitwise the same scalars and the result does not depend on scheduling.
+// the two matrix-vector operands in shared memory (band layout of band.cuh).
+//
+// Reductions: per-thread partial sums in FP32 (FP64 for the Parareal defect norms), a warp
+// butterfly, then one warp per CTA adds the warp partials and the CTAs' partials in FP64.
+// A butterfly adds the same two operands on both lanes of every pair, so all lanes -- and
+// all CTAs, which read the same partials in the same order -- get bitwise the same total.
+// The BiCGSTAB scalars (alpha, omega, beta) are computed once per CTA by that warp and
+// broadcast through shared memory (FP64 arithmetic on every thread would be slow here).
 //
 // The serial Parareal sweep of eq. (parareal) runs in the same kernel: for n = n_first..N-1
 //   G_new = G(u_n^{k+1});  u_{n+1}^{k+1} = F_n + (G_new - G_old_n);  G_old_n = G_new,
-// with FP64 partial sums of ||u_{n+1}^{k+1} - u_{n+1}^k||^2 and ||u_{n+1}^{k+1}||^2 per slice
-// and, at the end, delta_k = max_n ||du_n|| / max_n ||u_n|| (reading c5).  The correction is
+// with FP64 sums of ||u_{n+1}^{k+1} - u_{n+1}^k||^2 and ||u_{n+1}^{k+1}||^2 per slice and, at
+// the end, delta_k = max_n ||du_n|| / max_n ||u_n|| (reading c5).  The correction is
 // evaluated as F + (G_new - G_old) so that an unchanged slice gives a zero bracket exactly.
-#include <cooperative_groups.h>
-
 #include <cmath>
 #include <cstdio>
 
-#include "common.cuh"
-
-namespace cg = cooperative_groups;
+#include "band.cuh"
 
 namespace bsp {
 
@@ -32,109 +33,96 @@ struct SweepParams {
   float h;
 };
 
-template <int NCOL, int NT, int K>
-struct CBand {
-  static constexpr int G = NT / NCOL;
-  static constexpr int BH = G * K;
-  static constexpr int NW = NT / 32;
+// BiCGSTAB scalar state shared by a CTA (identical in every CTA of the cluster).
+struct Scal {
+  double tot[4];
+  double rho, alpha, omega, stop2, tol;
+  float af, of, bf;
+  int conv, fail;
 };
 
 // Jacobi-scaled operator A^ y = y - invd * (off-diagonal part of dtau R_h) y on the thread's
-// column strip; zero on non-interior nodes (invd = 0 there and y = 0 there).
-template <int NCOL, int K>
-__device__ __forceinline__ void scaled_matvec(const float* __restrict__ y, const float* upr,
-                                              const float* dnr, const float2* __restrict__ rowc,
+// column strip; zero on non-interior nodes (invd = 0 and y = 0 there).
+template <class CFG>
+__device__ __forceinline__ void scaled_matvec(const float* __restrict__ y,
+                                              const float2* __restrict__ rowc,
                                               const float* __restrict__ ID, int col, int il,
                                               int ir, int r0, float ce, float cw, float cg0,
-                                              float cgi, float (&out)[K]) {
-  float nW = upr[il], nC = upr[col], nE = upr[ir];
-  const float sDW = dnr[il], sDC = dnr[col], sDE = dnr[ir];
-  float cW = y[r0 * NCOL + il], cC = y[r0 * NCOL + col], cE = y[r0 * NCOL + ir];
+                                              float cgi, float (&out)[CFG::K]) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K;
+  const int p0 = r0 + 1;
+  float nW = y[(p0 - 1) * NCOL + il], nC = y[(p0 - 1) * NCOL + col], nE = y[(p0 - 1) * NCOL + ir];
+  float cW = y[p0 * NCOL + il], cC = y[p0 * NCOL + col], cE = y[p0 * NCOL + ir];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int r = r0 + k;
-    float sW, sC, sE;
-    if (k < K - 1) {
-      sW = y[(r + 1) * NCOL + il]; sC = y[(r + 1) * NCOL + col]; sE = y[(r + 1) * NCOL + ir];
-    } else {
-      sW = sDW; sC = sDC; sE = sDE;
-    }
-    const float2 rc = rowc[r];
+    const int p = p0 + k;
+    const float sW = y[(p + 1) * NCOL + il], sC = y[(p + 1) * NCOL + col], sE = y[(p + 1) * NCOL + ir];
+    const float2 rc = rowc[p - 1];
     const float cg = fmaf((float)k, cgi, cg0);
-    out[k] = cC - ID[r * NCOL + col] *
+    out[k] = cC - ID[(p - 1) * NCOL + col] *
                       (ce * cE + cw * cW + rc.x * sC + rc.y * nC + cg * ((sE - nE) - (sW - nW)));
     nW = cW; nC = cC; nE = cE;
     cW = sW; cC = sC; cE = sE;
   }
 }
 
-// Deterministic cluster-wide sum of NV values: butterfly within each warp, butterfly of
-// the warp partials in warp 0, then one lane per CTA of the cluster reads that CTA's
-// partial and warp 0 sums them by butterfly.  A butterfly gives every lane the same bits
-// (each level adds the same two operands), so every CTA obtains identical totals.
-// `round` alternates the slot so a fast CTA never overwrites partials still being read.
-template <int NV, int NW>
-__device__ __forceinline__ void cluster_sum(cg::cluster_group& cluster, double (&v)[NV],
-                                            double* wpart, double* slots, double* bcast,
-                                            int& round, int C) {
+template <class T>
+__device__ __forceinline__ T warp_butterfly(T x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
+
+// Cluster-wide sum of NV per-thread values of type T.  On return sc->tot holds the FP64
+// totals and `fin(sc)` has been applied once per CTA (by thread 0) before the closing CTA
+// barrier, so every thread may read what fin wrote.  `round` alternates the slot buffers so
+// that a fast CTA never overwrites partials a slow CTA is still reading.
+template <class CFG, int NV, class T, class Fin>
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, const T (&v)[NV], double* wpart,
+                                            double* slots, Scal* sc, int& round, int rank, int C,
+                                            Fin fin) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    double x = v[q];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) wpart[warp * NV + q] = x;
+    const T x = warp_butterfly<T>(v[q]);
+    if (lane == 0) wpart[warp * 4 + q] = (double)x;
   }
   __syncthreads();
-  double* slot = slots + (round & 1) * NV;
+  double* slot = slots + (round & 1) * kMaxCluster * 4;
   if (warp == 0) {
+    double tot[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double x = lane < NW ? wpart[lane * NV + q] : 0.0;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-      if (C == 1) {
-        if (lane == 0) bcast[q] = x;
-      } else if (lane == 0) {
-        slot[q] = x;
+    for (int q = 0; q < NV; ++q)
+      tot[q] = warp_butterfly<double>(lane < CFG::NW ? wpart[lane * 4 + q] : 0.0);
+    if (C == 1) {
+      if (lane == 0) {
+        for (int q = 0; q < NV; ++q) sc->tot[q] = tot[q];
+        fin(sc);
       }
+    } else if (lane < C) {
+      double* dst = cl.map_shared_rank(slot, lane) + rank * 4;
+      for (int q = 0; q < NV; ++q) dst[q] = tot[q];
     }
   }
   if (C > 1) {
-    cluster.sync();
+    cl.sync();
     if (warp == 0) {
+      double tot[NV];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        double x = lane < C ? cluster.map_shared_rank(slot, lane)[q] : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        if (lane == 0) bcast[q] = x;
+      for (int q = 0; q < NV; ++q) tot[q] = warp_butterfly<double>(lane < C ? slot[lane * 4 + q] : 0.0);
+      if (lane == 0) {
+        for (int q = 0; q < NV; ++q) sc->tot[q] = tot[q];
+        fin(sc);
       }
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = bcast[q];
   ++round;
 }
 
-template <int NCOL, int NT, int BH>
-__device__ __forceinline__ void set_far_field_c(float* u, const PayoffF& pf, float tau, float h,
-                                                int M, int jbase, int tid) {
-  const bool has_last_row = (jbase <= M - 1) && (M - 1 < jbase + BH);
-  const int n_entries = BH + (has_last_row ? (M - 1) : 0);
-  for (int e = tid; e < n_entries; e += NT) {
-    int r, c;
-    if (e < BH) { r = e; c = M - 1; if (jbase + r > M - 1) continue; }
-    else { r = M - 1 - jbase; c = e - BH; }
-    u[r * NCOL + c] = far_field(pf, c * h, (jbase + r) * h, tau);
-  }
-}
-
-template <int NCOL, int NT, int K>
-__global__ void __launch_bounds__(NT, 1) sweep_band_kernel(const __grid_constant__ SweepParams sp) {
-  using CB = CBand<NCOL, NT, K>;
-  constexpr int G = CB::G, BH = CB::BH, NW = CB::NW;
+template <class CFG>
+__global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_constant__ SweepParams sp) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, PLANE = CFG::PLANE;
   cg::cluster_group cluster = cg::this_cluster();
   const ItemDesc& d = sp.d;
   const SweepArgs& a = sp.a;
@@ -149,39 +137,29 @@ __global__ void __launch_bounds__(NT, 1) sweep_band_kernel(const __grid_constant
   const PayoffF pf = make_payoff(d);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* u = reinterpret_cast<float*>(smem_raw);   // state w / u
-  float* P = u + BH * NCOL;                        // search direction p
-  float* S = P + BH * NCOL;                        // s
-  float* RH = S + BH * NCOL;                       // shadow residual r^
-  float* ID = RH + BH * NCOL;                      // inverse diagonal (0 off the PDE rows)
+  float* u = reinterpret_cast<float*>(smem_raw);   // state w / u          [PLANE]
+  float* P = u + PLANE;                            // search direction p   [PLANE]
+  float* S = P + PLANE;                            // s                    [PLANE]
+  float* RH = S + PLANE;                           // shadow residual r^   [PLANE]
+  float* ID = RH + PLANE;                          // inverse diagonal     [BH*NCOL]
   float2* rowc = reinterpret_cast<float2*>(ID + BH * NCOL);
   double* wpart = reinterpret_cast<double*>(rowc + BH);   // [NW][4]
-  double* slots = wpart + NW * 4;                         // [2][4]
-  double* bcast = slots + 8;                              // [4]
+  double* slots = wpart + CFG::NW * 4;                    // [2][16][4]
+  Scal* sc = reinterpret_cast<Scal*>(slots + 2 * kMaxCluster * 4);
 
-  const bool has_prev = rank > 0, has_next = rank < C - 1;
-  auto up_row = [&](float* buf) -> const float* {
-    if (grp > 0) return buf + (r0 - 1) * NCOL;
-    return has_prev ? cluster.map_shared_rank(buf, rank - 1) + (BH - 1) * NCOL : buf;
-  };
-  auto dn_row = [&](float* buf) -> const float* {
-    if (grp < G - 1) return buf + (r0 + K) * NCOL;
-    return has_next ? cluster.map_shared_rank(buf, rank + 1) : buf + (BH - 1) * NCOL;
-  };
-  const float* u_up = up_row(u);
-  const float* u_dn = dn_row(u);
-  const float* P_up = up_row(P);
-  const float* P_dn = dn_row(P);
-  const float* S_up = up_row(S);
-  const float* S_dn = dn_row(S);
+  const HaloPush pu = halo_push<CFG>(cluster, u, rank, C);
+  const HaloPush pP = halo_push<CFG>(cluster, P, rank, C);
+  const HaloPush pS = halo_push<CFG>(cluster, S, rank, C);
 
-  for (int e = tid; e < BH * NCOL; e += NT) {
+  for (int e = tid; e < BH * NCOL; e += CFG::NT) {
     const int r = e / NCOL, c = e % NCOL;
     const int j = jbase + r;
     ID[e] = (j < M - 1 && c < M - 1) ? inv_diag(d, c, j) : 0.f;
+  }
+  for (int e = tid; e < PLANE; e += CFG::NT) {
     P[e] = 0.f; S[e] = 0.f; RH[e] = 0.f;
   }
-  for (int r = tid; r < BH; r += NT) {
+  for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
     row_coefs(d, jbase + r, cs, cn, gj);
     rowc[r] = make_float2(cs, cn);
@@ -192,141 +170,131 @@ __global__ void __launch_bounds__(NT, 1) sweep_band_kernel(const __grid_constant
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
   const float rdt = (float)(d.r * d.dtau);
+  const double tol = a.tol;
   int round = 0;
   int iters_max = 0;
+  bool failed = false;
 
-  // initial state of the first slice
+  // initial state of the first slice (own rows and halo rows)
   const float* src;
   if (a.mode == SWEEP_PROP) src = a.in;
   else if (a.mode == SWEEP_INIT) src = a.U;
   else src = a.Gold + (size_t)a.n_first * MM;   // ITER: G(u_k) is unchanged -> reuse G_old_k
-  for (int e = tid; e < BH * NCOL; e += NT) {
-    const int r = e / NCOL, c = e % NCOL;
-    const int j = jbase + r;
-    u[e] = (j < M && c < M) ? src[(size_t)j * M + c] : 0.f;
-  }
-  __syncthreads();
+  band_load<CFG>(u, src, M, jbase, tid);
+  cluster_barrier(cluster, C);
 
   const int n_end = (a.mode == SWEEP_PROP) ? a.n_first + 1 : a.N;
-  bool failed = false;
   for (int n = a.n_first; n < n_end; ++n) {
     const bool skip_g = (a.mode == SWEEP_ITER && n == a.n_first);
     if (!skip_g) {
       for (int cstep = 0; cstep < a.csteps; ++cstep) {
         const double tau_new = d.tau0 + a.slice_len * n + (cstep + 1) * d.dtau;
-        set_far_field_c<NCOL, NT, BH>(u, pf, (float)tau_new, h, M, jbase, tid);
-        if (C > 1) cluster.sync(); else __syncthreads();
+        band_far_field<CFG>(u, pu, pf, (float)tau_new, h, M, jbase, tid);
+        cluster_barrier(cluster, C);
         // b^ = D^{-1} dtau R_h w ;  x = 0 ;  r = r^ = p = b^
         float x[K], rr[K], vv[K], tt[K];
-        double acc[1];
+        float part[1] = {0.f};
         {
-          float nW = u_up[il], nC = u_up[col], nE = u_up[ir];
-          float cW = u[r0 * NCOL + il], cC = u[r0 * NCOL + col], cE = u[r0 * NCOL + ir];
-          float part = 0.f;
+          const int p0 = r0 + 1;
+          float nW = u[(p0 - 1) * NCOL + il], nC = u[(p0 - 1) * NCOL + col], nE = u[(p0 - 1) * NCOL + ir];
+          float cW = u[p0 * NCOL + il], cC = u[p0 * NCOL + col], cE = u[p0 * NCOL + ir];
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const int r = r0 + k;
-            float sW, sC, sE;
-            if (k < K - 1) {
-              sW = u[(r + 1) * NCOL + il]; sC = u[(r + 1) * NCOL + col]; sE = u[(r + 1) * NCOL + ir];
-            } else {
-              sW = u_dn[il]; sC = u_dn[col]; sE = u_dn[ir];
-            }
-            const float2 rc = rowc[r];
+            const int p = p0 + k;
+            const float sW = u[(p + 1) * NCOL + il], sC = u[(p + 1) * NCOL + col],
+                        sE = u[(p + 1) * NCOL + ir];
+            const float2 rc = rowc[p - 1];
             const float cg = fmaf((float)k, cgi, cg0);
             const float b = ce * (cE - cC) - cw * (cC - cW) + rc.x * (sC - cC) - rc.y * (cC - nC) +
                             cg * ((sE - nE) - (sW - nW)) - rdt * cC;
-            const float bh = b * ID[r * NCOL + col];
+            const float bh = b * ID[(p - 1) * NCOL + col];
             x[k] = 0.f; rr[k] = bh; vv[k] = 0.f; tt[k] = 0.f;
-            part = fmaf(bh, bh, part);
+            part[0] = fmaf(bh, bh, part[0]);
             nW = cW; nC = cC; nE = cE;
             cW = sW; cC = sC; cE = sE;
           }
-          acc[0] = (double)part;
         }
-        // P and RH are not read by anyone between the barrier above and the next one.
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          const int idx = (r0 + k) * NCOL + col;
-          P[idx] = rr[k];
-          RH[idx] = rr[k];
+          band_store<CFG>(P, pP, r0 + k, col, rr[k]);
+          RH[(r0 + k + 1) * NCOL + col] = rr[k];
         }
-        cluster_sum<1, NW>(cluster, acc, wpart, slots, bcast, round, C);   // also publishes P
-        const double bnorm2 = acc[0];
-        double rho = bnorm2;
-        double alpha = 1.0, omega = 1.0;
-        const double stop2 = a.tol * a.tol * bnorm2;
+        cluster_sum<CFG, 1>(cluster, part, wpart, slots, sc, round, rank, C, [tol](Scal* s) {
+          s->rho = s->tot[0];
+          s->stop2 = tol * tol * s->tot[0];
+          s->conv = s->tot[0] <= 1e-60;
+          s->fail = 0;
+          s->alpha = s->omega = 1.0;
+        });
         int it = 0;
-        bool conv = (bnorm2 <= 1e-60);
-        while (!conv && it < a.maxit) {
+        while (!sc->conv && it < a.maxit) {
           ++it;
           // v = A^ p ;  alpha = rho / (r^, v)
-          scaled_matvec<NCOL, K>(P, P_up, P_dn, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
-          double red1[1];
-          {
-            float part = 0.f;
+          scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
+          float p1[1] = {0.f};
 #pragma unroll
-            for (int k = 0; k < K; ++k) part = fmaf(RH[(r0 + k) * NCOL + col], vv[k], part);
-            red1[0] = (double)part;
-          }
-          cluster_sum<1, NW>(cluster, red1, wpart, slots, bcast, round, C);
-          if (red1[0] == 0.0) { failed = true; break; }
-          alpha = rho / red1[0];
-          const float af = (float)alpha;
+          for (int k = 0; k < K; ++k) p1[0] = fmaf(RH[(r0 + k + 1) * NCOL + col], vv[k], p1[0]);
+          cluster_sum<CFG, 1>(cluster, p1, wpart, slots, sc, round, rank, C, [](Scal* s) {
+            if (s->tot[0] == 0.0) { s->fail = 1; return; }
+            s->alpha = s->rho / s->tot[0];
+            s->af = (float)s->alpha;
+          });
+          if (sc->fail) break;
+          const float af = sc->af;
           // s = r - alpha v
 #pragma unroll
-          for (int k = 0; k < K; ++k) S[(r0 + k) * NCOL + col] = fmaf(-af, vv[k], rr[k]);
-          if (C > 1) cluster.sync(); else __syncthreads();
+          for (int k = 0; k < K; ++k) band_store<CFG>(S, pS, r0 + k, col, fmaf(-af, vv[k], rr[k]));
+          cluster_barrier(cluster, C);
           // t = A^ s ;  omega = (t, s) / (t, t)
-          scaled_matvec<NCOL, K>(S, S_up, S_dn, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, tt);
-          double red2[2];
-          {
-            float p0 = 0.f, p1 = 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-              const float sv = S[(r0 + k) * NCOL + col];
-              p0 = fmaf(tt[k], sv, p0);
-              p1 = fmaf(tt[k], tt[k], p1);
-            }
-            red2[0] = (double)p0; red2[1] = (double)p1;
-          }
-          cluster_sum<2, NW>(cluster, red2, wpart, slots, bcast, round, C);
-          omega = (red2[1] > 0.0) ? red2[0] / red2[1] : 0.0;
-          const float of = (float)omega;
-          // x += alpha p + omega s ;  r = s - omega t
-          double red3[2];
-          {
-            float p0 = 0.f, p1 = 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-              const int idx = (r0 + k) * NCOL + col;
-              const float sv = S[idx];
-              x[k] += af * P[idx] + of * sv;
-              rr[k] = fmaf(-of, tt[k], sv);
-              p0 = fmaf(RH[idx], rr[k], p0);
-              p1 = fmaf(rr[k], rr[k], p1);
-            }
-            red3[0] = (double)p0; red3[1] = (double)p1;
-          }
-          cluster_sum<2, NW>(cluster, red3, wpart, slots, bcast, round, C);
-          if (red3[1] <= stop2) { conv = true; break; }
-          if (omega == 0.0 || rho == 0.0) { failed = true; break; }
-          const double beta = (red3[0] / rho) * (alpha / omega);
-          rho = red3[0];
-          const float bf = (float)beta;
+          scaled_matvec<CFG>(S, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, tt);
+          float p2[2] = {0.f, 0.f};
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const int idx = (r0 + k) * NCOL + col;
-            P[idx] = rr[k] + bf * (P[idx] - of * vv[k]);
+            const float sv = S[(r0 + k + 1) * NCOL + col];
+            p2[0] = fmaf(tt[k], sv, p2[0]);
+            p2[1] = fmaf(tt[k], tt[k], p2[1]);
           }
-          if (C > 1) cluster.sync(); else __syncthreads();
-        }
-        if (!conv) failed = true;
-        iters_max = it > iters_max ? it : iters_max;
-        // u^{m+1} = w + d (x = 0 off the PDE rows, whose values already hold g(tau_new))
+          cluster_sum<CFG, 2>(cluster, p2, wpart, slots, sc, round, rank, C, [](Scal* s) {
+            s->omega = s->tot[1] > 0.0 ? s->tot[0] / s->tot[1] : 0.0;
+            s->of = (float)s->omega;
+          });
+          const float of = sc->of;
+          // x += alpha p + omega s ;  r = s - omega t
+          float p3[2] = {0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < K; ++k) u[(r0 + k) * NCOL + col] += x[k];
-        if (C > 1) cluster.sync(); else __syncthreads();
+          for (int k = 0; k < K; ++k) {
+            const int idx = (r0 + k + 1) * NCOL + col;
+            const float sv = S[idx];
+            x[k] += af * P[idx] + of * sv;
+            rr[k] = fmaf(-of, tt[k], sv);
+            p3[0] = fmaf(RH[idx], rr[k], p3[0]);
+            p3[1] = fmaf(rr[k], rr[k], p3[1]);
+          }
+          cluster_sum<CFG, 2>(cluster, p3, wpart, slots, sc, round, rank, C, [](Scal* s) {
+            if (s->tot[1] <= s->stop2) { s->conv = 1; return; }
+            if (s->omega == 0.0 || s->rho == 0.0) { s->fail = 1; return; }
+            const double beta = (s->tot[0] / s->rho) * (s->alpha / s->omega);
+            s->rho = s->tot[0];
+            s->bf = (float)beta;
+          });
+          if (sc->conv || sc->fail) break;
+          const float bf = sc->bf;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int idx = (r0 + k + 1) * NCOL + col;
+            band_store<CFG>(P, pP, r0 + k, col, rr[k] + bf * (P[idx] - of * vv[k]));
+          }
+          cluster_barrier(cluster, C);
+        }
+        if (!sc->conv) failed = true;
+        iters_max = it > iters_max ? it : iters_max;
+        // u^{m+1} = w + d (d = 0 off the PDE rows, whose values already hold g(tau_new))
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int idx = (r0 + k + 1) * NCOL + col;
+          band_store<CFG>(u, pu, r0 + k, col, u[idx] + x[k]);
+        }
+        cluster_barrier(cluster, C);
       }
     }
 
@@ -335,7 +303,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_band_kernel(const __grid_constant
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const int j = jbase + r0 + k;
-          if (j < M) a.out[(size_t)j * M + col] = u[(r0 + k) * NCOL + col];
+          if (j < M) a.out[(size_t)j * M + col] = u[(r0 + k + 1) * NCOL + col];
         }
       }
     } else if (a.mode == SWEEP_INIT) {
@@ -347,41 +315,45 @@ __global__ void __launch_bounds__(NT, 1) sweep_band_kernel(const __grid_constant
         for (int k = 0; k < K; ++k) {
           const int j = jbase + r0 + k;
           if (j < M) {
-            const float g = u[(r0 + k) * NCOL + col];
+            const float g = u[(r0 + k + 1) * NCOL + col];
             Un[(size_t)j * M + col] = g;
             Gn[(size_t)j * M + col] = g;
-            nr[0] += (double)g * (double)g;
+            nr[0] = fma((double)g, (double)g, nr[0]);
           }
         }
       }
-      cluster_sum<1, NW>(cluster, nr, wpart, slots, bcast, round, C);
-      if (rank == 0 && tid == 0) { a.norms[2 * (n + 1)] = nr[0]; a.norms[2 * (n + 1) + 1] = 0.0; }
+      double* norms = a.norms;
+      const int slot_n = n + 1;
+      cluster_sum<CFG, 1>(cluster, nr, wpart, slots, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
+        if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = 0.0; }
+      });
     } else {
       // correction u_{n+1} = F_n + (G_new - G_old_n) and defect partials
       double nr[2] = {0.0, 0.0};
-      if (col < M) {
-        float* Un = a.U + (size_t)(n + 1) * MM;
-        const float* Fn = a.Fb + (size_t)n * MM;
-        float* Gn = a.Gold + (size_t)n * MM;
+      float* Un = a.U + (size_t)(n + 1) * MM;
+      const float* Fn = a.Fb + (size_t)n * MM;
+      float* Gn = a.Gold + (size_t)n * MM;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const int r = r0 + k, j = jbase + r;
-          if (j < M) {
-            const size_t gi = (size_t)j * M + col;
-            const float gnew = u[r * NCOL + col];
-            const float unew = Fn[gi] + (gnew - Gn[gi]);
-            const float uold = Un[gi];
-            Un[gi] = unew;
-            Gn[gi] = gnew;
-            u[r * NCOL + col] = unew;
-            const double du = (double)unew - (double)uold;
-            nr[0] += (double)unew * (double)unew;
-            nr[1] += du * du;
-          }
+      for (int k = 0; k < K; ++k) {
+        const int j = jbase + r0 + k;
+        if (col < M && j < M) {
+          const size_t gi = (size_t)j * M + col;
+          const float gnew = u[(r0 + k + 1) * NCOL + col];
+          const float unew = Fn[gi] + (gnew - Gn[gi]);
+          const float uold = Un[gi];
+          Un[gi] = unew;
+          Gn[gi] = gnew;
+          band_store<CFG>(u, pu, r0 + k, col, unew);
+          const double du = (double)unew - (double)uold;
+          nr[0] = fma((double)unew, (double)unew, nr[0]);
+          nr[1] = fma(du, du, nr[1]);
         }
       }
-      cluster_sum<2, NW>(cluster, nr, wpart, slots, bcast, round, C);
-      if (rank == 0 && tid == 0) { a.norms[2 * (n + 1)] = nr[0]; a.norms[2 * (n + 1) + 1] = nr[1]; }
+      double* norms = a.norms;
+      const int slot_n = n + 1;
+      cluster_sum<CFG, 2>(cluster, nr, wpart, slots, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
+        if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = s->tot[1]; }
+      });
     }
   }
 
@@ -399,17 +371,17 @@ __global__ void __launch_bounds__(NT, 1) sweep_band_kernel(const __grid_constant
   }
 }
 
-template <int NCOL, int NT, int K>
-static int launch_sweep_k(const bs_grid* g, const SweepParams& sp, cudaStream_t s) {
-  using CB = CBand<NCOL, NT, K>;
-  const size_t smem = (size_t)5 * CB::BH * NCOL * sizeof(float) + (size_t)CB::BH * sizeof(float2) +
-                      (CB::NW * 4 + 8 + 4) * sizeof(double);
-  auto kern = sweep_band_kernel<NCOL, NT, K>;
+template <class CFG>
+static int launch_sweep_k(const SweepParams& sp, cudaStream_t s) {
+  const size_t smem = (size_t)4 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
+                      (size_t)CFG::BH * sizeof(float2) +
+                      (CFG::NW * 4 + 2 * kMaxCluster * 4) * sizeof(double) + sizeof(Scal);
+  auto kern = sweep_band_kernel<CFG>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (sp.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sp.sh.C, 1, 1);
-  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.blockDim = dim3(CFG::NT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -432,10 +404,10 @@ int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaSt
   if (sp.sh.C < 1 || sp.sh.C > kMaxCluster)
     return set_error(BS_ERR_ARG, "coarse propagator: grid M=%d not supported", g->M);
   switch (sp.sh.ncol) {
-    case 32: return launch_sweep_k<32, 256, 4>(g, sp, s);
-    case 64: return launch_sweep_k<64, 512, 8>(g, sp, s);
-    case 128: return launch_sweep_k<128, 512, 16>(g, sp, s);
-    case 256: return launch_sweep_k<256, 512, 16>(g, sp, s);
+    case 32: return launch_sweep_k<BandCfg<32, 256, 4>>(sp, s);
+    case 64: return launch_sweep_k<BandCfg<64, 512, 8>>(sp, s);
+    case 128: return launch_sweep_k<BandCfg<128, 512, 16>>(sp, s);
+    case 256: return launch_sweep_k<BandCfg<256, 512, 16>>(sp, s);
   }
   return set_error(BS_ERR_ARG, "coarse propagator: no band shape for M=%d", g->M);
 }

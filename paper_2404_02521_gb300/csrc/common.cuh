@@ -29,7 +29,9 @@ struct ItemDesc {
   double s1, s2, rho, r;
   double K, w1, w2, K2, cash;
   int payoff;
-  int sweeps;     // Jacobi sweeps per implicit step (fine) / unused (coarse)
+  int sweeps;     // fine: Jacobi sweeps per warm-started implicit step (unused by coarse)
+  int sweeps0;    // fine: Jacobi sweeps of the first step of a launch (cold start)
+  int pad;
 };
 
 // Band decomposition of an M x M slice over a cluster of C CTAs: each CTA owns BH = G*K
@@ -171,8 +173,18 @@ int cuda_error(cudaError_t e, const char* what);
 ItemDesc make_item(const bs_params& p, double tau0, double dtau);
 int check_params(const bs_params* p);
 double jacobi_contraction(int M, const bs_params& p, double dtau);
-int sweeps_for(double q);
+int sweeps_for(double q, bool cold);
 BandShape band_shape(int M);
+
+struct Options {
+  int fine_sweeps = 0;
+  double jacobi_target = 1.0 / 1024.0;            // warm-started steps: q^m <= 2^-10
+  double jacobi_target_cold = 1.0 / 4194304.0;    // first step of a launch: q^m <= 2^-22
+  double krylov_tol = 1e-6;
+  int krylov_maxit = 400;
+  int phase_timing = 0;
+};
+extern Options g_opt;
 
 struct Workspace {
   void* ptr = nullptr;
@@ -187,13 +199,16 @@ struct bs_grid {
   double xmax;
   int device;
   bsp::BandShape shape;
-  int* status;                 // device: bit 0 = Krylov cap hit
+  int* status;                 // device: [0] bit 0 = Krylov cap hit, [1] max iterations
   double* dscal;               // device: scalar outputs (defect)
   double* dnorms;              // device: per-slice squared norms / defects
   bsp::Workspace ws_par;       // Parareal F / Gold buffers
   // cached contraction
   double q_key[6];
   double q_val;
+  // phase accounting (bs_phase_stats)
+  double ms_fine = 0.0, ms_coarse = 0.0;
+  int n_fine = 0, n_coarse = 0, n_other = 0;
 };
 
 // Kernel launchers implemented in the .cu files.

@@ -1,10 +1,8 @@
 // K1: fine propagator F (Sec. 3.1) -- implicit Euler steps of eq. (fd), batched over
 // independent states (time slices and requests), one thread-block cluster per state.
 //
-// Each cluster keeps its whole M x M state on chip for all nsteps: CTA `rank` owns a band
-// of BH rows (all ncol >= M columns) in shared memory, and the halo rows above and below
-// the band are read from the neighbouring CTAs' shared memory (DSMEM) after a cluster
-// barrier.  HBM is touched once to load the state and once to store it.
+// Each cluster keeps its whole M x M state on chip for all nsteps (band layout of
+// band.cuh): HBM is touched once to load the state and once to store it.
 //
 // Per implicit step  (I - dtau R_h) u^{m+1} = u^m  the increment  d = u^{m+1} - u^m  solves
 //   (I - dtau R_h) d = dtau R_h w,   w = u^m inside, g(tau^{m+1}) on the far edges,
@@ -12,16 +10,13 @@
 //   d <- (b + sum_k c_k d_k) / (1 + sum_k c_k + r dtau),   b = dtau R_h w,
 // started from the previous step's increment.  The Gershgorin bound q < 1 of the system
 // (checked on the host) makes every sweep a max-norm contraction by q; the sweep count is
-// chosen so that q^sweeps <= 2^-22.  The state is a compensated pair (hi, lo): u = hi + lo,
-// updated by an error-free two-sum, so that increments below half an ulp of u are not lost
-// over tens of thousands of steps; b is evaluated from hi.
-#include <cooperative_groups.h>
-
+// chosen so that q^sweeps is below a target (2^-22 for the first, cold-started step of a
+// launch, 2^-10 for the warm-started steps after it).  The state is a compensated
+// pair (hi, lo): u = hi + lo, updated by an error-free two-sum, so that increments below half
+// an ulp of u are not lost over tens of thousands of steps; b is evaluated from hi.
 #include <cstdio>
 
-#include "common.cuh"
-
-namespace cg = cooperative_groups;
+#include "band.cuh"
 
 namespace bsp {
 
@@ -33,107 +28,134 @@ struct FineBatch {
   float h;
 };
 
-// Shape of the band kernel: NT threads, NCOL (>= M) columns, each thread owns one column
-// and K consecutive rows of the band, G = NT / NCOL row groups, band height BH = G * K.
-template <int NCOL, int NT, int K>
-struct BandCfg {
-  static constexpr int G = NT / NCOL;
-  static constexpr int BH = G * K;
-};
-
-// Far-field values at tau for the band's Dirichlet nodes (column M-1 and, in the last band,
-// row M-1), written into hi.  One evaluation per thread.
-template <int NCOL, int NT, int BH>
-__device__ __forceinline__ void set_far_field(float* hi, const PayoffF& pf, float tau, float h,
-                                              int M, int jbase, int tid) {
-  const bool has_last_row = (jbase <= M - 1) && (M - 1 < jbase + BH);
-  const int n_entries = BH + (has_last_row ? (M - 1) : 0);
-  for (int e = tid; e < n_entries; e += NT) {
-    int r, c;
-    if (e < BH) {
-      r = e;
-      c = M - 1;
-      if (jbase + r > M - 1) continue;
-    } else {
-      r = M - 1 - jbase;
-      c = e - BH;
-    }
-    hi[r * NCOL + c] = far_field(pf, c * h, (jbase + r) * h, tau);
-  }
+__device__ __forceinline__ void cl_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cl_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-// One Jacobi sweep over the thread's column strip.  The thread's own column of the old
-// increment is in dv[] (registers); west/east columns and the rows just outside the strip
-// come from shared memory (rows outside the band from the neighbouring CTAs).  FIRST also
-// evaluates b = dtau R_h w from hi; LAST also applies the increment to (hi, lo).
-// Non-interior nodes have invd = 0, so they write a zero increment without a branch.
-template <int NCOL, int K, bool FIRST, bool LAST>
+// b = dtau R_h w at one node from the 3x3 neighbourhood of hi (eq. fd in index units).
+__device__ __forceinline__ float rhs_point(float ce, float cw, float cs, float cn, float cg, float rdt,
+                                           float nW, float nC, float nE, float cW, float cC,
+                                           float cE, float sW, float sC, float sE) {
+  return ce * (cE - cC) - cw * (cC - cW) + cs * (sC - cC) - cn * (cC - nC) +
+         cg * ((sE - nE) - (sW - nW)) - rdt * cC;
+}
+
+// Jacobi update of one node from the old increments around it.
+__device__ __forceinline__ float jacobi_point(float b, float invd, float ce, float cw, float cs,
+                                              float cn, float cg, float nW, float nC, float nE,
+                                              float cW, float cE, float sW, float sC, float sE) {
+  const float t1 = fmaf(ce, cE, fmaf(cw, cW, b));
+  const float t2 = fmaf(cs, sC, cn * nC);
+  const float t3 = cg * ((sE - nE) - (sW - nW));
+  return ((t1 + t2) + t3) * invd;
+}
+
+// Compensated update (hi, lo) += v: error-free two-sum, then renormalise.
+__device__ __forceinline__ float two_sum_update(float h0, float v, float& lo) {
+  const float s = h0 + v;
+  const float bb = s - h0;
+  const float err = (h0 - (s - bb)) + (v - bb);
+  const float l = lo + err;
+  const float hn = s + l;
+  lo = l - (hn - s);
+  return hn;
+}
+
+// One Jacobi sweep over the thread's column strip (own band rows r0..r0+K-1, plane rows
+// r0+1..r0+K).  Strip rows 1..K-2 read only rows of the strip itself, written by this CTA
+// in the previous sweep; they are updated before the cluster wait.  The two end rows read
+// the rows just outside the strip (other row groups or the halo copies of the neighbouring
+// CTAs) and are updated after it, so the barrier latency overlaps the interior work.
+// The thread's own column of the old increment is in dv[].  FIRST also evaluates
+// b = dtau R_h w from hi; LAST also applies the increment to (hi, lo).  Nodes that are not
+// PDE rows have invd = 0 and write a zero increment.
+template <class CFG, bool FIRST, bool LAST>
 __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* __restrict__ wr,
-                                           const float* upr, const float* dnr, float* hi,
-                                           const float* hup, const float* hdn,
-                                           const float2* __restrict__ rowc, float (&dv)[K],
-                                           float (&b)[K], const float (&invd)[K], float (&lo)[K],
+                                           float* hi, const HaloPush& wr_push,
+                                           const HaloPush& hi_push, const float2* __restrict__ rowc,
+                                           float (&dv)[CFG::K], float (&b)[CFG::K],
+                                           const float (&invd)[CFG::K], float (&lo)[CFG::K],
                                            int col, int il, int ir, int r0, float ce, float cw,
-                                           float cg0, float cgi, float rdt) {
-  // rows r0-1 and r0+K (halo of the strip)
-  float nW = upr[il], nC = upr[col], nE = upr[ir];
-  const float sDW = dnr[il], sDC = dnr[col], sDE = dnr[ir];
-  float cW = rd[r0 * NCOL + il], cE = rd[r0 * NCOL + ir];
+                                           float cg0, float cgi, float rdt, bool clustered) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K;
+  static_assert(K >= 4, "strip needs interior rows");
+  const int p0 = r0 + 1;
+  // rows 0 and 1 of the strip
+  const float r0W = rd[p0 * NCOL + il], r0E = rd[p0 * NCOL + ir];
+  const float r1W = rd[(p0 + 1) * NCOL + il], r1E = rd[(p0 + 1) * NCOL + ir];
+  const float dv1_old = dv[1];
+  float nW = r0W, nC = dv[0], nE = r0E;
+  float cW = r1W, cE = r1E;
+  float h0W = 0.f, h0C = 0.f, h0E = 0.f, h1W = 0.f, h1C = 0.f, h1E = 0.f;
   float hnW = 0.f, hnC = 0.f, hnE = 0.f, hcW = 0.f, hcC = 0.f, hcE = 0.f;
-  float hsDW = 0.f, hsDC = 0.f, hsDE = 0.f;
   if (FIRST) {
-    hnW = hup[il]; hnC = hup[col]; hnE = hup[ir];
-    hcW = hi[r0 * NCOL + il]; hcC = hi[r0 * NCOL + col]; hcE = hi[r0 * NCOL + ir];
-    hsDW = hdn[il]; hsDC = hdn[col]; hsDE = hdn[ir];
+    h0W = hi[p0 * NCOL + il]; h0C = hi[p0 * NCOL + col]; h0E = hi[p0 * NCOL + ir];
+    h1W = hi[(p0 + 1) * NCOL + il]; h1C = hi[(p0 + 1) * NCOL + col]; h1E = hi[(p0 + 1) * NCOL + ir];
+    hnW = h0W; hnC = h0C; hnE = h0E;
+    hcW = h1W; hcC = h1C; hcE = h1E;
   }
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int r = r0 + k;
-    float sW, sC, sE;
-    if (k < K - 1) {
-      sW = rd[(r + 1) * NCOL + il];
-      sE = rd[(r + 1) * NCOL + ir];
-      sC = dv[k + 1];
-    } else {
-      sW = sDW; sC = sDC; sE = sDE;
-    }
-    const float2 rc = rowc[r];
+  for (int k = 1; k <= K - 2; ++k) {
+    const int p = p0 + k;
+    const float sW = rd[(p + 1) * NCOL + il], sE = rd[(p + 1) * NCOL + ir];
+    const float sC = dv[k + 1];
+    const float2 rc = rowc[p - 1];
     const float cg = fmaf((float)k, cgi, cg0);
     if (FIRST) {
-      float hsW, hsC, hsE;
-      if (k < K - 1) {
-        hsW = hi[(r + 1) * NCOL + il]; hsC = hi[(r + 1) * NCOL + col]; hsE = hi[(r + 1) * NCOL + ir];
-      } else {
-        hsW = hsDW; hsC = hsDC; hsE = hsDE;
-      }
-      b[k] = ce * (hcE - hcC) - cw * (hcC - hcW) + rc.x * (hsC - hcC) - rc.y * (hcC - hnC) +
-             cg * ((hsE - hnE) - (hsW - hnW)) - rdt * hcC;
+      const float hsW = hi[(p + 1) * NCOL + il], hsC = hi[(p + 1) * NCOL + col],
+                  hsE = hi[(p + 1) * NCOL + ir];
+      b[k] = rhs_point(ce, cw, rc.x, rc.y, cg, rdt, hnW, hnC, hnE, hcW, hcC, hcE, hsW, hsC, hsE);
       hnW = hcW; hnC = hcC; hnE = hcE;
       hcW = hsW; hcC = hsC; hcE = hsE;
     }
-    const float v = (b[k] + ce * cE + cw * cW + rc.x * sC + rc.y * nC + cg * ((sE - nE) - (sW - nW))) * invd[k];
-    wr[r * NCOL + col] = v;
+    const float v = jacobi_point(b[k], invd[k], ce, cw, rc.x, rc.y, cg, nW, nC, nE, cW, cE, sW, sC, sE);
+    wr[p * NCOL + col] = v;
     nC = dv[k];
     dv[k] = v;
     nW = cW; nE = cE;
     cW = sW; cE = sE;
-    if (LAST) {
-      const float h0 = hi[r * NCOL + col];
-      const float s = h0 + v;
-      const float bb = s - h0;
-      const float err = (h0 - (s - bb)) + (v - bb);
-      const float l = lo[k] + err;
-      const float hn = s + l;
-      lo[k] = l - (hn - s);
-      hi[r * NCOL + col] = hn;
+    if (LAST) hi[p * NCOL + col] = two_sum_update(hi[p * NCOL + col], v, lo[k]);
+  }
+  if (clustered) cl_wait();
+  {  // last strip row: north = old row K-2 (window), south = plane row p0+K
+    const int k = K - 1, p = p0 + k;
+    const float sW = rd[(p + 1) * NCOL + il], sC = rd[(p + 1) * NCOL + col], sE = rd[(p + 1) * NCOL + ir];
+    const float2 rc = rowc[p - 1];
+    const float cg = fmaf((float)k, cgi, cg0);
+    if (FIRST) {
+      const float hsW = hi[(p + 1) * NCOL + il], hsC = hi[(p + 1) * NCOL + col],
+                  hsE = hi[(p + 1) * NCOL + ir];
+      b[k] = rhs_point(ce, cw, rc.x, rc.y, cg, rdt, hnW, hnC, hnE, hcW, hcC, hcE, hsW, hsC, hsE);
     }
+    const float v = jacobi_point(b[k], invd[k], ce, cw, rc.x, rc.y, cg, nW, nC, nE, cW, cE, sW, sC, sE);
+    band_store<CFG>(wr, wr_push, p - 1, col, v);
+    dv[k] = v;
+    if (LAST) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[k]));
+  }
+  {  // first strip row: north = plane row p0-1, south = old row 1
+    const int p = p0;
+    const float qW = rd[(p - 1) * NCOL + il], qC = rd[(p - 1) * NCOL + col], qE = rd[(p - 1) * NCOL + ir];
+    const float2 rc = rowc[p - 1];
+    const float cg = cg0;
+    if (FIRST) {
+      const float hqW = hi[(p - 1) * NCOL + il], hqC = hi[(p - 1) * NCOL + col],
+                  hqE = hi[(p - 1) * NCOL + ir];
+      b[0] = rhs_point(ce, cw, rc.x, rc.y, cg, rdt, hqW, hqC, hqE, h0W, h0C, h0E, h1W, h1C, h1E);
+    }
+    const float v = jacobi_point(b[0], invd[0], ce, cw, rc.x, rc.y, cg, qW, qC, qE, r0W, r0E, r1W,
+                                 dv1_old, r1E);
+    band_store<CFG>(wr, wr_push, p - 1, col, v);
+    dv[0] = v;
+    if (LAST) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[0]));
   }
 }
 
-template <int NCOL, int NT, int K>
-__global__ void __launch_bounds__(NT, 1) fine_band_kernel(const __grid_constant__ FineBatch fb) {
-  constexpr int G = BandCfg<NCOL, NT, K>::G;
-  constexpr int BH = BandCfg<NCOL, NT, K>::BH;
+template <class CFG>
+__global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_constant__ FineBatch fb) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, PLANE = CFG::PLANE;
   cg::cluster_group cluster = cg::this_cluster();
   const ItemDesc& d = fb.it[blockIdx.y];
   const int M = fb.sh.M, C = fb.sh.C;
@@ -147,44 +169,25 @@ __global__ void __launch_bounds__(NT, 1) fine_band_kernel(const __grid_constant_
 
   extern __shared__ __align__(16) float smem[];
   float* hi = smem;
-  float* dA = hi + BH * NCOL;
-  float* dB = dA + BH * NCOL;
-  float2* rowc = reinterpret_cast<float2*>(dB + BH * NCOL);
+  float* dA = hi + PLANE;
+  float* dB = dA + PLANE;
+  float2* rowc = reinterpret_cast<float2*>(dB + PLANE);
 
-  for (int e = tid; e < BH * NCOL; e += NT) {
-    const int r = e / NCOL, c = e % NCOL;
-    const int j = jbase + r;
-    hi[e] = (j < M && c < M) ? d.in[(size_t)j * M + c] : 0.f;
+  band_load<CFG>(hi, d.in, M, jbase, tid);
+  for (int e = tid; e < PLANE; e += CFG::NT) {
     dA[e] = 0.f;
     dB[e] = 0.f;
   }
-  for (int r = tid; r < BH; r += NT) {
+  for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
     row_coefs(d, jbase + r, cs, cn, gj);
     rowc[r] = make_float2(cs, cn);
   }
-  if (fb.nsteps > 0) {
-    __syncthreads();
-    set_far_field<NCOL, NT, BH>(hi, pf, (float)(d.tau0 + d.dtau), h, M, jbase, tid);
-  }
-
-  // halo-row sources: rows r0-1 and r0+K of each buffer (clamped at the domain edges, where
-  // the coefficients that would use them vanish or the node is not a PDE row)
-  const bool has_prev = rank > 0, has_next = rank < C - 1;
-  auto up_row = [&](float* buf) -> const float* {
-    if (grp > 0) return buf + (r0 - 1) * NCOL;
-    return has_prev ? cluster.map_shared_rank(buf, rank - 1) + (BH - 1) * NCOL : buf;
-  };
-  auto dn_row = [&](float* buf) -> const float* {
-    if (grp < G - 1) return buf + (r0 + K) * NCOL;
-    return has_next ? cluster.map_shared_rank(buf, rank + 1) : buf + (BH - 1) * NCOL;
-  };
-  const float* upA = up_row(dA);
-  const float* dnA = dn_row(dA);
-  const float* upB = up_row(dB);
-  const float* dnB = dn_row(dB);
-  const float* hup = up_row(hi);
-  const float* hdn = dn_row(hi);
+  const HaloPush hi_push = halo_push<CFG>(cluster, hi, rank, C);
+  const HaloPush pA = halo_push<CFG>(cluster, dA, rank, C);
+  const HaloPush pB = halo_push<CFG>(cluster, dB, rank, C);
+  cluster_barrier(cluster, C);   // neighbours' loads done before far-field mirrors land
+  if (fb.nsteps > 0) band_far_field<CFG>(hi, hi_push, pf, (float)(d.tau0 + d.dtau), h, M, jbase, tid);
 
   float ce = 0.f, cw = 0.f, cgi = 0.f;
   column_coefs(d, col, ce, cw, cgi);
@@ -201,53 +204,57 @@ __global__ void __launch_bounds__(NT, 1) fine_band_kernel(const __grid_constant_
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
   const float rdt = (float)(d.r * d.dtau);
-  const int m = d.sweeps;
-  if (C > 1) cluster.sync(); else __syncthreads();
+  cluster_barrier(cluster, C);
 
+  // Split cluster barrier: each sweep arrives after its writes and waits (inside the sweep)
+  // only before the rows that read other CTAs' data; one arrive here opens the first phase.
+  const bool clustered = C > 1;
+  if (clustered) cl_arrive();
   int par = 0;
   for (int step = 0; step < fb.nsteps; ++step) {
+    const int m = step == 0 ? d.sweeps0 : d.sweeps;   // the first step starts cold
     for (int s = 0; s < m; ++s) {
       const float* rd = par ? dB : dA;
       float* wr = par ? dA : dB;
-      const float* upr = par ? upB : upA;
-      const float* dnr = par ? dnB : dnA;
+      const HaloPush& wp = par ? pA : pB;
       if (s == 0)
-        fine_sweep<NCOL, K, true, false>(rd, wr, upr, dnr, hi, hup, hdn, rowc, dv, b, invd, lo, col,
-                                         il, ir, r0, ce, cw, cg0, cgi, rdt);
+        fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0,
+                                     ce, cw, cg0, cgi, rdt, clustered);
       else if (s == m - 1)
-        fine_sweep<NCOL, K, false, true>(rd, wr, upr, dnr, hi, hup, hdn, rowc, dv, b, invd, lo, col,
-                                         il, ir, r0, ce, cw, cg0, cgi, rdt);
+        fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0,
+                                     ce, cw, cg0, cgi, rdt, clustered);
       else
-        fine_sweep<NCOL, K, false, false>(rd, wr, upr, dnr, hi, hup, hdn, rowc, dv, b, invd, lo,
-                                          col, il, ir, r0, ce, cw, cg0, cgi, rdt);
+        fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir,
+                                      r0, ce, cw, cg0, cgi, rdt, clustered);
       // After the first sweep has read hi, move the far-field data to the next step (the
       // last sweep, at least one barrier later, leaves those nodes unchanged).
       if (s == 1 && step + 1 < fb.nsteps)
-        set_far_field<NCOL, NT, BH>(hi, pf, (float)(d.tau0 + (step + 2) * d.dtau), h, M, jbase, tid);
+        band_far_field<CFG>(hi, hi_push, pf, (float)(d.tau0 + (step + 2) * d.dtau), h, M, jbase, tid);
       par ^= 1;
-      if (C > 1) cluster.sync(); else __syncthreads();
+      if (clustered) cl_arrive();
+      __syncthreads();
     }
   }
+  if (clustered) cl_wait();   // no CTA leaves while a neighbour may still store into it
 
   if (col < M) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int j = jbase + r0 + k;
-      if (j < M) d.out[(size_t)j * M + col] = hi[(r0 + k) * NCOL + col] + lo[k];
+      if (j < M) d.out[(size_t)j * M + col] = hi[(r0 + k + 1) * NCOL + col] + lo[k];
     }
   }
 }
 
-template <int NCOL, int NT, int K>
-static int launch_band(const bs_grid* g, const FineBatch& fb, cudaStream_t s) {
-  constexpr int BH = BandCfg<NCOL, NT, K>::BH;
-  const size_t smem = (size_t)3 * BH * NCOL * sizeof(float) + (size_t)BH * sizeof(float2);
-  auto kern = fine_band_kernel<NCOL, NT, K>;
+template <class CFG>
+static int launch_band(const FineBatch& fb, cudaStream_t s) {
+  const size_t smem = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * sizeof(float2);
+  auto kern = fine_band_kernel<CFG>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (fb.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(fb.sh.C, fb.n, 1);
-  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.blockDim = dim3(CFG::NT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -275,10 +282,10 @@ int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cuda
     fb.h = (float)(g->xmax / (g->M - 1));
     int rc;
     switch (sh.ncol) {
-      case 32: rc = launch_band<32, 256, 4>(g, fb, s); break;
-      case 64: rc = launch_band<64, 512, 8>(g, fb, s); break;
-      case 128: rc = launch_band<128, 512, 16>(g, fb, s); break;
-      case 256: rc = launch_band<256, 512, 16>(g, fb, s); break;
+      case 32: rc = launch_band<BandCfg<32, 256, 4>>(fb, s); break;
+      case 64: rc = launch_band<BandCfg<64, 512, 8>>(fb, s); break;
+      case 128: rc = launch_band<BandCfg<128, 512, 16>>(fb, s); break;
+      case 256: rc = launch_band<BandCfg<256, 512, 16>>(fb, s); break;
       default: rc = set_error(BS_ERR_ARG, "fine_propagate_batched: no band shape for M=%d", g->M);
     }
     if (rc != BS_OK) return rc;

@@ -8,7 +8,6 @@ Calls only oracle/ (and the seeded workload description).  Run from the reposito
 Takes about 12 minutes per rho on one CPU core.
 """
 import json
-import multiprocessing as mp
 import os
 import sys
 import time
@@ -57,6 +56,5 @@ def run(rho):
 
 if __name__ == "__main__":
     rhos = [float(a) for a in sys.argv[1:]] or list(wl.EXCHANGE_RHOS)
-    with mp.get_context("spawn").Pool(len(rhos)) as pool:
-        for p in pool.map(run, rhos):
-            print(p)
+    for rho in rhos:
+        print(run(rho), flush=True)
