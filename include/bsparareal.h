@@ -177,6 +177,28 @@ int bs_grid_stats(bs_grid* g, int* krylov_iters_max, int* krylov_failed);
 int bs_phase_stats(bs_grid* g, double* fine_ms, int* fine_launches, double* coarse_ms,
                    int* coarse_launches, int* other_launches);
 
+/* Parareal with the numerical coarse model, for callers that cannot allocate device memory:
+ * code on a latency-critical pricing path where a device allocation (which may synchronise
+ * the whole device and take milliseconds) is not allowed, or code embedded in a host
+ * framework that owns all device memory through its own allocator.  The paper has no
+ * counterpart to this entry point; it computes what parareal_solve computes with
+ * coarse_kind = BS_COARSE_NUM (same kernels, same results), but takes the grid as M and xmax
+ * instead of a bs_grid handle and keeps its scratch (fine and coarse slice buffers, norms,
+ * status) in one fixed device array inside the library: about 32 MiB, held by every GPU that
+ * loads the library until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *  - Capacity: N * M * M <= 4,194,304 and N <= 1024 (for example N = 64 slices of 256 x 256);
+ *    larger problems return BS_ERR_ARG with a message naming the limit.
+ *  - The caller still owns u_out (device float[(N+1)*M*M]); k_done and defect_hist as in
+ *    parareal_solve.  Synchronous, same return codes as parareal_solve.
+ *  - The first call on a device looks up the array's device address (which may also load the
+ *    library's device code); make that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (two host threads, or two
+ *    streams) race and must be serialised by the caller. */
+int parareal_solve_noalloc(int M, double xmax, const bs_params* p, int N, int fine_steps,
+                           int coarse_steps, double tol, int Kmax, float* u_out, int* k_done,
+                           double* defect_hist, bs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,11 +8,13 @@ from ._lib import (BASKET, CALL1, CASH_OR_NOTHING, COARSE_NUM, COARSE_PINO, EXCH
                    BSError, Grid, Pino, bs_fine_sweeps, bs_grid_stats, bs_payoff, bs_phase_stats, bs_set_option,
                    OPT_PHASE_TIMING, PARAREAL_USER_U0,
                    OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_MAXIT, OPT_KRYLOV_TOL, coarse_propagate,
-                   fine_propagate_batched, last_error, load, parareal_solve, to_params)
+                   fine_propagate_batched, last_error, load, parareal_solve, parareal_solve_noalloc,
+                   to_params)
 
 __all__ = ["BASKET", "CALL1", "CASH_OR_NOTHING", "COARSE_NUM", "COARSE_PINO", "EXCHANGE",
            "EXPORTS", "BSError", "Grid", "Pino", "bs_fine_sweeps", "bs_grid_stats", "bs_payoff", "bs_phase_stats",
            "OPT_PHASE_TIMING", "PARAREAL_USER_U0",
            "bs_set_option", "OPT_FINE_SWEEPS", "OPT_JACOBI_TARGET", "OPT_KRYLOV_MAXIT", "OPT_KRYLOV_TOL",
            "coarse_propagate", "fine_propagate_batched", "last_error", "load", "parareal_solve",
+           "parareal_solve_noalloc",
            "to_params"]

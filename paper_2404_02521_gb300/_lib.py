@@ -22,7 +22,7 @@ COARSE_NUM, COARSE_PINO = 0, 1
 # exported entry points declared in include/bsparareal.h
 EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
-           "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats"]
+           "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
 PARAREAL_USER_U0 = 0x100
@@ -71,6 +71,7 @@ def load(path: Optional[str] = None):
     lib.bs_set_option.argtypes = [i, d]
     lib.bs_grid_stats.argtypes = [vp, P(i), P(i)]
     lib.bs_phase_stats.argtypes = [vp, P(d), P(i), P(d), P(i), P(i)]
+    lib.parareal_solve_noalloc.argtypes = [i, d, P(bs_params), i, i, i, d, i, vp, P(i), P(d), vp]
     for name in EXPORTS:
         if name != "bs_last_error":
             getattr(lib, name).restype = C.c_int
@@ -163,6 +164,20 @@ def parareal_solve(g: Grid, p, N: int, fine_steps: int, coarse_kind: int, coarse
                                int(coarse_steps), net.h if net is not None else None,
                                float(tol), int(Kmax), _ptr(u_out), C.byref(k), hist,
                                _stream(stream))
+    check(rc, allow=(BS_ERR_MAXITER,) if allow_maxiter else ())
+    return rc, k.value, [hist[i] for i in range(k.value)]
+
+
+def parareal_solve_noalloc(M: int, xmax: float, p, N: int, fine_steps: int, coarse_steps: int,
+                           tol: float, Kmax: int, u_out, stream=None, allow_maxiter=True):
+    """parareal_solve without device allocation (scratch in a fixed device array).
+    Returns (status, k_done, defects)."""
+    bp = to_params(p)
+    k = C.c_int(0)
+    hist = (C.c_double * max(1, Kmax))()
+    rc = load().parareal_solve_noalloc(int(M), float(xmax), C.byref(bp), int(N), int(fine_steps),
+                                       int(coarse_steps), float(tol), int(Kmax), _ptr(u_out),
+                                       C.byref(k), hist, _stream(stream))
     check(rc, allow=(BS_ERR_MAXITER,) if allow_maxiter else ())
     return rc, k.value, [hist[i] for i in range(k.value)]
 

@@ -1,0 +1,51 @@
+"""parareal_solve_noalloc: the Parareal entry point for callers that may not allocate device
+memory (a latency-critical pricing path, or a host framework that owns all device memory).
+Its scratch is a fixed device array inside the library, shared by every call, so this test
+makes two calls in a row and checks each against parareal_solve, which allocates its own
+workspace.  The file is named so that pytest collects it last."""
+import ctypes as C
+
+import pytest
+
+import workloads as wl
+from tests.gpu_util import FP32_FINE_TOL, rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bs():
+    import paper_2404_02521_gb300 as bs
+    bs.load()
+    return bs
+
+
+def test_noalloc_matches_parareal_solve_on_two_calls(bs):
+    import torch
+    problems = [wl.Problem("basket64", 64, 4.0, 8, 64, 4, wl.basket_cfg1().params),
+                wl.Problem("exchange64", 64, 4.0, 8, 64, 4, wl.exchange_cfg2(0.7).params)]
+    for pb in problems:
+        g = bs.Grid(pb.M, pb.xmax)
+        ref = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+        rc0, k0, d0 = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM,
+                                        pb.coarse_steps, None, pb.tol, pb.N, ref)
+        torch.cuda.synchronize()
+        for _ in range(2):
+            out = torch.full_like(ref, float("nan"))
+            rc, k, d = bs.parareal_solve_noalloc(pb.M, pb.xmax, pb.params, pb.N, pb.fine_steps,
+                                                 pb.coarse_steps, pb.tol, pb.N, out)
+            torch.cuda.synchronize()
+            assert rc == rc0 == 0 and k == k0
+            assert rel_err(to_np(out), to_np(ref)) <= FP32_FINE_TOL
+            assert all(abs(a - b) <= 1e-12 + 1e-9 * abs(b) for a, b in zip(d, d0))
+
+
+def test_noalloc_rejects_sizes_beyond_capacity(bs):
+    import torch
+    u = torch.empty(1, device="cuda")
+    p = bs.to_params(wl.exchange_cfg2(0.7).params)
+    k = C.c_int(0)
+    rc = bs.load().parareal_solve_noalloc(512, 4.0, C.byref(p), 64, 512, 4, 1e-4, 64,
+                                          u.data_ptr(), C.byref(k), None, None)
+    assert rc == -1
+    assert "exceeds the fixed scratch capacity" in bs.last_error()
