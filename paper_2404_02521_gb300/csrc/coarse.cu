@@ -73,47 +73,40 @@ __device__ __forceinline__ T warp_butterfly(T x) {
   return x;
 }
 
-// Cluster-wide sum of NV per-thread values of type T.  On return sc->tot holds the FP64
-// totals and `fin(sc)` has been applied once per CTA (by thread 0) before the closing CTA
-// barrier, so every thread may read what fin wrote.  `round` alternates the slot buffers so
-// that a fast CTA never overwrites partials a slow CTA is still reading.
+// Cluster-wide sum of NV per-thread values of type T.  Each warp reduces its values by a
+// butterfly and stores the warp partial into slot (rank, warp) of every CTA of the cluster;
+// after one cluster barrier, warp 0 of every CTA adds the C * NW partials in a fixed order
+// (lane l takes entries l, l+32, ...; then a butterfly), so every CTA gets bitwise the same
+// FP64 totals in sc->tot.  `fin(sc)` then runs once per CTA (thread 0) before the closing
+// CTA barrier.  `round` alternates two slot arrays so that a fast CTA never overwrites
+// partials that a slow CTA is still adding.
 template <class CFG, int NV, class T, class Fin>
-__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, const T (&v)[NV], double* wpart,
-                                            double* slots, Scal* sc, int& round, int rank, int C,
-                                            Fin fin) {
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, const T (&v)[NV], double* slots,
+                                            Scal* sc, int& round, int rank, int C, Fin fin) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* slot = slots + (round & 1) * (kMaxCluster * CFG::NW * 4);
+  T x[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    const T x = warp_butterfly<T>(v[q]);
-    if (lane == 0) wpart[warp * 4 + q] = (double)x;
+  for (int q = 0; q < NV; ++q) x[q] = warp_butterfly<T>(v[q]);
+  if (lane < C) {
+    double* dst = (C > 1 ? cl.map_shared_rank(slot, lane) : slot) + (rank * CFG::NW + warp) * 4;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) dst[q] = (double)x[q];
   }
-  __syncthreads();
-  double* slot = slots + (round & 1) * kMaxCluster * 4;
+  if (C > 1) cl.sync(); else __syncthreads();
   if (warp == 0) {
+    const int n = C * CFG::NW;
     double tot[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q)
-      tot[q] = warp_butterfly<double>(lane < CFG::NW ? wpart[lane * 4 + q] : 0.0);
-    if (C == 1) {
-      if (lane == 0) {
-        for (int q = 0; q < NV; ++q) sc->tot[q] = tot[q];
-        fin(sc);
-      }
-    } else if (lane < C) {
-      double* dst = cl.map_shared_rank(slot, lane) + rank * 4;
-      for (int q = 0; q < NV; ++q) dst[q] = tot[q];
+    for (int q = 0; q < NV; ++q) {
+      double acc = 0.0;
+      for (int i = lane; i < n; i += 32) acc += slot[i * 4 + q];
+      tot[q] = warp_butterfly<double>(acc);
     }
-  }
-  if (C > 1) {
-    cl.sync();
-    if (warp == 0) {
-      double tot[NV];
+    if (lane == 0) {
 #pragma unroll
-      for (int q = 0; q < NV; ++q) tot[q] = warp_butterfly<double>(lane < C ? slot[lane * 4 + q] : 0.0);
-      if (lane == 0) {
-        for (int q = 0; q < NV; ++q) sc->tot[q] = tot[q];
-        fin(sc);
-      }
+      for (int q = 0; q < NV; ++q) sc->tot[q] = tot[q];
+      fin(sc);
     }
   }
   __syncthreads();
@@ -143,9 +136,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   float* RH = S + PLANE;                           // shadow residual r^   [PLANE]
   float* ID = RH + PLANE;                          // inverse diagonal     [BH*NCOL]
   float2* rowc = reinterpret_cast<float2*>(ID + BH * NCOL);
-  double* wpart = reinterpret_cast<double*>(rowc + BH);   // [NW][4]
-  double* slots = wpart + CFG::NW * 4;                    // [2][16][4]
-  Scal* sc = reinterpret_cast<Scal*>(slots + 2 * kMaxCluster * 4);
+  double* slots = reinterpret_cast<double*>(rowc + BH);   // [2][16 CTAs x NW warps][4]
+  Scal* sc = reinterpret_cast<Scal*>(slots + 2 * kMaxCluster * CFG::NW * 4);
 
   const HaloPush pu = halo_push<CFG>(cluster, u, rank, C);
   const HaloPush pP = halo_push<CFG>(cluster, P, rank, C);
@@ -183,6 +175,9 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   band_load<CFG>(u, src, M, jbase, tid);
   cluster_barrier(cluster, C);
 
+  float xw[K];   // increment of the previous coarse step: initial guess of the next solve
+#pragma unroll
+  for (int k = 0; k < K; ++k) xw[k] = 0.f;
   const int n_end = (a.mode == SWEEP_PROP) ? a.n_first + 1 : a.N;
   for (int n = a.n_first; n < n_end; ++n) {
     const bool skip_g = (a.mode == SWEEP_ITER && n == a.n_first);
@@ -191,9 +186,10 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         const double tau_new = d.tau0 + a.slice_len * n + (cstep + 1) * d.dtau;
         band_far_field<CFG>(u, pu, pf, (float)tau_new, h, M, jbase, tid);
         cluster_barrier(cluster, C);
-        // b^ = D^{-1} dtau R_h w ;  x = 0 ;  r = r^ = p = b^
+        // b^ = D^{-1} dtau R_h w.  The solve starts from the previous coarse step's increment
+        // xw (the increments of consecutive steps are close): x = xw, r = r^ = p = b^ - A^ xw.
         float x[K], rr[K], vv[K], tt[K];
-        float part[1] = {0.f};
+        float part[2] = {0.f, 0.f};
         {
           const int p0 = r0 + 1;
           float nW = u[(p0 - 1) * NCOL + il], nC = u[(p0 - 1) * NCOL + col], nE = u[(p0 - 1) * NCOL + ir];
@@ -208,86 +204,99 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             const float b = ce * (cE - cC) - cw * (cC - cW) + rc.x * (sC - cC) - rc.y * (cC - nC) +
                             cg * ((sE - nE) - (sW - nW)) - rdt * cC;
             const float bh = b * ID[(p - 1) * NCOL + col];
-            x[k] = 0.f; rr[k] = bh; vv[k] = 0.f; tt[k] = 0.f;
+            x[k] = xw[k]; rr[k] = bh; vv[k] = 0.f; tt[k] = 0.f;
             part[0] = fmaf(bh, bh, part[0]);
             nW = cW; nC = cC; nE = cE;
             cW = sW; cC = sC; cE = sE;
           }
         }
 #pragma unroll
+        for (int k = 0; k < K; ++k) band_store<CFG>(P, pP, r0 + k, col, x[k]);
+        cluster_barrier(cluster, C);
+        scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          rr[k] -= vv[k];
+          part[1] = fmaf(rr[k], rr[k], part[1]);
+        }
+        // every CTA has finished reading P before the barrier inside the reduction below;
+        // P is rewritten only after it
+        cluster_sum<CFG, 2>(cluster, part, slots, sc, round, rank, C, [tol](Scal* s) {
+          s->rho = s->tot[1];
+          s->stop2 = tol * tol * s->tot[0];
+          s->conv = s->tot[1] <= s->stop2 || s->tot[0] <= 1e-60;
+          s->fail = 0;
+          s->alpha = s->omega = 1.0;
+        });
+#pragma unroll
         for (int k = 0; k < K; ++k) {
           band_store<CFG>(P, pP, r0 + k, col, rr[k]);
           RH[(r0 + k + 1) * NCOL + col] = rr[k];
         }
-        cluster_sum<CFG, 1>(cluster, part, wpart, slots, sc, round, rank, C, [tol](Scal* s) {
-          s->rho = s->tot[0];
-          s->stop2 = tol * tol * s->tot[0];
-          s->conv = s->tot[0] <= 1e-60;
-          s->fail = 0;
-          s->alpha = s->omega = 1.0;
-        });
+        cluster_barrier(cluster, C);
+        // BiCGSTAB with two reductions per iteration: omega, (r^, r_new) and beta follow from
+        // (t,s), (t,t), (r^,s), (r^,t); the residual norm is reduced explicitly with (r^, v)
+        // of the next iteration, so convergence is detected half an iteration later.
         int it = 0;
         while (!sc->conv && it < a.maxit) {
           ++it;
-          // v = A^ p ;  alpha = rho / (r^, v)
+          // v = A^ p ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
           scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
-          float p1[1] = {0.f};
+          float p1[2] = {0.f, 0.f};
 #pragma unroll
-          for (int k = 0; k < K; ++k) p1[0] = fmaf(RH[(r0 + k + 1) * NCOL + col], vv[k], p1[0]);
-          cluster_sum<CFG, 1>(cluster, p1, wpart, slots, sc, round, rank, C, [](Scal* s) {
+          for (int k = 0; k < K; ++k) {
+            p1[0] = fmaf(RH[(r0 + k + 1) * NCOL + col], vv[k], p1[0]);
+            p1[1] = fmaf(rr[k], rr[k], p1[1]);
+          }
+          cluster_sum<CFG, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) {
+            if (s->tot[1] <= s->stop2) { s->conv = 1; return; }
             if (s->tot[0] == 0.0) { s->fail = 1; return; }
             s->alpha = s->rho / s->tot[0];
             s->af = (float)s->alpha;
           });
-          if (sc->fail) break;
+          if (sc->conv || sc->fail) break;
           const float af = sc->af;
           // s = r - alpha v
 #pragma unroll
           for (int k = 0; k < K; ++k) band_store<CFG>(S, pS, r0 + k, col, fmaf(-af, vv[k], rr[k]));
           cluster_barrier(cluster, C);
-          // t = A^ s ;  omega = (t, s) / (t, t)
+          // t = A^ s ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
           scaled_matvec<CFG>(S, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, tt);
-          float p2[2] = {0.f, 0.f};
+          float p2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const float sv = S[(r0 + k + 1) * NCOL + col];
+            const int idx = (r0 + k + 1) * NCOL + col;
+            const float sv = S[idx], rh = RH[idx];
             p2[0] = fmaf(tt[k], sv, p2[0]);
             p2[1] = fmaf(tt[k], tt[k], p2[1]);
+            p2[2] = fmaf(rh, sv, p2[2]);
+            p2[3] = fmaf(rh, tt[k], p2[3]);
           }
-          cluster_sum<CFG, 2>(cluster, p2, wpart, slots, sc, round, rank, C, [](Scal* s) {
+          cluster_sum<CFG, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) {
             s->omega = s->tot[1] > 0.0 ? s->tot[0] / s->tot[1] : 0.0;
             s->of = (float)s->omega;
+            const double rho_new = s->tot[2] - s->omega * s->tot[3];
+            if (s->omega == 0.0 || s->rho == 0.0) { s->fail = 1; s->bf = 0.f; return; }
+            s->bf = (float)((rho_new / s->rho) * (s->alpha / s->omega));
+            s->rho = rho_new;
           });
-          const float of = sc->of;
-          // x += alpha p + omega s ;  r = s - omega t
-          float p3[2] = {0.f, 0.f};
+          const float of = sc->of, bf = sc->bf;
+          // x += alpha p + omega s ;  r = s - omega t ;  p = r + beta (p - omega v)
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             const int idx = (r0 + k + 1) * NCOL + col;
-            const float sv = S[idx];
-            x[k] += af * P[idx] + of * sv;
+            const float sv = S[idx], pv = P[idx];
+            x[k] += af * pv + of * sv;
             rr[k] = fmaf(-of, tt[k], sv);
-            p3[0] = fmaf(RH[idx], rr[k], p3[0]);
-            p3[1] = fmaf(rr[k], rr[k], p3[1]);
+            band_store<CFG>(P, pP, r0 + k, col, rr[k] + bf * (pv - of * vv[k]));
           }
-          cluster_sum<CFG, 2>(cluster, p3, wpart, slots, sc, round, rank, C, [](Scal* s) {
-            if (s->tot[1] <= s->stop2) { s->conv = 1; return; }
-            if (s->omega == 0.0 || s->rho == 0.0) { s->fail = 1; return; }
-            const double beta = (s->tot[0] / s->rho) * (s->alpha / s->omega);
-            s->rho = s->tot[0];
-            s->bf = (float)beta;
-          });
-          if (sc->conv || sc->fail) break;
-          const float bf = sc->bf;
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int idx = (r0 + k + 1) * NCOL + col;
-            band_store<CFG>(P, pP, r0 + k, col, rr[k] + bf * (P[idx] - of * vv[k]));
-          }
+          if (sc->fail) break;
           cluster_barrier(cluster, C);
         }
         if (!sc->conv) failed = true;
         iters_max = it > iters_max ? it : iters_max;
+#pragma unroll
+        for (int k = 0; k < K; ++k) xw[k] = x[k];
         // u^{m+1} = w + d (d = 0 off the PDE rows, whose values already hold g(tau_new))
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
       }
       double* norms = a.norms;
       const int slot_n = n + 1;
-      cluster_sum<CFG, 1>(cluster, nr, wpart, slots, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
+      cluster_sum<CFG, 1>(cluster, nr, slots, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
         if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = 0.0; }
       });
     } else {
@@ -351,7 +360,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
       }
       double* norms = a.norms;
       const int slot_n = n + 1;
-      cluster_sum<CFG, 2>(cluster, nr, wpart, slots, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
+      cluster_sum<CFG, 2>(cluster, nr, slots, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
         if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = s->tot[1]; }
       });
     }
@@ -375,7 +384,7 @@ template <class CFG>
 static int launch_sweep_k(const SweepParams& sp, cudaStream_t s) {
   const size_t smem = (size_t)4 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
                       (size_t)CFG::BH * sizeof(float2) +
-                      (CFG::NW * 4 + 2 * kMaxCluster * 4) * sizeof(double) + sizeof(Scal);
+                      (2 * kMaxCluster * CFG::NW * 4) * sizeof(double) + sizeof(Scal);
   auto kern = sweep_band_kernel<CFG>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (sp.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
