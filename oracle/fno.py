@@ -65,12 +65,23 @@ def fno_forward(a: np.ndarray, w: dict, mx: int, my: int) -> np.ndarray:
 
 
 def pino_coarse(u: np.ndarray, xmax: float, tau_n: float, dtau: float, params, w: dict,
-                mx: int, my: int) -> np.ndarray:
-    """One PINO coarse step: u(tau_n) -> u(tau_n + dtau) on an M x M grid."""
+                mx: int, my: int, Mp: int = None) -> np.ndarray:
+    """One PINO coarse step: u(tau_n) -> u(tau_n + dtau) on an M x M grid.
+
+    The network runs on an Mp x Mp grid (default Mp = M): u is restricted to it bilinearly,
+    the network output is prolonged back bilinearly and added to u (reading of the
+    resolution change of Sec. 4.4), then the far-field data are set.
+    """
     M = u.shape[0]
+    Mp = M if Mp is None else Mp
     X, Y = fd.mesh(M, xmax)
-    a = input_channels(u, X, Y, tau_n, dtau, params)
-    out = u + fno_forward(a, w, mx, my)
+    up = u if Mp == M else bilinear_resample(u, Mp)
+    Xp, Yp = fd.mesh(Mp, xmax)
+    a = input_channels(up, Xp, Yp, tau_n, dtau, params)
+    wout = fno_forward(a, w, mx, my)
+    if Mp != M:
+        wout = bilinear_resample(wout, M)
+    out = u + wout
     g = fd.dirichlet(params)(X, Y, tau_n + dtau)
     out[M - 1, :] = g[M - 1, :]
     out[:, M - 1] = g[:, M - 1]

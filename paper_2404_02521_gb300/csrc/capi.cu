@@ -251,7 +251,11 @@ int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_pa
     const_cast<bs_grid*>(g)->n_coarse += 1;
     return launch_sweep(g, d, a, (cudaStream_t)stream);
   }
-  if (kind == BS_COARSE_PINO) return set_error(BS_ERR_ARG, "coarse_propagate: PINO not loaded");
+  if (kind == BS_COARSE_PINO) {
+    const_cast<bs_grid*>(g)->n_coarse += 1;
+    return pino_propagate(const_cast<bs_pino*>(net), g, make_item(*p, tau0, dtau_slice), u_in, u_out,
+                          tau0, dtau_slice, (cudaStream_t)stream);
+  }
   return set_error(BS_ERR_ARG, "coarse_propagate: unknown kind %d", kind);
 }
 
@@ -308,13 +312,6 @@ int bs_phase_stats(bs_grid* g, double* fine_ms, int* fine_launches, double* coar
   return BS_OK;
 }
 
-int pino_load(const char* path, bs_pino** net) {
-  if (net) *net = nullptr;
-  return set_error(BS_ERR_FILE, "pino_load: %s: PINO support not built", path ? path : "(null)");
-}
-
-int pino_destroy(bs_pino* net) { return BS_OK; }
-
 // CUDA events bracketing one launch group on the caller's stream (BS_OPT_PHASE_TIMING).
 struct PhaseTimer {
   cudaEvent_t e[2] = {nullptr, nullptr};
@@ -356,8 +353,12 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   if (N < 1 || fine_steps < 1 || Kmax < 0 || Kmax > N || !(p->T > 0.0))
     return set_error(BS_ERR_ARG, "parareal_solve: N=%d fine_steps=%d Kmax=%d T=%g", N, fine_steps,
                      Kmax, p->T);
-  if (coarse_kind != BS_COARSE_NUM) return set_error(BS_ERR_ARG, "parareal_solve: coarse kind %d unsupported", coarse_kind);
-  if (coarse_steps < 1) return set_error(BS_ERR_ARG, "parareal_solve: coarse_steps < 1");
+  if (coarse_kind != BS_COARSE_NUM && coarse_kind != BS_COARSE_PINO)
+    return set_error(BS_ERR_ARG, "parareal_solve: coarse kind %d unsupported", coarse_kind);
+  const bool pino = coarse_kind == BS_COARSE_PINO;
+  if (pino && (rc = pino_check(net, g->M))) return rc;
+  if (!pino && coarse_steps < 1) return set_error(BS_ERR_ARG, "parareal_solve: coarse_steps < 1");
+  if (pino) coarse_steps = 1;
   cudaStream_t s = (cudaStream_t)stream;
   const int M = g->M;
   const size_t MM = (size_t)M * M;
@@ -367,11 +368,27 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   const int sweeps0 = grid_sweeps(g, *p, dtau_f, true);
   if (sweeps == 0)
     return set_error(BS_ERR_ARG, "parareal_solve: Jacobi contraction %.3f >= 0.8; more fine steps needed", g->q_val);
-  rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1));
+  const size_t part_bytes = pino ? pino_partials_bytes(M, N) : 0;
+  rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1) + part_bytes);
   if (rc) return rc;
   float* Fb = (float*)g->ws_par.ptr;
   float* Gold = Fb + (size_t)N * MM;
   double* norms = (double*)(Gold + (size_t)N * MM);
+  double* partials = norms + 2 * (N + 1);
+  bs_pino* pnet = const_cast<bs_pino*>(net);
+  // one serial coarse sweep (numerical: one persistent cluster kernel; PINO: per slice the
+  // network kernels and the correction), counted into the grid's launch statistics
+  auto sweep = [&](const ItemDesc& d, const SweepArgs& sa) -> int {
+    if (!pino) {
+      g->n_coarse += 1;
+      return launch_sweep(g, d, sa, s);
+    }
+    const int per_slice = pino_launches_per_step(pnet);
+    for (int n = sa.n_first; n < sa.N; ++n)
+      g->n_coarse += (sa.mode == SWEEP_ITER && n == sa.n_first) ? 1 : per_slice;
+    g->n_coarse += 1;
+    return pino_sweep(pnet, g, d, sa, partials, s);
+  };
   BS_CUDA_TRY(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), s));
   PhaseTimer tf, tc;
   tf.on = tc.on = g_opt.phase_timing != 0;
@@ -397,10 +414,9 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   a.mode = SWEEP_INIT;
   a.n_first = 0;
   if ((rc = tc.begin(s))) return rc;
-  rc = launch_sweep(g, dc, a, s);
+  rc = sweep(dc, a);
   if (rc) return rc;
   if ((rc = tc.end(s))) return rc;
-  g->n_coarse += 1;
   double ms_c = 0.0, ms_f = 0.0;
   if (tc.on) {
     BS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -429,15 +445,19 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
     a.mode = SWEEP_ITER;
     a.n_first = k;
     if ((rc = tc.begin(s))) return rc;
-    rc = launch_sweep(g, dc, a, s);
+    rc = sweep(dc, a);
     if (rc) return rc;
     if ((rc = tc.end(s))) return rc;
-    g->n_coarse += 1;
     double host[1];
     int hstat = 0;
     BS_CUDA_TRY(cudaMemcpyAsync(host, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
     BS_CUDA_TRY(cudaMemcpyAsync(&hstat, g->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     BS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (pino) {
+      int perr = 0;
+      if ((rc = pino_error_flag(pnet, &perr))) return rc;
+      if (perr) return set_error(BS_ERR_CUDA, "parareal_solve: a PINO tensor-core tile timed out");
+    }
     ms_f += tf.elapsed();
     ms_c += tc.elapsed();
     if (defect_hist) defect_hist[k] = host[0];

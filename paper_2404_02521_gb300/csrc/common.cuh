@@ -234,4 +234,13 @@ struct SweepArgs {
   int maxit;
 };
 int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
+// PINO coarse propagator (pino.cu)
+int pino_check(const bs_pino* net, int M);
+int pino_propagate(bs_pino* net, const bs_grid* g, const ItemDesc& d, const float* in, float* out,
+                   double tau0, double dtau, cudaStream_t s);
+int pino_sweep(bs_pino* net, const bs_grid* g, const ItemDesc& d, const SweepArgs& a,
+               double* partials, cudaStream_t s);
+size_t pino_partials_bytes(int M, int N);
+int pino_error_flag(const bs_pino* net, int* flag);
+int pino_launches_per_step(const bs_pino* net);
 }  // namespace bsp

@@ -1,0 +1,107 @@
+"""GPU parity of the PINO coarse propagator (tensor-core BF16 FNO, Sec. 3.4-3.5) against the
+FP64 oracle forward of the same weights, and Parareal with the PINO as G."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fd
+from oracle import fno
+from tests.gpu_util import FP32_FINE_TOL, rel_err, start_state, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+# BF16 operands (unit roundoff 2^-9) pass through about 30 rounded contractions between the
+# input and the network output (6 per Fourier layer, 4 layers, lifting and projection); with
+# FP32 accumulation the output error stays within a few percent of the output's magnitude.
+PINO_REL_TOL = 4e-2
+
+
+@pytest.fixture(scope="module")
+def bs():
+    import paper_2404_02521_gb300 as bs
+    bs.load()
+    return bs
+
+
+@pytest.fixture(scope="module")
+def weights(tmp_path_factory):
+    from paper_2404_02521_gb300 import pino_io
+    arch = wl.PinoArch()
+    w = wl.pino_random_weights(arch, seed=11, spectral_scale=8.0)
+    path = str(tmp_path_factory.mktemp("pino") / "w.bin")
+    pino_io.write_weights(path, w, arch.in_channels, arch.width, arch.modes_x, arch.modes_y,
+                          arch.layers, arch.proj_hidden)
+    w2, _ = pino_io.read_weights(path)   # the float32 values the library loads
+    return path, w2, arch
+
+
+def network_grid(M):
+    return 128 if M <= 128 else 256
+
+
+@pytest.mark.parametrize("M,payoff", [(128, wl.BASKET), (256, wl.EXCHANGE), (96, wl.EXCHANGE),
+                                      (200, wl.BASKET), (64, wl.BASKET)])
+def test_pino_step_matches_oracle(bs, weights, M, payoff):
+    import torch
+    path, w, arch = weights
+    net = bs.Pino(path)
+    p = wl.basket_cfg1().params if payoff == wl.BASKET else wl.exchange_cfg2(-0.5).params
+    u0 = start_state(M, 4.0, p, "random", seed=M)
+    g = bs.Grid(M, 4.0)
+    uin = to_gpu(u0)
+    out = torch.empty_like(uin)
+    tau0, dtau = 0.25, 1.0 / 64
+    bs.coarse_propagate(g, bs.COARSE_PINO, net, p, uin, out, tau0, dtau, 1)
+    torch.cuda.synchronize()
+    want = fno.pino_coarse(u0.astype(np.float64), 4.0, tau0, dtau, p, w, arch.modes_x,
+                           arch.modes_y, Mp=network_grid(M))
+    got = to_np(out)
+    d_got, d_want = got - u0, want - u0.astype(np.float64)
+    err = float(np.max(np.abs(d_got - d_want)) / np.max(np.abs(d_want)))
+    print(f"M={M}: network-output rel. err {err:.3e}")
+    assert err <= PINO_REL_TOL
+    # far-field edges are the closed form exactly as on the fine path
+    assert np.max(np.abs(got[M - 1] - want[M - 1])) < 1e-5 * (1 + np.max(np.abs(want)))
+
+
+def test_pino_parareal_invariants(bs, weights):
+    # Parareal with any coarse model reproduces serial fine after N iterations (bitwise), and
+    # the first k+1 slices are exact after k iterations.
+    import torch
+    path, _, _ = weights
+    net = bs.Pino(path)
+    pb = wl.Problem("pino128", 128, 4.0, 4, 1024, 1, wl.basket_cfg1().params)
+    g = bs.Grid(pb.M, pb.xmax)
+    S = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+    bs.bs_payoff(g, pb.params, S[0])
+    sl = pb.params.T / pb.N
+    for n in range(pb.N):
+        bs.fine_propagate_batched(g, [pb.params], [S[n]], [S[n + 1]], [n * sl],
+                                  [sl / pb.fine_steps], pb.fine_steps)
+    U = torch.empty_like(S)
+    rc, k, d = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_PINO, 1, net, 0.0,
+                                 pb.N, U)
+    torch.cuda.synchronize()
+    assert k == pb.N and torch.equal(U, S)
+    for K in (1, 2):
+        rc, k, d = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_PINO, 1, net,
+                                     0.0, K, U)
+        torch.cuda.synchronize()
+        assert torch.equal(U[: K + 1], S[: K + 1])
+    assert rel_err(to_np(S), fd.serial_fine(pb)) <= FP32_FINE_TOL
+
+
+def test_pino_load_rejects_bad_files(bs, tmp_path):
+    p = tmp_path / "bad.bin"
+    p.write_bytes(b"BSPINO01" + b"\0" * 16)
+    with pytest.raises(bs.BSError):
+        bs.Pino(str(p))
+    q = tmp_path / "short.bin"
+    from paper_2404_02521_gb300 import pino_io
+    arch = wl.PinoArch(width=8, modes_x=2, modes_y=2, layers=1, proj_hidden=16)
+    pino_io.write_weights(str(q), wl.pino_random_weights(arch), 9, 8, 2, 2, 1, 16)
+    q.write_bytes(q.read_bytes()[:-4])
+    with pytest.raises(bs.BSError):
+        bs.Pino(str(q))
