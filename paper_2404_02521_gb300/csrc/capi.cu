@@ -175,6 +175,7 @@ int bs_grid_destroy(bs_grid* g) {
   cudaFree(g->dscal);
   if (g->dnorms) cudaFree(g->dnorms);
   if (g->ws_par.ptr) cudaFree(g->ws_par.ptr);
+  if (g->ws_fine.ptr) cudaFree(g->ws_fine.ptr);
   delete g;
   return BS_OK;
 }
@@ -222,7 +223,7 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* co
                                     cudaMemcpyDeviceToDevice, s));
     return BS_OK;
   }
-  const_cast<bs_grid*>(g)->n_fine += (B + kMaxItems - 1) / kMaxItems;
+  const_cast<bs_grid*>(g)->n_fine += fine_launches(g, B, nsteps);
   return launch_fine(g, items.data(), B, nsteps, s);
 }
 
@@ -441,7 +442,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
     rc = launch_fine(g, items.data(), B, fine_steps, s);
     if (rc) return rc;
     if ((rc = tf.end(s))) return rc;
-    g->n_fine += (B + kMaxItems - 1) / kMaxItems;
+    g->n_fine += fine_launches(g, B, fine_steps);
     a.mode = SWEEP_ITER;
     a.n_first = k;
     if ((rc = tc.begin(s))) return rc;

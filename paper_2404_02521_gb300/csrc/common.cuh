@@ -203,6 +203,7 @@ struct bs_grid {
   double* dscal;               // device: scalar outputs (defect)
   double* dnorms;              // device: per-slice squared norms / defects
   bsp::Workspace ws_par;       // Parareal F / Gold buffers
+  bsp::Workspace ws_fine;      // tile fine stepper (M > 256): ping-pong hi, lo, increment
   // cached contraction
   double q_key[6];
   double q_val;
@@ -214,6 +215,7 @@ struct bs_grid {
 // Kernel launchers implemented in the .cu files.
 namespace bsp {
 int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s);
+int fine_launches(const bs_grid* g, int n, int nsteps);   // kernels launch_fine enqueues
 int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s);
 // Coarse numerical propagation / Parareal serial sweep (see coarse.cu).
 enum { SWEEP_PROP = 0, SWEEP_INIT = 1, SWEEP_ITER = 2 };

@@ -14,6 +14,7 @@
 // launch, 2^-10 for the warm-started steps after it).  The state is a compensated
 // pair (hi, lo): u = hi + lo, updated by an error-free two-sum, so that increments below half
 // an ulp of u are not lost over tens of thousands of steps; b is evaluated from hi.
+#include <algorithm>
 #include <cstdio>
 
 #include "band.cuh"
@@ -246,6 +247,181 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Tile variant for grids that do not fit a cluster (M > 256): one implicit step per launch.
+// A CTA owns a TX x TY interior tile and loads the surrounding region of (TX + 2H) x
+// (TY + 2H) nodes (H >= the step's sweep count) of hi and of the previous increment from
+// global memory.  Every sweep's result is exact one node further from the region's cut
+// edges, so after H sweeps the interior matches a whole-grid sweep bit for bit; the domain
+// edges need no halo (zero coefficients at x = 0, y = 0; Dirichlet at the far edges).  The
+// interior's (hi, lo, increment) go to the other half of a ping-pong workspace.
+// ---------------------------------------------------------------------------------------
+struct TileBatch {
+  ItemDesc it[kMaxItems];
+  float* ws;        // per item: [2][hi, lo, increment][M*M]
+  int n, M, H, nsteps_total;
+  float h;
+};
+
+template <class CFG>
+__global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_constant__ TileBatch tb,
+                                                               int step, int first, int last, int par) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, PLANE = CFG::PLANE;
+  const ItemDesc& d = tb.it[blockIdx.z];
+  const int M = tb.M, H = tb.H;
+  const size_t MM = (size_t)M * M;
+  const int TX = NCOL - 2 * H, TY = BH - 2 * H;
+  const int ix0 = blockIdx.x * TX - H, jy0 = blockIdx.y * TY - H;   // region origin
+  float* ws = tb.ws + (size_t)(blockIdx.z) * 6 * MM;
+  const float* hi_g = first ? d.in : ws + (size_t)(par * 3 + 0) * MM;
+  const float* lo_g = ws + (size_t)(par * 3 + 1) * MM;
+  const float* dv_g = ws + (size_t)(par * 3 + 2) * MM;
+  float* hi_o = ws + (size_t)((par ^ 1) * 3 + 0) * MM;
+  float* lo_o = ws + (size_t)((par ^ 1) * 3 + 1) * MM;
+  float* dv_o = ws + (size_t)((par ^ 1) * 3 + 2) * MM;
+  const int tid = threadIdx.x;
+  const int col = tid % NCOL, grp = tid / NCOL;
+  const int r0 = grp * K;
+  const PayoffF pf = make_payoff(d);
+
+  extern __shared__ __align__(16) float smem[];
+  float* hi = smem;
+  float* dA = hi + PLANE;
+  float* dB = dA + PLANE;
+  float2* rowc = reinterpret_cast<float2*>(dB + PLANE);
+  const float tau_new = (float)(d.tau0 + (step + 1) * d.dtau);
+  for (int e = tid; e < PLANE; e += CFG::NT) {
+    const int pr = e / NCOL, c = e % NCOL;
+    const int j = jy0 + pr - 1, i = ix0 + c;
+    const bool in = (i >= 0 && i < M && j >= 0 && j < M);
+    float hv = 0.f, dvv = 0.f;
+    if (in) {
+      hv = hi_g[(size_t)j * M + i];
+      if (!first) dvv = dv_g[(size_t)j * M + i];
+      if (i == M - 1 || j == M - 1) hv = far_field(pf, i * tb.h, j * tb.h, tau_new);
+    }
+    hi[e] = hv;
+    dA[e] = dvv;
+    dB[e] = 0.f;
+  }
+  for (int r = tid; r < BH; r += CFG::NT) {
+    float cs, cn, gj;
+    row_coefs(d, jy0 + r, cs, cn, gj);
+    rowc[r] = make_float2(cs, cn);
+  }
+  const int ig = ix0 + col;
+  float ce = 0.f, cw = 0.f, cgi = 0.f;
+  column_coefs(d, ig, ce, cw, cgi);
+  const float cg0 = cgi * (float)(jy0 + r0);
+  float dv[K], b[K], invd[K], lo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int j = jy0 + r0 + k;
+    const bool pde = ig >= 0 && ig < M - 1 && j >= 0 && j < M - 1;
+    invd[k] = pde ? inv_diag(d, ig, j) : 0.f;
+    const bool in = ig >= 0 && ig < M && j >= 0 && j < M;
+    lo[k] = (in && !first && pde) ? lo_g[(size_t)j * M + ig] : 0.f;
+    b[k] = 0.f;
+    dv[k] = (in && !first) ? dv_g[(size_t)j * M + ig] : 0.f;
+  }
+  const int il = col > 0 ? col - 1 : 0;
+  const int ir = col + 1 < NCOL ? col + 1 : col;
+  const float rdt = (float)(d.r * d.dtau);
+  const int m = first ? d.sweeps0 : d.sweeps;
+  const HaloPush none = {nullptr, nullptr};
+  __syncthreads();
+  int p = 0;
+  for (int s = 0; s < m; ++s) {
+    const float* rd = p ? dB : dA;
+    float* wr = p ? dA : dB;
+    if (s == 0)
+      fine_sweep<CFG, true, false>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                   cg0, cgi, rdt, false);
+    else if (s == m - 1)
+      fine_sweep<CFG, false, true>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                   cg0, cgi, rdt, false);
+    else
+      fine_sweep<CFG, false, false>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce,
+                                    cw, cg0, cgi, rdt, false);
+    p ^= 1;
+    __syncthreads();
+  }
+  // interior of the tile
+  if (col >= H && col < H + TX && ig < M) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int r = r0 + k, j = jy0 + r;
+      if (r >= H && r < H + TY && j < M) {
+        const size_t gi = (size_t)j * M + ig;
+        const float hv = hi[(r + 1) * NCOL + col];
+        if (last) {
+          d.out[gi] = hv + lo[k];
+        } else {
+          hi_o[gi] = hv;
+          lo_o[gi] = lo[k];
+          dv_o[gi] = dv[k];
+        }
+      }
+    }
+  }
+}
+
+typedef BandCfg<128, 512, 16> TileCfg;
+
+// u_out = hi + lo from the second workspace half (after a single tile step)
+__global__ void tile_finish_kernel(const __grid_constant__ TileBatch tb) {
+  const ItemDesc& d = tb.it[blockIdx.y];
+  const size_t MM = (size_t)tb.M * tb.M;
+  const float* ws = tb.ws + (size_t)blockIdx.y * 6 * MM;
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e < MM) d.out[e] = ws[3 * MM + e] + ws[4 * MM + e];
+}
+
+static int launch_tiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
+  const int M = g->M;
+  const size_t MM = (size_t)M * M;
+  int H = 2;
+  for (int k = 0; k < n; ++k) H = std::max(H, std::max(items[k].sweeps, items[k].sweeps0));
+  if (H > 24)
+    return set_error(BS_ERR_ARG, "fine_propagate_batched: %d sweeps per step exceed the tile halo "
+                     "of large grids (24); take smaller fine steps", H);
+  int rc = ensure(const_cast<bs_grid*>(g)->ws_fine, (size_t)std::min(n, kMaxItems) * 6 * MM * sizeof(float));
+  if (rc) return rc;
+  const size_t smem = (size_t)3 * TileCfg::PLANE * sizeof(float) + (size_t)TileCfg::BH * sizeof(float2);
+  auto kern = fine_tile_kernel<TileCfg>;
+  BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int TX = TileCfg::NCOL - 2 * H, TY = TileCfg::BH - 2 * H;
+  for (int base = 0; base < n; base += kMaxItems) {
+    TileBatch tb;
+    tb.n = std::min(n - base, kMaxItems);
+    for (int k = 0; k < tb.n; ++k) tb.it[k] = items[base + k];
+    tb.ws = (float*)g->ws_fine.ptr;
+    tb.M = M;
+    tb.H = H;
+    tb.nsteps_total = nsteps;
+    tb.h = (float)(g->xmax / (M - 1));
+    const dim3 grid((M + TX - 1) / TX, (M + TY - 1) / TY, tb.n);
+    // A single step would read u_in and write u_out in the same launch (they may alias):
+    // keep its result in the workspace and form u_out in a separate pass.
+    const bool one = nsteps == 1;
+    for (int step = 0; step < nsteps; ++step) {
+      kern<<<grid, TileCfg::NT, smem, s>>>(tb, step, step == 0, step == nsteps - 1 && !one, step & 1);
+      BS_CUDA_TRY(cudaGetLastError());
+    }
+    if (one) {
+      tile_finish_kernel<<<dim3((unsigned)((MM + 255) / 256), tb.n), 256, 0, s>>>(tb);
+      BS_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return BS_OK;
+}
+
+int fine_launches(const bs_grid* g, int n, int nsteps) {
+  const int chunks = (n + kMaxItems - 1) / kMaxItems;
+  if (g->shape.C >= 1 && g->shape.C <= kMaxCluster) return chunks;
+  return chunks * (nsteps + (nsteps == 1 ? 1 : 0));
+}
+
 template <class CFG>
 static int launch_band(const FineBatch& fb, cudaStream_t s) {
   const size_t smem = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * sizeof(float2);
@@ -270,9 +446,7 @@ static int launch_band(const FineBatch& fb, cudaStream_t s) {
 
 int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
   const BandShape sh = g->shape;
-  if (sh.C < 1 || sh.C > kMaxCluster)
-    return set_error(BS_ERR_ARG, "fine_propagate_batched: grid M=%d is not supported by the "
-                                 "cluster-resident stepper", g->M);
+  if (sh.C < 1 || sh.C > kMaxCluster) return launch_tiles(g, items, n, nsteps, s);
   for (int base = 0; base < n; base += kMaxItems) {
     FineBatch fb;
     fb.n = (n - base) < kMaxItems ? (n - base) : kMaxItems;

@@ -14,7 +14,7 @@ prediction, with centred differences and the slice as one implicit step -- and a
 term on the far edges.  Adam, learning rate 1e-3 decayed by 0.96 at fixed intervals.
 
 Usage (on a GPU machine):
-    python -m paper_2404_02521_gb300.pino_train --out weights.bin [--problems 256] [--iters 6000]
+    python -m paper_2404_02521_gb300.pino_train --out weights.bin [--problems 256] [--iters 6000] [--slices 12,64]
 """
 from __future__ import annotations
 
@@ -153,9 +153,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--M", type=int, default=128)
-    ap.add_argument("--N", type=int, default=64)
-    ap.add_argument("--fine-steps", type=int, default=512)
-    ap.add_argument("--problems", type=int, default=256)
+    ap.add_argument("--slices", default="12,64", help="slice counts N of [0, 1] to train on")
+    ap.add_argument("--fine-dtau", type=float, default=1.0 / 32768)
+    ap.add_argument("--problems", type=int, default=256, help="trajectories per slice count")
     ap.add_argument("--iters", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--physics-weight", type=float, default=1e-4)
@@ -165,36 +165,41 @@ def main():
     torch.manual_seed(args.seed)
     bs.load()
     t0 = time.time()
-    U, prm, P0, P1 = generate(args.M, args.N, args.fine_steps, args.problems, args.seed, dev)
-    print(f"data: {args.problems} trajectories x {args.N} slices in {time.time() - t0:.1f} s", flush=True)
-    M, N = args.M, args.N
+    M = args.M
+    sets = []
+    for q, N in enumerate(int(v) for v in args.slices.split(",")):
+        fine = max(1, int(round(1.0 / (N * args.fine_dtau))))
+        U, prm, P0, P1 = generate(M, N, fine, args.problems, args.seed + 7 * q, dev)
+        sets.append(dict(N=N, U=U, prm=prm, P0=P0, P1=P1, dtau=1.0 / N))
+        print(f"data: {args.problems} trajectories x {N} slices of {fine} fine steps "
+              f"({time.time() - t0:.1f} s)", flush=True)
     h = 4.0 / (M - 1)
     x = torch.arange(M, device=dev, dtype=torch.float32) * h
     Xg, Yg = x.view(1, M).expand(M, M), x.view(M, 1).expand(M, M)
-    dtau = 1.0 / N
     model = FNO().to(dev)
     opt = torch.optim.Adam(model.parameters(), lr=1e-3)
     sched = torch.optim.lr_scheduler.StepLR(opt, step_size=max(1, args.iters // 100), gamma=0.96)
     n_train = int(0.9 * args.problems)
     gen = torch.Generator(device="cpu").manual_seed(args.seed)
 
-    def batch(lo, hi, B):
+    def batch(ds, lo, hi, B):
+        N, U, P0, P1, dtau = ds["N"], ds["U"], ds["P0"], ds["P1"], ds["dtau"]
         k = torch.randint(lo, hi, (B,), generator=gen)
         n = torch.randint(0, N, (B,), generator=gen)
         pert = torch.rand(B, generator=gen) < 0.5     # half on-trajectory, half perturbed
         kd, nd, pd = k.to(dev), n.to(dev), pert.to(dev).view(B, 1, 1)
         u0 = torch.where(pd, P0[kd, nd], U[kd, nd])
         u1 = torch.where(pd, P1[kd, nd], U[kd, nd + 1])
-        p = prm[kd]
+        p = ds["prm"][kd]
         one = torch.ones(B, M, M, device=dev)
         tau = (nd.float() * dtau).view(B, 1, 1)
         a = torch.stack([u0, Xg.expand(B, M, M), Yg.expand(B, M, M), tau * one, dtau * one,
                          p[:, 0].view(B, 1, 1) * one, p[:, 1].view(B, 1, 1) * one,
                          p[:, 2].view(B, 1, 1) * one, p[:, 3].view(B, 1, 1) * one], dim=1)
-        return a, u0, u1, p
+        return a, u0, u1, p, dtau
 
     for it in range(args.iters):
-        a, u0, u1, p = batch(0, n_train, args.batch)
+        a, u0, u1, p, dtau = batch(sets[it % len(sets)], 0, n_train, args.batch)
         pred = u0 + model(a)
         # squared error relative to each sample's own increment: late slices, whose increments
         # are small, weigh as much as the early ones near the payoff kink
@@ -207,13 +212,16 @@ def main():
         loss.backward()
         opt.step()
         sched.step()
-        if it % 500 == 0 or it == args.iters - 1:
+        if it % 1000 == 0 or it == args.iters - 1:
+            msg = []
             with torch.no_grad():
-                a, u0, u1, p = batch(n_train, args.problems, 64)
-                pred = u0 + model(a)
-                rel = torch.sqrt(torch.mean((pred - u1) ** 2) / torch.mean((u1 - u0) ** 2))
-            print(f"it {it} loss {loss.item():.3e} data {data.item():.3e} phys {phys.item():.3e} "
-                  f"held-out increment rel. rms err {rel.item():.3f}", flush=True)
+                for ds in sets:
+                    a, u0, u1, p, _ = batch(ds, n_train, args.problems, 64)
+                    pred = u0 + model(a)
+                    rel = torch.sqrt(torch.mean((pred - u1) ** 2) / torch.mean((u1 - u0) ** 2))
+                    msg.append(f"N={ds['N']}: {rel.item():.3f}")
+            print(f"it {it} loss {loss.item():.3e} held-out increment rel. rms err " + ", ".join(msg),
+                  flush=True)
     model.export(args.out)
     print(f"wrote {args.out} after {time.time() - t0:.1f} s", flush=True)
 

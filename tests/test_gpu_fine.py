@@ -45,6 +45,28 @@ def test_fine_matches_oracle(bs, M, pi):
     assert rel_err(to_np(uout), want) <= FP32_FINE_TOL
 
 
+@pytest.mark.parametrize("M,pi", [(300, 0), (300, 2), (512, 1)])
+def test_fine_tiles_match_oracle(bs, M, pi):
+    # grids beyond one cluster: one implicit step per launch over haloed tiles
+    import torch
+    p = PARAMS[pi]
+    xmax = 4.0
+    dtau = dtau_for(M, p)
+    nsteps = 6
+    u0 = start_state(M, xmax, p, "random" if pi else "payoff", seed=M)
+    g = bs.Grid(M, xmax)
+    uin = to_gpu(u0)
+    uout = torch.empty_like(uin)
+    bs.fine_propagate_batched(g, [p, p], [uin, uin], [uout, torch.empty_like(uin)], [0.1, 0.1],
+                              [dtau, dtau], nsteps)
+    one = uin.clone()
+    bs.fine_propagate_batched(g, [p], [one], [one], [0.1], [dtau], 1)    # in place, one step
+    torch.cuda.synchronize()
+    want = oracle_fine(M, xmax, p, u0, 0.1, dtau, nsteps)
+    assert rel_err(to_np(uout), want) <= FP32_FINE_TOL
+    assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
+
+
 def test_batch_invariance_and_in_place(bs):
     import torch
     M, xmax = 100, 4.0
