@@ -176,6 +176,7 @@ int bs_grid_destroy(bs_grid* g) {
   if (g->dnorms) cudaFree(g->dnorms);
   if (g->ws_par.ptr) cudaFree(g->ws_par.ptr);
   if (g->ws_fine.ptr) cudaFree(g->ws_fine.ptr);
+  if (g->ws_coarse.ptr) cudaFree(g->ws_coarse.ptr);
   delete g;
   return BS_OK;
 }

@@ -404,14 +404,290 @@ static int launch_sweep_k(const SweepParams& sp, cudaStream_t s) {
   return BS_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Grids beyond one cluster's shared memory (M > 256): the same BiCGSTAB and Parareal sweep
+// with the vectors in a global workspace.  One cluster of CG CTAs owns the system; CTA rank
+// handles rows [rank*BHg, rank*BHg + BHg).  Stencil operands written by other CTAs are read
+// with ld.global.cg (L2, never a stale L1 line); the cluster barrier's release/acquire
+// orders them.
+// ---------------------------------------------------------------------------------------
+constexpr int kGThreads = 1024;
+struct GCfg {
+  static constexpr int NW = kGThreads / 32;
+};
+
+struct GlobalVecs {
+  float *u, *x, *r, *rh, *p, *v, *s, *t, *id;
+};
+
+struct GSweepParams {
+  ItemDesc d;
+  SweepArgs a;
+  GlobalVecs w;
+  int M, C;
+  float h;
+};
+
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+
+// A^ y at node (i, j) (PDE rows only), y read through L2.
+__device__ __forceinline__ float g_matvec(const float* y, const float* id, int M, int i, int j,
+                                          float ce, float cw, float cs, float cn, float cg) {
+  const size_t e = (size_t)j * M + i;
+  const float* r0 = y + e - M;
+  const float* r2 = y + e + M;
+  const float yc = ldcg(y + e);
+  const float yw = i > 0 ? ldcg(y + e - 1) : 0.f, ye = ldcg(y + e + 1);
+  const float yn = j > 0 ? ldcg(r0) : 0.f, ys = ldcg(r2);
+  const float ynw = (i > 0 && j > 0) ? ldcg(r0 - 1) : 0.f, yne = j > 0 ? ldcg(r0 + 1) : 0.f;
+  const float ysw = i > 0 ? ldcg(r2 - 1) : 0.f, yse = ldcg(r2 + 1);
+  return yc - id[e] * (ce * ye + cw * yw + cs * ys + cn * yn + cg * ((yse - yne) - (ysw - ynw)));
+}
+
+__device__ __forceinline__ void g_coefs(const ItemDesc& d, int i, int j, float& ce, float& cw,
+                                        float& cs, float& cn, float& cg) {
+  float cgi, gj;
+  column_coefs(d, i, ce, cw, cgi);
+  row_coefs(d, j, cs, cn, gj);
+  cg = cgi * gj;
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid_constant__ GSweepParams gp) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const ItemDesc& d = gp.d;
+  const SweepArgs& a = gp.a;
+  const GlobalVecs& w = gp.w;
+  const int M = gp.M, C = gp.C;
+  const int rank = C > 1 ? (int)cluster.block_rank() : 0;
+  const int tid = threadIdx.x;
+  const size_t MM = (size_t)M * M;
+  const int BHg = (M + C - 1) / C;
+  const int j0 = rank * BHg, j1 = min(M, j0 + BHg);
+  const size_t e0 = (size_t)j0 * M, e1 = (size_t)j1 * M;
+  const PayoffF pf = make_payoff(d);
+  const float rdt = (float)(d.r * d.dtau);
+  const double tol = a.tol;
+  __shared__ double slots[2 * kMaxCluster * GCfg::NW * 4];
+  __shared__ Scal scs;
+  Scal* sc = &scs;
+  int round = 0, iters_max = 0;
+  bool failed = false;
+  auto barrier = [&]() { __threadfence(); cluster_barrier(cluster, C); };
+
+  for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+    const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+    w.id[e] = (i < M - 1 && j < M - 1) ? inv_diag(d, i, j) : 0.f;
+    w.x[e] = 0.f;
+    const float* src = a.mode == SWEEP_PROP ? a.in : a.mode == SWEEP_INIT ? a.U : a.Gold + (size_t)a.n_first * MM;
+    w.u[e] = src[e];
+  }
+  barrier();
+  const int n_end = (a.mode == SWEEP_PROP) ? a.n_first + 1 : a.N;
+  for (int n = a.n_first; n < n_end; ++n) {
+    const bool skip_g = (a.mode == SWEEP_ITER && n == a.n_first);
+    if (!skip_g) {
+      for (int cstep = 0; cstep < a.csteps; ++cstep) {
+        const float tau_new = (float)(d.tau0 + a.slice_len * n + (cstep + 1) * d.dtau);
+        for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+          const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+          if (i == M - 1 || j == M - 1) w.u[e] = far_field(pf, i * gp.h, j * gp.h, tau_new);
+        }
+        barrier();
+        // b^ = D^{-1} dtau R_h w ;  r = b^ - A^ x (x = previous increment)
+        float part[2] = {0.f, 0.f};
+        for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+          const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+          float bh = 0.f, rr = 0.f;
+          if (i < M - 1 && j < M - 1) {
+            float ce, cw, cs, cn, cg;
+            g_coefs(d, i, j, ce, cw, cs, cn, cg);
+            const float* y = w.u;
+            const float c = ldcg(y + e);
+            const float yw = i > 0 ? ldcg(y + e - 1) : 0.f, ye = ldcg(y + e + 1);
+            const float yn = j > 0 ? ldcg(y + e - M) : 0.f, ys = ldcg(y + e + M);
+            const float ynw = (i > 0 && j > 0) ? ldcg(y + e - M - 1) : 0.f, yne = j > 0 ? ldcg(y + e - M + 1) : 0.f;
+            const float ysw = i > 0 ? ldcg(y + e + M - 1) : 0.f, yse = ldcg(y + e + M + 1);
+            const float b = ce * (ye - c) - cw * (c - yw) + cs * (ys - c) - cn * (c - yn) +
+                            cg * ((yse - yne) - (ysw - ynw)) - rdt * c;
+            bh = b * w.id[e];
+            rr = bh - g_matvec(w.x, w.id, M, i, j, ce, cw, cs, cn, cg);
+          }
+          w.r[e] = rr;
+          w.rh[e] = rr;
+          part[0] = fmaf(bh, bh, part[0]);
+          part[1] = fmaf(rr, rr, part[1]);
+        }
+        cluster_sum<GCfg, 2>(cluster, part, slots, sc, round, rank, C, [tol](Scal* s) {
+          s->rho = s->tot[1];
+          s->stop2 = tol * tol * s->tot[0];
+          s->conv = s->tot[1] <= s->stop2 || s->tot[0] <= 1e-60;
+          s->fail = 0;
+          s->alpha = s->omega = 1.0;
+        });
+        for (size_t e = e0 + tid; e < e1; e += kGThreads) w.p[e] = w.r[e];
+        barrier();
+        int it = 0;
+        while (!sc->conv && it < a.maxit) {
+          ++it;
+          float p1[2] = {0.f, 0.f};
+          for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+            const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+            float vv = 0.f;
+            if (i < M - 1 && j < M - 1) {
+              float ce, cw, cs, cn, cg;
+              g_coefs(d, i, j, ce, cw, cs, cn, cg);
+              vv = g_matvec(w.p, w.id, M, i, j, ce, cw, cs, cn, cg);
+            }
+            w.v[e] = vv;
+            const float rr = w.r[e];
+            p1[0] = fmaf(w.rh[e], vv, p1[0]);
+            p1[1] = fmaf(rr, rr, p1[1]);
+          }
+          cluster_sum<GCfg, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) {
+            if (s->tot[1] <= s->stop2) { s->conv = 1; return; }
+            if (s->tot[0] == 0.0) { s->fail = 1; return; }
+            s->alpha = s->rho / s->tot[0];
+            s->af = (float)s->alpha;
+          });
+          if (sc->conv || sc->fail) break;
+          const float af = sc->af;
+          for (size_t e = e0 + tid; e < e1; e += kGThreads) w.s[e] = fmaf(-af, w.v[e], w.r[e]);
+          barrier();
+          float p2[4] = {0.f, 0.f, 0.f, 0.f};
+          for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+            const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+            float tt = 0.f;
+            if (i < M - 1 && j < M - 1) {
+              float ce, cw, cs, cn, cg;
+              g_coefs(d, i, j, ce, cw, cs, cn, cg);
+              tt = g_matvec(w.s, w.id, M, i, j, ce, cw, cs, cn, cg);
+            }
+            w.t[e] = tt;
+            const float sv = w.s[e], rh = w.rh[e];
+            p2[0] = fmaf(tt, sv, p2[0]);
+            p2[1] = fmaf(tt, tt, p2[1]);
+            p2[2] = fmaf(rh, sv, p2[2]);
+            p2[3] = fmaf(rh, tt, p2[3]);
+          }
+          cluster_sum<GCfg, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) {
+            s->omega = s->tot[1] > 0.0 ? s->tot[0] / s->tot[1] : 0.0;
+            s->of = (float)s->omega;
+            const double rho_new = s->tot[2] - s->omega * s->tot[3];
+            if (s->omega == 0.0 || s->rho == 0.0) { s->fail = 1; s->bf = 0.f; return; }
+            s->bf = (float)((rho_new / s->rho) * (s->alpha / s->omega));
+            s->rho = rho_new;
+          });
+          const float of = sc->of, bf = sc->bf;
+          for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+            const float sv = w.s[e], pv = w.p[e], tt = w.t[e];
+            w.x[e] += af * pv + of * sv;
+            const float rr = fmaf(-of, tt, sv);
+            w.r[e] = rr;
+            w.p[e] = rr + bf * (pv - of * w.v[e]);
+          }
+          if (sc->fail) break;
+          barrier();
+        }
+        if (!sc->conv) failed = true;
+        iters_max = it > iters_max ? it : iters_max;
+        for (size_t e = e0 + tid; e < e1; e += kGThreads) w.u[e] += w.x[e];
+        barrier();
+      }
+    }
+    if (a.mode == SWEEP_PROP) {
+      for (size_t e = e0 + tid; e < e1; e += kGThreads) a.out[e] = w.u[e];
+    } else {
+      double nr[2] = {0.0, 0.0};
+      float* Un = a.U + (size_t)(n + 1) * MM;
+      const float* Fn = a.Fb + (size_t)n * MM;
+      float* Gn = a.Gold + (size_t)n * MM;
+      for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+        const float gnew = w.u[e];
+        if (a.mode == SWEEP_INIT) {
+          Un[e] = gnew;
+          Gn[e] = gnew;
+          nr[0] = fma((double)gnew, (double)gnew, nr[0]);
+        } else {
+          const float unew = Fn[e] + (gnew - Gn[e]);
+          const double du = (double)unew - (double)Un[e];
+          Un[e] = unew;
+          Gn[e] = gnew;
+          w.u[e] = unew;
+          nr[0] = fma((double)unew, (double)unew, nr[0]);
+          nr[1] = fma(du, du, nr[1]);
+        }
+      }
+      double* norms = a.norms;
+      const int slot_n = n + 1;
+      const bool iter = a.mode == SWEEP_ITER;
+      cluster_sum<GCfg, 2>(cluster, nr, slots, sc, round, rank, C, [norms, slot_n, rank, iter](Scal* s) {
+        if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = iter ? s->tot[1] : 0.0; }
+      });
+      barrier();
+    }
+  }
+  if (rank == 0 && tid == 0) {
+    if (failed) atomicOr(a.status, 1);
+    atomicMax(a.status + 1, iters_max);
+    if (a.mode == SWEEP_ITER) {
+      double num = 0.0, den = 0.0;
+      for (int n = 1; n <= a.N; ++n) {
+        den = fmax(den, a.norms[2 * n]);
+        if (n >= a.n_first + 1) num = fmax(num, a.norms[2 * n + 1]);
+      }
+      a.defect[0] = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
+    }
+  }
+}
+
+static int launch_sweep_global(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s) {
+  const int M = g->M;
+  const size_t MM = (size_t)M * M;
+  int rc = ensure(const_cast<bs_grid*>(g)->ws_coarse, 9 * MM * sizeof(float));
+  if (rc) return rc;
+  GSweepParams gp;
+  gp.d = d;
+  gp.a = a;
+  float* base = (float*)g->ws_coarse.ptr;
+  gp.w = GlobalVecs{base, base + MM, base + 2 * MM, base + 3 * MM, base + 4 * MM, base + 5 * MM,
+                    base + 6 * MM, base + 7 * MM, base + 8 * MM};
+  gp.M = M;
+  gp.h = (float)(g->xmax / (M - 1));
+  for (int C : {16, 8}) {
+    gp.C = C;
+    if (C > 8) {
+      cudaError_t e = cudaFuncSetAttribute(sweep_global_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) { cudaGetLastError(); continue; }
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(kGThreads, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, sweep_global_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    BS_CUDA_TRY(cudaLaunchKernelEx(&cfg, sweep_global_kernel, gp));
+    return BS_OK;
+  }
+  return set_error(BS_ERR_CUDA, "coarse propagator: no cluster shape available for M=%d", M);
+}
+
 int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s) {
   SweepParams sp;
   sp.d = d;
   sp.a = a;
   sp.sh = g->shape;
   sp.h = (float)(g->xmax / (g->M - 1));
-  if (sp.sh.C < 1 || sp.sh.C > kMaxCluster)
-    return set_error(BS_ERR_ARG, "coarse propagator: grid M=%d not supported", g->M);
+  if (sp.sh.C < 1 || sp.sh.C > kMaxCluster) return launch_sweep_global(g, d, a, s);
   switch (sp.sh.ncol) {
     case 32: return launch_sweep_k<BandCfg<32, 256, 4>>(sp, s);
     case 64: return launch_sweep_k<BandCfg<64, 512, 8>>(sp, s);

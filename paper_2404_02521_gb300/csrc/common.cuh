@@ -204,6 +204,7 @@ struct bs_grid {
   double* dnorms;              // device: per-slice squared norms / defects
   bsp::Workspace ws_par;       // Parareal F / Gold buffers
   bsp::Workspace ws_fine;      // tile fine stepper (M > 256): ping-pong hi, lo, increment
+  bsp::Workspace ws_coarse;    // global-memory coarse solver (M > 256): Krylov vectors
   // cached contraction
   double q_key[6];
   double q_val;

@@ -22,7 +22,7 @@ def bs():
     return bs
 
 
-@pytest.mark.parametrize("M,pi", [(33, 0), (64, 1), (100, 2), (200, 0), (256, 1)])
+@pytest.mark.parametrize("M,pi", [(33, 0), (64, 1), (100, 2), (200, 0), (256, 1), (300, 2), (512, 1)])
 def test_coarse_matches_oracle(bs, M, pi):
     import torch
     P = [wl.Params(0.3, 0.2, 0.5, 0.05, payoff=wl.BASKET),
@@ -106,6 +106,21 @@ def test_exact_prefix_on_gpu(bs):
         rc, k, _, U = gpu_parareal(bs, pb, 0.0, K)
         assert k == K
         assert torch.equal(U[: K + 1], S[: K + 1]), K
+
+
+def test_parareal_large_grid(bs):
+    # M = 300: tile fine stepper and the global-memory coarse solver
+    import torch
+    pb = wl.Problem("exchange300", 300, 4.0, 4, 256, 2,
+                    wl.Params(0.1, 0.12, 0.7, 0.03, 0.25, payoff=wl.EXCHANGE))
+    rc, k, defects, U = gpu_parareal(bs, pb, 1e-4, pb.N)
+    assert rc == 0 and k < pb.N
+    serial = fd.serial_fine(pb)
+    assert rel_err(to_np(U), serial) <= 1e-3
+    rc, k, _, U = gpu_parareal(bs, pb, 0.0, pb.N)
+    S = gpu_serial_fine(bs, pb)
+    assert torch.equal(U, S)
+    assert rel_err(to_np(S), serial) <= FP32_FINE_TOL
 
 
 def test_maxiter_status(bs):
