@@ -159,15 +159,34 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  *  BS_OPT_KRYLOV_MAXIT   iteration cap of a coarse BiCGSTAB solve (default 400)
  *  BS_OPT_PHASE_TIMING   1: parareal_solve brackets its fine and coarse launches with CUDA
  *                        events on the caller's stream (read back by bs_phase_stats); 0: off
+ *  BS_OPT_COARSE_VARIANT  -1 (default): the coarse sweep of grids with M <= 256 uses the band
+ *                        variant measured fastest for that M (bs_coarse_variant); k >= 0:
+ *                        always variant k (it must fit the grid, else the launch fails with
+ *                        BS_ERR_ARG).  Variants differ only in work split and reduction order.
  * Returns BS_OK or BS_ERR_ARG for an unknown option or an out-of-range value. */
 enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
-       BS_OPT_KRYLOV_MAXIT = 3, BS_OPT_PHASE_TIMING = 4, BS_OPT_JACOBI_TARGET_COLD = 5 };
+       BS_OPT_KRYLOV_MAXIT = 3, BS_OPT_PHASE_TIMING = 4, BS_OPT_JACOBI_TARGET_COLD = 5,
+       BS_OPT_COARSE_VARIANT = 6 };
 int bs_set_option(int option, double value);
 
+/* Coarse-sweep autotuner (no counterpart in the paper, which has one CPU code path).  For
+ * M <= 256 the serial coarse sweep runs on one thread-block cluster; the band variants
+ * (columns per CTA, threads per CTA, rows per thread, hence cluster size) trade per-iteration
+ * arithmetic against cluster-barrier latency.  The first coarse launch on a grid times each
+ * variant that the device can launch on a short PROP solve from the payoff of p with coarse
+ * step dtau_coarse, and caches the fastest per (device, M) for the process; this call runs
+ * that measurement now (if not already done) and returns the chosen variant index in
+ * *variant (-1 for M > 256, which uses the global-memory solver).  Synchronous on `stream`;
+ * allocates and frees two M*M FP32 buffers.  Returns BS_OK, BS_ERR_ARG or BS_ERR_CUDA. */
+int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* variant,
+                      bs_stream stream);
+
 /* Diagnostics of the coarse solves enqueued on this grid since the last parareal_solve or
- * bs_grid_stats call: the largest BiCGSTAB iteration count and whether any solve hit its
- * cap.  Synchronous (waits for the device), then resets the counters. */
-int bs_grid_stats(bs_grid* g, int* krylov_iters_max, int* krylov_failed);
+ * bs_grid_stats call: the largest BiCGSTAB iteration count, whether any solve hit its cap,
+ * the summed iteration count and the number of implicit-Euler solves.  Any output pointer
+ * may be NULL.  Synchronous (waits for the device), then resets the counters. */
+int bs_grid_stats(bs_grid* g, int* krylov_iters_max, int* krylov_failed, int* krylov_iters_total,
+                  int* krylov_solves);
 
 /* Per-phase accounting on this grid since the last call: kernel launches of the fine
  * propagator, of the coarse propagator / serial Parareal sweep, and of everything else

@@ -5,16 +5,16 @@ is its thin Python binding.  Importing a function that needs the library loads i
 loudly if it cannot be built or loaded.
 """
 from ._lib import (BASKET, CALL1, CASH_OR_NOTHING, COARSE_NUM, COARSE_PINO, EXCHANGE, EXPORTS,
-                   BSError, Grid, Pino, bs_fine_sweeps, bs_grid_stats, bs_payoff, bs_phase_stats, bs_set_option,
-                   OPT_PHASE_TIMING, PARAREAL_USER_U0,
-                   OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_MAXIT, OPT_KRYLOV_TOL, coarse_propagate,
-                   fine_propagate_batched, last_error, load, parareal_solve, parareal_solve_noalloc,
-                   to_params)
+                   OPT_COARSE_VARIANT, OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_JACOBI_TARGET_COLD,
+                   OPT_KRYLOV_MAXIT, OPT_KRYLOV_TOL, OPT_PHASE_TIMING, PARAREAL_USER_U0, BSError,
+                   Grid, Pino, bs_coarse_variant, bs_fine_sweeps, bs_grid_stats, bs_payoff,
+                   bs_phase_stats, bs_set_option, coarse_propagate, fine_propagate_batched,
+                   last_error, load, parareal_solve, parareal_solve_noalloc, to_params)
 
 __all__ = ["BASKET", "CALL1", "CASH_OR_NOTHING", "COARSE_NUM", "COARSE_PINO", "EXCHANGE",
-           "EXPORTS", "BSError", "Grid", "Pino", "bs_fine_sweeps", "bs_grid_stats", "bs_payoff", "bs_phase_stats",
-           "OPT_PHASE_TIMING", "PARAREAL_USER_U0",
-           "bs_set_option", "OPT_FINE_SWEEPS", "OPT_JACOBI_TARGET", "OPT_KRYLOV_MAXIT", "OPT_KRYLOV_TOL",
-           "coarse_propagate", "fine_propagate_batched", "last_error", "load", "parareal_solve",
-           "parareal_solve_noalloc",
-           "to_params"]
+           "EXPORTS", "OPT_COARSE_VARIANT", "OPT_FINE_SWEEPS", "OPT_JACOBI_TARGET",
+           "OPT_JACOBI_TARGET_COLD", "OPT_KRYLOV_MAXIT", "OPT_KRYLOV_TOL", "OPT_PHASE_TIMING",
+           "PARAREAL_USER_U0", "BSError", "Grid", "Pino", "bs_coarse_variant", "bs_fine_sweeps",
+           "bs_grid_stats", "bs_payoff", "bs_phase_stats", "bs_set_option", "coarse_propagate",
+           "fine_propagate_batched", "last_error", "load", "parareal_solve",
+           "parareal_solve_noalloc", "to_params"]

@@ -22,9 +22,11 @@ COARSE_NUM, COARSE_PINO = 0, 1
 # exported entry points declared in include/bsparareal.h
 EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
-           "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc"]
+           "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
+           "bs_coarse_variant"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
+OPT_COARSE_VARIANT = 6
 PARAREAL_USER_U0 = 0x100
 
 
@@ -69,7 +71,8 @@ def load(path: Optional[str] = None):
     lib.parareal_solve.argtypes = [vp, P(bs_params), i, i, i, i, vp, d, i, vp, P(i), P(d), vp]
     lib.bs_fine_sweeps.argtypes = [vp, P(bs_params), d, i]
     lib.bs_set_option.argtypes = [i, d]
-    lib.bs_grid_stats.argtypes = [vp, P(i), P(i)]
+    lib.bs_grid_stats.argtypes = [vp, P(i), P(i), P(i), P(i)]
+    lib.bs_coarse_variant.argtypes = [vp, P(bs_params), d, P(i), vp]
     lib.bs_phase_stats.argtypes = [vp, P(d), P(i), P(d), P(i), P(i)]
     lib.parareal_solve_noalloc.argtypes = [i, d, P(bs_params), i, i, i, d, i, vp, P(i), P(d), vp]
     for name in EXPORTS:
@@ -191,10 +194,21 @@ def bs_set_option(option: int, value: float):
     return check(load().bs_set_option(int(option), float(value)))
 
 
-def bs_grid_stats(g: Grid):
-    """(max BiCGSTAB iterations, any solve hit its cap) since the last reset."""
-    it, fail = C.c_int(0), C.c_int(0)
-    check(load().bs_grid_stats(g.h, C.byref(it), C.byref(fail)))
+def bs_coarse_variant(g: Grid, p, dtau_coarse: float, stream=None) -> int:
+    """Coarse band variant used on this grid (measured on first use; -1 for M > 256)."""
+    bp = to_params(p)
+    v = C.c_int(-1)
+    check(load().bs_coarse_variant(g.h, C.byref(bp), float(dtau_coarse), C.byref(v), _stream(stream)))
+    return v.value
+
+
+def bs_grid_stats(g: Grid, detail: bool = False):
+    """(max BiCGSTAB iterations, any solve hit its cap) since the last reset; with detail,
+    also (summed iterations, number of implicit solves)."""
+    it, fail, tot, ns = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
+    check(load().bs_grid_stats(g.h, C.byref(it), C.byref(fail), C.byref(tot), C.byref(ns)))
+    if detail:
+        return it.value, bool(fail.value), tot.value, ns.value
     return it.value, bool(fail.value)
 
 

@@ -157,8 +157,8 @@ int bs_grid_create(int M, double xmax, bs_grid** out) {
   std::memset(g->q_key, 0, sizeof(g->q_key));
   g->q_val = 0.0;
   cudaError_t e = cudaGetDevice(&g->device);
-  if (e == cudaSuccess) e = cudaMalloc(&g->status, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(g->status, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->status, kStatusWords * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->status, 0, kStatusWords * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->dscal, 8 * sizeof(double));
   g->dnorms = nullptr;
   if (e != cudaSuccess) {
@@ -224,7 +224,7 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* co
                                     cudaMemcpyDeviceToDevice, s));
     return BS_OK;
   }
-  const_cast<bs_grid*>(g)->n_fine += fine_launches(g, B, nsteps);
+  const_cast<bs_grid*>(g)->n_fine += fine_launches(g, items.data(), B, nsteps);
   return launch_fine(g, items.data(), B, nsteps, s);
 }
 
@@ -276,6 +276,11 @@ int bs_set_option(int option, double value) {
       if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_JACOBI_TARGET_COLD must be in (0, 1)");
       g_opt.jacobi_target_cold = value;
       return BS_OK;
+    case BS_OPT_COARSE_VARIANT:
+      if (!(value == std::floor(value) && value >= -1.0 && value < 64.0))
+        return set_error(BS_ERR_ARG, "BS_OPT_COARSE_VARIANT must be -1 or a variant index");
+      g_opt.coarse_variant = (int)value;
+      return BS_OK;
     case BS_OPT_KRYLOV_TOL:
       if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_KRYLOV_TOL must be in (0, 1)");
       g_opt.krylov_tol = value;
@@ -291,13 +296,32 @@ int bs_set_option(int option, double value) {
   return set_error(BS_ERR_ARG, "bs_set_option: unknown option %d", option);
 }
 
-int bs_grid_stats(bs_grid* g, int* krylov_iters_max, int* krylov_failed) {
+int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* variant,
+                      bs_stream stream) {
+  if (!g || !variant) return set_error(BS_ERR_ARG, "bs_coarse_variant: NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!(dtau_coarse > 0.0)) return set_error(BS_ERR_ARG, "bs_coarse_variant: dtau_coarse <= 0");
+  *variant = -1;
+  if (g->M > 256) return BS_OK;
+  if (g->coarse_variant < 0) {
+    rc = coarse_autotune(g, make_item(*p, 0.0, dtau_coarse), (cudaStream_t)stream, 4, nullptr);
+    if (rc) return rc;
+  }
+  *variant = g->coarse_variant;
+  return BS_OK;
+}
+
+int bs_grid_stats(bs_grid* g, int* krylov_iters_max, int* krylov_failed, int* krylov_iters_total,
+                  int* krylov_solves) {
   if (!g) return set_error(BS_ERR_ARG, "bs_grid_stats: NULL grid");
-  int h[2] = {0, 0};
-  BS_CUDA_TRY(cudaMemcpy(h, g->status, 2 * sizeof(int), cudaMemcpyDeviceToHost));
-  BS_CUDA_TRY(cudaMemset(g->status, 0, 2 * sizeof(int)));
+  int h[kStatusWords] = {};
+  BS_CUDA_TRY(cudaMemcpy(h, g->status, kStatusWords * sizeof(int), cudaMemcpyDeviceToHost));
+  BS_CUDA_TRY(cudaMemset(g->status, 0, kStatusWords * sizeof(int)));
   if (krylov_iters_max) *krylov_iters_max = h[1];
   if (krylov_failed) *krylov_failed = h[0] & 1;
+  if (krylov_iters_total) *krylov_iters_total = h[2];
+  if (krylov_solves) *krylov_solves = h[3];
   return BS_OK;
 }
 
@@ -391,7 +415,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
     g->n_coarse += 1;
     return pino_sweep(pnet, g, d, sa, partials, s);
   };
-  BS_CUDA_TRY(cudaMemsetAsync(g->status, 0, 2 * sizeof(int), s));
+  BS_CUDA_TRY(cudaMemsetAsync(g->status, 0, kStatusWords * sizeof(int), s));
   PhaseTimer tf, tc;
   tf.on = tc.on = g_opt.phase_timing != 0;
 
@@ -443,7 +467,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
     rc = launch_fine(g, items.data(), B, fine_steps, s);
     if (rc) return rc;
     if ((rc = tf.end(s))) return rc;
-    g->n_fine += fine_launches(g, B, fine_steps);
+    g->n_fine += fine_launches(g, items.data(), B, fine_steps);
     a.mode = SWEEP_ITER;
     a.n_first = k;
     if ((rc = tc.begin(s))) return rc;

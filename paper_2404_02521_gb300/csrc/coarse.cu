@@ -7,12 +7,14 @@
 // models in single precision, Sec. 4.1).  One thread-block cluster holds the whole state and
 // the two matrix-vector operands in shared memory (band layout of band.cuh).
 //
-// Reductions: per-thread partial sums in FP32 (FP64 for the Parareal defect norms), a warp
-// butterfly, then one warp per CTA adds the warp partials and the CTAs' partials in FP64.
-// A butterfly adds the same two operands on both lanes of every pair, so all lanes -- and
-// all CTAs, which read the same partials in the same order -- get bitwise the same total.
-// The BiCGSTAB scalars (alpha, omega, beta) are computed once per CTA by that warp and
-// broadcast through shared memory (FP64 arithmetic on every thread would be slow here).
+// Reductions: per-thread partial sums, a warp butterfly, then one warp per CTA adds the warp
+// partials of all CTAs in a fixed order -- in FP32 for the Krylov dot products, in FP64 for
+// the Parareal defect norms.  A butterfly adds the same two operands on both lanes of every
+// pair, so all lanes -- and all CTAs, which read the same partials in the same order -- get
+// bitwise the same total.  The BiCGSTAB scalars (alpha, omega, beta) are computed once per
+// CTA by that warp and broadcast through shared memory.  FP64 is kept off the iteration: at
+// this GPU's FP64 rate, FP64 butterflies and divisions on one warp cost more than the rest of
+// an iteration.
 //
 // The serial Parareal sweep of eq. (parareal) runs in the same kernel: for n = n_first..N-1
 //   G_new = G(u_n^{k+1});  u_{n+1}^{k+1} = F_n + (G_new - G_old_n);  G_old_n = G_new,
@@ -21,6 +23,9 @@
 // evaluated as F + (G_new - G_old) so that an unchanged slice gives a zero bracket exactly.
 #include <cmath>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "band.cuh"
 
@@ -33,13 +38,20 @@ struct SweepParams {
   float h;
 };
 
-// BiCGSTAB scalar state shared by a CTA (identical in every CTA of the cluster).
+// BiCGSTAB scalar state shared by a CTA (identical in every CTA of the cluster).  The
+// Krylov dot products and scalars are FP32 like the vectors; only the Parareal norms are
+// FP64 (tot), since FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU
+// and sits on the serial path of every iteration.
 struct Scal {
-  double tot[4];
-  double rho, alpha, omega, stop2, tol;
+  double tot[4];    // FP64 totals of the last cluster_sum<double>
+  float totf[4];    // FP32 totals of the last cluster_sum<float>
+  float rho, alpha, omega, stop2;
   float af, of, bf;
   int conv, fail;
 };
+
+__device__ __forceinline__ double* scal_tot(Scal* s, double) { return s->tot; }
+__device__ __forceinline__ float* scal_tot(Scal* s, float) { return s->totf; }
 
 // Jacobi-scaled operator A^ y = y - invd * (off-diagonal part of dtau R_h) y on the thread's
 // column strip; zero on non-interior nodes (invd = 0 and y = 0 there).
@@ -77,41 +89,70 @@ __device__ __forceinline__ T warp_butterfly(T x) {
 // butterfly and stores the warp partial into slot (rank, warp) of every CTA of the cluster;
 // after one cluster barrier, warp 0 of every CTA adds the C * NW partials in a fixed order
 // (lane l takes entries l, l+32, ...; then a butterfly), so every CTA gets bitwise the same
-// FP64 totals in sc->tot.  `fin(sc)` then runs once per CTA (thread 0) before the closing
-// CTA barrier.  `round` alternates two slot arrays so that a fast CTA never overwrites
-// partials that a slow CTA is still adding.
+// totals in scal_tot(sc) (type T).  `fin(sc)` then runs once per CTA (thread 0) before the
+// closing CTA barrier.  `round` alternates two slot arrays so that a fast CTA never
+// overwrites partials that a slow CTA is still adding.
 template <class CFG, int NV, class T, class Fin>
 __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, const T (&v)[NV], double* slots,
                                             Scal* sc, int& round, int rank, int C, Fin fin) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* slot = slots + (round & 1) * (kMaxCluster * CFG::NW * 4);
+  T* slot = reinterpret_cast<T*>(slots) + (round & 1) * (kMaxCluster * CFG::NW * 4);
   T x[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) x[q] = warp_butterfly<T>(v[q]);
   if (lane < C) {
-    double* dst = (C > 1 ? cl.map_shared_rank(slot, lane) : slot) + (rank * CFG::NW + warp) * 4;
+    T* dst = (C > 1 ? cl.map_shared_rank(slot, lane) : slot) + (rank * CFG::NW + warp) * 4;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) dst[q] = (double)x[q];
+    for (int q = 0; q < NV; ++q) dst[q] = x[q];
   }
   if (C > 1) cl.sync(); else __syncthreads();
   if (warp == 0) {
     const int n = C * CFG::NW;
-    double tot[NV];
+    T tot[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double acc = 0.0;
+      T acc = T(0);
       for (int i = lane; i < n; i += 32) acc += slot[i * 4 + q];
-      tot[q] = warp_butterfly<double>(acc);
+      tot[q] = warp_butterfly<T>(acc);
     }
     if (lane == 0) {
+      T* out = scal_tot(sc, T(0));
 #pragma unroll
-      for (int q = 0; q < NV; ++q) sc->tot[q] = tot[q];
+      for (int q = 0; q < NV; ++q) out[q] = tot[q];
       fin(sc);
     }
   }
   __syncthreads();
   ++round;
 }
+
+// BiCGSTAB scalar updates shared by the band and global kernels (run by one thread per CTA).
+struct KrylovFin {
+  // start: totf = {(b^, b^), (r, r)}
+  static __device__ __forceinline__ void start(Scal* s, float tol) {
+    s->rho = s->totf[1];
+    s->stop2 = tol * tol * s->totf[0];
+    s->conv = s->totf[1] <= s->stop2 || !(s->totf[0] > 1e-30f);
+    s->fail = 0;
+    s->alpha = s->omega = 1.f;
+  }
+  // after v = A^ p: totf = {(r^, v), (r, r)}
+  static __device__ __forceinline__ void alpha(Scal* s) {
+    if (s->totf[1] <= s->stop2) { s->conv = 1; return; }
+    if (s->totf[0] == 0.f) { s->fail = 1; return; }
+    s->alpha = s->rho / s->totf[0];
+    s->af = s->alpha;
+  }
+  // after t = A^ s: totf = {(t, s), (t, t), (r^, s), (r^, t)}
+  static __device__ __forceinline__ void omega(Scal* s) {
+    s->omega = s->totf[1] > 0.f ? s->totf[0] / s->totf[1] : 0.f;
+    s->of = s->omega;
+    const float rho_new = s->totf[2] - s->omega * s->totf[3];
+    if (s->omega == 0.f || s->rho == 0.f) { s->fail = 1; s->bf = 0.f; return; }
+    s->bf = (rho_new / s->rho) * (s->alpha / s->omega);
+    s->rho = rho_new;
+  }
+};
 
 template <class CFG>
 __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_constant__ SweepParams sp) {
@@ -162,9 +203,9 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
   const float rdt = (float)(d.r * d.dtau);
-  const double tol = a.tol;
+  const float tol = (float)a.tol;
   int round = 0;
-  int iters_max = 0;
+  int iters_max = 0, iters_total = 0, nsolves = 0;
   bool failed = false;
 
   // initial state of the first slice (own rows and halo rows)
@@ -221,13 +262,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         }
         // every CTA has finished reading P before the barrier inside the reduction below;
         // P is rewritten only after it
-        cluster_sum<CFG, 2>(cluster, part, slots, sc, round, rank, C, [tol](Scal* s) {
-          s->rho = s->tot[1];
-          s->stop2 = tol * tol * s->tot[0];
-          s->conv = s->tot[1] <= s->stop2 || s->tot[0] <= 1e-60;
-          s->fail = 0;
-          s->alpha = s->omega = 1.0;
-        });
+        cluster_sum<CFG, 2>(cluster, part, slots, sc, round, rank, C,
+                            [tol](Scal* s) { KrylovFin::start(s, tol); });
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           band_store<CFG>(P, pP, r0 + k, col, rr[k]);
@@ -248,12 +284,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             p1[0] = fmaf(RH[(r0 + k + 1) * NCOL + col], vv[k], p1[0]);
             p1[1] = fmaf(rr[k], rr[k], p1[1]);
           }
-          cluster_sum<CFG, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) {
-            if (s->tot[1] <= s->stop2) { s->conv = 1; return; }
-            if (s->tot[0] == 0.0) { s->fail = 1; return; }
-            s->alpha = s->rho / s->tot[0];
-            s->af = (float)s->alpha;
-          });
+          cluster_sum<CFG, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
           if (sc->conv || sc->fail) break;
           const float af = sc->af;
           // s = r - alpha v
@@ -272,14 +303,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             p2[2] = fmaf(rh, sv, p2[2]);
             p2[3] = fmaf(rh, tt[k], p2[3]);
           }
-          cluster_sum<CFG, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) {
-            s->omega = s->tot[1] > 0.0 ? s->tot[0] / s->tot[1] : 0.0;
-            s->of = (float)s->omega;
-            const double rho_new = s->tot[2] - s->omega * s->tot[3];
-            if (s->omega == 0.0 || s->rho == 0.0) { s->fail = 1; s->bf = 0.f; return; }
-            s->bf = (float)((rho_new / s->rho) * (s->alpha / s->omega));
-            s->rho = rho_new;
-          });
+          cluster_sum<CFG, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
           const float of = sc->of, bf = sc->bf;
           // x += alpha p + omega s ;  r = s - omega t ;  p = r + beta (p - omega v)
 #pragma unroll
@@ -295,6 +319,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         }
         if (!sc->conv) failed = true;
         iters_max = it > iters_max ? it : iters_max;
+        iters_total += it;
+        ++nsolves;
 #pragma unroll
         for (int k = 0; k < K; ++k) xw[k] = x[k];
         // u^{m+1} = w + d (d = 0 off the PDE rows, whose values already hold g(tau_new))
@@ -369,6 +395,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   if (rank == 0 && tid == 0) {
     if (failed) atomicOr(a.status, 1);
     atomicMax(a.status + 1, iters_max);
+    atomicAdd(a.status + 2, iters_total);
+    atomicAdd(a.status + 3, nsolves);
     if (a.mode == SWEEP_ITER) {
       double num = 0.0, den = 0.0;
       for (int n = 1; n <= a.N; ++n) {
@@ -466,11 +494,11 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   const size_t e0 = (size_t)j0 * M, e1 = (size_t)j1 * M;
   const PayoffF pf = make_payoff(d);
   const float rdt = (float)(d.r * d.dtau);
-  const double tol = a.tol;
+  const float tol = (float)a.tol;
   __shared__ double slots[2 * kMaxCluster * GCfg::NW * 4];
   __shared__ Scal scs;
   Scal* sc = &scs;
-  int round = 0, iters_max = 0;
+  int round = 0, iters_max = 0, iters_total = 0, nsolves = 0;
   bool failed = false;
   auto barrier = [&]() { __threadfence(); cluster_barrier(cluster, C); };
 
@@ -517,13 +545,8 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
           part[0] = fmaf(bh, bh, part[0]);
           part[1] = fmaf(rr, rr, part[1]);
         }
-        cluster_sum<GCfg, 2>(cluster, part, slots, sc, round, rank, C, [tol](Scal* s) {
-          s->rho = s->tot[1];
-          s->stop2 = tol * tol * s->tot[0];
-          s->conv = s->tot[1] <= s->stop2 || s->tot[0] <= 1e-60;
-          s->fail = 0;
-          s->alpha = s->omega = 1.0;
-        });
+        cluster_sum<GCfg, 2>(cluster, part, slots, sc, round, rank, C,
+                             [tol](Scal* s) { KrylovFin::start(s, tol); });
         for (size_t e = e0 + tid; e < e1; e += kGThreads) w.p[e] = w.r[e];
         barrier();
         int it = 0;
@@ -543,12 +566,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
             p1[0] = fmaf(w.rh[e], vv, p1[0]);
             p1[1] = fmaf(rr, rr, p1[1]);
           }
-          cluster_sum<GCfg, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) {
-            if (s->tot[1] <= s->stop2) { s->conv = 1; return; }
-            if (s->tot[0] == 0.0) { s->fail = 1; return; }
-            s->alpha = s->rho / s->tot[0];
-            s->af = (float)s->alpha;
-          });
+          cluster_sum<GCfg, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
           if (sc->conv || sc->fail) break;
           const float af = sc->af;
           for (size_t e = e0 + tid; e < e1; e += kGThreads) w.s[e] = fmaf(-af, w.v[e], w.r[e]);
@@ -569,14 +587,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
             p2[2] = fmaf(rh, sv, p2[2]);
             p2[3] = fmaf(rh, tt, p2[3]);
           }
-          cluster_sum<GCfg, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) {
-            s->omega = s->tot[1] > 0.0 ? s->tot[0] / s->tot[1] : 0.0;
-            s->of = (float)s->omega;
-            const double rho_new = s->tot[2] - s->omega * s->tot[3];
-            if (s->omega == 0.0 || s->rho == 0.0) { s->fail = 1; s->bf = 0.f; return; }
-            s->bf = (float)((rho_new / s->rho) * (s->alpha / s->omega));
-            s->rho = rho_new;
-          });
+          cluster_sum<GCfg, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
           const float of = sc->of, bf = sc->bf;
           for (size_t e = e0 + tid; e < e1; e += kGThreads) {
             const float sv = w.s[e], pv = w.p[e], tt = w.t[e];
@@ -590,6 +601,8 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
         }
         if (!sc->conv) failed = true;
         iters_max = it > iters_max ? it : iters_max;
+        iters_total += it;
+        ++nsolves;
         for (size_t e = e0 + tid; e < e1; e += kGThreads) w.u[e] += w.x[e];
         barrier();
       }
@@ -629,6 +642,8 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   if (rank == 0 && tid == 0) {
     if (failed) atomicOr(a.status, 1);
     atomicMax(a.status + 1, iters_max);
+    atomicAdd(a.status + 2, iters_total);
+    atomicAdd(a.status + 3, nsolves);
     if (a.mode == SWEEP_ITER) {
       double num = 0.0, den = 0.0;
       for (int n = 1; n <= a.N; ++n) {
@@ -681,20 +696,208 @@ static int launch_sweep_global(const bs_grid* g, const ItemDesc& d, const SweepA
   return set_error(BS_ERR_CUDA, "coarse propagator: no cluster shape available for M=%d", M);
 }
 
+// ---------------------------------------------------------------------------------------
+// Band variants of the cluster-resident coarse sweep.  A variant fixes the columns per CTA
+// (NCOL >= M), the threads per CTA and the rows per thread; its cluster size follows from M.
+// More CTAs per system shorten the arithmetic of each BiCGSTAB iteration but not its cluster
+// barriers, so the best variant depends on M and on the machine: coarse_autotune times the
+// candidates once per M (a few short PROP solves) and caches the winner for the process, so
+// that every solve of that grid size runs the same kernel and reduction order.
+// ---------------------------------------------------------------------------------------
+struct CoarseVariant {
+  int ncol, nt, k;
+  bool is_default;   // the shape used when no measurement is available
+};
+static const CoarseVariant kCoarseVariants[] = {
+    {32, 256, 4, true},   {32, 128, 2, false},  {64, 512, 8, true},   {64, 256, 4, false},
+    {128, 512, 16, true}, {128, 512, 4, false}, {256, 512, 16, true}, {256, 512, 8, false}};
+constexpr int kNumCoarseVariants = (int)(sizeof(kCoarseVariants) / sizeof(kCoarseVariants[0]));
+
+static int variant_ncol(int M) {
+  return M <= 32 ? 32 : M <= 64 ? 64 : M <= 128 ? 128 : M <= 256 ? 256 : 0;
+}
+
+static BandShape variant_shape(int v, int M) {
+  const CoarseVariant& cv = kCoarseVariants[v];
+  BandShape sh = {};
+  sh.M = M;
+  sh.ncol = cv.ncol;
+  sh.G = cv.nt / cv.ncol;
+  sh.K = cv.k;
+  sh.BH = sh.G * sh.K;
+  sh.C = (M + sh.BH - 1) / sh.BH;
+  return sh;
+}
+
+static bool variant_fits(int v, int M) {
+  return kCoarseVariants[v].ncol == variant_ncol(M) && variant_shape(v, M).C <= kMaxCluster;
+}
+
+static int launch_variant(int v, SweepParams sp, cudaStream_t s) {
+  sp.sh = variant_shape(v, sp.sh.M);
+  switch (v) {
+    case 0: return launch_sweep_k<BandCfg<32, 256, 4>>(sp, s);
+    case 1: return launch_sweep_k<BandCfg<32, 128, 2>>(sp, s);
+    case 2: return launch_sweep_k<BandCfg<64, 512, 8>>(sp, s);
+    case 3: return launch_sweep_k<BandCfg<64, 256, 4>>(sp, s);
+    case 4: return launch_sweep_k<BandCfg<128, 512, 16>>(sp, s);
+    case 5: return launch_sweep_k<BandCfg<128, 512, 4>>(sp, s);
+    case 6: return launch_sweep_k<BandCfg<256, 512, 16>>(sp, s);
+    case 7: return launch_sweep_k<BandCfg<256, 512, 8>>(sp, s);
+  }
+  return set_error(BS_ERR_ARG, "coarse propagator: no band variant %d", v);
+}
+
+// Whether the device can hold one cluster of the variant (clusters above 8 CTAs are
+// non-portable and depend on the GPC layout).
+template <class CFG>
+static bool cluster_fits(const BandShape& sh) {
+  const size_t smem = (size_t)4 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
+                      (size_t)CFG::BH * sizeof(float2) +
+                      (2 * kMaxCluster * CFG::NW * 4) * sizeof(double) + sizeof(Scal);
+  auto kern = sweep_band_kernel<CFG>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      (sh.C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sh.C, 1, 1);
+  cfg.blockDim = dim3(CFG::NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = sh.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
+}
+
+static bool variant_launchable(int v, int M) {
+  if (!variant_fits(v, M)) return false;
+  const BandShape sh = variant_shape(v, M);
+  switch (v) {
+    case 0: return cluster_fits<BandCfg<32, 256, 4>>(sh);
+    case 1: return cluster_fits<BandCfg<32, 128, 2>>(sh);
+    case 2: return cluster_fits<BandCfg<64, 512, 8>>(sh);
+    case 3: return cluster_fits<BandCfg<64, 256, 4>>(sh);
+    case 4: return cluster_fits<BandCfg<128, 512, 16>>(sh);
+    case 5: return cluster_fits<BandCfg<128, 512, 4>>(sh);
+    case 6: return cluster_fits<BandCfg<256, 512, 16>>(sh);
+    case 7: return cluster_fits<BandCfg<256, 512, 8>>(sh);
+  }
+  return false;
+}
+
+static int default_variant(int M) {
+  for (int v = 0; v < kNumCoarseVariants; ++v)
+    if (kCoarseVariants[v].is_default && variant_fits(v, M)) return v;
+  return -1;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_tuned;   // (device, M) -> variant
+
+int coarse_cached_variant(int device, int M) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find({device, M});
+  return it != g_tuned.end() ? it->second : default_variant(M);
+}
+
+// Times every launchable variant on a PROP solve of `steps` coarse steps from the payoff
+// state of d (best of three after one warm-up) and caches the fastest for (device, M).
+int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, int* chosen) {
+  const int M = g->M;
+  const size_t MM = (size_t)M * M;
+  float* buf = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = default_variant(M);
+  float best_ms = 1e30f;
+  int rc = BS_OK;
+  if (cudaMalloc(&buf, 2 * MM * sizeof(float)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    rc = cuda_error(cudaGetLastError(), "coarse_autotune");
+  }
+  if (rc == BS_OK) rc = launch_payoff(g, d, buf, s);
+  for (int v = 0; rc == BS_OK && v < kNumCoarseVariants; ++v) {
+    if (!variant_launchable(v, M)) continue;
+    SweepParams sp;
+    sp.d = d;
+    sp.d.tau0 = 0.0;
+    sp.a = SweepArgs{};
+    sp.a.mode = SWEEP_PROP;
+    sp.a.N = 1;
+    sp.a.csteps = steps;
+    sp.a.in = buf;
+    sp.a.out = buf + MM;
+    sp.a.status = g->status;
+    sp.a.tol = g_opt.krylov_tol;
+    sp.a.maxit = g_opt.krylov_maxit;
+    sp.sh.M = M;
+    sp.h = (float)(g->xmax / (M - 1));
+    float t_min = 1e30f;
+    for (int rep = 0; rc == BS_OK && rep < 4; ++rep) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) { rc = cuda_error(cudaGetLastError(), "coarse_autotune"); break; }
+      if ((rc = launch_variant(v, sp, s))) break;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = cuda_error(cudaGetLastError(), "coarse_autotune");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < t_min) t_min = ms;
+    }
+    if (rc == BS_OK && t_min < best_ms) {
+      best_ms = t_min;
+      best = v;
+    }
+  }
+  if (buf) cudaFree(buf);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  // the tuning solves' iteration counts are not the caller's
+  if (rc == BS_OK && cudaMemsetAsync(g->status, 0, kStatusWords * sizeof(int), s) != cudaSuccess)
+    rc = cuda_error(cudaGetLastError(), "coarse_autotune");
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[{g->device, M}] = best;
+  }
+  g->coarse_variant = best;
+  if (chosen) *chosen = best;
+  return BS_OK;
+}
+
 int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s) {
   SweepParams sp;
   sp.d = d;
   sp.a = a;
   sp.sh = g->shape;
   sp.h = (float)(g->xmax / (g->M - 1));
-  if (sp.sh.C < 1 || sp.sh.C > kMaxCluster) return launch_sweep_global(g, d, a, s);
-  switch (sp.sh.ncol) {
-    case 32: return launch_sweep_k<BandCfg<32, 256, 4>>(sp, s);
-    case 64: return launch_sweep_k<BandCfg<64, 512, 8>>(sp, s);
-    case 128: return launch_sweep_k<BandCfg<128, 512, 16>>(sp, s);
-    case 256: return launch_sweep_k<BandCfg<256, 512, 16>>(sp, s);
+  if (variant_ncol(g->M) == 0) return launch_sweep_global(g, d, a, s);
+  bs_grid* gm = const_cast<bs_grid*>(g);
+  if (g_opt.coarse_variant < 0 && gm->coarse_variant < 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+    if (capturing) {
+      gm->coarse_variant = coarse_cached_variant(g->device, g->M);
+    } else {
+      int rc = coarse_autotune(gm, d, s, 4, nullptr);
+      if (rc) return rc;
+    }
   }
-  return set_error(BS_ERR_ARG, "coarse propagator: no band shape for M=%d", g->M);
+  const int v = g_opt.coarse_variant >= 0 ? g_opt.coarse_variant : gm->coarse_variant;
+  if (v < 0 || v >= kNumCoarseVariants || !variant_fits(v, g->M))
+    return set_error(BS_ERR_ARG, "coarse propagator: band variant %d does not fit M=%d", v, g->M);
+  sp.sh.M = g->M;
+  return launch_variant(v, sp, s);
 }
 
 }  // namespace bsp

@@ -20,6 +20,7 @@ namespace bsp {
 constexpr int kMaxItems = 96;        // items per fine launch (kernel-parameter descriptors)
 constexpr int kThreads = 512;        // threads per CTA of the band kernels
 constexpr int kMaxCluster = 16;
+constexpr int kStatusWords = 4;   // status words of a grid (see bs_grid::status)
 
 // Per-item description carried in kernel parameters.
 struct ItemDesc {
@@ -183,6 +184,7 @@ struct Options {
   double krylov_tol = 1e-6;
   int krylov_maxit = 400;
   int phase_timing = 0;
+  int coarse_variant = -1;   // >= 0: force this coarse band variant; -1: measured per grid size
 };
 extern Options g_opt;
 
@@ -199,12 +201,14 @@ struct bs_grid {
   double xmax;
   int device;
   bsp::BandShape shape;
-  int* status;                 // device: [0] bit 0 = Krylov cap hit, [1] max iterations
+  int* status;                 // device int[kStatusWords]: [0] bit 0 = Krylov cap hit,
+                               // [1] max iterations, [2] total iterations, [3] solves
   double* dscal;               // device: scalar outputs (defect)
   double* dnorms;              // device: per-slice squared norms / defects
   bsp::Workspace ws_par;       // Parareal F / Gold buffers
   bsp::Workspace ws_fine;      // tile fine stepper (M > 256): ping-pong hi, lo, increment
   bsp::Workspace ws_coarse;    // global-memory coarse solver (M > 256): Krylov vectors
+  int coarse_variant = -1;     // band variant of the coarse sweep (-1: not chosen yet)
   // cached contraction
   double q_key[6];
   double q_val;
@@ -216,7 +220,7 @@ struct bs_grid {
 // Kernel launchers implemented in the .cu files.
 namespace bsp {
 int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s);
-int fine_launches(const bs_grid* g, int n, int nsteps);   // kernels launch_fine enqueues
+int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps);   // kernels launch_fine enqueues
 int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s);
 // Coarse numerical propagation / Parareal serial sweep (see coarse.cu).
 enum { SWEEP_PROP = 0, SWEEP_INIT = 1, SWEEP_ITER = 2 };
@@ -237,6 +241,8 @@ struct SweepArgs {
   int maxit;
 };
 int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
+int coarse_cached_variant(int device, int M);   // tuned (or default) variant, no allocation
+int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, int* chosen);
 // PINO coarse propagator (pino.cu)
 int pino_check(const bs_pino* net, int M);
 int pino_propagate(bs_pino* net, const bs_grid* g, const ItemDesc& d, const float* in, float* out,

@@ -248,13 +248,16 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
 }
 
 // ---------------------------------------------------------------------------------------
-// Tile variant for grids that do not fit a cluster (M > 256): one implicit step per launch.
-// A CTA owns a TX x TY interior tile and loads the surrounding region of (TX + 2H) x
-// (TY + 2H) nodes (H >= the step's sweep count) of hi and of the previous increment from
-// global memory.  Every sweep's result is exact one node further from the region's cut
-// edges, so after H sweeps the interior matches a whole-grid sweep bit for bit; the domain
-// edges need no halo (zero coefficients at x = 0, y = 0; Dirichlet at the far edges).  The
-// interior's (hi, lo, increment) go to the other half of a ping-pong workspace.
+// Tile variant for grids that do not fit a cluster (M > 256): one implicit step per launch,
+// or several launches per step when its sweeps exceed the halo.  A CTA owns a TX x TY
+// interior tile and loads the surrounding region of (TX + 2H) x (TY + 2H) nodes (H >= the
+// launch's sweep count) of hi and of the current increment from global memory.  Every
+// sweep's result is exact one node further from the region's cut edges, so after H sweeps
+// the interior matches a whole-grid sweep bit for bit; the domain edges need no halo (zero
+// coefficients at x = 0, y = 0; Dirichlet at the far edges).  The interior's (hi, lo,
+// increment) go to the other half of a ping-pong workspace.  A launch runs sweeps
+// [s_begin, s_end) of the step; it applies the increment to (hi, lo) only if the item's
+// step ends in it, and copies an item whose step has already ended.
 // ---------------------------------------------------------------------------------------
 struct TileBatch {
   ItemDesc it[kMaxItems];
@@ -265,7 +268,8 @@ struct TileBatch {
 
 template <class CFG>
 __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_constant__ TileBatch tb,
-                                                               int step, int first, int last, int par) {
+                                                               int step, int first, int last, int par,
+                                                               int s_begin, int s_end) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, PLANE = CFG::PLANE;
   const ItemDesc& d = tb.it[blockIdx.z];
   const int M = tb.M, H = tb.H;
@@ -327,17 +331,23 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
   const float rdt = (float)(d.r * d.dtau);
-  const int m = first ? d.sweeps0 : d.sweeps;
+  const int m_item = step == 0 ? d.sweeps0 : d.sweeps;   // the first step starts cold
+  const int nsw = max(0, min(s_end, m_item) - s_begin);
+  const bool commit = nsw > 0 && min(s_end, m_item) == m_item;
   const HaloPush none = {nullptr, nullptr};
   __syncthreads();
   int p = 0;
-  for (int s = 0; s < m; ++s) {
+  for (int s = 0; s < nsw; ++s) {
     const float* rd = p ? dB : dA;
     float* wr = p ? dA : dB;
-    if (s == 0)
+    const bool fst = s == 0, lst = commit && s == nsw - 1;
+    if (fst && lst)
+      fine_sweep<CFG, true, true>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                  cg0, cgi, rdt, false);
+    else if (fst)
       fine_sweep<CFG, true, false>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
                                    cg0, cgi, rdt, false);
-    else if (s == m - 1)
+    else if (lst)
       fine_sweep<CFG, false, true>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
                                    cg0, cgi, rdt, false);
     else
@@ -377,38 +387,56 @@ __global__ void tile_finish_kernel(const __grid_constant__ TileBatch tb) {
   if (e < MM) d.out[e] = ws[3 * MM + e] + ws[4 * MM + e];
 }
 
+// Sweeps of one step per tile launch (the halo width): larger halos leave too small an
+// interior of the 128 x 64 region.
+constexpr int kTileMaxHalo = 24;
+
+// Launches of one step whose largest sweep count is m: the step is split evenly.
+static int tile_launches_per_step(int m) { return (m + kTileMaxHalo - 1) / kTileMaxHalo; }
+
 static int launch_tiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
   const int M = g->M;
   const size_t MM = (size_t)M * M;
-  int H = 2;
-  for (int k = 0; k < n; ++k) H = std::max(H, std::max(items[k].sweeps, items[k].sweeps0));
-  if (H > 24)
-    return set_error(BS_ERR_ARG, "fine_propagate_batched: %d sweeps per step exceed the tile halo "
-                     "of large grids (24); take smaller fine steps", H);
+  int m_cold = 1, m_warm = 1;
+  for (int k = 0; k < n; ++k) {
+    m_cold = std::max(m_cold, items[k].sweeps0);
+    m_warm = std::max(m_warm, items[k].sweeps);
+  }
   int rc = ensure(const_cast<bs_grid*>(g)->ws_fine, (size_t)std::min(n, kMaxItems) * 6 * MM * sizeof(float));
   if (rc) return rc;
   const size_t smem = (size_t)3 * TileCfg::PLANE * sizeof(float) + (size_t)TileCfg::BH * sizeof(float2);
   auto kern = fine_tile_kernel<TileCfg>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int TX = TileCfg::NCOL - 2 * H, TY = TileCfg::BH - 2 * H;
   for (int base = 0; base < n; base += kMaxItems) {
     TileBatch tb;
     tb.n = std::min(n - base, kMaxItems);
     for (int k = 0; k < tb.n; ++k) tb.it[k] = items[base + k];
     tb.ws = (float*)g->ws_fine.ptr;
     tb.M = M;
-    tb.H = H;
     tb.nsteps_total = nsteps;
     tb.h = (float)(g->xmax / (M - 1));
-    const dim3 grid((M + TX - 1) / TX, (M + TY - 1) / TY, tb.n);
-    // A single step would read u_in and write u_out in the same launch (they may alias):
-    // keep its result in the workspace and form u_out in a separate pass.
-    const bool one = nsteps == 1;
+    int par = 0;
+    bool pending_finish = false;
     for (int step = 0; step < nsteps; ++step) {
-      kern<<<grid, TileCfg::NT, smem, s>>>(tb, step, step == 0, step == nsteps - 1 && !one, step & 1);
-      BS_CUDA_TRY(cudaGetLastError());
+      const int m = step == 0 ? m_cold : m_warm;
+      const int nl = tile_launches_per_step(m);
+      const int chunk = (m + nl - 1) / nl;
+      for (int l = 0; l < nl; ++l) {
+        const int s0 = l * chunk, s1 = std::min(m, s0 + chunk);
+        tb.H = std::max(2, s1 - s0);
+        const int TX = TileCfg::NCOL - 2 * tb.H, TY = TileCfg::BH - 2 * tb.H;
+        const dim3 grid((M + TX - 1) / TX, (M + TY - 1) / TY, tb.n);
+        const bool first = step == 0 && l == 0;
+        const bool final_launch = step == nsteps - 1 && l == nl - 1;
+        // A launch that reads u_in must not write u_out (they may alias): keep its result in
+        // the workspace and form u_out in a separate pass.
+        pending_finish = final_launch && first;
+        kern<<<grid, TileCfg::NT, smem, s>>>(tb, step, first, final_launch && !first, par, s0, s1);
+        BS_CUDA_TRY(cudaGetLastError());
+        par ^= 1;
+      }
     }
-    if (one) {
+    if (pending_finish) {
       tile_finish_kernel<<<dim3((unsigned)((MM + 255) / 256), tb.n), 256, 0, s>>>(tb);
       BS_CUDA_TRY(cudaGetLastError());
     }
@@ -416,10 +444,21 @@ static int launch_tiles(const bs_grid* g, const ItemDesc* items, int n, int nste
   return BS_OK;
 }
 
-int fine_launches(const bs_grid* g, int n, int nsteps) {
+int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps) {
   const int chunks = (n + kMaxItems - 1) / kMaxItems;
   if (g->shape.C >= 1 && g->shape.C <= kMaxCluster) return chunks;
-  return chunks * (nsteps + (nsteps == 1 ? 1 : 0));
+  if (nsteps < 1) return 0;
+  int total = 0;
+  for (int base = 0; base < n; base += kMaxItems) {
+    int m_cold = 1, m_warm = 1;
+    for (int k = base; k < std::min(n, base + kMaxItems); ++k) {
+      m_cold = std::max(m_cold, items[k].sweeps0);
+      m_warm = std::max(m_warm, items[k].sweeps);
+    }
+    const int first = tile_launches_per_step(m_cold);
+    total += first + (nsteps - 1) * tile_launches_per_step(m_warm) + (nsteps == 1 && first == 1 ? 1 : 0);
+  }
+  return total;
 }
 
 template <class CFG>

@@ -16,7 +16,7 @@ namespace bsp {
 
 constexpr size_t kNoAllocMaxNM2 = size_t(1) << 22;   // N * M * M <= 4,194,304
 constexpr int kNoAllocMaxN = 1024;
-constexpr size_t kNoAllocStatusOff = 0;                                  // int[2]
+constexpr size_t kNoAllocStatusOff = 0;                                  // int[kStatusWords]
 constexpr size_t kNoAllocDefectOff = 256;                                // double[8]
 constexpr size_t kNoAllocNormsOff = 512;                                 // double[2(N+1)]
 constexpr size_t kNoAllocBufOff =
@@ -94,9 +94,12 @@ extern "C" int parareal_solve_noalloc(int M, double xmax, const bs_params* p, in
   g.shape = shape;
   g.status = status;
   g.dscal = defect;
+  // the measured coarse variant if this process has one for M (tuning would allocate)
+  BS_CUDA_TRY(cudaGetDevice(&g.device));
+  g.coarse_variant = coarse_cached_variant(g.device, M);
   cudaStream_t s = (cudaStream_t)stream;
   // the array keeps the previous call's contents: the status word must start at zero
-  BS_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));
+  BS_CUDA_TRY(cudaMemsetAsync(status, 0, kStatusWords * sizeof(int), s));
 
   ItemDesc dc = make_item(*p, 0.0, slice / coarse_steps);
   if ((rc = launch_payoff(&g, dc, u_out, s))) return rc;

@@ -1,0 +1,140 @@
+"""Single-kernel workloads for profiling the library's kernels (e.g. under ncu).
+
+    python -m paper_2404_02521_gb300.kernel_cases <case> [--reps R]
+
+Each case builds its inputs on the device, runs the kernel once untimed and then R times,
+and prints the CUDA-event time per launch.  The cases are the launches of the benchmark
+workloads, one kernel each:
+
+  fine256    F on all 64 slices of the 256x256 exchange workload, 512 steps (one launch)
+  coarse256  the initial serial coarse sweep of that workload (64 slices x 4 BiCGSTAB steps)
+  tile1024   F on 48 slices of a 1024x1024 basket grid, 4 steps (haloed tiles, a launch
+             per step; 48 x 4 MB of state exceeds the 129 MB L2)
+  coarse512  coarse propagation of one 512x512 state, 4 steps (global-memory BiCGSTAB)
+  pino128    the PINO coarse propagator on 64 states of 128x128 (random weights)
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import tempfile
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _timed(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def case_fine256(bs, wl, torch):
+    pb = wl.exchange_cfg2(0.7)
+    M, N = pb.M, pb.N
+    g = bs.Grid(M, pb.xmax)
+    U = torch.empty((N, M, M), device="cuda")
+    bs.bs_payoff(g, pb.params, U[0])
+    U[1:].copy_(U[0].expand(N - 1, M, M))
+    F = torch.empty_like(U)
+    sl = pb.params.T / N
+    args = ([pb.params] * N, list(U), list(F), [n * sl for n in range(N)], [pb.dtau_fine] * N,
+            pb.fine_steps)
+    return lambda: bs.fine_propagate_batched(g, *args)
+
+
+def case_coarse256(bs, wl, torch):
+    pb = wl.exchange_cfg2(0.7)
+    g = bs.Grid(pb.M, pb.xmax)
+    U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+    bs.bs_coarse_variant(g, pb.params, pb.dtau_coarse)
+
+    def run():
+        # Kmax = 0: the payoff and the initial coarse sweep only
+        try:
+            bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM, pb.coarse_steps,
+                              None, pb.tol, 0, U)
+        except bs.BSError:
+            pass   # "tol not met after 0 iterations" is the expected status
+    return run
+
+
+def case_tile1024(bs, wl, torch):
+    p = wl.basket_cfg1().params
+    M, B, steps = 1024, 48, 4
+    g = bs.Grid(M, 4.0)
+    U = torch.empty((B, M, M), device="cuda")
+    bs.bs_payoff(g, p, U[0])
+    U[1:].copy_(U[0].expand(B - 1, M, M))
+    F = torch.empty_like(U)
+    dtau = p.T / (128 * 1024)
+    args = ([p] * B, list(U), list(F), [0.01 * n for n in range(B)], [dtau] * B, steps)
+    return lambda: bs.fine_propagate_batched(g, *args)
+
+
+def case_coarse512(bs, wl, torch):
+    p = wl.Params(0.25, 0.35, 0.7, 0.03, payoff=wl.EXCHANGE)
+    M = 512
+    g = bs.Grid(M, 4.0)
+    u = torch.empty((M, M), device="cuda")
+    bs.bs_payoff(g, p, u)
+    o = torch.empty_like(u)
+    return lambda: bs.coarse_propagate(g, bs.COARSE_NUM, None, p, u, o, 0.25, 4.0 / 256, 4)
+
+
+def case_pino128(bs, wl, torch):
+    from paper_2404_02521_gb300 import pino_io
+    arch = wl.PinoArch()
+    w = wl.pino_random_weights(arch, seed=3)
+    fd, path = tempfile.mkstemp(suffix=".bin")
+    os.close(fd)
+    pino_io.write_weights(path, w, arch.in_channels, arch.width, arch.modes_x, arch.modes_y,
+                          arch.layers, arch.proj_hidden)
+    net = bs.Pino(path)
+    os.unlink(path)
+    pb = wl.pino_cfg3()
+    M, N = pb.M, pb.N
+    g = bs.Grid(M, pb.xmax)
+    U = torch.empty((N + 1, M, M), device="cuda")
+
+    def run():
+        try:
+            bs.parareal_solve(g, pb.params, N, pb.fine_steps, bs.COARSE_PINO, 1, net, pb.tol, 0, U)
+        except bs.BSError:
+            pass   # Kmax = 0: payoff and the initial PINO sweep only
+    run.net = net
+    return run
+
+
+CASES = {"fine256": case_fine256, "coarse256": case_coarse256, "tile1024": case_tile1024,
+         "coarse512": case_coarse512, "pino128": case_pino128}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=sorted(CASES))
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    import torch
+
+    import paper_2404_02521_gb300 as bs
+    import workloads as wl
+    bs.load()
+    fn = CASES[args.case](bs, wl, torch)
+    ms = _timed(fn, args.reps)
+    print(f"{args.case}: " + " ".join(f"{t:.3f}" for t in ms) + " ms per launch group")
+
+
+if __name__ == "__main__":
+    main()

@@ -67,6 +67,40 @@ def test_fine_tiles_match_oracle(bs, M, pi):
     assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
 
 
+def test_tile_step_split_over_launches(bs):
+    # the cold first step needs more sweeps than one tile launch's halo holds: it runs as
+    # two launches (the first leaves the increment unapplied); an item with fewer sweeps in
+    # the same batch is copied through the extra launch
+    import torch
+    M, xmax = 300, 4.0
+    p = PARAMS[0]
+    g = bs.Grid(M, xmax)
+    lo, hi = 1e-6, 1e-2
+    for _ in range(60):           # step with 28..40 cold sweeps (Jacobi bound still < 0.8)
+        mid = (lo * hi) ** 0.5
+        m0 = bs.bs_fine_sweeps(g, p, mid, first_step=True)
+        if m0 == 0 or m0 > 40:
+            hi = mid
+        elif m0 < 28:
+            lo = mid
+        else:
+            break
+    dtau = mid
+    assert 24 < bs.bs_fine_sweeps(g, p, dtau, first_step=True) <= 40
+    small = dtau / 16
+    assert bs.bs_fine_sweeps(g, p, small, first_step=True) <= 24
+    u0 = start_state(M, xmax, p, "payoff")
+    uin = to_gpu(u0)
+    outs = [torch.empty_like(uin) for _ in range(2)]
+    bs.fine_propagate_batched(g, [p, p], [uin, uin], outs, [0.1, 0.1], [dtau, small], 3)
+    one = uin.clone()
+    bs.fine_propagate_batched(g, [p], [one], [one], [0.1], [dtau], 1)
+    torch.cuda.synchronize()
+    assert rel_err(to_np(outs[0]), oracle_fine(M, xmax, p, u0, 0.1, dtau, 3)) <= FP32_FINE_TOL
+    assert rel_err(to_np(outs[1]), oracle_fine(M, xmax, p, u0, 0.1, small, 3)) <= FP32_FINE_TOL
+    assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
+
+
 def test_batch_invariance_and_in_place(bs):
     import torch
     M, xmax = 100, 4.0

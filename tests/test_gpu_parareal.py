@@ -123,6 +123,36 @@ def test_parareal_large_grid(bs):
     assert rel_err(to_np(S), serial) <= FP32_FINE_TOL
 
 
+@pytest.mark.parametrize("M", [64, 200])
+def test_coarse_variants_agree(bs, M):
+    # every band variant that fits the grid solves the same systems to the Krylov tolerance;
+    # the solve count and the iteration statistics are reported per grid
+    import torch
+    p = wl.Params(0.25, 0.35, 0.7, 0.03, payoff=wl.EXCHANGE)
+    u0 = start_state(M, 4.0, p, "random", seed=7)
+    want = fd.ImplicitEuler(M, 4.0, p, 1.0 / 256).propagate(u0.astype(np.float64), 0.25, 4)
+    g = bs.Grid(M, 4.0)
+    uin = to_gpu(u0)
+    fits = 0
+    try:
+        for v in range(8):
+            bs.bs_set_option(bs.OPT_COARSE_VARIANT, v)
+            out = torch.empty_like(uin)
+            try:
+                bs.coarse_propagate(g, bs.COARSE_NUM, None, p, uin, out, 0.25, 4.0 / 256, 4)
+            except bs.BSError:
+                continue          # variant for another column count
+            torch.cuda.synchronize()
+            fits += 1
+            assert rel_err(to_np(out), want) <= COARSE_TOL, v
+            mx, failed, tot, ns = bs.bs_grid_stats(g, detail=True)
+            assert ns == 4 and not failed and 0 < tot <= 4 * mx
+    finally:
+        bs.bs_set_option(bs.OPT_COARSE_VARIANT, -1)
+    assert fits == 2
+    assert bs.bs_coarse_variant(bs.Grid(M, 4.0), p, 1.0 / 256) >= 0
+
+
 def test_maxiter_status(bs):
     pb = cfg_small(wl.BASKET, M=40, N=6, fine=24, coarse=1)
     rc, k, defects, _ = gpu_parareal(bs, pb, 1e-14, 2)
