@@ -176,7 +176,8 @@ int bs_set_option(int option, double value);
  * variant that the device can launch on a short PROP solve from the payoff of p with coarse
  * step dtau_coarse, and caches the fastest per (device, M) for the process; this call runs
  * that measurement now (if not already done) and returns the chosen variant index in
- * *variant (-1 for M > 256, which uses the global-memory solver).  Synchronous on `stream`;
+ * *variant (-1 for M > 256, which uses the global-memory solver; the forced index when
+ * BS_OPT_COARSE_VARIANT is set, without measuring).  Synchronous on `stream`;
  * allocates and frees two M*M FP32 buffers.  Returns BS_OK, BS_ERR_ARG or BS_ERR_CUDA. */
 int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* variant,
                       bs_stream stream);

@@ -49,7 +49,12 @@ ItemDesc make_item(const bs_params& p, double tau0, double dtau) {
   d.payoff = p.payoff;
   d.sweeps = 0;
   d.sweeps0 = 0;
-  d.pad = 0;
+  d.ax = (float)(0.5 * p.sigma1 * p.sigma1 * dtau);
+  d.mx = (float)(0.5 * p.r * dtau);
+  d.ay = (float)(0.5 * p.sigma2 * p.sigma2 * dtau);
+  d.my = (float)(0.5 * p.r * dtau);
+  d.gxy = (float)(0.25 * p.rho * p.sigma1 * p.sigma2 * dtau);
+  d.rdt = (float)(p.r * dtau);
   return d;
 }
 
@@ -304,6 +309,10 @@ int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* v
   if (!(dtau_coarse > 0.0)) return set_error(BS_ERR_ARG, "bs_coarse_variant: dtau_coarse <= 0");
   *variant = -1;
   if (g->M > 256) return BS_OK;
+  if (g_opt.coarse_variant >= 0) {   // forced by BS_OPT_COARSE_VARIANT
+    *variant = g_opt.coarse_variant;
+    return BS_OK;
+  }
   if (g->coarse_variant < 0) {
     rc = coarse_autotune(g, make_item(*p, 0.0, dtau_coarse), (cudaStream_t)stream, 4, nullptr);
     if (rc) return rc;

@@ -31,6 +31,8 @@
 
 namespace bsp {
 
+constexpr int kKrylovAttempts = 3;   // BiCGSTAB starts per implicit step (restarts on breakdown)
+
 struct SweepParams {
   ItemDesc d;       // dtau = coarse step
   SweepArgs a;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   const float cg0 = cgi * (float)(jbase + r0);
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
-  const float rdt = (float)(d.r * d.dtau);
+  const float rdt = d.rdt;
   const float tol = (float)a.tol;
   int round = 0;
   int iters_max = 0, iters_total = 0, nsolves = 0;
@@ -230,92 +232,99 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         // b^ = D^{-1} dtau R_h w.  The solve starts from the previous coarse step's increment
         // xw (the increments of consecutive steps are close): x = xw, r = r^ = p = b^ - A^ xw.
         float x[K], rr[K], vv[K], tt[K];
-        float part[2] = {0.f, 0.f};
-        {
-          const int p0 = r0 + 1;
-          float nW = u[(p0 - 1) * NCOL + il], nC = u[(p0 - 1) * NCOL + col], nE = u[(p0 - 1) * NCOL + ir];
-          float cW = u[p0 * NCOL + il], cC = u[p0 * NCOL + col], cE = u[p0 * NCOL + ir];
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int p = p0 + k;
-            const float sW = u[(p + 1) * NCOL + il], sC = u[(p + 1) * NCOL + col],
-                        sE = u[(p + 1) * NCOL + ir];
-            const float2 rc = rowc[p - 1];
-            const float cg = fmaf((float)k, cgi, cg0);
-            const float b = ce * (cE - cC) - cw * (cC - cW) + rc.x * (sC - cC) - rc.y * (cC - nC) +
-                            cg * ((sE - nE) - (sW - nW)) - rdt * cC;
-            const float bh = b * ID[(p - 1) * NCOL + col];
-            x[k] = xw[k]; rr[k] = bh; vv[k] = 0.f; tt[k] = 0.f;
-            part[0] = fmaf(bh, bh, part[0]);
-            nW = cW; nC = cC; nE = cE;
-            cW = sW; cC = sC; cE = sE;
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < K; ++k) band_store<CFG>(P, pP, r0 + k, col, x[k]);
-        cluster_barrier(cluster, C);
-        scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          rr[k] -= vv[k];
-          part[1] = fmaf(rr[k], rr[k], part[1]);
-        }
-        // every CTA has finished reading P before the barrier inside the reduction below;
-        // P is rewritten only after it
-        cluster_sum<CFG, 2>(cluster, part, slots, sc, round, rank, C,
-                            [tol](Scal* s) { KrylovFin::start(s, tol); });
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          band_store<CFG>(P, pP, r0 + k, col, rr[k]);
-          RH[(r0 + k + 1) * NCOL + col] = rr[k];
-        }
-        cluster_barrier(cluster, C);
-        // BiCGSTAB with two reductions per iteration: omega, (r^, r_new) and beta follow from
-        // (t,s), (t,t), (r^,s), (r^,t); the residual norm is reduced explicitly with (r^, v)
-        // of the next iteration, so convergence is detected half an iteration later.
         int it = 0;
-        while (!sc->conv && it < a.maxit) {
-          ++it;
-          // v = A^ p ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
+        // A breakdown (a zero denominator in alpha, omega or beta) restarts the solve from
+        // the current iterate with a fresh shadow residual.
+        for (int attempt = 0; attempt < kKrylovAttempts; ++attempt) {
+          float part[2] = {0.f, 0.f};
+          {
+            const int p0 = r0 + 1;
+            float nW = u[(p0 - 1) * NCOL + il], nC = u[(p0 - 1) * NCOL + col], nE = u[(p0 - 1) * NCOL + ir];
+            float cW = u[p0 * NCOL + il], cC = u[p0 * NCOL + col], cE = u[p0 * NCOL + ir];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const int p = p0 + k;
+              const float sW = u[(p + 1) * NCOL + il], sC = u[(p + 1) * NCOL + col],
+                          sE = u[(p + 1) * NCOL + ir];
+              const float2 rc = rowc[p - 1];
+              const float cg = fmaf((float)k, cgi, cg0);
+              const float b = ce * (cE - cC) - cw * (cC - cW) + rc.x * (sC - cC) - rc.y * (cC - nC) +
+                              cg * ((sE - nE) - (sW - nW)) - rdt * cC;
+              const float bh = b * ID[(p - 1) * NCOL + col];
+              x[k] = xw[k]; rr[k] = bh; vv[k] = 0.f; tt[k] = 0.f;
+              part[0] = fmaf(bh, bh, part[0]);
+              nW = cW; nC = cC; nE = cE;
+              cW = sW; cC = sC; cE = sE;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < K; ++k) band_store<CFG>(P, pP, r0 + k, col, x[k]);
+          cluster_barrier(cluster, C);
           scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
-          float p1[2] = {0.f, 0.f};
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            p1[0] = fmaf(RH[(r0 + k + 1) * NCOL + col], vv[k], p1[0]);
-            p1[1] = fmaf(rr[k], rr[k], p1[1]);
+            rr[k] -= vv[k];
+            part[1] = fmaf(rr[k], rr[k], part[1]);
           }
-          cluster_sum<CFG, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
-          if (sc->conv || sc->fail) break;
-          const float af = sc->af;
-          // s = r - alpha v
+          // every CTA has finished reading P before the barrier inside the reduction below;
+          // P is rewritten only after it
+          cluster_sum<CFG, 2>(cluster, part, slots, sc, round, rank, C,
+                              [tol](Scal* s) { KrylovFin::start(s, tol); });
 #pragma unroll
-          for (int k = 0; k < K; ++k) band_store<CFG>(S, pS, r0 + k, col, fmaf(-af, vv[k], rr[k]));
+          for (int k = 0; k < K; ++k) {
+            band_store<CFG>(P, pP, r0 + k, col, rr[k]);
+            RH[(r0 + k + 1) * NCOL + col] = rr[k];
+          }
           cluster_barrier(cluster, C);
-          // t = A^ s ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
-          scaled_matvec<CFG>(S, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, tt);
-          float p2[4] = {0.f, 0.f, 0.f, 0.f};
+          // BiCGSTAB with two reductions per iteration: omega, (r^, r_new) and beta follow from
+          // (t,s), (t,t), (r^,s), (r^,t); the residual norm is reduced explicitly with (r^, v)
+          // of the next iteration, so convergence is detected half an iteration later.
+          while (!sc->conv && it < a.maxit) {
+            ++it;
+            // v = A^ p ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
+            scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
+            float p1[2] = {0.f, 0.f};
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int idx = (r0 + k + 1) * NCOL + col;
-            const float sv = S[idx], rh = RH[idx];
-            p2[0] = fmaf(tt[k], sv, p2[0]);
-            p2[1] = fmaf(tt[k], tt[k], p2[1]);
-            p2[2] = fmaf(rh, sv, p2[2]);
-            p2[3] = fmaf(rh, tt[k], p2[3]);
-          }
-          cluster_sum<CFG, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
-          const float of = sc->of, bf = sc->bf;
-          // x += alpha p + omega s ;  r = s - omega t ;  p = r + beta (p - omega v)
+            for (int k = 0; k < K; ++k) {
+              p1[0] = fmaf(RH[(r0 + k + 1) * NCOL + col], vv[k], p1[0]);
+              p1[1] = fmaf(rr[k], rr[k], p1[1]);
+            }
+            cluster_sum<CFG, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
+            if (sc->conv || sc->fail) break;
+            const float af = sc->af;
+            // s = r - alpha v
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int idx = (r0 + k + 1) * NCOL + col;
-            const float sv = S[idx], pv = P[idx];
-            x[k] += af * pv + of * sv;
-            rr[k] = fmaf(-of, tt[k], sv);
-            band_store<CFG>(P, pP, r0 + k, col, rr[k] + bf * (pv - of * vv[k]));
+            for (int k = 0; k < K; ++k) band_store<CFG>(S, pS, r0 + k, col, fmaf(-af, vv[k], rr[k]));
+            cluster_barrier(cluster, C);
+            // t = A^ s ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
+            scaled_matvec<CFG>(S, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, tt);
+            float p2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const int idx = (r0 + k + 1) * NCOL + col;
+              const float sv = S[idx], rh = RH[idx];
+              p2[0] = fmaf(tt[k], sv, p2[0]);
+              p2[1] = fmaf(tt[k], tt[k], p2[1]);
+              p2[2] = fmaf(rh, sv, p2[2]);
+              p2[3] = fmaf(rh, tt[k], p2[3]);
+            }
+            cluster_sum<CFG, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
+            const float of = sc->of, bf = sc->bf;
+            // x += alpha p + omega s ;  r = s - omega t ;  p = r + beta (p - omega v)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const int idx = (r0 + k + 1) * NCOL + col;
+              const float sv = S[idx], pv = P[idx];
+              x[k] += af * pv + of * sv;
+              rr[k] = fmaf(-of, tt[k], sv);
+              band_store<CFG>(P, pP, r0 + k, col, rr[k] + bf * (pv - of * vv[k]));
+            }
+            if (sc->fail) break;
+            cluster_barrier(cluster, C);
           }
-          if (sc->fail) break;
-          cluster_barrier(cluster, C);
+          if (sc->conv || !sc->fail) break;
+#pragma unroll
+          for (int k = 0; k < K; ++k) xw[k] = x[k];
         }
         if (!sc->conv) failed = true;
         iters_max = it > iters_max ? it : iters_max;
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   const int j0 = rank * BHg, j1 = min(M, j0 + BHg);
   const size_t e0 = (size_t)j0 * M, e1 = (size_t)j1 * M;
   const PayoffF pf = make_payoff(d);
-  const float rdt = (float)(d.r * d.dtau);
+  const float rdt = d.rdt;
   const float tol = (float)a.tol;
   __shared__ double slots[2 * kMaxCluster * GCfg::NW * 4];
   __shared__ Scal scs;
@@ -521,83 +530,88 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
           if (i == M - 1 || j == M - 1) w.u[e] = far_field(pf, i * gp.h, j * gp.h, tau_new);
         }
         barrier();
-        // b^ = D^{-1} dtau R_h w ;  r = b^ - A^ x (x = previous increment)
-        float part[2] = {0.f, 0.f};
-        for (size_t e = e0 + tid; e < e1; e += kGThreads) {
-          const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
-          float bh = 0.f, rr = 0.f;
-          if (i < M - 1 && j < M - 1) {
-            float ce, cw, cs, cn, cg;
-            g_coefs(d, i, j, ce, cw, cs, cn, cg);
-            const float* y = w.u;
-            const float c = ldcg(y + e);
-            const float yw = i > 0 ? ldcg(y + e - 1) : 0.f, ye = ldcg(y + e + 1);
-            const float yn = j > 0 ? ldcg(y + e - M) : 0.f, ys = ldcg(y + e + M);
-            const float ynw = (i > 0 && j > 0) ? ldcg(y + e - M - 1) : 0.f, yne = j > 0 ? ldcg(y + e - M + 1) : 0.f;
-            const float ysw = i > 0 ? ldcg(y + e + M - 1) : 0.f, yse = ldcg(y + e + M + 1);
-            const float b = ce * (ye - c) - cw * (c - yw) + cs * (ys - c) - cn * (c - yn) +
-                            cg * ((yse - yne) - (ysw - ynw)) - rdt * c;
-            bh = b * w.id[e];
-            rr = bh - g_matvec(w.x, w.id, M, i, j, ce, cw, cs, cn, cg);
-          }
-          w.r[e] = rr;
-          w.rh[e] = rr;
-          part[0] = fmaf(bh, bh, part[0]);
-          part[1] = fmaf(rr, rr, part[1]);
-        }
-        cluster_sum<GCfg, 2>(cluster, part, slots, sc, round, rank, C,
-                             [tol](Scal* s) { KrylovFin::start(s, tol); });
-        for (size_t e = e0 + tid; e < e1; e += kGThreads) w.p[e] = w.r[e];
-        barrier();
         int it = 0;
-        while (!sc->conv && it < a.maxit) {
-          ++it;
-          float p1[2] = {0.f, 0.f};
+        // restart from the current iterate after a breakdown (see the band kernel)
+        for (int attempt = 0; attempt < kKrylovAttempts; ++attempt) {
+          if (attempt > 0) barrier();   // the other CTAs' last x updates are visible
+          // b^ = D^{-1} dtau R_h w ;  r = b^ - A^ x (x = previous increment)
+          float part[2] = {0.f, 0.f};
           for (size_t e = e0 + tid; e < e1; e += kGThreads) {
             const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
-            float vv = 0.f;
+            float bh = 0.f, rr = 0.f;
             if (i < M - 1 && j < M - 1) {
               float ce, cw, cs, cn, cg;
               g_coefs(d, i, j, ce, cw, cs, cn, cg);
-              vv = g_matvec(w.p, w.id, M, i, j, ce, cw, cs, cn, cg);
+              const float* y = w.u;
+              const float c = ldcg(y + e);
+              const float yw = i > 0 ? ldcg(y + e - 1) : 0.f, ye = ldcg(y + e + 1);
+              const float yn = j > 0 ? ldcg(y + e - M) : 0.f, ys = ldcg(y + e + M);
+              const float ynw = (i > 0 && j > 0) ? ldcg(y + e - M - 1) : 0.f, yne = j > 0 ? ldcg(y + e - M + 1) : 0.f;
+              const float ysw = i > 0 ? ldcg(y + e + M - 1) : 0.f, yse = ldcg(y + e + M + 1);
+              const float b = ce * (ye - c) - cw * (c - yw) + cs * (ys - c) - cn * (c - yn) +
+                              cg * ((yse - yne) - (ysw - ynw)) - rdt * c;
+              bh = b * w.id[e];
+              rr = bh - g_matvec(w.x, w.id, M, i, j, ce, cw, cs, cn, cg);
             }
-            w.v[e] = vv;
-            const float rr = w.r[e];
-            p1[0] = fmaf(w.rh[e], vv, p1[0]);
-            p1[1] = fmaf(rr, rr, p1[1]);
-          }
-          cluster_sum<GCfg, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
-          if (sc->conv || sc->fail) break;
-          const float af = sc->af;
-          for (size_t e = e0 + tid; e < e1; e += kGThreads) w.s[e] = fmaf(-af, w.v[e], w.r[e]);
-          barrier();
-          float p2[4] = {0.f, 0.f, 0.f, 0.f};
-          for (size_t e = e0 + tid; e < e1; e += kGThreads) {
-            const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
-            float tt = 0.f;
-            if (i < M - 1 && j < M - 1) {
-              float ce, cw, cs, cn, cg;
-              g_coefs(d, i, j, ce, cw, cs, cn, cg);
-              tt = g_matvec(w.s, w.id, M, i, j, ce, cw, cs, cn, cg);
-            }
-            w.t[e] = tt;
-            const float sv = w.s[e], rh = w.rh[e];
-            p2[0] = fmaf(tt, sv, p2[0]);
-            p2[1] = fmaf(tt, tt, p2[1]);
-            p2[2] = fmaf(rh, sv, p2[2]);
-            p2[3] = fmaf(rh, tt, p2[3]);
-          }
-          cluster_sum<GCfg, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
-          const float of = sc->of, bf = sc->bf;
-          for (size_t e = e0 + tid; e < e1; e += kGThreads) {
-            const float sv = w.s[e], pv = w.p[e], tt = w.t[e];
-            w.x[e] += af * pv + of * sv;
-            const float rr = fmaf(-of, tt, sv);
             w.r[e] = rr;
-            w.p[e] = rr + bf * (pv - of * w.v[e]);
+            w.rh[e] = rr;
+            part[0] = fmaf(bh, bh, part[0]);
+            part[1] = fmaf(rr, rr, part[1]);
           }
-          if (sc->fail) break;
+          cluster_sum<GCfg, 2>(cluster, part, slots, sc, round, rank, C,
+                               [tol](Scal* s) { KrylovFin::start(s, tol); });
+          for (size_t e = e0 + tid; e < e1; e += kGThreads) w.p[e] = w.r[e];
           barrier();
+          while (!sc->conv && it < a.maxit) {
+            ++it;
+            float p1[2] = {0.f, 0.f};
+            for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+              const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+              float vv = 0.f;
+              if (i < M - 1 && j < M - 1) {
+                float ce, cw, cs, cn, cg;
+                g_coefs(d, i, j, ce, cw, cs, cn, cg);
+                vv = g_matvec(w.p, w.id, M, i, j, ce, cw, cs, cn, cg);
+              }
+              w.v[e] = vv;
+              const float rr = w.r[e];
+              p1[0] = fmaf(w.rh[e], vv, p1[0]);
+              p1[1] = fmaf(rr, rr, p1[1]);
+            }
+            cluster_sum<GCfg, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
+            if (sc->conv || sc->fail) break;
+            const float af = sc->af;
+            for (size_t e = e0 + tid; e < e1; e += kGThreads) w.s[e] = fmaf(-af, w.v[e], w.r[e]);
+            barrier();
+            float p2[4] = {0.f, 0.f, 0.f, 0.f};
+            for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+              const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+              float tt = 0.f;
+              if (i < M - 1 && j < M - 1) {
+                float ce, cw, cs, cn, cg;
+                g_coefs(d, i, j, ce, cw, cs, cn, cg);
+                tt = g_matvec(w.s, w.id, M, i, j, ce, cw, cs, cn, cg);
+              }
+              w.t[e] = tt;
+              const float sv = w.s[e], rh = w.rh[e];
+              p2[0] = fmaf(tt, sv, p2[0]);
+              p2[1] = fmaf(tt, tt, p2[1]);
+              p2[2] = fmaf(rh, sv, p2[2]);
+              p2[3] = fmaf(rh, tt, p2[3]);
+            }
+            cluster_sum<GCfg, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
+            const float of = sc->of, bf = sc->bf;
+            for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+              const float sv = w.s[e], pv = w.p[e], tt = w.t[e];
+              w.x[e] += af * pv + of * sv;
+              const float rr = fmaf(-of, tt, sv);
+              w.r[e] = rr;
+              w.p[e] = rr + bf * (pv - of * w.v[e]);
+            }
+            if (sc->fail) break;
+            barrier();
+          }
+          if (sc->conv || !sc->fail) break;
         }
         if (!sc->conv) failed = true;
         iters_max = it > iters_max ? it : iters_max;

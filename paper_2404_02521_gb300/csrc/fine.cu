@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
   }
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
-  const float rdt = (float)(d.r * d.dtau);
+  const float rdt = d.rdt;
   cluster_barrier(cluster, C);
 
   // Split cluster barrier: each sweep arrives after its writes and waits (inside the sweep)
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
   }
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
-  const float rdt = (float)(d.r * d.dtau);
+  const float rdt = d.rdt;
   const int m_item = step == 0 ? d.sweeps0 : d.sweeps;   // the first step starts cold
   const int nsw = max(0, min(s_end, m_item) - s_begin);
   const bool commit = nsw > 0 && min(s_end, m_item) == m_item;

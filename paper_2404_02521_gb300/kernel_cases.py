@@ -125,12 +125,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=sorted(CASES))
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--coarse-variant", type=int, default=-1,
+                    help="force this coarse band variant (skips the autotuner's timing launches)")
     args = ap.parse_args()
     import torch
 
     import paper_2404_02521_gb300 as bs
     import workloads as wl
     bs.load()
+    bs.bs_set_option(bs.OPT_COARSE_VARIANT, args.coarse_variant)
     fn = CASES[args.case](bs, wl, torch)
     ms = _timed(fn, args.reps)
     print(f"{args.case}: " + " ".join(f"{t:.3f}" for t in ms) + " ms per launch group")

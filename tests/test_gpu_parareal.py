@@ -153,6 +153,21 @@ def test_coarse_variants_agree(bs, M):
     assert bs.bs_coarse_variant(bs.Grid(M, 4.0), p, 1.0 / 256) >= 0
 
 
+@pytest.mark.parametrize("variant", [6, 7])
+def test_full_size_parareal_each_variant(bs, variant):
+    # rho = 0 on the 256 x 256 workload with each band variant of the coarse sweep; a Krylov
+    # breakdown (zero omega in FP32) restarts the solve instead of failing it
+    pb = wl.exchange_cfg2(0.0)
+    try:
+        bs.bs_set_option(bs.OPT_COARSE_VARIANT, variant)
+        rc, k, defects, U = gpu_parareal(bs, pb, pb.tol, pb.N)
+    finally:
+        bs.bs_set_option(bs.OPT_COARSE_VARIANT, -1)
+    assert rc == 0 and k <= 3
+    rc2, k2, _, U2 = gpu_parareal(bs, pb, pb.tol, pb.N)
+    assert float((U - U2).abs().max() / U2.abs().max()) <= pb.tol
+
+
 def test_maxiter_status(bs):
     pb = cfg_small(wl.BASKET, M=40, N=6, fine=24, coarse=1)
     rc, k, defects, _ = gpu_parareal(bs, pb, 1e-14, 2)
