@@ -328,7 +328,7 @@ int bs_grid_stats(bs_grid* g, int* krylov_iters_max, int* krylov_failed, int* kr
   BS_CUDA_TRY(cudaMemcpy(h, g->status, kStatusWords * sizeof(int), cudaMemcpyDeviceToHost));
   BS_CUDA_TRY(cudaMemset(g->status, 0, kStatusWords * sizeof(int)));
   if (krylov_iters_max) *krylov_iters_max = h[1];
-  if (krylov_failed) *krylov_failed = h[0] & 1;
+  if (krylov_failed) *krylov_failed = h[0];   // bit 0: iteration cap, bit 1: exchange timeout
   if (krylov_iters_total) *krylov_iters_total = h[2];
   if (krylov_solves) *krylov_solves = h[3];
   return BS_OK;
@@ -500,6 +500,8 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
       *k_done = k + 1;
       g->ms_fine += ms_f;
       g->ms_coarse += ms_c;
+      if (hstat & 2)
+        return set_error(BS_ERR_CUDA, "parareal_solve: a cluster exchange of the coarse sweep timed out");
       return set_error(BS_ERR_NOCONV, "parareal_solve: a coarse BiCGSTAB solve hit its iteration cap");
     }
     if (host[0] <= tol) {

@@ -88,41 +88,47 @@ __device__ __forceinline__ T warp_butterfly(T x) {
 }
 
 // Cluster-wide sum of NV per-thread values of type T.  Each warp reduces its values by a
-// butterfly and stores the warp partial into slot (rank, warp) of every CTA of the cluster;
-// after one cluster barrier, warp 0 of every CTA adds the C * NW partials in a fixed order
-// (lane l takes entries l, l+32, ...; then a butterfly), so every CTA gets bitwise the same
-// totals in scal_tot(sc) (type T).  `fin(sc)` then runs once per CTA (thread 0) before the
-// closing CTA barrier.  `round` alternates two slot arrays so that a fast CTA never
-// overwrites partials that a slow CTA is still adding.
+// butterfly; warp 0 adds the warp partials (wpart) and lanes 0..C-1 store the CTA partial into
+// slot `rank` of every CTA of the cluster; after one cluster barrier, thread 0 of every CTA
+// adds the C partials in rank order, so every CTA gets bitwise the same totals in
+// scal_tot(sc) (type T), and runs `fin(sc)` before the closing CTA barrier.  `round`
+// alternates two slot arrays so that a fast CTA never overwrites partials that a slow CTA is
+// still adding.  slots: double[2][kMaxCluster][4]; wpart: double[NW][4].
 template <class CFG, int NV, class T, class Fin>
 __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, const T (&v)[NV], double* slots,
-                                            Scal* sc, int& round, int rank, int C, Fin fin) {
+                                            double* wpart, Scal* sc, int& round, int rank, int C,
+                                            Fin fin) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* slot = reinterpret_cast<T*>(slots) + (round & 1) * (kMaxCluster * CFG::NW * 4);
+  T* slot = reinterpret_cast<T*>(slots) + (round & 1) * (kMaxCluster * 4);
+  T* wp = reinterpret_cast<T*>(wpart);
   T x[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) x[q] = warp_butterfly<T>(v[q]);
-  if (lane < C) {
-    T* dst = (C > 1 ? cl.map_shared_rank(slot, lane) : slot) + (rank * CFG::NW + warp) * 4;
+  if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) dst[q] = x[q];
+    for (int q = 0; q < NV; ++q) wp[warp * 4 + q] = x[q];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    T c[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) c[q] = warp_butterfly<T>(lane < CFG::NW ? wp[lane * 4 + q] : T(0));
+    if (lane < C) {
+      T* dst = (C > 1 ? cl.map_shared_rank(slot, lane) : slot) + rank * 4;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) dst[q] = c[q];
+    }
   }
   if (C > 1) cl.sync(); else __syncthreads();
-  if (warp == 0) {
-    const int n = C * CFG::NW;
-    T tot[NV];
+  if (threadIdx.x == 0) {
+    T* out = scal_tot(sc, T(0));
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       T acc = T(0);
-      for (int i = lane; i < n; i += 32) acc += slot[i * 4 + q];
-      tot[q] = warp_butterfly<T>(acc);
+      for (int i = 0; i < C; ++i) acc += slot[i * 4 + q];
+      out[q] = acc;
     }
-    if (lane == 0) {
-      T* out = scal_tot(sc, T(0));
-#pragma unroll
-      for (int q = 0; q < NV; ++q) out[q] = tot[q];
-      fin(sc);
-    }
+    fin(sc);
   }
   __syncthreads();
   ++round;
@@ -156,9 +162,148 @@ struct KrylovFin {
   }
 };
 
+// ---------------------------------------------------------------------------------------
+// Point-to-point cluster exchange for the BiCGSTAB iterations.  A round moves every CTA's
+// partial sums to every CTA of the cluster, plus (optionally) one halo row from each band
+// neighbour, with st.async stores into the receivers' shared memory.  Each store completes
+// its byte count on the receiver's mbarrier for that round's parity; a CTA waits on its own
+// mbarrier until all expected bytes have landed.  No cluster-wide barrier and no fence are
+// needed: the complete-tx of st.async releases the data and the mbarrier wait acquires it.
+//
+// Buffer reuse: rounds alternate two mbarriers and two partial-slot arrays.  A CTA sends
+// round r+2 data only after round r+1 has completed for it, which needs this CTA's round r+1
+// partial, which this CTA sends only after it has finished reading the round r slots (and
+// the round r halo rows; halo rows of v are double-buffered by iteration parity since they
+// are read once more after the following round).
+// ---------------------------------------------------------------------------------------
+constexpr int kXchgWaitPolls = 1 << 22;   // bound on mbarrier polls per round
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mb, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(count) : "memory");
+}
+// the local arrival of a round, announcing the bytes the round's stores will complete
+__device__ __forceinline__ void mbar_arm(uint64_t* mb, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mb)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* mb, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(mb)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void st_async_f32(uint32_t dst, float v, uint32_t mb) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];\n" ::"r"(dst),
+               "r"(__float_as_uint(v)), "r"(mb)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_v2(uint32_t dst, float a, float b, uint32_t mb) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];\n" ::"r"(dst),
+               "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(mb)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_v4(uint32_t dst, float a, float b, float c, float d, uint32_t mb) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];\n" ::"r"(dst),
+      "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d)),
+      "r"(mb)
+      : "memory");
+}
+
+struct Xchg {
+  uint64_t* mb;     // [2] mbarriers (one per round parity), arrival count 1
+  float* kslot;     // [2][kMaxCluster][4] partial sums by source rank
+  float* wpart;     // [NW][4] warp partials
+  uint32_t phase;   // bit b: parity of the current phase of mb[b]
+  int round;
+  bool dead;        // a wait ran out: skip further waits (the sweep reports an error)
+};
+
+// One exchange round: sum NV values over the cluster (every CTA gets bitwise the same totals:
+// the CTA partials are added in rank order).  The caller has already sent the halo rows
+// this round carries; halo_bytes is what this CTA receives of them.
+template <class CFG, int NV>
+__device__ __forceinline__ void xround(Xchg& xs, const float (&v)[NV], float (&tot)[NV], int rank, int C,
+                                       uint32_t halo_bytes) {
+  static_assert(NV == 2 || NV == 4, "partials travel as one v2 or v4 store");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = xs.round & 1;
+  if (threadIdx.x == 0) mbar_arm(xs.mb + b, (uint32_t)(C * NV * 4) + halo_bytes);
+  float w[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) w[q] = warp_butterfly<float>(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) xs.wpart[warp * 4 + q] = w[q];
+  }
+  __syncthreads();
+  float* slot = xs.kslot + b * (kMaxCluster * 4);
+  if (warp == 0) {
+    float c[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) c[q] = warp_butterfly<float>(lane < CFG::NW ? xs.wpart[lane * 4 + q] : 0.f);
+    if (lane < C) {
+      const uint32_t dst = cluster_addr(smem_addr(slot + rank * 4), lane);
+      const uint32_t mb = cluster_addr(smem_addr(xs.mb + b), lane);
+      if constexpr (NV == 2) st_async_v2(dst, c[0], c[1], mb);
+      else st_async_v4(dst, c[0], c[1], c[2], c[3], mb);
+    }
+  }
+  if (!xs.dead) {
+    const uint32_t par = (xs.phase >> b) & 1u;
+    int polls = 0;
+    while (!mbar_test(xs.mb + b, par)) {
+      if (++polls >= kXchgWaitPolls) {
+        xs.dead = true;
+        break;
+      }
+    }
+  }
+  xs.phase ^= 1u << b;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    float acc = 0.f;
+    for (int i = 0; i < C; ++i) acc += slot[i * 4 + q];
+    tot[q] = acc;
+  }
+  ++xs.round;
+}
+
+// Shared-memory layout of sweep_band_kernel (floats first, every array a multiple of 16 B).
+template <class CFG>
+struct SweepSmem {
+  static constexpr int NCOL = CFG::NCOL, BH = CFG::BH, PLANE = CFG::PLANE, NW = CFG::NW;
+  static constexpr size_t u = 0, P = u + PLANE, S = P + PLANE;          // planes (with halo rows)
+  static constexpr size_t RH = S + PLANE, ID = RH + BH * NCOL, XP = ID + BH * NCOL;   // own rows
+  static constexpr size_t VH = XP + BH * NCOL;   // [2 parity][2: top, bottom][NCOL] v halo rows
+  static constexpr size_t TH = VH + 4 * NCOL;    // [2: top, bottom][NCOL] t halo rows
+  static constexpr size_t KSLOT = TH + 2 * NCOL; // [2][kMaxCluster][4] exchange partials
+  static constexpr size_t KWP = KSLOT + 2 * kMaxCluster * 4;   // [NW][4]
+  static constexpr size_t ROWC = KWP + NW * 4;   // float2 [BH]
+  static constexpr size_t FLOATS = ROWC + 2 * BH;
+  // doubles after the floats: slots [2][kMaxCluster][4], wpart [NW][4]; then mbarriers, Scal
+  static constexpr size_t SLOTS_B = FLOATS * 4, WPART_B = SLOTS_B + 2 * kMaxCluster * 4 * 8;
+  static constexpr size_t MB_B = WPART_B + NW * 4 * 8, SCAL_B = MB_B + 16;
+  static constexpr size_t BYTES = SCAL_B + sizeof(Scal);
+  static_assert(FLOATS % 4 == 0, "16-byte alignment of the double arrays");
+};
+
 template <class CFG>
 __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_constant__ SweepParams sp) {
-  constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, PLANE = CFG::PLANE;
+  constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, G = CFG::G;
+  using L = SweepSmem<CFG>;
   cg::cluster_group cluster = cg::this_cluster();
   const ItemDesc& d = sp.d;
   const SweepArgs& a = sp.a;
@@ -173,33 +318,56 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   const PayoffF pf = make_payoff(d);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* u = reinterpret_cast<float*>(smem_raw);   // state w / u          [PLANE]
-  float* P = u + PLANE;                            // search direction p   [PLANE]
-  float* S = P + PLANE;                            // s                    [PLANE]
-  float* RH = S + PLANE;                           // shadow residual r^   [PLANE]
-  float* ID = RH + PLANE;                          // inverse diagonal     [BH*NCOL]
-  float* XP = ID + BH * NCOL;                      // increment before xw  [BH*NCOL]
-  float2* rowc = reinterpret_cast<float2*>(XP + BH * NCOL);
-  double* slots = reinterpret_cast<double*>(rowc + BH);   // [2][16 CTAs x NW warps][4]
-  Scal* sc = reinterpret_cast<Scal*>(slots + 2 * kMaxCluster * CFG::NW * 4);
+  float* fs = reinterpret_cast<float*>(smem_raw);
+  float* u = fs + L::u;      // state w / u          [PLANE]
+  float* P = fs + L::P;      // search direction p   [PLANE]
+  float* S = fs + L::S;      // s                    [PLANE]
+  float* RH = fs + L::RH;    // shadow residual r^   [BH*NCOL]
+  float* ID = fs + L::ID;    // inverse diagonal     [BH*NCOL]
+  float* XP = fs + L::XP;    // increment before xw  [BH*NCOL]
+  float* VH = fs + L::VH;
+  float* TH = fs + L::TH;
+  float2* rowc = reinterpret_cast<float2*>(fs + L::ROWC);
+  double* slots = reinterpret_cast<double*>(smem_raw + L::SLOTS_B);
+  double* wpart = reinterpret_cast<double*>(smem_raw + L::WPART_B);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::MB_B);
+  Scal* sc = reinterpret_cast<Scal*>(smem_raw + L::SCAL_B);
 
   const HaloPush pu = halo_push<CFG>(cluster, u, rank, C);
   const HaloPush pP = halo_push<CFG>(cluster, P, rank, C);
-  const HaloPush pS = halo_push<CFG>(cluster, S, rank, C);
+  const bool has_up = rank > 0, has_down = rank < C - 1;
+  // receivers of this thread's halo stores (v and t rows): group 0 sends band row 0 to the
+  // bottom halo of rank-1, group G-1 sends band row BH-1 to the top halo of rank+1
+  const bool send_up = grp == 0 && has_up, send_down = grp == G - 1 && has_down;
+  const uint32_t halo_bytes = (uint32_t)((has_up ? 1 : 0) + (has_down ? 1 : 0)) * NCOL * 4;
 
   for (int e = tid; e < BH * NCOL; e += CFG::NT) {
     const int r = e / NCOL, c = e % NCOL;
     const int j = jbase + r;
     ID[e] = (j < M - 1 && c < M - 1) ? inv_diag(d, c, j) : 0.f;
+    RH[e] = 0.f;
   }
-  for (int e = tid; e < PLANE; e += CFG::NT) {
-    P[e] = 0.f; S[e] = 0.f; RH[e] = 0.f;
+  for (int e = tid; e < CFG::PLANE; e += CFG::NT) {
+    P[e] = 0.f; S[e] = 0.f;
   }
+  for (int e = tid; e < 6 * NCOL; e += CFG::NT) VH[e] = 0.f;   // VH and TH
   for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
     row_coefs(d, jbase + r, cs, cn, gj);
     rowc[r] = make_float2(cs, cn);
   }
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  Xchg xs;
+  xs.mb = mbar;
+  xs.kslot = fs + L::KSLOT;
+  xs.wpart = fs + L::KWP;
+  xs.phase = 0;
+  xs.round = 0;
+  xs.dead = false;
   float ce = 0.f, cw = 0.f, cgi = 0.f;
   column_coefs(d, col, ce, cw, cgi);
   const float cg0 = cgi * (float)(jbase + r0);
@@ -209,6 +377,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   const float tol = (float)a.tol;
   int round = 0;
   int iters_max = 0, iters_total = 0, nsolves = 0;
+  int kit = 0;   // BiCGSTAB iterations run by this kernel (parity of the v halo buffers)
   bool failed = false;
 
   // initial state of the first slice (own rows and halo rows)
@@ -217,7 +386,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   else if (a.mode == SWEEP_INIT) src = a.U;
   else src = a.Gold + (size_t)a.n_first * MM;   // ITER: G(u_k) is unchanged -> reuse G_old_k
   band_load<CFG>(u, src, M, jbase, tid);
-  cluster_barrier(cluster, C);
+  cluster_barrier(cluster, C);   // also publishes the mbarrier initialisation
 
   // Initial guess of each solve: the linear extrapolation 2 d_{m-1} - d_{m-2} of the two
   // previous coarse increments (d_{m-1} after one step, 0 at the start); the increments of
@@ -234,8 +403,6 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         const double tau_new = d.tau0 + a.slice_len * n + (cstep + 1) * d.dtau;
         band_far_field<CFG>(u, pu, pf, (float)tau_new, h, M, jbase, tid);
         cluster_barrier(cluster, C);
-        // b^ = D^{-1} dtau R_h w.  The solve starts from the previous coarse step's increment
-        // xw (the increments of consecutive steps are close): x = xw, r = r^ = p = b^ - A^ xw.
         if (nhist >= 2) {
 #pragma unroll
           for (int k = 0; k < K; ++k) {
@@ -250,9 +417,13 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         }
         float x[K], rr[K], vv[K], tt[K];
         int it = 0;
+        bool conv = false;
         // A breakdown (a zero denominator in alpha, omega or beta) restarts the solve from
         // the current iterate with a fresh shadow residual.
         for (int attempt = 0; attempt < kKrylovAttempts; ++attempt) {
+          // a restart rewrites the neighbours' P halo rows: they must have left the iteration
+          if (attempt > 0) cluster_barrier(cluster, C);
+          // b^ = D^{-1} dtau R_h w;  x = initial guess;  r = r^ = p = b^ - A^ x
           float part[2] = {0.f, 0.f};
           {
             const int p0 = r0 + 1;
@@ -265,9 +436,9 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
                           sE = u[(p + 1) * NCOL + ir];
               const float2 rc = rowc[p - 1];
               const float cg = fmaf((float)k, cgi, cg0);
-              const float b = ce * (cE - cC) - cw * (cC - cW) + rc.x * (sC - cC) - rc.y * (cC - nC) +
-                              cg * ((sE - nE) - (sW - nW)) - rdt * cC;
-              const float bh = b * ID[(p - 1) * NCOL + col];
+              const float bb = ce * (cE - cC) - cw * (cC - cW) + rc.x * (sC - cC) - rc.y * (cC - nC) +
+                               cg * ((sE - nE) - (sW - nW)) - rdt * cC;
+              const float bh = bb * ID[(p - 1) * NCOL + col];
               x[k] = xw[k]; rr[k] = bh; vv[k] = 0.f; tt[k] = 0.f;
               part[0] = fmaf(bh, bh, part[0]);
               nW = cW; nC = cC; nE = cE;
@@ -285,48 +456,80 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
           }
           // every CTA has finished reading P before the barrier inside the reduction below;
           // P is rewritten only after it
-          cluster_sum<CFG, 2>(cluster, part, slots, sc, round, rank, C,
+          cluster_sum<CFG, 2>(cluster, part, slots, wpart, sc, round, rank, C,
                               [tol](Scal* s) { KrylovFin::start(s, tol); });
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             band_store<CFG>(P, pP, r0 + k, col, rr[k]);
-            RH[(r0 + k + 1) * NCOL + col] = rr[k];
+            RH[(r0 + k) * NCOL + col] = rr[k];
           }
           cluster_barrier(cluster, C);
-          // BiCGSTAB with two reductions per iteration: omega, (r^, r_new) and beta follow from
-          // (t,s), (t,t), (r^,s), (r^,t); the residual norm is reduced explicitly with (r^, v)
-          // of the next iteration, so convergence is detected half an iteration later.
-          while (!sc->conv && it < a.maxit) {
+          float rho = sc->rho;
+          const float stop2 = sc->stop2;
+          conv = sc->conv != 0;
+          bool fail = false;
+          // r on the halo rows (kept by the threads that own those columns of the edge groups;
+          // the P halo rows hold r here)
+          float rh_top = grp == 0 ? P[col] : 0.f;
+          float rh_bot = grp == G - 1 ? P[(BH + 1) * NCOL + col] : 0.f;
+          // BiCGSTAB iterations with two exchange rounds each.  The halo rows of s and p are
+          // computed locally from r, v and t on the halo rows (v and t arrive with the rounds),
+          // so the matrix-vector products need no cluster barrier.
+          while (!conv && it < a.maxit) {
             ++it;
+            const int par = kit & 1;
+            float* vh_top = VH + (2 * par) * NCOL;
+            float* vh_bot = VH + (2 * par + 1) * NCOL;
             // v = A^ p ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
             scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
+            {
+              const uint32_t mb = smem_addr(xs.mb + (xs.round & 1));
+              if (send_up) st_async_f32(cluster_addr(smem_addr(vh_bot + col), rank - 1), vv[0], cluster_addr(mb, rank - 1));
+              if (send_down) st_async_f32(cluster_addr(smem_addr(vh_top + col), rank + 1), vv[K - 1], cluster_addr(mb, rank + 1));
+            }
             float p1[2] = {0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              p1[0] = fmaf(RH[(r0 + k + 1) * NCOL + col], vv[k], p1[0]);
+              p1[0] = fmaf(RH[(r0 + k) * NCOL + col], vv[k], p1[0]);
               p1[1] = fmaf(rr[k], rr[k], p1[1]);
             }
-            cluster_sum<CFG, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
-            if (sc->conv || sc->fail) break;
-            const float af = sc->af;
-            // s = r - alpha v
+            float ta[2];
+            xround<CFG, 2>(xs, p1, ta, rank, C, halo_bytes);
+            if (xs.dead) { conv = true; break; }
+            if (ta[1] <= stop2) { conv = true; break; }
+            if (ta[0] == 0.f) { fail = true; break; }
+            const float af = rho / ta[0];
+            // s = r - alpha v, own rows and halo rows
 #pragma unroll
-            for (int k = 0; k < K; ++k) band_store<CFG>(S, pS, r0 + k, col, fmaf(-af, vv[k], rr[k]));
-            cluster_barrier(cluster, C);
+            for (int k = 0; k < K; ++k) S[(r0 + k + 1) * NCOL + col] = fmaf(-af, vv[k], rr[k]);
+            if (grp == 0) S[col] = has_up ? fmaf(-af, vh_top[col], rh_top) : 0.f;
+            if (grp == G - 1) S[(BH + 1) * NCOL + col] = has_down ? fmaf(-af, vh_bot[col], rh_bot) : 0.f;
+            __syncthreads();
             // t = A^ s ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
             scaled_matvec<CFG>(S, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, tt);
+            {
+              const uint32_t mb = smem_addr(xs.mb + (xs.round & 1));
+              if (send_up) st_async_f32(cluster_addr(smem_addr(TH + NCOL + col), rank - 1), tt[0], cluster_addr(mb, rank - 1));
+              if (send_down) st_async_f32(cluster_addr(smem_addr(TH + col), rank + 1), tt[K - 1], cluster_addr(mb, rank + 1));
+            }
             float p2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const int idx = (r0 + k + 1) * NCOL + col;
-              const float sv = S[idx], rh = RH[idx];
+              const float sv = S[(r0 + k + 1) * NCOL + col], rh = RH[(r0 + k) * NCOL + col];
               p2[0] = fmaf(tt[k], sv, p2[0]);
               p2[1] = fmaf(tt[k], tt[k], p2[1]);
               p2[2] = fmaf(rh, sv, p2[2]);
               p2[3] = fmaf(rh, tt[k], p2[3]);
             }
-            cluster_sum<CFG, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
-            const float of = sc->of, bf = sc->bf;
+            float tb[4];
+            xround<CFG, 4>(xs, p2, tb, rank, C, halo_bytes);
+            if (xs.dead) { conv = true; break; }
+            const float of = tb[1] > 0.f ? tb[0] / tb[1] : 0.f;
+            const float rho_new = tb[2] - of * tb[3];
+            float bf = 0.f;
+            if (of == 0.f || rho == 0.f) fail = true;
+            else bf = (rho_new / rho) * (af / of);
+            rho = rho_new;
             // x += alpha p + omega s ;  r = s - omega t ;  p = r + beta (p - omega v)
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -334,16 +537,25 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
               const float sv = S[idx], pv = P[idx];
               x[k] += af * pv + of * sv;
               rr[k] = fmaf(-of, tt[k], sv);
-              band_store<CFG>(P, pP, r0 + k, col, rr[k] + bf * (pv - of * vv[k]));
+              P[idx] = rr[k] + bf * (pv - of * vv[k]);
             }
-            if (sc->fail) break;
-            cluster_barrier(cluster, C);
+            if (grp == 0) {
+              rh_top = has_up ? fmaf(-of, TH[col], S[col]) : 0.f;
+              P[col] = has_up ? rh_top + bf * (P[col] - of * vh_top[col]) : 0.f;
+            }
+            if (grp == G - 1) {
+              rh_bot = has_down ? fmaf(-of, TH[NCOL + col], S[(BH + 1) * NCOL + col]) : 0.f;
+              P[(BH + 1) * NCOL + col] = has_down ? rh_bot + bf * (P[(BH + 1) * NCOL + col] - of * vh_bot[col]) : 0.f;
+            }
+            __syncthreads();
+            ++kit;
+            if (fail) break;
           }
-          if (sc->conv || !sc->fail) break;
+          if (conv || !fail) break;
 #pragma unroll
           for (int k = 0; k < K; ++k) xw[k] = x[k];
         }
-        if (!sc->conv) failed = true;
+        if (!conv) failed = true;
         iters_max = it > iters_max ? it : iters_max;
         iters_total += it;
         ++nsolves;
@@ -386,7 +598,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
       }
       double* norms = a.norms;
       const int slot_n = n + 1;
-      cluster_sum<CFG, 1>(cluster, nr, slots, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
+      cluster_sum<CFG, 1>(cluster, nr, slots, wpart, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
         if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = 0.0; }
       });
     } else {
@@ -413,11 +625,12 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
       }
       double* norms = a.norms;
       const int slot_n = n + 1;
-      cluster_sum<CFG, 2>(cluster, nr, slots, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
+      cluster_sum<CFG, 2>(cluster, nr, slots, wpart, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
         if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = s->tot[1]; }
       });
     }
   }
+  cluster_barrier(cluster, C);   // no CTA leaves while another may still address its memory
 
   if (rank == 0 && tid == 0) {
     if (failed) atomicOr(a.status, 1);
@@ -433,14 +646,13 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
       a.defect[0] = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
     }
   }
+  if (xs.dead && tid == 0) atomicOr(a.status, 2);
 }
 
-// Dynamic shared memory of sweep_band_kernel: planes u, P, S, RH; ID and XP (own rows);
-// row coefficients; reduction slots; scalars.
+// Dynamic shared memory of sweep_band_kernel.
 template <class CFG>
 static size_t sweep_smem_bytes() {
-  return (size_t)4 * CFG::PLANE * sizeof(float) + (size_t)2 * CFG::BH * CFG::NCOL * sizeof(float) +
-         (size_t)CFG::BH * sizeof(float2) + (2 * kMaxCluster * CFG::NW * 4) * sizeof(double) + sizeof(Scal);
+  return SweepSmem<CFG>::BYTES;
 }
 
 template <class CFG>
@@ -528,7 +740,8 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   const PayoffF pf = make_payoff(d);
   const float rdt = d.rdt;
   const float tol = (float)a.tol;
-  __shared__ double slots[2 * kMaxCluster * GCfg::NW * 4];
+  __shared__ double slots[2 * kMaxCluster * 4];
+  __shared__ double wpart[GCfg::NW * 4];
   __shared__ Scal scs;
   Scal* sc = &scs;
   int round = 0, iters_max = 0, iters_total = 0, nsolves = 0, nhist = 0;
@@ -588,7 +801,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
             part[0] = fmaf(bh, bh, part[0]);
             part[1] = fmaf(rr, rr, part[1]);
           }
-          cluster_sum<GCfg, 2>(cluster, part, slots, sc, round, rank, C,
+          cluster_sum<GCfg, 2>(cluster, part, slots, wpart, sc, round, rank, C,
                                [tol](Scal* s) { KrylovFin::start(s, tol); });
           for (size_t e = e0 + tid; e < e1; e += kGThreads) w.p[e] = w.r[e];
           barrier();
@@ -608,7 +821,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
               p1[0] = fmaf(w.rh[e], vv, p1[0]);
               p1[1] = fmaf(rr, rr, p1[1]);
             }
-            cluster_sum<GCfg, 2>(cluster, p1, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
+            cluster_sum<GCfg, 2>(cluster, p1, slots, wpart, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
             if (sc->conv || sc->fail) break;
             const float af = sc->af;
             for (size_t e = e0 + tid; e < e1; e += kGThreads) w.s[e] = fmaf(-af, w.v[e], w.r[e]);
@@ -629,7 +842,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
               p2[2] = fmaf(rh, sv, p2[2]);
               p2[3] = fmaf(rh, tt, p2[3]);
             }
-            cluster_sum<GCfg, 4>(cluster, p2, slots, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
+            cluster_sum<GCfg, 4>(cluster, p2, slots, wpart, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
             const float of = sc->of, bf = sc->bf;
             for (size_t e = e0 + tid; e < e1; e += kGThreads) {
               const float sv = w.s[e], pv = w.p[e], tt = w.t[e];
@@ -678,7 +891,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
       double* norms = a.norms;
       const int slot_n = n + 1;
       const bool iter = a.mode == SWEEP_ITER;
-      cluster_sum<GCfg, 2>(cluster, nr, slots, sc, round, rank, C, [norms, slot_n, rank, iter](Scal* s) {
+      cluster_sum<GCfg, 2>(cluster, nr, slots, wpart, sc, round, rank, C, [norms, slot_n, rank, iter](Scal* s) {
         if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = iter ? s->tot[1] : 0.0; }
       });
       barrier();

@@ -207,8 +207,9 @@ struct bs_grid {
   double xmax;
   int device;
   bsp::BandShape shape;
-  int* status;                 // device int[kStatusWords]: [0] bit 0 = Krylov cap hit,
-                               // [1] max iterations, [2] total iterations, [3] solves
+  int* status;                 // device int[kStatusWords]: [0] bit 0 = Krylov cap hit, bit 1 =
+                               // a cluster exchange timed out; [1] max iterations, [2] total
+                               // iterations, [3] solves
   double* dscal;               // device: scalar outputs (defect)
   double* dnorms;              // device: per-slice squared norms / defects
   bsp::Workspace ws_par;       // Parareal F / Gold buffers

@@ -148,6 +148,8 @@ extern "C" int parareal_solve_noalloc(int M, double xmax, const bs_params* p, in
     if (defect_hist) defect_hist[k] = host_defect;
     if (host_status) {
       *k_done = k + 1;
+      if (host_status & 2)
+        return set_error(BS_ERR_CUDA, "parareal_solve_noalloc: a cluster exchange of the coarse sweep timed out");
       return set_error(BS_ERR_NOCONV, "parareal_solve_noalloc: a coarse BiCGSTAB solve hit its iteration cap");
     }
     if (host_defect <= tol) {
