@@ -27,6 +27,7 @@ EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
 OPT_COARSE_VARIANT = 6
+OPT_JACOBI_TARGET_EXTRAP = 7
 PARAREAL_USER_U0 = 0x100
 
 
@@ -185,9 +186,14 @@ def parareal_solve_noalloc(M: int, xmax: float, p, N: int, fine_steps: int, coar
     return rc, k.value, [hist[i] for i in range(k.value)]
 
 
-def bs_fine_sweeps(g: Grid, p, dtau: float, first_step: bool = False) -> int:
+START_WARM, START_COLD, START_EXTRAP = 0, 1, 2
+
+
+def bs_fine_sweeps(g: Grid, p, dtau: float, first_step=False) -> int:
+    """Jacobi sweeps per fine step; first_step: True/1 = cold first step, False/0 = warm
+    start, 2 = extrapolated start."""
     bp = to_params(p)
-    return int(load().bs_fine_sweeps(g.h, C.byref(bp), float(dtau), int(bool(first_step))))
+    return int(load().bs_fine_sweeps(g.h, C.byref(bp), float(dtau), int(first_step)))
 
 
 def bs_set_option(option: int, value: float):

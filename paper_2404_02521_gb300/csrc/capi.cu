@@ -49,6 +49,7 @@ ItemDesc make_item(const bs_params& p, double tau0, double dtau) {
   d.payoff = p.payoff;
   d.sweeps = 0;
   d.sweeps0 = 0;
+  d.sweepsx = 0;
   d.ax = (float)(0.5 * p.sigma1 * p.sigma1 * dtau);
   d.mx = (float)(0.5 * p.r * dtau);
   d.ay = (float)(0.5 * p.sigma2 * p.sigma2 * dtau);
@@ -79,11 +80,13 @@ Options g_opt;
 
 // Sweeps so that q^m <= target (at least 3: the first sweep forms b, the last applies d, and
 // the far-field update sits between them).
-int sweeps_for(double q, bool cold) {
+int sweeps_for(double q, int start) {
   if (!(q < 0.8)) return 0;
   if (g_opt.fine_sweeps > 0) return g_opt.fine_sweeps;
   if (q <= 0.0) return 3;
-  const double target = cold ? g_opt.jacobi_target_cold : g_opt.jacobi_target;
+  const double target = start == START_COLD     ? g_opt.jacobi_target_cold
+                        : start == START_EXTRAP ? g_opt.jacobi_target_extrap
+                                                : g_opt.jacobi_target;
   int m = (int)std::ceil(std::log(target) / std::log(q));
   return m < 3 ? 3 : m;
 }
@@ -132,13 +135,13 @@ int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s)
   return BS_OK;
 }
 
-static int grid_sweeps(bs_grid* g, const bs_params& p, double dtau, bool cold = false) {
+static int grid_sweeps(bs_grid* g, const bs_params& p, double dtau, int start = START_WARM) {
   const double key[6] = {p.sigma1, p.sigma2, p.rho, p.r, dtau, (double)g->M};
   if (std::memcmp(key, g->q_key, sizeof(key)) != 0) {
     g->q_val = jacobi_contraction(g->M, p, dtau);
     std::memcpy(g->q_key, key, sizeof(key));
   }
-  return sweeps_for(g->q_val, cold);
+  return sweeps_for(g->q_val, start);
 }
 
 }  // namespace bsp
@@ -196,7 +199,8 @@ int bs_payoff(const bs_grid* g, const bs_params* p, float* u, bs_stream stream) 
 
 int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_step) {
   if (!g || check_params(p) || !(dtau > 0.0)) return 0;
-  return grid_sweeps(const_cast<bs_grid*>(g), *p, dtau, first_step != 0);
+  if (first_step < 0 || first_step > 2) return 0;
+  return grid_sweeps(const_cast<bs_grid*>(g), *p, dtau, first_step);
 }
 
 int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* const* u_in,
@@ -215,7 +219,8 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* co
     d.in = u_in[b];
     d.out = u_out[b];
     d.sweeps = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b]);
-    d.sweeps0 = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], true);
+    d.sweeps0 = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], START_COLD);
+    d.sweepsx = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], START_EXTRAP);
     if (d.sweeps == 0)
       return set_error(BS_ERR_ARG, "fine_propagate_batched: Jacobi contraction %.3f >= 0.8 for "
                        "item %d; take smaller fine steps", g->q_val, b);
@@ -280,6 +285,10 @@ int bs_set_option(int option, double value) {
     case BS_OPT_JACOBI_TARGET_COLD:
       if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_JACOBI_TARGET_COLD must be in (0, 1)");
       g_opt.jacobi_target_cold = value;
+      return BS_OK;
+    case BS_OPT_JACOBI_TARGET_EXTRAP:
+      if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_JACOBI_TARGET_EXTRAP must be in (0, 1)");
+      g_opt.jacobi_target_extrap = value;
       return BS_OK;
     case BS_OPT_COARSE_VARIANT:
       if (!(value == std::floor(value) && value >= -1.0 && value < 64.0))
@@ -400,7 +409,8 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   const double slice = p->T / N;
   const double dtau_f = slice / fine_steps;
   const int sweeps = grid_sweeps(g, *p, dtau_f);
-  const int sweeps0 = grid_sweeps(g, *p, dtau_f, true);
+  const int sweeps0 = grid_sweeps(g, *p, dtau_f, START_COLD);
+  const int sweepsx = grid_sweeps(g, *p, dtau_f, START_EXTRAP);
   if (sweeps == 0)
     return set_error(BS_ERR_ARG, "parareal_solve: Jacobi contraction %.3f >= 0.8; more fine steps needed", g->q_val);
   const size_t part_bytes = pino ? pino_partials_bytes(M, N) : 0;
@@ -470,6 +480,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
       d.out = Fb + (size_t)n * MM;
       d.sweeps = sweeps;
       d.sweeps0 = sweeps0;
+      d.sweepsx = sweepsx;
       items[(size_t)(n - k)] = d;
     }
     if ((rc = tf.begin(s))) return rc;

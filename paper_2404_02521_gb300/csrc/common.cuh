@@ -30,8 +30,9 @@ struct ItemDesc {
   double s1, s2, rho, r;
   double K, w1, w2, K2, cash;
   int payoff;
-  int sweeps;     // fine: Jacobi sweeps per warm-started implicit step (unused by coarse)
+  int sweeps;     // fine: Jacobi sweeps of the second step of a launch (warm start)
   int sweeps0;    // fine: Jacobi sweeps of the first step of a launch (cold start)
+  int sweepsx;    // fine: Jacobi sweeps of later steps (extrapolated start; tiles: warm)
   // Stencil constants of eq. (fd) in index units, rounded once from FP64 on the host:
   // east/west = ax*i^2 +- mx*i, south/north = ay*j^2 +- my*j, cross = gxy*i*j, rdt = r*dtau.
   float ax, mx, ay, my, gxy, rdt;
@@ -180,13 +181,15 @@ int cuda_error(cudaError_t e, const char* what);
 ItemDesc make_item(const bs_params& p, double tau0, double dtau);
 int check_params(const bs_params* p);
 double jacobi_contraction(int M, const bs_params& p, double dtau);
-int sweeps_for(double q, bool cold);
+enum SweepStart { START_WARM = 0, START_COLD = 1, START_EXTRAP = 2 };
+int sweeps_for(double q, int start);
 BandShape band_shape(int M);
 
 struct Options {
   int fine_sweeps = 0;
   double jacobi_target = 1.0 / 1024.0;            // warm-started steps: q^m <= 2^-10
   double jacobi_target_cold = 1.0 / 4194304.0;    // first step of a launch: q^m <= 2^-22
+  double jacobi_target_extrap = 1.0 / 16.0;       // extrapolated starts: q^m <= 2^-4
   double krylov_tol = 1e-6;
   int krylov_maxit = 400;
   int phase_timing = 0;

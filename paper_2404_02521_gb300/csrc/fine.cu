@@ -65,14 +65,24 @@ __device__ __forceinline__ float two_sum_update(float h0, float v, float& lo) {
   return hn;
 }
 
+// Initial guess of the next step from this step's increment v: with extrap, the linear
+// extrapolation 2 d_m - d_{m-1} (d_{m-1} from dp, own rows), else v itself; dp <- v.
+__device__ __forceinline__ float next_guess(float v, float* dp, int e, bool extrap) {
+  if (!dp) return v;
+  const float prev = dp[e];
+  dp[e] = v;
+  return extrap ? 2.f * v - prev : v;
+}
+
 // One Jacobi sweep over the thread's column strip (own band rows r0..r0+K-1, plane rows
 // r0+1..r0+K).  Strip rows 1..K-2 read only rows of the strip itself, written by this CTA
 // in the previous sweep; they are updated before the cluster wait.  The two end rows read
 // the rows just outside the strip (other row groups or the halo copies of the neighbouring
 // CTAs) and are updated after it, so the barrier latency overlaps the interior work.
 // The thread's own column of the old increment is in dv[].  FIRST also evaluates
-// b = dtau R_h w from hi; LAST also applies the increment to (hi, lo).  Nodes that are not
-// PDE rows have invd = 0 and write a zero increment.
+// b = dtau R_h w from hi; LAST also applies the increment to (hi, lo) and leaves the next
+// step's initial guess (next_guess) in wr and dv[].  Nodes that are not PDE rows have
+// invd = 0 and write a zero increment.
 template <class CFG, bool FIRST, bool LAST>
 __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* __restrict__ wr,
                                            float* hi, const HaloPush& wr_push,
@@ -80,7 +90,8 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
                                            float (&dv)[CFG::K], float (&b)[CFG::K],
                                            const float (&invd)[CFG::K], float (&lo)[CFG::K],
                                            int col, int il, int ir, int r0, float ce, float cw,
-                                           float cg0, float cgi, float rdt, bool clustered) {
+                                           float cg0, float cgi, float rdt, bool clustered,
+                                           float* dp = nullptr, bool extrap = false) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K;
   static_assert(K >= 4, "strip needs interior rows");
   const int p0 = r0 + 1;
@@ -113,9 +124,10 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
       hcW = hsW; hcC = hsC; hcE = hsE;
     }
     const float v = jacobi_point(b[k], invd[k], ce, cw, rc.x, rc.y, cg, nW, nC, nE, cW, cE, sW, sC, sE);
-    wr[p * NCOL + col] = v;
+    const float g = LAST ? next_guess(v, dp, (r0 + k) * NCOL + col, extrap) : v;
+    wr[p * NCOL + col] = g;
     nC = dv[k];
-    dv[k] = v;
+    dv[k] = g;
     nW = cW; nE = cE;
     cW = sW; cE = sE;
     if (LAST) hi[p * NCOL + col] = two_sum_update(hi[p * NCOL + col], v, lo[k]);
@@ -132,8 +144,9 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
       b[k] = rhs_point(ce, cw, rc.x, rc.y, cg, rdt, hnW, hnC, hnE, hcW, hcC, hcE, hsW, hsC, hsE);
     }
     const float v = jacobi_point(b[k], invd[k], ce, cw, rc.x, rc.y, cg, nW, nC, nE, cW, cE, sW, sC, sE);
-    band_store<CFG>(wr, wr_push, p - 1, col, v);
-    dv[k] = v;
+    const float g = LAST ? next_guess(v, dp, (r0 + k) * NCOL + col, extrap) : v;
+    band_store<CFG>(wr, wr_push, p - 1, col, g);
+    dv[k] = g;
     if (LAST) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[k]));
   }
   {  // first strip row: north = plane row p0-1, south = old row 1
@@ -148,8 +161,9 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
     }
     const float v = jacobi_point(b[0], invd[0], ce, cw, rc.x, rc.y, cg, qW, qC, qE, r0W, r0E, r1W,
                                  dv1_old, r1E);
-    band_store<CFG>(wr, wr_push, p - 1, col, v);
-    dv[0] = v;
+    const float g = LAST ? next_guess(v, dp, r0 * NCOL + col, extrap) : v;
+    band_store<CFG>(wr, wr_push, p - 1, col, g);
+    dv[0] = g;
     if (LAST) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[0]));
   }
 }
@@ -172,7 +186,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
   float* hi = smem;
   float* dA = hi + PLANE;
   float* dB = dA + PLANE;
-  float2* rowc = reinterpret_cast<float2*>(dB + PLANE);
+  float* DP = dB + PLANE;   // d_{m-1}, own rows [BH*NCOL]
+  float2* rowc = reinterpret_cast<float2*>(DP + BH * NCOL);
 
   band_load<CFG>(hi, d.in, M, jbase, tid);
   for (int e = tid; e < PLANE; e += CFG::NT) {
@@ -212,8 +227,11 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
   const bool clustered = C > 1;
   if (clustered) cl_arrive();
   int par = 0;
+  // Sweeps per step: the first step starts cold (zero increment), the second from the first
+  // increment, every later one from the extrapolation 2 d_{m-1} - d_{m-2}, which its last
+  // sweep leaves in the plane (next_guess).
   for (int step = 0; step < fb.nsteps; ++step) {
-    const int m = step == 0 ? d.sweeps0 : d.sweeps;   // the first step starts cold
+    const int m = step == 0 ? d.sweeps0 : step == 1 ? d.sweeps : d.sweepsx;
     for (int s = 0; s < m; ++s) {
       const float* rd = par ? dB : dA;
       float* wr = par ? dA : dB;
@@ -223,7 +241,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
                                      ce, cw, cg0, cgi, rdt, clustered);
       else if (s == m - 1)
         fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0,
-                                     ce, cw, cg0, cgi, rdt, clustered);
+                                     ce, cw, cg0, cgi, rdt, clustered, DP, step >= 1);
       else
         fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir,
                                       r0, ce, cw, cg0, cgi, rdt, clustered);
@@ -463,7 +481,8 @@ int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps) {
 
 template <class CFG>
 static int launch_band(const FineBatch& fb, cudaStream_t s) {
-  const size_t smem = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * sizeof(float2);
+  const size_t smem = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
+                      (size_t)CFG::BH * sizeof(float2);
   auto kern = fine_band_kernel<CFG>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (fb.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
