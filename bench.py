@@ -53,15 +53,27 @@ def fp32_peak_tflops(sm_mhz):
 
 
 # Algorithmic FLOPs of one fine point-step with m Jacobi sweeps: each sweep is the 9-point
-# update (5 FMA + 3 add + 1 multiply = 14 FLOP), plus b = dtau R_h w (16 FLOP) and the
-# compensated update (8 FLOP) once per step.  A launch of s steps takes m0 sweeps in its
-# first (cold-started) step and m in the others.
+# update (5 FMA + 3 add + 1 multiply = 14 FLOP), plus b = dtau R_h w (16 FLOP), the
+# compensated update (8 FLOP) and the next step's extrapolated guess (1 FMA = 2 FLOP) once
+# per step.  A launch of s steps takes m0 sweeps in its first (cold) step, m1 in the second
+# (warm start) and mx in the others (extrapolated start).
 def fine_flops_per_point_step(m):
-    return 14 * m + 24
+    return 14 * m + 26
 
 
-def fine_flops_per_point_launch(m, m0, steps):
-    return (steps - 1) * fine_flops_per_point_step(m) + fine_flops_per_point_step(m0)
+def fine_flops_per_point_launch(m0, m1, mx, steps):
+    f = fine_flops_per_point_step(m0)
+    if steps > 1:
+        f += fine_flops_per_point_step(m1)
+    if steps > 2:
+        f += (steps - 2) * fine_flops_per_point_step(mx)
+    return f
+
+
+# Algorithmic FLOPs of one BiCGSTAB iteration per node of the coarse solve: two Jacobi-scaled
+# 9-point products (15 FLOP each: 4 FMA, 1 multiply, 3 add, and the scaled subtraction), six
+# dot-product terms (12) and the vector updates s, x, r, p (13).
+COARSE_FLOPS_PER_NODE_ITER = 55
 
 
 class ClockSampler:
@@ -141,6 +153,14 @@ def barrier(world):
         dist.barrier()
 
 
+KERNEL_SOURCES = {
+    "fine_band_kernel": ["paper_2404_02521_gb300/csrc/fine.cu", "paper_2404_02521_gb300/csrc/band.cuh",
+                         "paper_2404_02521_gb300/csrc/common.cuh"],
+    "sweep_band_kernel": ["paper_2404_02521_gb300/csrc/coarse.cu", "paper_2404_02521_gb300/csrc/band.cuh",
+                          "paper_2404_02521_gb300/csrc/common.cuh"],
+}
+
+
 def traffic_for(kernel, source_files):
     """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -215,9 +235,21 @@ def gpu_arm(args, world, rank, local):
     pts_per_step = sum(pb.M * pb.M * pb.N * pb.fine_steps for pb in problems)
     value = world * args.steps * pts_per_step / (t_max_ms / 1e3)
 
+    # coarse iteration counts: one more (untimed) solve per rho; the solves are deterministic,
+    # so these are the timed solves' counts
+    krylov_iters = 0
+    krylov_solves = 0
+    for pb in problems:
+        solve(pb)
+        _, _, tot, ns = bs.bs_grid_stats(g, detail=True)
+        krylov_iters += tot
+        krylov_solves += ns
+    bs.bs_phase_stats(g)
+
     # fine stepper alone: every slice of every rho in one batched launch per rho
-    m_sweeps = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine)
-    m_cold = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, first_step=True)
+    m_sweeps = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_WARM)
+    m_cold = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_COLD)
+    m_extrap = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_EXTRAP)
     Fb = torch.empty((N, M, M), device=dev)
     for pb in problems:
         bs.bs_payoff(g, pb.params, U[0])
@@ -286,38 +318,45 @@ def gpu_arm(args, world, rank, local):
     for kl in ks:
         for k in kl:
             fine_pt_launches += sum((N - kk) for kk in range(k)) * M * M
-    fine_flops = fine_pt_launches * fine_flops_per_point_launch(m_sweeps, m_cold, pb0.fine_steps)
+    fine_flops = fine_pt_launches * fine_flops_per_point_launch(m_cold, m_sweeps, m_extrap, pb0.fine_steps)
     peak_fp32 = fp32_peak_tflops(sm_max)
     fine_tflops = fine_flops / (phases["fine_ms"] / 1e3) / 1e12 if phases["fine_ms"] > 0 else 0.0
+    # coarse: the timed region ran args.steps x the counted solves
+    coarse_flops = args.steps * krylov_iters * M * M * COARSE_FLOPS_PER_NODE_ITER
+    coarse_tflops = coarse_flops / (phases["coarse_ms"] / 1e3) / 1e12 if phases["coarse_ms"] > 0 else 0.0
+    variant = bs.bs_coarse_variant(g, pb0.params, pb0.dtau_coarse)
+    # CTAs of the coarse cluster at M = 256: band variant 7 holds 16 rows per CTA, 6 holds 32
+    cluster_ctas = -(-M // 16) if variant == 7 else -(-M // 32)
+    iter_us = 1e3 * phases["coarse_ms"] / max(1, args.steps * krylov_iters)
     kernels = {
         "fine_band_kernel": {"ms_total": phases["fine_ms"], "launches": phases["fine_launches"],
                              "ms_per_launch": fine_launch_ms, "bound": "alu",
                              "achieved_tflops": fine_tflops,
                              "peak_tflops": peak_fp32,
-                             "frac": fine_tflops / peak_fp32},
+                             "frac": fine_tflops / peak_fp32,
+                             "sweeps_per_step": {"cold": m_cold, "warm": m_sweeps, "extrapolated": m_extrap}},
         "sweep_band_kernel": {"ms_total": phases["coarse_ms"], "launches": phases["coarse_launches"],
-                              "ms_per_launch": coarse_launch_ms,
-                              "note": "serial coarse sweep: BiCGSTAB latency-bound (cluster barriers)"},
+                              "ms_per_launch": coarse_launch_ms, "bound": "alu",
+                              "achieved_tflops": coarse_tflops, "peak_tflops": peak_fp32,
+                              "frac": coarse_tflops / peak_fp32,
+                              "band_variant": variant, "cluster_ctas": cluster_ctas,
+                              "frac_of_cluster_sms": coarse_tflops / (peak_fp32 * cluster_ctas / 152),
+                              "krylov_iters_per_solve": krylov_iters / len(problems),
+                              "implicit_solves_per_solve": krylov_solves / len(problems),
+                              "us_per_krylov_iter": iter_us,
+                              "note": "serial coarse sweep on one thread-block cluster: latency-bound"},
     }
     dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
-    if dominant == "fine_band_kernel":
-        roof = {"kernel": dominant, "bound": "alu", "achieved": fine_tflops, "peak": peak_fp32,
-                "unit": "TFLOP/s", "frac": fine_tflops / peak_fp32,
-                "traffic": traffic_for("fine_band_kernel", ["paper_2404_02521_gb300/csrc/fine.cu"]),
-                "peak_source": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({pk_kind} max clock)"}
-    else:
-        # algorithmic FLOPs of the coarse sweep: per BiCGSTAB iteration and node, two
-        # matrix-vector products (2 x 14) and the dot/axpy work (22)
-        roof = {"kernel": dominant, "bound": "alu", "achieved": None, "peak": peak_fp32,
-                "unit": "TFLOP/s", "frac": None,
-                "traffic": traffic_for("sweep_band_kernel", ["paper_2404_02521_gb300/csrc/coarse.cu"]),
-                "peak_source": f"FP32 lanes x 2 x {sm_max:.0f} MHz ({pk_kind} max clock)",
-                "note": "latency-bound serial coarse solve; see kernels"}
+    kd = kernels[dominant]
+    roof = {"kernel": dominant, "bound": "alu", "achieved": kd["achieved_tflops"], "peak": peak_fp32,
+            "unit": "TFLOP/s", "frac": kd["frac"],
+            "traffic": traffic_for(dominant, KERNEL_SOURCES[dominant]),
+            "peak_source": f"FP32 lanes x 2 x {sm_max:.0f} MHz of 152 SMs ({pk_kind} max clock)"}
     launches = phases["fine_launches"] + phases["coarse_launches"] + phases["other_launches"]
     return {
         "value": value, "t_ms": t_max_ms, "ks": ks, "fine_rate": fine_rate, "fine_ms": fine_ms,
         "serial_ms": serial_ms, "e2e": e2e_value, "roof": roof, "kernels": kernels, "clocks": clk,
-        "launches": launches, "sweeps": m_sweeps, "sweeps_cold": m_cold, "pts_per_step": pts_per_step,
+        "launches": launches, "sweeps": m_extrap, "sweeps_cold": m_cold, "pts_per_step": pts_per_step,
         "h2d": len(problems) * M * M * 4, "d2h": len(problems) * M * M * 4,
     }
 

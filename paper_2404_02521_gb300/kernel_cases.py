@@ -10,6 +10,8 @@ workloads, one kernel each:
   coarse256  the initial serial coarse sweep of that workload (64 slices x 4 BiCGSTAB steps)
   tile1024   F on 48 slices of a 1024x1024 basket grid, 4 steps (haloed tiles, a launch
              per step; 48 x 4 MB of state exceeds the 129 MB L2)
+  solve256   one Parareal solve of that workload (rho = 0.7): payoff, initial coarse sweep,
+             then per iteration the batched F launch and a correcting coarse sweep
   coarse512  coarse propagation of one 512x512 state, 4 steps (global-memory BiCGSTAB)
   pino128    the PINO coarse propagator on 64 states of 128x128 (random weights)
 """
@@ -70,6 +72,14 @@ def case_coarse256(bs, wl, torch):
     return run
 
 
+def case_solve256(bs, wl, torch):
+    pb = wl.exchange_cfg2(0.7)
+    g = bs.Grid(pb.M, pb.xmax)
+    U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+    return lambda: bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM,
+                                     pb.coarse_steps, None, pb.tol, pb.N, U)
+
+
 def case_tile1024(bs, wl, torch):
     p = wl.basket_cfg1().params
     M, B, steps = 1024, 48, 4
@@ -117,7 +127,8 @@ def case_pino128(bs, wl, torch):
     return run
 
 
-CASES = {"fine256": case_fine256, "coarse256": case_coarse256, "tile1024": case_tile1024,
+CASES = {"fine256": case_fine256, "coarse256": case_coarse256, "solve256": case_solve256,
+         "tile1024": case_tile1024,
          "coarse512": case_coarse512, "pino128": case_pino128}
 
 
