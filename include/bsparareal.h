@@ -23,6 +23,8 @@
 #ifndef BSPARAREAL_H
 #define BSPARAREAL_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -226,6 +228,83 @@ int bs_phase_stats(bs_grid* g, double* fine_ms, int* fine_launches, double* coar
 int parareal_solve_noalloc(int M, double xmax, const bs_params* p, int N, int fine_steps,
                            int coarse_steps, double tol, int Kmax, float* u_out, int* k_done,
                            double* defect_hist, bs_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: continuous batching of Parareal pricing requests (no counterpart in the paper,
+ * which prices one option per run).
+ *
+ * A server owns one device arena of hbm_budget_bytes.  Each admitted request keeps its whole
+ * Parareal state in the arena -- U [N+1][M][M], F and G_old [N][M][M] in FP32 and 2(N+1) FP64
+ * norms, request_bytes = (3N+1) M^2 * 4 + 16 (N+1), rounded up to 256 -- from admission to
+ * completion.  Requests are admitted in submission order while one of max_active slots is
+ * free and the arena has room (first fit); a request that does not fit waits.  Every
+ * request runs the numerical-coarse Parareal of parareal_solve (eq. parareal; reading c5
+ * stopping norm) on its own CUDA stream; the fine propagation of all requests due at the
+ * same time is batched into one fine_propagate launch per (grid size, fine steps), and the
+ * serial coarse sweeps of different requests overlap on their streams.  A request's result
+ * does not depend on what it was batched with: every slice of a fine launch is computed
+ * independently, and each coarse sweep belongs to one request.
+ *
+ * The server is driven by the caller: bs_server_progress polls the requests' CUDA events
+ * (no blocking), retires finished requests, admits waiting ones and launches the next
+ * batched work; call it in a loop.  bs_server_poll returns finished requests.  A server is
+ * used from one host thread at a time (calls are serialised by an internal lock).
+ * --------------------------------------------------------------------------------------- */
+typedef struct bs_server bs_server;       /* opaque */
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* device arena for request state, >= 1 MiB */
+  int max_active;            /* requests on the device at once (one CUDA stream each), 1..256 */
+} bs_server_config;
+
+typedef struct {
+  bs_params p;               /* option parameters; p.T is the maturity */
+  int M;                     /* grid nodes per axis, 4..4096 */
+  double xmax;               /* domain [0, xmax]^2 */
+  int N;                     /* time slices */
+  int fine_steps;            /* implicit steps per slice of F; <= 0: 64, doubled until the
+                                Jacobi bound of a step is <= 0.7 */
+  int coarse_steps;          /* implicit steps per slice of the numerical G, >= 1 */
+  double tol;                /* Parareal tolerance on the defect (> 0) */
+  int Kmax;                  /* iteration cap, 1..N */
+  float* u_out;              /* [M*M] caller buffer (host or device) for u(T) = U[N]; it
+                                must stay valid until the request is reported done */
+} bs_request;
+
+typedef struct {
+  long long id;              /* from bs_server_submit */
+  int status;                /* BS_OK, BS_ERR_MAXITER (u_out holds the last iterate),
+                                BS_ERR_NOCONV or BS_ERR_CUDA */
+  int iterations;            /* Parareal iterations run */
+  double defect;             /* last defect */
+  double latency_ms;         /* host time from bs_server_submit to completion */
+  int fine_steps;            /* fine steps per slice used */
+} bs_result;
+
+typedef struct {
+  size_t arena_bytes, arena_used;
+  long long fine_batches;    /* batched fine launches (groups) */
+  long long fine_items;      /* slices propagated by them */
+  long long coarse_sweeps;   /* coarse sweeps launched */
+  long long launches;        /* kernels launched by the server */
+} bs_server_stats_t;
+
+/* Allocates the arena (cudaMalloc) and per-slot streams, events and pinned words on the
+ * current device.  BS_ERR_ARG for a budget below 1 MiB or max_active outside 1..256. */
+int bs_server_create(const bs_server_config* cfg, bs_server** out);
+/* Queues a request (copied); *id identifies it in bs_server_poll.  Host-only.  BS_ERR_ARG
+ * for invalid sizes or parameters, for explicit fine_steps whose Jacobi bound is >= 0.8, or
+ * for a request larger than the whole arena. */
+int bs_server_submit(bs_server* s, const bs_request* r, long long* id);
+/* Advances the server without blocking (see above); *active and *pending (either may be
+ * NULL) receive the numbers of admitted and waiting requests.  The first request of a grid
+ * size M <= 256 runs the coarse autotuner once (a few milliseconds, synchronous). */
+int bs_server_progress(bs_server* s, int* active, int* pending);
+/* Moves up to max_results finished requests into out[] (oldest first); *n receives the count. */
+int bs_server_poll(bs_server* s, bs_result* out, int max_results, int* n);
+int bs_server_stats(bs_server* s, bs_server_stats_t* st);
+/* Waits for the device, then releases everything (requests still in flight are dropped). */
+int bs_server_destroy(bs_server* s);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,8 @@ COARSE_NUM, COARSE_PINO = 0, 1
 EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
-           "bs_coarse_variant"]
+           "bs_coarse_variant", "bs_server_create", "bs_server_submit", "bs_server_progress",
+           "bs_server_poll", "bs_server_stats", "bs_server_destroy"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
 OPT_COARSE_VARIANT = 6
@@ -36,6 +37,27 @@ class bs_params(C.Structure):
                 ("r", C.c_double), ("T", C.c_double), ("strike", C.c_double),
                 ("w1", C.c_double), ("w2", C.c_double), ("payoff", C.c_int),
                 ("reserved", C.c_int), ("strike2", C.c_double), ("cash", C.c_double)]
+
+
+class bs_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int)]
+
+
+class bs_request(C.Structure):
+    _fields_ = [("p", bs_params), ("M", C.c_int), ("xmax", C.c_double), ("N", C.c_int),
+                ("fine_steps", C.c_int), ("coarse_steps", C.c_int), ("tol", C.c_double),
+                ("Kmax", C.c_int), ("u_out", C.c_void_p)]
+
+
+class bs_result(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("status", C.c_int), ("iterations", C.c_int),
+                ("defect", C.c_double), ("latency_ms", C.c_double), ("fine_steps", C.c_int)]
+
+
+class bs_server_stats_t(C.Structure):
+    _fields_ = [("arena_bytes", C.c_size_t), ("arena_used", C.c_size_t),
+                ("fine_batches", C.c_longlong), ("fine_items", C.c_longlong),
+                ("coarse_sweeps", C.c_longlong), ("launches", C.c_longlong)]
 
 
 class BSError(RuntimeError):
@@ -74,6 +96,12 @@ def load(path: Optional[str] = None):
     lib.bs_set_option.argtypes = [i, d]
     lib.bs_grid_stats.argtypes = [vp, P(i), P(i), P(i), P(i)]
     lib.bs_coarse_variant.argtypes = [vp, P(bs_params), d, P(i), vp]
+    lib.bs_server_create.argtypes = [P(bs_server_config), P(vp)]
+    lib.bs_server_submit.argtypes = [vp, P(bs_request), P(C.c_longlong)]
+    lib.bs_server_progress.argtypes = [vp, P(i), P(i)]
+    lib.bs_server_poll.argtypes = [vp, P(bs_result), i, P(i)]
+    lib.bs_server_stats.argtypes = [vp, P(bs_server_stats_t)]
+    lib.bs_server_destroy.argtypes = [vp]
     lib.bs_phase_stats.argtypes = [vp, P(d), P(i), P(d), P(i), P(i)]
     lib.parareal_solve_noalloc.argtypes = [i, d, P(bs_params), i, i, i, d, i, vp, P(i), P(d), vp]
     for name in EXPORTS:
@@ -238,6 +266,58 @@ class Pino:
     def close(self):
         if self.h:
             load().pino_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """bs_server handle: continuous batching of Parareal requests (numerical coarse G)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 32):
+        cfg = bs_server_config(int(hbm_budget_bytes), int(max_active))
+        h = C.c_void_p()
+        check(load().bs_server_create(C.byref(cfg), C.byref(h)))
+        self.h = h
+        self._keep = {}   # id -> output buffer kept alive until the request is done
+
+    def submit(self, p, M, xmax, N, u_out, fine_steps=0, coarse_steps=1, tol=1e-4, Kmax=None) -> int:
+        r = bs_request(to_params(p), int(M), float(xmax), int(N), int(fine_steps), int(coarse_steps),
+                       float(tol), int(N if Kmax is None else Kmax), _ptr(u_out))
+        rid = C.c_longlong(0)
+        check(load().bs_server_submit(self.h, C.byref(r), C.byref(rid)))
+        self._keep[rid.value] = u_out
+        return rid.value
+
+    def progress(self):
+        a, q = C.c_int(0), C.c_int(0)
+        check(load().bs_server_progress(self.h, C.byref(a), C.byref(q)))
+        return a.value, q.value
+
+    def poll(self, max_results: int = 256):
+        buf = (bs_result * max_results)()
+        n = C.c_int(0)
+        check(load().bs_server_poll(self.h, buf, int(max_results), C.byref(n)))
+        out = []
+        for k in range(n.value):
+            r = buf[k]
+            self._keep.pop(r.id, None)
+            out.append({"id": r.id, "status": r.status, "iterations": r.iterations, "defect": r.defect,
+                        "latency_ms": r.latency_ms, "fine_steps": r.fine_steps})
+        return out
+
+    def stats(self) -> dict:
+        st = bs_server_stats_t()
+        check(load().bs_server_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in bs_server_stats_t._fields_}
+
+    def close(self):
+        if self.h:
+            load().bs_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -135,7 +135,7 @@ int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s)
   return BS_OK;
 }
 
-static int grid_sweeps(bs_grid* g, const bs_params& p, double dtau, int start = START_WARM) {
+int grid_sweeps(bs_grid* g, const bs_params& p, double dtau, int start) {
   const double key[6] = {p.sigma1, p.sigma2, p.rho, p.r, dtau, (double)g->M};
   if (std::memcmp(key, g->q_key, sizeof(key)) != 0) {
     g->q_val = jacobi_contraction(g->M, p, dtau);

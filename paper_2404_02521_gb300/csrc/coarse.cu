@@ -59,9 +59,9 @@ __device__ __forceinline__ float* scal_tot(Scal* s, float) { return s->totf; }
 // column strip; zero on non-interior nodes (invd = 0 and y = 0 there).
 template <class CFG>
 __device__ __forceinline__ void scaled_matvec(const float* __restrict__ y,
-                                              const float2* __restrict__ rowc,
+                                              const float4* __restrict__ rowc,
                                               const float* __restrict__ ID, int col, int il,
-                                              int ir, int r0, float ce, float cw, float cg0,
+                                              int ir, int r0, float ce, float cw,
                                               float cgi, float (&out)[CFG::K]) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K;
   const int p0 = r0 + 1;
@@ -71,8 +71,8 @@ __device__ __forceinline__ void scaled_matvec(const float* __restrict__ y,
   for (int k = 0; k < K; ++k) {
     const int p = p0 + k;
     const float sW = y[(p + 1) * NCOL + il], sC = y[(p + 1) * NCOL + col], sE = y[(p + 1) * NCOL + ir];
-    const float2 rc = rowc[p - 1];
-    const float cg = fmaf((float)k, cgi, cg0);
+    const float4 rc = rowc[p - 1];
+    const float cg = cgi * rc.z;
     out[k] = cC - ID[(p - 1) * NCOL + col] *
                       (ce * cE + cw * cW + rc.x * sC + rc.y * nC + cg * ((sE - nE) - (sW - nW)));
     nW = cW; nC = cC; nE = cE;
@@ -291,8 +291,8 @@ struct SweepSmem {
   static constexpr size_t TH = VH + 4 * NCOL;    // [2: top, bottom][NCOL] t halo rows
   static constexpr size_t KSLOT = TH + 2 * NCOL; // [2][kMaxCluster][4] exchange partials
   static constexpr size_t KWP = KSLOT + 2 * kMaxCluster * 4;   // [NW][4]
-  static constexpr size_t ROWC = KWP + NW * 4;   // float2 [BH]
-  static constexpr size_t FLOATS = ROWC + 2 * BH;
+  static constexpr size_t ROWC = KWP + NW * 4;   // float4 [BH]: cs, cn, (float)j, 0
+  static constexpr size_t FLOATS = ROWC + 4 * BH;
   // doubles after the floats: slots [2][kMaxCluster][4], wpart [NW][4]; then mbarriers, Scal
   static constexpr size_t SLOTS_B = FLOATS * 4, WPART_B = SLOTS_B + 2 * kMaxCluster * 4 * 8;
   static constexpr size_t MB_B = WPART_B + NW * 4 * 8, SCAL_B = MB_B + 16;
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   float* XP = fs + L::XP;    // increment before xw  [BH*NCOL]
   float* VH = fs + L::VH;
   float* TH = fs + L::TH;
-  float2* rowc = reinterpret_cast<float2*>(fs + L::ROWC);
+  float4* rowc = reinterpret_cast<float4*>(fs + L::ROWC);
   double* slots = reinterpret_cast<double*>(smem_raw + L::SLOTS_B);
   double* wpart = reinterpret_cast<double*>(smem_raw + L::WPART_B);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::MB_B);
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
     row_coefs(d, jbase + r, cs, cn, gj);
-    rowc[r] = make_float2(cs, cn);
+    rowc[r] = make_float4(cs, cn, gj, 0.f);   // gj = (float)j exactly
   }
   if (tid == 0) {
     mbar_init(mbar, 1);
@@ -370,7 +370,6 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   xs.dead = false;
   float ce = 0.f, cw = 0.f, cgi = 0.f;
   column_coefs(d, col, ce, cw, cgi);
-  const float cg0 = cgi * (float)(jbase + r0);
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
   const float rdt = d.rdt;
@@ -434,8 +433,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
               const int p = p0 + k;
               const float sW = u[(p + 1) * NCOL + il], sC = u[(p + 1) * NCOL + col],
                           sE = u[(p + 1) * NCOL + ir];
-              const float2 rc = rowc[p - 1];
-              const float cg = fmaf((float)k, cgi, cg0);
+              const float4 rc = rowc[p - 1];
+              const float cg = cgi * rc.z;
               const float bb = ce * (cE - cC) - cw * (cC - cW) + rc.x * (sC - cC) - rc.y * (cC - nC) +
                                cg * ((sE - nE) - (sW - nW)) - rdt * cC;
               const float bh = bb * ID[(p - 1) * NCOL + col];
@@ -448,7 +447,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
 #pragma unroll
           for (int k = 0; k < K; ++k) band_store<CFG>(P, pP, r0 + k, col, x[k]);
           cluster_barrier(cluster, C);
-          scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
+          scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             rr[k] -= vv[k];
@@ -481,7 +480,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             float* vh_top = VH + (2 * par) * NCOL;
             float* vh_bot = VH + (2 * par + 1) * NCOL;
             // v = A^ p ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
-            scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, vv);
+            scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
             {
               const uint32_t mb = smem_addr(xs.mb + (xs.round & 1));
               if (send_up) st_async_f32(cluster_addr(smem_addr(vh_bot + col), rank - 1), vv[0], cluster_addr(mb, rank - 1));
@@ -506,7 +505,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             if (grp == G - 1) S[(BH + 1) * NCOL + col] = has_down ? fmaf(-af, vh_bot[col], rh_bot) : 0.f;
             __syncthreads();
             // t = A^ s ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
-            scaled_matvec<CFG>(S, rowc, ID, col, il, ir, r0, ce, cw, cg0, cgi, tt);
+            scaled_matvec<CFG>(S, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
             {
               const uint32_t mb = smem_addr(xs.mb + (xs.round & 1));
               if (send_up) st_async_f32(cluster_addr(smem_addr(TH + NCOL + col), rank - 1), tt[0], cluster_addr(mb, rank - 1));

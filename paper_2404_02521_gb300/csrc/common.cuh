@@ -232,6 +232,8 @@ namespace bsp {
 int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s);
 int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps);   // kernels launch_fine enqueues
 int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s);
+// Jacobi sweeps per fine step on this grid (cached contraction bound; 0 if q >= 0.8)
+int grid_sweeps(bs_grid* g, const bs_params& p, double dtau, int start = START_WARM);
 // Coarse numerical propagation / Parareal serial sweep (see coarse.cu).
 enum { SWEEP_PROP = 0, SWEEP_INIT = 1, SWEEP_ITER = 2 };
 struct SweepArgs {

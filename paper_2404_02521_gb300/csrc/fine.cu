@@ -86,11 +86,11 @@ __device__ __forceinline__ float next_guess(float v, float* dp, int e, bool extr
 template <class CFG, bool FIRST, bool LAST>
 __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* __restrict__ wr,
                                            float* hi, const HaloPush& wr_push,
-                                           const HaloPush& hi_push, const float2* __restrict__ rowc,
+                                           const HaloPush& hi_push, const float4* __restrict__ rowc,
                                            float (&dv)[CFG::K], float (&b)[CFG::K],
                                            const float (&invd)[CFG::K], float (&lo)[CFG::K],
                                            int col, int il, int ir, int r0, float ce, float cw,
-                                           float cg0, float cgi, float rdt, bool clustered,
+                                           float cgi, float rdt, bool clustered,
                                            float* dp = nullptr, bool extrap = false) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K;
   static_assert(K >= 4, "strip needs interior rows");
@@ -114,8 +114,8 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
     const int p = p0 + k;
     const float sW = rd[(p + 1) * NCOL + il], sE = rd[(p + 1) * NCOL + ir];
     const float sC = dv[k + 1];
-    const float2 rc = rowc[p - 1];
-    const float cg = fmaf((float)k, cgi, cg0);
+    const float4 rc = rowc[p - 1];
+    const float cg = cgi * rc.z;
     if (FIRST) {
       const float hsW = hi[(p + 1) * NCOL + il], hsC = hi[(p + 1) * NCOL + col],
                   hsE = hi[(p + 1) * NCOL + ir];
@@ -136,8 +136,8 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
   {  // last strip row: north = old row K-2 (window), south = plane row p0+K
     const int k = K - 1, p = p0 + k;
     const float sW = rd[(p + 1) * NCOL + il], sC = rd[(p + 1) * NCOL + col], sE = rd[(p + 1) * NCOL + ir];
-    const float2 rc = rowc[p - 1];
-    const float cg = fmaf((float)k, cgi, cg0);
+    const float4 rc = rowc[p - 1];
+    const float cg = cgi * rc.z;
     if (FIRST) {
       const float hsW = hi[(p + 1) * NCOL + il], hsC = hi[(p + 1) * NCOL + col],
                   hsE = hi[(p + 1) * NCOL + ir];
@@ -152,8 +152,8 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
   {  // first strip row: north = plane row p0-1, south = old row 1
     const int p = p0;
     const float qW = rd[(p - 1) * NCOL + il], qC = rd[(p - 1) * NCOL + col], qE = rd[(p - 1) * NCOL + ir];
-    const float2 rc = rowc[p - 1];
-    const float cg = cg0;
+    const float4 rc = rowc[p - 1];
+    const float cg = cgi * rc.z;
     if (FIRST) {
       const float hqW = hi[(p - 1) * NCOL + il], hqC = hi[(p - 1) * NCOL + col],
                   hqE = hi[(p - 1) * NCOL + ir];
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
   float* dA = hi + PLANE;
   float* dB = dA + PLANE;
   float* DP = dB + PLANE;   // d_{m-1}, own rows [BH*NCOL]
-  float2* rowc = reinterpret_cast<float2*>(DP + BH * NCOL);
+  float4* rowc = reinterpret_cast<float4*>(DP + BH * NCOL);
 
   band_load<CFG>(hi, d.in, M, jbase, tid);
   for (int e = tid; e < PLANE; e += CFG::NT) {
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
   for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
     row_coefs(d, jbase + r, cs, cn, gj);
-    rowc[r] = make_float2(cs, cn);
+    rowc[r] = make_float4(cs, cn, gj, 0.f);   // gj = (float)j exactly
   }
   const HaloPush hi_push = halo_push<CFG>(cluster, hi, rank, C);
   const HaloPush pA = halo_push<CFG>(cluster, dA, rank, C);
@@ -207,7 +207,6 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
 
   float ce = 0.f, cw = 0.f, cgi = 0.f;
   column_coefs(d, col, ce, cw, cgi);
-  const float cg0 = cgi * (float)(jbase + r0);
   float dv[K], b[K], invd[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -238,13 +237,13 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
       const HaloPush& wp = par ? pA : pB;
       if (s == 0)
         fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0,
-                                     ce, cw, cg0, cgi, rdt, clustered);
+                                     ce, cw, cgi, rdt, clustered);
       else if (s == m - 1)
         fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0,
-                                     ce, cw, cg0, cgi, rdt, clustered, DP, step >= 1);
+                                     ce, cw, cgi, rdt, clustered, DP, step >= 1);
       else
         fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir,
-                                      r0, ce, cw, cg0, cgi, rdt, clustered);
+                                      r0, ce, cw, cgi, rdt, clustered);
       // After the first sweep has read hi, move the far-field data to the next step (the
       // last sweep, at least one barrier later, leaves those nodes unchanged).
       if (s == 1 && step + 1 < fb.nsteps)
@@ -310,7 +309,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
   float* hi = smem;
   float* dA = hi + PLANE;
   float* dB = dA + PLANE;
-  float2* rowc = reinterpret_cast<float2*>(dB + PLANE);
+  float4* rowc = reinterpret_cast<float4*>(dB + PLANE);
   const float tau_new = (float)(d.tau0 + (step + 1) * d.dtau);
   for (int e = tid; e < PLANE; e += CFG::NT) {
     const int pr = e / NCOL, c = e % NCOL;
@@ -329,12 +328,11 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
   for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
     row_coefs(d, jy0 + r, cs, cn, gj);
-    rowc[r] = make_float2(cs, cn);
+    rowc[r] = make_float4(cs, cn, gj, 0.f);   // gj = (float)j exactly
   }
   const int ig = ix0 + col;
   float ce = 0.f, cw = 0.f, cgi = 0.f;
   column_coefs(d, ig, ce, cw, cgi);
-  const float cg0 = cgi * (float)(jy0 + r0);
   float dv[K], b[K], invd[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -361,16 +359,16 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
     const bool fst = s == 0, lst = commit && s == nsw - 1;
     if (fst && lst)
       fine_sweep<CFG, true, true>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                  cg0, cgi, rdt, false);
+                                  cgi, rdt, false);
     else if (fst)
       fine_sweep<CFG, true, false>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                   cg0, cgi, rdt, false);
+                                   cgi, rdt, false);
     else if (lst)
       fine_sweep<CFG, false, true>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                   cg0, cgi, rdt, false);
+                                   cgi, rdt, false);
     else
       fine_sweep<CFG, false, false>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce,
-                                    cw, cg0, cgi, rdt, false);
+                                    cw, cgi, rdt, false);
     p ^= 1;
     __syncthreads();
   }
@@ -422,7 +420,7 @@ static int launch_tiles(const bs_grid* g, const ItemDesc* items, int n, int nste
   }
   int rc = ensure(const_cast<bs_grid*>(g)->ws_fine, (size_t)std::min(n, kMaxItems) * 6 * MM * sizeof(float));
   if (rc) return rc;
-  const size_t smem = (size_t)3 * TileCfg::PLANE * sizeof(float) + (size_t)TileCfg::BH * sizeof(float2);
+  const size_t smem = (size_t)3 * TileCfg::PLANE * sizeof(float) + (size_t)TileCfg::BH * sizeof(float4);
   auto kern = fine_tile_kernel<TileCfg>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int base = 0; base < n; base += kMaxItems) {
@@ -482,7 +480,7 @@ int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps) {
 template <class CFG>
 static int launch_band(const FineBatch& fb, cudaStream_t s) {
   const size_t smem = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
-                      (size_t)CFG::BH * sizeof(float2);
+                      (size_t)CFG::BH * sizeof(float4);
   auto kern = fine_band_kernel<CFG>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (fb.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));

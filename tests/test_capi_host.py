@@ -64,3 +64,20 @@ def test_missing_weight_file(lib, tmp_path):
     rc = lib.pino_load(str(tmp_path / "nope.bin").encode(), C.byref(h))
     assert rc == _lib.BS_ERR_FILE
     assert not h.value
+
+
+def test_server_rejects_bad_arguments(lib):
+    from paper_2404_02521_gb300 import _lib
+    h = C.c_void_p()
+    assert lib.bs_server_create(None, C.byref(h)) == _lib.BS_ERR_ARG
+    cfg = _lib.bs_server_config(1024, 4)            # budget below 1 MiB
+    assert lib.bs_server_create(C.byref(cfg), C.byref(h)) == _lib.BS_ERR_ARG
+    cfg = _lib.bs_server_config(1 << 30, 0)         # no slots
+    assert lib.bs_server_create(C.byref(cfg), C.byref(h)) == _lib.BS_ERR_ARG
+    req = _lib.bs_request()
+    rid = C.c_longlong(0)
+    assert lib.bs_server_submit(None, C.byref(req), C.byref(rid)) == _lib.BS_ERR_ARG
+    n = C.c_int(0)
+    assert lib.bs_server_poll(None, None, 0, C.byref(n)) == _lib.BS_ERR_ARG
+    assert lib.bs_server_progress(None, None, None) == _lib.BS_ERR_ARG
+    assert lib.bs_server_destroy(None) == 0

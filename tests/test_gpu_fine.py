@@ -101,6 +101,26 @@ def test_tile_step_split_over_launches(bs):
     assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
 
 
+def test_tile_batch_composition_invariance(bs):
+    # a tile item's result does not depend on the halo width chosen for its batch (the
+    # halo follows the largest sweep count in the launch)
+    import torch
+    M = 300
+    pA = wl.Params(0.25, 0.35, 0.7, 0.03, payoff=wl.EXCHANGE)
+    pB = wl.Params(0.45, 0.3, -0.3, 0.06, payoff=wl.BASKET)
+    g = bs.Grid(M, 4.0)
+    u0 = to_gpu(start_state(M, 4.0, pA, "random", seed=3))
+    dA = 1.0 / 65536
+    for dB, nsteps in ((1.0 / 65536, 1), (1.0 / 16384, 3)):
+        a = torch.empty_like(u0)
+        bs.fine_propagate_batched(g, [pA], [u0], [a], [0.1], [dA], nsteps)
+        ab = [torch.empty_like(u0) for _ in range(2)]
+        bs.fine_propagate_batched(g, [pA, pB], [u0, u0], ab, [0.1, 0.2], [dA, dB], nsteps)
+        torch.cuda.synchronize()
+        assert bs.bs_fine_sweeps(g, pB, dB, True) > bs.bs_fine_sweeps(g, pA, dA, True)
+        assert torch.equal(a, ab[0])
+
+
 def test_batch_invariance_and_in_place(bs):
     import torch
     M, xmax = 100, 4.0

@@ -1,0 +1,94 @@
+"""Serving runtime (bs_server): continuous batching of Parareal requests of different grid
+sizes and slice counts.  Each result must be the same alone and in the mix (bitwise: every
+slice of a batched fine launch and every coarse sweep is computed independently of the other
+requests), admission must respect the HBM budget, and the results must be the Parareal
+solutions the oracle defines."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests.gpu_util import rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bs():
+    import paper_2404_02521_gb300 as bs
+    bs.load()
+    return bs
+
+
+def mix():
+    rng = np.random.default_rng(7)
+    out = []
+    for k, (M, N) in enumerate([(40, 4), (64, 8), (100, 4), (64, 6), (300, 4), (33, 8), (128, 4)]):
+        payoff = wl.BASKET if k % 2 == 0 else wl.EXCHANGE
+        p = wl.random_params(rng, payoff, float(rng.uniform(0.25, 1.0)))
+        out.append(wl.Problem(f"mix{k}", M, 4.0, N, 0, 1, p))
+    return out
+
+
+def alone(bs, reqs, fine_steps):
+    import torch
+    from paper_2404_02521_gb300 import serving
+    outs = [torch.empty((r.M, r.M), device="cuda") for r in reqs]
+    serving.service_times(reqs, fine_steps, outs)
+    return outs
+
+
+def test_mix_equals_alone_bitwise(bs):
+    import torch
+    from paper_2404_02521_gb300 import serving
+    reqs = mix()
+    outs = [torch.zeros((r.M, r.M), device="cuda") for r in reqs]
+    sv = bs.Server(1 << 30, 8)
+    # two waves: the second arrives while the first is on the GPU
+    arrivals = [0.0, 0.0, 0.0, 0.0, 0.01, 0.01, 0.02]
+    res, _ = serving.replay(sv, reqs, arrivals, outs)
+    st = sv.stats()
+    sv.close()
+    assert all(r["status"] == 0 for r in res), res
+    assert st["arena_used"] == 0 and st["fine_batches"] >= 1
+    fs = [r["fine_steps"] for r in res]
+    ref = alone(bs, reqs, fs)
+    for r, a, b in zip(reqs, outs, ref):
+        assert torch.equal(a, b), r.name
+
+
+def test_admission_waits_for_memory(bs):
+    # a budget that holds about two of the requests: the others wait and still finish
+    import torch
+    from paper_2404_02521_gb300 import serving
+    reqs = [wl.Problem(f"b{k}", 128, 4.0, 8, 0, 1, wl.basket_cfg1().params) for k in range(6)]
+    need = (3 * 8 + 1) * 128 * 128 * 4 + 16 * 9
+    sv = bs.Server(2 * need + 4096, 8)
+    outs = [torch.zeros((128, 128), device="cuda") for _ in reqs]
+    res, _ = serving.replay(sv, reqs, [0.0] * len(reqs), outs)
+    sv.close()
+    assert all(r["status"] == 0 for r in res)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+
+
+def test_serving_result_is_parareal_solution(bs):
+    # the served price surface equals the oracle's Parareal solution within the coarse
+    # tolerance and the serial fine solution within the Parareal tolerance
+    import torch
+    from oracle import fd
+    from oracle import parareal as opr
+    from paper_2404_02521_gb300 import serving
+    pb = wl.Problem("srv", 40, 4.0, 6, 0, 1, wl.basket_cfg1().params)
+    out = torch.zeros((40, 40), device="cuda")
+    sv = bs.Server(1 << 28, 2)
+    res, _ = serving.replay(sv, [pb], [0.0], [out])
+    sv.close()
+    fs = res[0]["fine_steps"]
+    pbf = wl.Problem("srv", 40, 4.0, 6, fs, 1, pb.params)
+    F = fd.SlicePropagator(40, 4.0, pb.params, 6, fs)
+    G = fd.SlicePropagator(40, 4.0, pb.params, 6, 1)
+    serial = fd.serial_fine(pbf)
+    Uo, ko, _, _ = opr.parareal(serial[0], F, G, 6, 1e-4, 6)
+    assert res[0]["iterations"] == ko
+    assert rel_err(to_np(out), Uo[6]) <= 6e-5
+    assert rel_err(to_np(out), serial[6]) <= 1e-3
