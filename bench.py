@@ -16,6 +16,7 @@ of the same workload, in the same unit.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -361,6 +362,62 @@ def gpu_arm(args, world, rank, local):
     }
 
 
+def serving_run(args):
+    """Serving sample: the first args.serve_requests requests of the seeded serving trace
+    (seed 12345: basket/exchange 50/50, sigma ~ U[0.1,0.5], rho ~ U[-0.7,0.7],
+    r ~ U[0,0.08], T ~ U[0.25,2], M in {64,128,256,512}, N in {16,32,64}; fine steps per slice
+    64 doubled until the Jacobi bound is <= 0.7, one coarse step per slice, tol 1e-4).
+    Poisson arrivals at args.serve_load x the measured one-at-a-time capacity."""
+    import numpy as np
+    import torch
+
+    import paper_2404_02521_gb300 as bs
+    from paper_2404_02521_gb300 import serving
+
+    n = args.serve_requests
+    reqs = [t.problem for t in wl.serving_trace(n, 0.0)]
+    fs = [bs.bs_fine_steps_for(r.M, r.params, r.N) for r in reqs]
+    # warm-up: one small request per grid size (autotuner, allocations, module loads)
+    seen = {}
+    for i, r in enumerate(reqs):
+        seen.setdefault(r.M, i)
+    warm = [wl.Problem("w", reqs[i].M, reqs[i].xmax, 16, 0, 1, dataclasses.replace(reqs[i].params, T=0.25))
+            for i in seen.values()]
+    wfs = [bs.bs_fine_steps_for(r.M, r.params, r.N) for r in warm]
+    serving.service_times(warm, wfs, [torch.empty((r.M, r.M), device="cuda") for r in warm])
+    sv = bs.Server(16 << 30, 32)
+    serving.replay(sv, warm, [0.0] * len(warm), [torch.empty((r.M, r.M), device="cuda") for r in warm])
+    # one request at a time through parareal_solve, back to back
+    alone = [torch.empty((r.M, r.M), device="cuda") for r in reqs]
+    st = serving.service_times(reqs, fs, alone)
+    svc = np.array([x["ms"] for x in st])
+    capacity = n / (svc.sum() / 1e3)
+    rate = args.serve_load * capacity
+    rng = np.random.default_rng(12345 + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+    arrivals -= arrivals[0]
+    outs = [torch.empty((r.M, r.M), device="cuda") for r in reqs]
+    res, makespan = serving.replay(sv, reqs, arrivals, outs)
+    stats = sv.stats()
+    sv.close()
+    lat = np.array([r["latency_ms"] for r in res])
+    fifo, fifo_span = serving.fifo_latencies(arrivals, svc)
+    same = sum(int(torch.equal(a, b)) for a, b in zip(outs, alone))
+    return {
+        "requests": n, "sample": f"first {n} requests of the seeded serving trace (seed 12345)",
+        "grids": sorted({r.M for r in reqs}), "arrival_rate_per_s": rate,
+        "load": args.serve_load, "one_at_a_time_capacity_per_s": capacity,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "solves_per_s": n / makespan, "makespan_s": makespan,
+        "one_at_a_time": {"p50_ms": float(np.percentile(fifo, 50)), "p99_ms": float(np.percentile(fifo, 99)),
+                          "solves_per_s": n / fifo_span, "service_ms_total": float(svc.sum())},
+        "status_ok": sum(int(r["status"] == 0) for r in res),
+        "parareal_iterations_mean": float(np.mean([r["iterations"] for r in res])),
+        "results_bitwise_equal_to_alone": same,
+        "fine_batches": stats["fine_batches"], "fine_slices_batched": stats["fine_items"],
+    }
+
+
 def oracle_sample(seconds_budget=15.0):
     """Oracle serial fine on the first rho of the workload, as many steps as fit the budget."""
     from oracle import fd
@@ -419,6 +476,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-load", type=float, default=0.8)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -438,6 +498,9 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"FP64 sparse-LU serial fine stepping of the 256x256 exchange workload "
                          f"(rho={wl.EXCHANGE_RHOS[0]}), first {st} of 32768 implicit steps, {dt:.1f} s"}
+    serving_res = None
+    if not args.no_serving and world == 1:
+        serving_res = serving_run(args)
     ks = r["ks"]
     mean_serial = statistics.mean(r["serial_ms"])
     per_solve = r["t_ms"] / (args.steps * len(wl.EXCHANGE_RHOS))
@@ -464,6 +527,7 @@ def main():
                 "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
+        "serving": serving_res,
     }
     print(json.dumps(out), flush=True)
 

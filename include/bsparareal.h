@@ -179,6 +179,13 @@ enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
        BS_OPT_COARSE_VARIANT = 6, BS_OPT_JACOBI_TARGET_EXTRAP = 7 };
 int bs_set_option(int option, double value);
 
+/* Fine steps per slice for a time step whose Jacobi bound q (the Gershgorin contraction of
+ * I - dtau R_h on an M x M grid, independent of xmax) is at most qmax: the smallest
+ * min_steps * 2^k (k >= 0, at most 2^20) with q(T / (N * steps)) <= qmax.  This is the rule
+ * the serving runtime applies to requests with fine_steps <= 0 (min_steps 64, qmax 0.7).
+ * Host-only.  BS_ERR_ARG for invalid arguments, qmax outside (0, 0.8), or no such count. */
+int bs_fine_steps_for(int M, const bs_params* p, int N, int min_steps, double qmax, int* steps);
+
 /* Coarse-sweep autotuner (no counterpart in the paper, which has one CPU code path).  For
  * M <= 256 the serial coarse sweep runs on one thread-block cluster; the band variants
  * (columns per CTA, threads per CTA, rows per thread, hence cluster size) trade per-iteration

@@ -24,7 +24,7 @@ EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
            "bs_coarse_variant", "bs_server_create", "bs_server_submit", "bs_server_progress",
-           "bs_server_poll", "bs_server_stats", "bs_server_destroy"]
+           "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
 OPT_COARSE_VARIANT = 6
@@ -102,6 +102,7 @@ def load(path: Optional[str] = None):
     lib.bs_server_poll.argtypes = [vp, P(bs_result), i, P(i)]
     lib.bs_server_stats.argtypes = [vp, P(bs_server_stats_t)]
     lib.bs_server_destroy.argtypes = [vp]
+    lib.bs_fine_steps_for.argtypes = [i, P(bs_params), i, i, d, P(i)]
     lib.bs_phase_stats.argtypes = [vp, P(d), P(i), P(d), P(i), P(i)]
     lib.parareal_solve_noalloc.argtypes = [i, d, P(bs_params), i, i, i, d, i, vp, P(i), P(d), vp]
     for name in EXPORTS:
@@ -212,6 +213,14 @@ def parareal_solve_noalloc(M: int, xmax: float, p, N: int, fine_steps: int, coar
                                        C.byref(k), hist, _stream(stream))
     check(rc, allow=(BS_ERR_MAXITER,) if allow_maxiter else ())
     return rc, k.value, [hist[i] for i in range(k.value)]
+
+
+def bs_fine_steps_for(M: int, p, N: int, min_steps: int = 64, qmax: float = 0.7) -> int:
+    """Smallest min_steps * 2^k fine steps per slice whose Jacobi bound is <= qmax."""
+    bp = to_params(p)
+    s = C.c_int(0)
+    check(load().bs_fine_steps_for(int(M), C.byref(bp), int(N), int(min_steps), float(qmax), C.byref(s)))
+    return s.value
 
 
 START_WARM, START_COLD, START_EXTRAP = 0, 1, 2

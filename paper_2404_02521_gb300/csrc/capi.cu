@@ -310,6 +310,22 @@ int bs_set_option(int option, double value) {
   return set_error(BS_ERR_ARG, "bs_set_option: unknown option %d", option);
 }
 
+int bs_fine_steps_for(int M, const bs_params* p, int N, int min_steps, double qmax, int* steps) {
+  if (!steps) return set_error(BS_ERR_ARG, "bs_fine_steps_for: NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (M < 4 || M > 4096 || N < 1 || min_steps < 1 || !(qmax > 0.0 && qmax < 0.8))
+    return set_error(BS_ERR_ARG, "bs_fine_steps_for: M=%d N=%d min_steps=%d qmax=%g", M, N, min_steps, qmax);
+  const double slice = p->T / N;
+  for (long long s = min_steps; s <= (1 << 20); s *= 2) {
+    if (jacobi_contraction(M, *p, slice / (double)s) <= qmax) {
+      *steps = (int)s;
+      return BS_OK;
+    }
+  }
+  return set_error(BS_ERR_ARG, "bs_fine_steps_for: no step count up to 2^20 reaches q <= %g", qmax);
+}
+
 int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* variant,
                       bs_stream stream) {
   if (!g || !variant) return set_error(BS_ERR_ARG, "bs_coarse_variant: NULL argument");

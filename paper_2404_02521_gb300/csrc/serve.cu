@@ -130,12 +130,10 @@ static size_t request_bytes(const bs_request& r) {
   return f + sizeof(double) * 2 * (r.N + 1);
 }
 
+// 64 steps per slice, doubled until the Jacobi bound of a fine step is at most 0.7
 static int auto_fine_steps(const bs_request& r) {
-  // 64 steps per slice, doubled until the Jacobi bound of a fine step is at most 0.7
-  const double slice = r.p.T / r.N;
-  for (int s = 64; s <= (1 << 20); s *= 2)
-    if (jacobi_contraction(r.M, r.p, slice / s) <= 0.7) return s;
-  return 0;
+  int s = 0;
+  return bs_fine_steps_for(r.M, &r.p, r.N, 64, 0.7, &s) == BS_OK ? s : 0;
 }
 
 static int take_grid(bs_server* sv, int M, double xmax, bs_grid** out) {
