@@ -57,17 +57,19 @@ def fp32_peak_tflops(sm_mhz):
 # update (5 FMA + 3 add + 1 multiply = 14 FLOP), plus b = dtau R_h w (16 FLOP), the
 # compensated update (8 FLOP) and the next step's extrapolated guess (1 FMA = 2 FLOP) once
 # per step.  A launch of s steps takes m0 sweeps in its first (cold) step, m1 in the second
-# (warm start) and mx in the others (extrapolated start).
+# (warm start), mx in steps 2-15 and mxl after them (extrapolated starts).
 def fine_flops_per_point_step(m):
     return 14 * m + 26
 
 
-def fine_flops_per_point_launch(m0, m1, mx, steps):
-    f = fine_flops_per_point_step(m0)
-    if steps > 1:
-        f += fine_flops_per_point_step(m1)
-    if steps > 2:
-        f += (steps - 2) * fine_flops_per_point_step(mx)
+EXTRAP_START, EXTRAP_LATE = 2, 16   # the library's default sweep schedule
+
+
+def fine_flops_per_point_launch(m0, m1, mx, mxl, steps):
+    f = 0
+    for step in range(steps):
+        m = m0 if step == 0 else m1 if step < EXTRAP_START else mx if step < EXTRAP_LATE else mxl
+        f += fine_flops_per_point_step(m)
     return f
 
 
@@ -251,6 +253,7 @@ def gpu_arm(args, world, rank, local):
     m_sweeps = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_WARM)
     m_cold = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_COLD)
     m_extrap = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_EXTRAP)
+    m_late = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_EXTRAP_LATE)
     Fb = torch.empty((N, M, M), device=dev)
     for pb in problems:
         bs.bs_payoff(g, pb.params, U[0])
@@ -319,7 +322,7 @@ def gpu_arm(args, world, rank, local):
     for kl in ks:
         for k in kl:
             fine_pt_launches += sum((N - kk) for kk in range(k)) * M * M
-    fine_flops = fine_pt_launches * fine_flops_per_point_launch(m_cold, m_sweeps, m_extrap, pb0.fine_steps)
+    fine_flops = fine_pt_launches * fine_flops_per_point_launch(m_cold, m_sweeps, m_extrap, m_late, pb0.fine_steps)
     peak_fp32 = fp32_peak_tflops(sm_max)
     fine_tflops = fine_flops / (phases["fine_ms"] / 1e3) / 1e12 if phases["fine_ms"] > 0 else 0.0
     # coarse: the timed region ran args.steps x the counted solves
@@ -335,7 +338,8 @@ def gpu_arm(args, world, rank, local):
                              "achieved_tflops": fine_tflops,
                              "peak_tflops": peak_fp32,
                              "frac": fine_tflops / peak_fp32,
-                             "sweeps_per_step": {"cold": m_cold, "warm": m_sweeps, "extrapolated": m_extrap}},
+                             "sweeps_per_step": {"cold": m_cold, "warm": m_sweeps, "extrapolated": m_extrap,
+                                                 "extrapolated_after_16": m_late}},
         "sweep_band_kernel": {"ms_total": phases["coarse_ms"], "launches": phases["coarse_launches"],
                               "ms_per_launch": coarse_launch_ms, "bound": "alu",
                               "achieved_tflops": coarse_tflops, "peak_tflops": peak_fp32,
@@ -357,7 +361,7 @@ def gpu_arm(args, world, rank, local):
     return {
         "value": value, "t_ms": t_max_ms, "ks": ks, "fine_rate": fine_rate, "fine_ms": fine_ms,
         "serial_ms": serial_ms, "e2e": e2e_value, "roof": roof, "kernels": kernels, "clocks": clk,
-        "launches": launches, "sweeps": m_extrap, "sweeps_cold": m_cold, "pts_per_step": pts_per_step,
+        "launches": launches, "sweeps": m_late, "sweeps_cold": m_cold, "pts_per_step": pts_per_step,
         "h2d": len(problems) * M * M * 4, "d2h": len(problems) * M * M * 4,
     }
 

@@ -147,8 +147,8 @@ int parareal_solve(const bs_grid* g, const bs_params* p, int N, int fine_steps,
 /* Number of Jacobi sweeps F uses per implicit step for these parameters and step size on
  * this grid, by how the step's solve starts: first_step = 1 for the first step of a launch
  * (zero increment), 0 for a step started from the previous increment (the second step; every
- * step after the first on the tile stepper of grids with M > 256), 2 for a step started from
- * the extrapolation of the two previous increments (third and later steps, M <= 256).
+ * step before BS_OPT_EXTRAP_START), 2 for a step started from the extrapolation of the two
+ * previous increments, 3 for such a step from BS_OPT_EXTRAP_LATE on.
  * 0 if Jacobi does not apply or first_step is out of range.  Host-only helper. */
 int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_step);
 
@@ -160,11 +160,18 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  *                        (default 2^-10)
  *  BS_OPT_JACOBI_TARGET_COLD  the same for the first step of a launch, which starts from a
  *                        zero increment (default 2^-22)
- *  BS_OPT_JACOBI_TARGET_EXTRAP  the same for the third and later steps of a launch, which
- *                        start from the extrapolation 2 d_{m-1} - d_{m-2} of the previous two
- *                        increments, an initial error smaller than the warm start's by about
- *                        dtau |u_ttt / u_tt| (default 2^-4; grids with M <= 256 -- the tile
- *                        stepper of larger grids warm-starts every step)
+ *  BS_OPT_JACOBI_TARGET_EXTRAP  the same for the steps of a launch from BS_OPT_EXTRAP_START
+ *                        on, which start from the extrapolation 2 d_{m-1} - d_{m-2} of the
+ *                        previous two increments (default 2^-6).  For a mode with
+ *                        dtau*lambda = a the extrapolation error is a^2 |d| against a |d| for
+ *                        the warm start: much smaller for slow modes, not for stiff ones
+ *  BS_OPT_EXTRAP_START   index (>= 2) of the first step of a launch that starts from the
+ *                        extrapolated guess; the steps before it are warm-started (default 2)
+ *  BS_OPT_EXTRAP_LATE    index of the first step that uses the late target below (default
+ *                        16: stiff modes, whose extrapolation is poor, decay by at least a
+ *                        factor 2 per step and are gone by then)
+ *  BS_OPT_JACOBI_TARGET_EXTRAP_LATE  the extrapolated-start target from BS_OPT_EXTRAP_LATE on
+ *                        (default 2^-4)
  *  BS_OPT_KRYLOV_TOL     relative residual at which a coarse BiCGSTAB solve stops (1e-6)
  *  BS_OPT_KRYLOV_MAXIT   iteration cap of a coarse BiCGSTAB solve (default 400)
  *  BS_OPT_PHASE_TIMING   1: parareal_solve brackets its fine and coarse launches with CUDA
@@ -176,7 +183,8 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  * Returns BS_OK or BS_ERR_ARG for an unknown option or an out-of-range value. */
 enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
        BS_OPT_KRYLOV_MAXIT = 3, BS_OPT_PHASE_TIMING = 4, BS_OPT_JACOBI_TARGET_COLD = 5,
-       BS_OPT_COARSE_VARIANT = 6, BS_OPT_JACOBI_TARGET_EXTRAP = 7 };
+       BS_OPT_COARSE_VARIANT = 6, BS_OPT_JACOBI_TARGET_EXTRAP = 7, BS_OPT_EXTRAP_START = 8,
+       BS_OPT_EXTRAP_LATE = 9, BS_OPT_JACOBI_TARGET_EXTRAP_LATE = 10 };
 int bs_set_option(int option, double value);
 
 /* Fine steps per slice for a time step whose Jacobi bound q (the Gershgorin contraction of

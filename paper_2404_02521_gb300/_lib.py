@@ -29,6 +29,9 @@ OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_
 OPT_JACOBI_TARGET_COLD = 5
 OPT_COARSE_VARIANT = 6
 OPT_JACOBI_TARGET_EXTRAP = 7
+OPT_EXTRAP_START = 8
+OPT_EXTRAP_LATE = 9
+OPT_JACOBI_TARGET_EXTRAP_LATE = 10
 PARAREAL_USER_U0 = 0x100
 
 
@@ -223,12 +226,12 @@ def bs_fine_steps_for(M: int, p, N: int, min_steps: int = 64, qmax: float = 0.7)
     return s.value
 
 
-START_WARM, START_COLD, START_EXTRAP = 0, 1, 2
+START_WARM, START_COLD, START_EXTRAP, START_EXTRAP_LATE = 0, 1, 2, 3
 
 
 def bs_fine_sweeps(g: Grid, p, dtau: float, first_step=False) -> int:
     """Jacobi sweeps per fine step; first_step: True/1 = cold first step, False/0 = warm
-    start, 2 = extrapolated start."""
+    start, 2 = extrapolated start, 3 = extrapolated start after the transient."""
     bp = to_params(p)
     return int(load().bs_fine_sweeps(g.h, C.byref(bp), float(dtau), int(first_step)))
 

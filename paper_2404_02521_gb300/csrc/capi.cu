@@ -50,6 +50,9 @@ ItemDesc make_item(const bs_params& p, double tau0, double dtau) {
   d.sweeps = 0;
   d.sweeps0 = 0;
   d.sweepsx = 0;
+  d.sweepsxl = 0;
+  d.xstart = g_opt.extrap_start;
+  d.xlate = g_opt.extrap_late > g_opt.extrap_start ? g_opt.extrap_late : g_opt.extrap_start;
   d.ax = (float)(0.5 * p.sigma1 * p.sigma1 * dtau);
   d.mx = (float)(0.5 * p.r * dtau);
   d.ay = (float)(0.5 * p.sigma2 * p.sigma2 * dtau);
@@ -84,9 +87,10 @@ int sweeps_for(double q, int start) {
   if (!(q < 0.8)) return 0;
   if (g_opt.fine_sweeps > 0) return g_opt.fine_sweeps;
   if (q <= 0.0) return 3;
-  const double target = start == START_COLD     ? g_opt.jacobi_target_cold
-                        : start == START_EXTRAP ? g_opt.jacobi_target_extrap
-                                                : g_opt.jacobi_target;
+  const double target = start == START_COLD          ? g_opt.jacobi_target_cold
+                        : start == START_EXTRAP      ? g_opt.jacobi_target_extrap
+                        : start == START_EXTRAP_LATE ? g_opt.jacobi_target_extrap_late
+                                                     : g_opt.jacobi_target;
   int m = (int)std::ceil(std::log(target) / std::log(q));
   return m < 3 ? 3 : m;
 }
@@ -199,7 +203,7 @@ int bs_payoff(const bs_grid* g, const bs_params* p, float* u, bs_stream stream) 
 
 int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_step) {
   if (!g || check_params(p) || !(dtau > 0.0)) return 0;
-  if (first_step < 0 || first_step > 2) return 0;
+  if (first_step < 0 || first_step > 3) return 0;
   return grid_sweeps(const_cast<bs_grid*>(g), *p, dtau, first_step);
 }
 
@@ -221,6 +225,7 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* co
     d.sweeps = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b]);
     d.sweeps0 = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], START_COLD);
     d.sweepsx = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], START_EXTRAP);
+    d.sweepsxl = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], START_EXTRAP_LATE);
     if (d.sweeps == 0)
       return set_error(BS_ERR_ARG, "fine_propagate_batched: Jacobi contraction %.3f >= 0.8 for "
                        "item %d; take smaller fine steps", g->q_val, b);
@@ -285,6 +290,20 @@ int bs_set_option(int option, double value) {
     case BS_OPT_JACOBI_TARGET_COLD:
       if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_JACOBI_TARGET_COLD must be in (0, 1)");
       g_opt.jacobi_target_cold = value;
+      return BS_OK;
+    case BS_OPT_EXTRAP_START:
+      if (!(value == std::floor(value) && value >= 2.0 && value <= 1e9))
+        return set_error(BS_ERR_ARG, "BS_OPT_EXTRAP_START must be an integer >= 2");
+      g_opt.extrap_start = (int)value;
+      return BS_OK;
+    case BS_OPT_EXTRAP_LATE:
+      if (!(value == std::floor(value) && value >= 2.0 && value <= 1e9))
+        return set_error(BS_ERR_ARG, "BS_OPT_EXTRAP_LATE must be an integer >= 2");
+      g_opt.extrap_late = (int)value;
+      return BS_OK;
+    case BS_OPT_JACOBI_TARGET_EXTRAP_LATE:
+      if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_JACOBI_TARGET_EXTRAP_LATE must be in (0, 1)");
+      g_opt.jacobi_target_extrap_late = value;
       return BS_OK;
     case BS_OPT_JACOBI_TARGET_EXTRAP:
       if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_JACOBI_TARGET_EXTRAP must be in (0, 1)");
@@ -427,6 +446,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   const int sweeps = grid_sweeps(g, *p, dtau_f);
   const int sweeps0 = grid_sweeps(g, *p, dtau_f, START_COLD);
   const int sweepsx = grid_sweeps(g, *p, dtau_f, START_EXTRAP);
+  const int sweepsxl = grid_sweeps(g, *p, dtau_f, START_EXTRAP_LATE);
   if (sweeps == 0)
     return set_error(BS_ERR_ARG, "parareal_solve: Jacobi contraction %.3f >= 0.8; more fine steps needed", g->q_val);
   const size_t part_bytes = pino ? pino_partials_bytes(M, N) : 0;
@@ -497,6 +517,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
       d.sweeps = sweeps;
       d.sweeps0 = sweeps0;
       d.sweepsx = sweepsx;
+      d.sweepsxl = sweepsxl;
       items[(size_t)(n - k)] = d;
     }
     if ((rc = tf.begin(s))) return rc;

@@ -32,7 +32,10 @@ struct ItemDesc {
   int payoff;
   int sweeps;     // fine: Jacobi sweeps of the second step of a launch (warm start)
   int sweeps0;    // fine: Jacobi sweeps of the first step of a launch (cold start)
-  int sweepsx;    // fine: Jacobi sweeps of later steps (extrapolated start; tiles: warm)
+  int sweepsx;    // fine: Jacobi sweeps of steps xstart .. xlate-1 (extrapolated start)
+  int sweepsxl;   // fine: Jacobi sweeps of steps >= xlate (extrapolated, transients decayed)
+  int xstart;     // fine: first step of a launch that starts from the extrapolated guess (>= 2)
+  int xlate;      // fine: first step that uses sweepsxl (>= xstart)
   // Stencil constants of eq. (fd) in index units, rounded once from FP64 on the host:
   // east/west = ax*i^2 +- mx*i, south/north = ay*j^2 +- my*j, cross = gxy*i*j, rdt = r*dtau.
   float ax, mx, ay, my, gxy, rdt;
@@ -181,7 +184,12 @@ int cuda_error(cudaError_t e, const char* what);
 ItemDesc make_item(const bs_params& p, double tau0, double dtau);
 int check_params(const bs_params* p);
 double jacobi_contraction(int M, const bs_params& p, double dtau);
-enum SweepStart { START_WARM = 0, START_COLD = 1, START_EXTRAP = 2 };
+enum SweepStart { START_WARM = 0, START_COLD = 1, START_EXTRAP = 2, START_EXTRAP_LATE = 3 };
+
+// Jacobi sweeps of step `step` (0-based) of a fine launch for this item.
+__host__ __device__ inline int step_sweeps(const ItemDesc& d, int step) {
+  return step == 0 ? d.sweeps0 : step < d.xstart ? d.sweeps : step < d.xlate ? d.sweepsx : d.sweepsxl;
+}
 int sweeps_for(double q, int start);
 BandShape band_shape(int M);
 
@@ -189,7 +197,10 @@ struct Options {
   int fine_sweeps = 0;
   double jacobi_target = 1.0 / 1024.0;            // warm-started steps: q^m <= 2^-10
   double jacobi_target_cold = 1.0 / 4194304.0;    // first step of a launch: q^m <= 2^-22
-  double jacobi_target_extrap = 1.0 / 16.0;       // extrapolated starts: q^m <= 2^-4
+  double jacobi_target_extrap = 1.0 / 64.0;       // extrapolated starts: q^m <= 2^-6
+  double jacobi_target_extrap_late = 1.0 / 16.0;  // ... from step extrap_late on: 2^-4
+  int extrap_start = 2;                           // first extrapolated step of a launch
+  int extrap_late = 16;                           // first step with the late target
   double krylov_tol = 1e-6;
   int krylov_maxit = 400;
   int phase_timing = 0;

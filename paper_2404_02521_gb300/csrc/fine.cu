@@ -226,11 +226,12 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
   const bool clustered = C > 1;
   if (clustered) cl_arrive();
   int par = 0;
-  // Sweeps per step: the first step starts cold (zero increment), the second from the first
-  // increment, every later one from the extrapolation 2 d_{m-1} - d_{m-2}, which its last
-  // sweep leaves in the plane (next_guess).
+  // Sweeps per step: the first step starts cold (zero increment), the next ones up to step
+  // xstart - 1 from the previous increment, every later one from the extrapolation
+  // 2 d_{m-1} - d_{m-2}, which the last sweep of the step before leaves in the plane
+  // (next_guess).
   for (int step = 0; step < fb.nsteps; ++step) {
-    const int m = step == 0 ? d.sweeps0 : step == 1 ? d.sweeps : d.sweepsx;
+    const int m = step_sweeps(d, step);
     for (int s = 0; s < m; ++s) {
       const float* rd = par ? dB : dA;
       float* wr = par ? dA : dB;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
                                      ce, cw, cgi, rdt, clustered);
       else if (s == m - 1)
         fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0,
-                                     ce, cw, cgi, rdt, clustered, DP, step >= 1);
+                                     ce, cw, cgi, rdt, clustered, DP, step + 1 >= d.xstart);
       else
         fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir,
                                       r0, ce, cw, cgi, rdt, clustered);
@@ -265,41 +266,53 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
 }
 
 // ---------------------------------------------------------------------------------------
-// Tile variant for grids that do not fit a cluster (M > 256): one implicit step per launch,
-// or several launches per step when its sweeps exceed the halo.  A CTA owns a TX x TY
-// interior tile and loads the surrounding region of (TX + 2H) x (TY + 2H) nodes (H >= the
-// launch's sweep count) of hi and of the current increment from global memory.  Every
-// sweep's result is exact one node further from the region's cut edges, so after H sweeps
-// the interior matches a whole-grid sweep bit for bit; the domain edges need no halo (zero
-// coefficients at x = 0, y = 0; Dirichlet at the far edges).  The interior's (hi, lo,
-// increment) go to the other half of a ping-pong workspace.  A launch runs sweeps
-// [s_begin, s_end) of the step; it applies the increment to (hi, lo) only if the item's
-// step ends in it, and copies an item whose step has already ended.
+// Cluster tiles for grids that do not fit one cluster (M > 256): one implicit step per launch,
+// or several launches per step when its sweeps exceed the halo.  A cluster of C CTAs owns a
+// region of 256 columns x 32C rows (CTA `rank` holds rows 32 rank .. 32 rank + 31 in the band
+// layout of band.cuh, so the rows between its CTAs are exchanged over DSMEM every sweep like
+// the band stepper's).  Only the region's outer edges are cut: they hold values that are not
+// updated, and every sweep's result is exact one node further from them, so after H sweeps
+// an interior of I x I nodes at offset (H, H) matches a whole-grid sweep bit for bit (the
+// domain edges need no halo: zero coefficients at x = 0, y = 0, Dirichlet at the far edges).
+// The grid is covered by ntx^2 such interiors.  (hi, lo, increment, previous increment) of
+// every node go to the other half of a ping-pong workspace; the increment slot holds the
+// next step's initial guess (extrapolated from the third step on, as in the band stepper).
+// A launch runs sweeps [s_begin, s_end) of the step; it applies the increment only if the
+// item's step ends in it, and copies an item whose step has already ended.
 // ---------------------------------------------------------------------------------------
-struct TileBatch {
+typedef BandCfg<256, 512, 16> CTileCfg;
+constexpr int kCTileMaxHalo = 32;   // sweeps per launch; the interior keeps >= 192 x 192 nodes
+
+struct CTileBatch {
   ItemDesc it[kMaxItems];
-  float* ws;        // per item: [2][hi, lo, increment][M*M]
-  int n, M, H, nsteps_total;
+  float* ws;        // per item: [2][hi, lo, increment, previous increment][M*M]
+  int n, M, H, I, ntx, C;
   float h;
 };
 
 template <class CFG>
-__global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_constant__ TileBatch tb,
-                                                               int step, int first, int last, int par,
-                                                               int s_begin, int s_end) {
+__global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_constant__ CTileBatch tb,
+                                                                int step, int first, int last, int par,
+                                                                int s_begin, int s_end) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, PLANE = CFG::PLANE;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = tb.C;
+  const int rank = (int)cluster.block_rank();
   const ItemDesc& d = tb.it[blockIdx.z];
-  const int M = tb.M, H = tb.H;
+  const int M = tb.M, H = tb.H, I = tb.I;
   const size_t MM = (size_t)M * M;
-  const int TX = NCOL - 2 * H, TY = BH - 2 * H;
-  const int ix0 = blockIdx.x * TX - H, jy0 = blockIdx.y * TY - H;   // region origin
-  float* ws = tb.ws + (size_t)(blockIdx.z) * 6 * MM;
-  const float* hi_g = first ? d.in : ws + (size_t)(par * 3 + 0) * MM;
-  const float* lo_g = ws + (size_t)(par * 3 + 1) * MM;
-  const float* dv_g = ws + (size_t)(par * 3 + 2) * MM;
-  float* hi_o = ws + (size_t)((par ^ 1) * 3 + 0) * MM;
-  float* lo_o = ws + (size_t)((par ^ 1) * 3 + 1) * MM;
-  float* dv_o = ws + (size_t)((par ^ 1) * 3 + 2) * MM;
+  const int tx = (int)blockIdx.y % tb.ntx, ty = (int)blockIdx.y / tb.ntx;
+  const int ix0 = tx * I - H, jy0 = ty * I - H;   // region origin
+  const int jb = jy0 + rank * BH;                 // row of this CTA's first own row
+  float* ws = tb.ws + (size_t)blockIdx.z * 8 * MM;
+  const float* hi_g = first ? d.in : ws + (size_t)(par * 4 + 0) * MM;
+  const float* lo_g = ws + (size_t)(par * 4 + 1) * MM;
+  const float* dv_g = ws + (size_t)(par * 4 + 2) * MM;
+  const float* dp_g = ws + (size_t)(par * 4 + 3) * MM;
+  float* hi_o = ws + (size_t)((par ^ 1) * 4 + 0) * MM;
+  float* lo_o = ws + (size_t)((par ^ 1) * 4 + 1) * MM;
+  float* dv_o = ws + (size_t)((par ^ 1) * 4 + 2) * MM;
+  float* dp_o = ws + (size_t)((par ^ 1) * 4 + 3) * MM;
   const int tid = threadIdx.x;
   const int col = tid % NCOL, grp = tid / NCOL;
   const int r0 = grp * K;
@@ -309,11 +322,14 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
   float* hi = smem;
   float* dA = hi + PLANE;
   float* dB = dA + PLANE;
-  float4* rowc = reinterpret_cast<float4*>(dB + PLANE);
+  float* DP = dB + PLANE;   // previous increment, own rows [BH*NCOL]
+  float4* rowc = reinterpret_cast<float4*>(DP + BH * NCOL);
   const float tau_new = (float)(d.tau0 + (step + 1) * d.dtau);
+  // own rows and both halo rows of hi and of the increment; the halo rows between CTAs are
+  // the neighbours' own rows now and are kept current by DSMEM pushes during the sweeps
   for (int e = tid; e < PLANE; e += CFG::NT) {
     const int pr = e / NCOL, c = e % NCOL;
-    const int j = jy0 + pr - 1, i = ix0 + c;
+    const int j = jb + pr - 1, i = ix0 + c;
     const bool in = (i >= 0 && i < M && j >= 0 && j < M);
     float hv = 0.f, dvv = 0.f;
     if (in) {
@@ -323,11 +339,17 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
     }
     hi[e] = hv;
     dA[e] = dvv;
-    dB[e] = 0.f;
+    dB[e] = dvv;
+  }
+  for (int e = tid; e < BH * NCOL; e += CFG::NT) {
+    const int r = e / NCOL, c = e % NCOL;
+    const int j = jb + r, i = ix0 + c;
+    const bool in = (i >= 0 && i < M && j >= 0 && j < M);
+    DP[e] = (in && !first) ? dp_g[(size_t)j * M + i] : 0.f;
   }
   for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
-    row_coefs(d, jy0 + r, cs, cn, gj);
+    row_coefs(d, jb + r, cs, cn, gj);
     rowc[r] = make_float4(cs, cn, gj, 0.f);   // gj = (float)j exactly
   }
   const int ig = ix0 + col;
@@ -336,7 +358,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
   float dv[K], b[K], invd[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int j = jy0 + r0 + k;
+    const int j = jb + r0 + k;
     const bool pde = ig >= 0 && ig < M - 1 && j >= 0 && j < M - 1;
     invd[k] = pde ? inv_diag(d, ig, j) : 0.f;
     const bool in = ig >= 0 && ig < M && j >= 0 && j < M;
@@ -347,113 +369,131 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_tile_kernel(const __grid_cons
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
   const float rdt = d.rdt;
-  const int m_item = step == 0 ? d.sweeps0 : d.sweeps;   // the first step starts cold
+  const HaloPush hi_push = halo_push<CFG>(cluster, hi, rank, C);
+  const HaloPush pA = halo_push<CFG>(cluster, dA, rank, C);
+  const HaloPush pB = halo_push<CFG>(cluster, dB, rank, C);
+  const int m_item = step_sweeps(d, step);
   const int nsw = max(0, min(s_end, m_item) - s_begin);
   const bool commit = nsw > 0 && min(s_end, m_item) == m_item;
-  const HaloPush none = {nullptr, nullptr};
-  __syncthreads();
+  cluster_barrier(cluster, C);   // every CTA's loads are done before the first push lands
+
+  cl_arrive();
   int p = 0;
   for (int s = 0; s < nsw; ++s) {
     const float* rd = p ? dB : dA;
     float* wr = p ? dA : dB;
+    const HaloPush& wp = p ? pA : pB;
     const bool fst = s == 0, lst = commit && s == nsw - 1;
     if (fst && lst)
-      fine_sweep<CFG, true, true>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                  cgi, rdt, false);
+      fine_sweep<CFG, true, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                  cgi, rdt, true, DP, step + 1 >= d.xstart);
     else if (fst)
-      fine_sweep<CFG, true, false>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                   cgi, rdt, false);
+      fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                   cgi, rdt, true);
     else if (lst)
-      fine_sweep<CFG, false, true>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                   cgi, rdt, false);
+      fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                   cgi, rdt, true, DP, step + 1 >= d.xstart);
     else
-      fine_sweep<CFG, false, false>(rd, wr, hi, none, none, rowc, dv, b, invd, lo, col, il, ir, r0, ce,
-                                    cw, cgi, rdt, false);
+      fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                    cgi, rdt, true);
     p ^= 1;
+    cl_arrive();
     __syncthreads();
   }
-  // interior of the tile
-  if (col >= H && col < H + TX && ig < M) {
+  cl_wait();   // no CTA leaves while a neighbour may still store into it
+
+  // the interior of the region
+  if (col >= H && col < H + I && ig < M) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int r = r0 + k, j = jy0 + r;
-      if (r >= H && r < H + TY && j < M) {
+      const int rr = rank * BH + r0 + k, j = jb + r0 + k;
+      if (rr >= H && rr < H + I && j < M) {
         const size_t gi = (size_t)j * M + ig;
-        const float hv = hi[(r + 1) * NCOL + col];
+        const float hv = hi[(r0 + k + 1) * NCOL + col];
         if (last) {
           d.out[gi] = hv + lo[k];
         } else {
           hi_o[gi] = hv;
           lo_o[gi] = lo[k];
           dv_o[gi] = dv[k];
+          dp_o[gi] = DP[(r0 + k) * NCOL + col];
         }
       }
     }
   }
 }
 
-typedef BandCfg<128, 512, 16> TileCfg;
-
-// u_out = hi + lo from the second workspace half (after a single tile step)
-__global__ void tile_finish_kernel(const __grid_constant__ TileBatch tb) {
+// u_out = hi + lo from the second workspace half (after a single launch)
+__global__ void ctile_finish_kernel(const __grid_constant__ CTileBatch tb) {
   const ItemDesc& d = tb.it[blockIdx.y];
   const size_t MM = (size_t)tb.M * tb.M;
-  const float* ws = tb.ws + (size_t)blockIdx.y * 6 * MM;
+  const float* ws = tb.ws + (size_t)blockIdx.y * 8 * MM;
   const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (e < MM) d.out[e] = ws[3 * MM + e] + ws[4 * MM + e];
+  if (e < MM) d.out[e] = ws[4 * MM + e] + ws[5 * MM + e];
 }
 
-// Sweeps of one step per tile launch (the halo width): larger halos leave too small an
-// interior of the 128 x 64 region.
-constexpr int kTileMaxHalo = 24;
-
 // Launches of one step whose largest sweep count is m: the step is split evenly.
-static int tile_launches_per_step(int m) { return (m + kTileMaxHalo - 1) / kTileMaxHalo; }
+static int ctile_launches_per_step(int m) { return (m + kCTileMaxHalo - 1) / kCTileMaxHalo; }
 
-static int launch_tiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
+// The largest sweep count of any item in step `step`.
+static int max_step_sweeps(const ItemDesc* items, int n, int step) {
+  int m = 1;
+  for (int k = 0; k < n; ++k) m = std::max(m, step_sweeps(items[k], step));
+  return m;
+}
+
+static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
   const int M = g->M;
   const size_t MM = (size_t)M * M;
-  int m_cold = 1, m_warm = 1;
-  for (int k = 0; k < n; ++k) {
-    m_cold = std::max(m_cold, items[k].sweeps0);
-    m_warm = std::max(m_warm, items[k].sweeps);
-  }
-  int rc = ensure(const_cast<bs_grid*>(g)->ws_fine, (size_t)std::min(n, kMaxItems) * 6 * MM * sizeof(float));
+  int rc = ensure(const_cast<bs_grid*>(g)->ws_fine, (size_t)std::min(n, kMaxItems) * 8 * MM * sizeof(float));
   if (rc) return rc;
-  const size_t smem = (size_t)3 * TileCfg::PLANE * sizeof(float) + (size_t)TileCfg::BH * sizeof(float4);
-  auto kern = fine_tile_kernel<TileCfg>;
+  const size_t smem = (size_t)3 * CTileCfg::PLANE * sizeof(float) +
+                      (size_t)CTileCfg::BH * CTileCfg::NCOL * sizeof(float) + (size_t)CTileCfg::BH * sizeof(float4);
+  auto kern = fine_ctile_kernel<CTileCfg>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int base = 0; base < n; base += kMaxItems) {
-    TileBatch tb;
+    CTileBatch tb;
     tb.n = std::min(n - base, kMaxItems);
     for (int k = 0; k < tb.n; ++k) tb.it[k] = items[base + k];
     tb.ws = (float*)g->ws_fine.ptr;
     tb.M = M;
-    tb.nsteps_total = nsteps;
     tb.h = (float)(g->xmax / (M - 1));
     int par = 0;
     bool pending_finish = false;
     for (int step = 0; step < nsteps; ++step) {
-      const int m = step == 0 ? m_cold : m_warm;
-      const int nl = tile_launches_per_step(m);
+      const int m = max_step_sweeps(tb.it, tb.n, step);
+      const int nl = ctile_launches_per_step(m);
       const int chunk = (m + nl - 1) / nl;
       for (int l = 0; l < nl; ++l) {
         const int s0 = l * chunk, s1 = std::min(m, s0 + chunk);
         tb.H = std::max(2, s1 - s0);
-        const int TX = TileCfg::NCOL - 2 * tb.H, TY = TileCfg::BH - 2 * tb.H;
-        const dim3 grid((M + TX - 1) / TX, (M + TY - 1) / TY, tb.n);
+        tb.ntx = (M + (CTileCfg::NCOL - 2 * tb.H) - 1) / (CTileCfg::NCOL - 2 * tb.H);
+        tb.I = (M + tb.ntx - 1) / tb.ntx;
+        tb.C = (tb.I + 2 * tb.H + CTileCfg::BH - 1) / CTileCfg::BH;
         const bool first = step == 0 && l == 0;
         const bool final_launch = step == nsteps - 1 && l == nl - 1;
         // A launch that reads u_in must not write u_out (they may alias): keep its result in
         // the workspace and form u_out in a separate pass.
         pending_finish = final_launch && first;
-        kern<<<grid, TileCfg::NT, smem, s>>>(tb, step, first, final_launch && !first, par, s0, s1);
-        BS_CUDA_TRY(cudaGetLastError());
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(tb.C, tb.ntx * tb.ntx, tb.n);
+        cfg.blockDim = dim3(CTileCfg::NT, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = tb.C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        BS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, tb, step, (int)first, (int)(final_launch && !first), par,
+                                       s0, s1));
         par ^= 1;
       }
     }
     if (pending_finish) {
-      tile_finish_kernel<<<dim3((unsigned)((MM + 255) / 256), tb.n), 256, 0, s>>>(tb);
+      ctile_finish_kernel<<<dim3((unsigned)((MM + 255) / 256), tb.n), 256, 0, s>>>(tb);
       BS_CUDA_TRY(cudaGetLastError());
     }
   }
@@ -466,13 +506,10 @@ int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps) {
   if (nsteps < 1) return 0;
   int total = 0;
   for (int base = 0; base < n; base += kMaxItems) {
-    int m_cold = 1, m_warm = 1;
-    for (int k = base; k < std::min(n, base + kMaxItems); ++k) {
-      m_cold = std::max(m_cold, items[k].sweeps0);
-      m_warm = std::max(m_warm, items[k].sweeps);
-    }
-    const int first = tile_launches_per_step(m_cold);
-    total += first + (nsteps - 1) * tile_launches_per_step(m_warm) + (nsteps == 1 && first == 1 ? 1 : 0);
+    const int nb = std::min(n - base, kMaxItems);
+    for (int step = 0; step < nsteps; ++step)
+      total += ctile_launches_per_step(max_step_sweeps(items + base, nb, step));
+    if (nsteps == 1 && ctile_launches_per_step(max_step_sweeps(items + base, nb, 0)) == 1) total += 1;
   }
   return total;
 }
@@ -502,7 +539,7 @@ static int launch_band(const FineBatch& fb, cudaStream_t s) {
 
 int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
   const BandShape sh = g->shape;
-  if (sh.C < 1 || sh.C > kMaxCluster) return launch_tiles(g, items, n, nsteps, s);
+  if (sh.C < 1 || sh.C > kMaxCluster) return launch_ctiles(g, items, n, nsteps, s);
   for (int base = 0; base < n; base += kMaxItems) {
     FineBatch fb;
     fb.n = (n - base) < kMaxItems ? (n - base) : kMaxItems;

@@ -75,7 +75,7 @@ extern "C" int parareal_solve_noalloc(int M, double xmax, const bs_params* p, in
   const double dtau_f = slice / fine_steps;
   const double q = jacobi_contraction(M, *p, dtau_f);
   const int sweeps = sweeps_for(q, START_WARM), sweeps0 = sweeps_for(q, START_COLD);
-  const int sweepsx = sweeps_for(q, START_EXTRAP);
+  const int sweepsx = sweeps_for(q, START_EXTRAP), sweepsxl = sweeps_for(q, START_EXTRAP_LATE);
   if (sweeps == 0)
     return set_error(BS_ERR_ARG, "parareal_solve_noalloc: Jacobi contraction %.3f >= 0.8", q);
 
@@ -135,6 +135,7 @@ extern "C" int parareal_solve_noalloc(int M, double xmax, const bs_params* p, in
         d.sweeps = sweeps;
         d.sweeps0 = sweeps0;
         d.sweepsx = sweepsx;
+        d.sweepsxl = sweepsxl;
         items[i] = d;
       }
       if ((rc = launch_fine(&g, items, B, fine_steps, s))) return rc;

@@ -89,7 +89,7 @@ struct Slot {
   size_t off = 0, bytes = 0;
   float *U = nullptr, *Fb = nullptr, *Gold = nullptr;
   double* norms = nullptr;
-  int k = 0, sweeps = 0, sweeps0 = 0, sweepsx = 0, result = BS_OK;
+  int k = 0, sweeps = 0, sweeps0 = 0, sweepsx = 0, sweepsxl = 0, result = BS_OK;
   double defect = 0.0, t_submit = 0.0;
 };
 
@@ -205,6 +205,7 @@ static int admit(bs_server* sv, Slot& sl, long long id, const bs_request& r, dou
   sl.sweeps = grid_sweeps(sl.g, r.p, dtau_f, START_WARM);
   sl.sweeps0 = grid_sweeps(sl.g, r.p, dtau_f, START_COLD);
   sl.sweepsx = grid_sweeps(sl.g, r.p, dtau_f, START_EXTRAP);
+  sl.sweepsxl = grid_sweeps(sl.g, r.p, dtau_f, START_EXTRAP_LATE);
   BS_CUDA_TRY(cudaMemsetAsync(sl.g->status, 0, kStatusWords * sizeof(int), sl.st));
   const ItemDesc dc = make_item(r.p, 0.0, slice / r.coarse_steps);
   if ((rc = launch_payoff(sl.g, dc, sl.U, sl.st))) return rc;
@@ -270,6 +271,7 @@ static int launch_group(bs_server* sv, const std::vector<Slot*>& grp) {
       d.sweeps = sl->sweeps;
       d.sweeps0 = sl->sweeps0;
       d.sweepsx = sl->sweepsx;
+      d.sweepsxl = sl->sweepsxl;
       items.push_back(d);
     }
   }

@@ -76,19 +76,19 @@ def test_tile_step_split_over_launches(bs):
     p = PARAMS[0]
     g = bs.Grid(M, xmax)
     lo, hi = 1e-6, 1e-2
-    for _ in range(60):           # step with 28..40 cold sweeps (Jacobi bound still < 0.8)
+    for _ in range(60):           # step with 36..48 cold sweeps (Jacobi bound still < 0.8)
         mid = (lo * hi) ** 0.5
         m0 = bs.bs_fine_sweeps(g, p, mid, first_step=True)
-        if m0 == 0 or m0 > 40:
+        if m0 == 0 or m0 > 48:
             hi = mid
-        elif m0 < 28:
+        elif m0 < 36:
             lo = mid
         else:
             break
     dtau = mid
-    assert 24 < bs.bs_fine_sweeps(g, p, dtau, first_step=True) <= 40
+    assert 32 < bs.bs_fine_sweeps(g, p, dtau, first_step=True) <= 48
     small = dtau / 16
-    assert bs.bs_fine_sweeps(g, p, small, first_step=True) <= 24
+    assert bs.bs_fine_sweeps(g, p, small, first_step=True) <= 32
     u0 = start_state(M, xmax, p, "payoff")
     uin = to_gpu(u0)
     outs = [torch.empty_like(uin) for _ in range(2)]
