@@ -187,6 +187,17 @@ enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
        BS_OPT_EXTRAP_LATE = 9, BS_OPT_JACOBI_TARGET_EXTRAP_LATE = 10 };
 int bs_set_option(int option, double value);
 
+/* Numerical coarse propagator on a coarser grid (the resolution change of Sec. 4.4 applied to
+ * the numerical coarse model): with Mc > 0, BS_COARSE_NUM on this grid computes
+ *     G(u) = P(G_c(R u)),   far-field data at the slice's end,
+ * where R restricts bilinearly to Mc x Mc nodes of the same domain, G_c takes the coarse
+ * implicit-Euler steps there, and P prolongs the coarse state bilinearly (spatially
+ * coarsened Parareal; converges quickly for smooth payoffs such as the basket).  This applies
+ * to coarse_propagate and parareal_solve (serial sweep: restrict, coarse solve and apply per
+ * slice).  Mc = 0 (default) or Mc = M: the coarse steps run on this grid.  Host-only.
+ * BS_ERR_ARG unless Mc is 0 or in [8, M]. */
+int bs_grid_set_coarse(bs_grid* g, int Mc);
+
 /* Fine steps per slice for a time step whose Jacobi bound q (the Gershgorin contraction of
  * I - dtau R_h on an M x M grid, independent of xmax) is at most qmax: the smallest
  * min_steps * 2^k (k >= 0, at most 2^20) with q(T / (N * steps)) <= qmax.  This is the rule

@@ -11,6 +11,7 @@ Modules
   fd            eq. (fd) assembled as a sparse matrix, implicit Euler by sparse LU
   parareal      textbook Parareal, eq. (parareal), with the defect norm
   fno           FP64 FNO / PINO forward (Sec. 3.4, 3.5)
+  resample      bilinear resampling; the numerical coarse model on a coarser grid (Sec. 4.4)
 
 Pinning: every function is checked by ``tests/test_oracle_*.py`` against facts
 the mathematics fixes (exactness of centred differences on x^a y^b, a, b <= 2,

@@ -22,6 +22,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import fd
+from .resample import bilinear_resample  # noqa: F401  (also used by the FNO tests)
 
 
 def spectral_conv(v: np.ndarray, R: np.ndarray, mx: int, my: int) -> np.ndarray:
@@ -86,15 +87,3 @@ def pino_coarse(u: np.ndarray, xmax: float, tau_n: float, dtau: float, params, w
     out[M - 1, :] = g[M - 1, :]
     out[:, M - 1] = g[:, M - 1]
     return out
-
-
-def bilinear_resample(u: np.ndarray, M_out: int) -> np.ndarray:
-    """Bilinear interpolation of a node-based field on [0, xmax]^2 from M_in to M_out nodes
-    per axis (both grids include both ends): node j of the output sits at j*(M_in-1)/(M_out-1)
-    in input index units."""
-    M_in = u.shape[0]
-    t = np.arange(M_out) * (M_in - 1) / (M_out - 1)
-    i0 = np.minimum(np.floor(t).astype(int), M_in - 2)
-    f = t - i0
-    rows = u[i0, :] * (1 - f)[:, None] + u[i0 + 1, :] * f[:, None]
-    return rows[:, i0] * (1 - f)[None, :] + rows[:, i0 + 1] * f[None, :]

@@ -24,7 +24,8 @@ EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
            "bs_coarse_variant", "bs_server_create", "bs_server_submit", "bs_server_progress",
-           "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for"]
+           "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for",
+           "bs_grid_set_coarse"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
 OPT_COARSE_VARIANT = 6
@@ -106,6 +107,7 @@ def load(path: Optional[str] = None):
     lib.bs_server_stats.argtypes = [vp, P(bs_server_stats_t)]
     lib.bs_server_destroy.argtypes = [vp]
     lib.bs_fine_steps_for.argtypes = [i, P(bs_params), i, i, d, P(i)]
+    lib.bs_grid_set_coarse.argtypes = [vp, i]
     lib.bs_phase_stats.argtypes = [vp, P(d), P(i), P(d), P(i), P(i)]
     lib.parareal_solve_noalloc.argtypes = [i, d, P(bs_params), i, i, i, d, i, vp, P(i), P(d), vp]
     for name in EXPORTS:
@@ -151,6 +153,11 @@ class Grid:
         h = C.c_void_p()
         check(lib.bs_grid_create(int(M), float(xmax), C.byref(h)))
         self.h, self.M, self.xmax = h, int(M), float(xmax)
+
+    def set_coarse(self, Mc: int):
+        """Run the numerical coarse propagator on an Mc x Mc grid with bilinear resampling
+        (0: on this grid)."""
+        check(load().bs_grid_set_coarse(self.h, int(Mc)))
 
     def close(self):
         if self.h:

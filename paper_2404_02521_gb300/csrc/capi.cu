@@ -189,6 +189,8 @@ int bs_grid_destroy(bs_grid* g) {
   if (g->ws_par.ptr) cudaFree(g->ws_par.ptr);
   if (g->ws_fine.ptr) cudaFree(g->ws_fine.ptr);
   if (g->ws_coarse.ptr) cudaFree(g->ws_coarse.ptr);
+  if (g->ws_rs.ptr) cudaFree(g->ws_rs.ptr);
+  if (g->coarse_grid) bs_grid_destroy(g->coarse_grid);
   delete g;
   return BS_OK;
 }
@@ -254,6 +256,10 @@ int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_pa
     if (net) return set_error(BS_ERR_ARG, "coarse_propagate: net must be NULL for BS_COARSE_NUM");
     if (nsteps < 1) return set_error(BS_ERR_ARG, "coarse_propagate: nsteps < 1");
     ItemDesc d = make_item(*p, tau0, dtau_slice / nsteps);
+    if (g->coarse_M > 0 && g->coarse_M != g->M) {
+      const_cast<bs_grid*>(g)->n_coarse += resampled_launches_per_slice();
+      return resampled_propagate(const_cast<bs_grid*>(g), d, u_in, u_out, tau0, nsteps, (cudaStream_t)stream);
+    }
     SweepArgs a = {};
     a.mode = SWEEP_PROP;
     a.n_first = 0;
@@ -327,6 +333,14 @@ int bs_set_option(int option, double value) {
       return BS_OK;
   }
   return set_error(BS_ERR_ARG, "bs_set_option: unknown option %d", option);
+}
+
+int bs_grid_set_coarse(bs_grid* g, int Mc) {
+  if (!g) return set_error(BS_ERR_ARG, "bs_grid_set_coarse: NULL grid");
+  if (Mc != 0 && (Mc < 8 || Mc > g->M))
+    return set_error(BS_ERR_ARG, "bs_grid_set_coarse: Mc=%d must be 0 or in [8, M=%d]", Mc, g->M);
+  g->coarse_M = Mc == g->M ? 0 : Mc;
+  return BS_OK;
 }
 
 int bs_fine_steps_for(int M, const bs_params* p, int N, int min_steps, double qmax, int* steps) {
@@ -459,7 +473,14 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   bs_pino* pnet = const_cast<bs_pino*>(net);
   // one serial coarse sweep (numerical: one persistent cluster kernel; PINO: per slice the
   // network kernels and the correction), counted into the grid's launch statistics
+  const bool resampled = !pino && g->coarse_M > 0 && g->coarse_M != g->M;
   auto sweep = [&](const ItemDesc& d, const SweepArgs& sa) -> int {
+    if (resampled) {
+      for (int n = sa.n_first; n < sa.N; ++n)
+        g->n_coarse += (sa.mode == SWEEP_ITER && n == sa.n_first) ? 1 : resampled_launches_per_slice();
+      g->n_coarse += 1;
+      return resampled_sweep(g, d, sa, s);
+    }
     if (!pino) {
       g->n_coarse += 1;
       return launch_sweep(g, d, sa, s);

@@ -230,6 +230,9 @@ struct bs_grid {
   bsp::Workspace ws_fine;      // tile fine stepper (M > 256): ping-pong hi, lo, increment
   bsp::Workspace ws_coarse;    // global-memory coarse solver (M > 256): Krylov vectors
   int coarse_variant = -1;     // band variant of the coarse sweep (-1: not chosen yet)
+  int coarse_M = 0;            // numerical G on an Mc x Mc grid with resampling (0: this grid)
+  bs_grid* coarse_grid = nullptr;   // that grid (created on first use)
+  bsp::Workspace ws_rs;        // resampling buffers and defect partials
   // cached contraction
   double q_key[6];
   double q_val;
@@ -265,6 +268,11 @@ struct SweepArgs {
 };
 int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
 int coarse_cached_variant(int device, int M);   // tuned (or default) variant, no allocation
+// Numerical G on the grid's coarse grid with bilinear resampling (resampled.cu).
+int resampled_propagate(bs_grid* g, const ItemDesc& d, const float* in, float* out, double tau0, int nsteps,
+                        cudaStream_t s);
+int resampled_sweep(bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
+int resampled_launches_per_slice();
 int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, int* chosen);
 // PINO coarse propagator (pino.cu)
 int pino_check(const bs_pino* net, int M);

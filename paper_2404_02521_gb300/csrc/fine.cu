@@ -54,6 +54,17 @@ __device__ __forceinline__ float jacobi_point(float b, float invd, float ce, flo
   return ((t1 + t2) + t3) * invd;
 }
 
+// Asynchronous 4-byte global -> shared copy; with ok == false the destination is zero-filled
+// and nothing is read.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Compensated update (hi, lo) += v: error-free two-sum, then renormalise.
 __device__ __forceinline__ float two_sum_update(float h0, float v, float& lo) {
   const float s = h0 + v;
@@ -323,29 +334,37 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   float* dA = hi + PLANE;
   float* dB = dA + PLANE;
   float* DP = dB + PLANE;   // previous increment, own rows [BH*NCOL]
-  float4* rowc = reinterpret_cast<float4*>(DP + BH * NCOL);
+  float* LO = DP + BH * NCOL;   // compensation words, own rows [BH*NCOL]
+  float4* rowc = reinterpret_cast<float4*>(LO + BH * NCOL);
   const float tau_new = (float)(d.tau0 + (step + 1) * d.dtau);
-  // own rows and both halo rows of hi and of the increment; the halo rows between CTAs are
-  // the neighbours' own rows now and are kept current by DSMEM pushes during the sweeps
+  // Own rows and both halo rows of hi and of the increment (the halo rows between CTAs are
+  // the neighbours' own rows now and are kept current by DSMEM pushes during the sweeps),
+  // and the own rows of the previous increment and of lo: asynchronous 4-byte copies, all in
+  // flight at once, zero-filled outside the domain.
   for (int e = tid; e < PLANE; e += CFG::NT) {
     const int pr = e / NCOL, c = e % NCOL;
     const int j = jb + pr - 1, i = ix0 + c;
     const bool in = (i >= 0 && i < M && j >= 0 && j < M);
-    float hv = 0.f, dvv = 0.f;
-    if (in) {
-      hv = hi_g[(size_t)j * M + i];
-      if (!first) dvv = dv_g[(size_t)j * M + i];
-      if (i == M - 1 || j == M - 1) hv = far_field(pf, i * tb.h, j * tb.h, tau_new);
-    }
-    hi[e] = hv;
-    dA[e] = dvv;
-    dB[e] = dvv;
+    const size_t gi = in ? (size_t)j * M + i : 0;
+    cp_async4(hi + e, hi_g + gi, in);
+    cp_async4(dA + e, dv_g + gi, in && !first);
   }
   for (int e = tid; e < BH * NCOL; e += CFG::NT) {
     const int r = e / NCOL, c = e % NCOL;
     const int j = jb + r, i = ix0 + c;
     const bool in = (i >= 0 && i < M && j >= 0 && j < M);
-    DP[e] = (in && !first) ? dp_g[(size_t)j * M + i] : 0.f;
+    const size_t gi = in ? (size_t)j * M + i : 0;
+    cp_async4(DP + e, dp_g + gi, in && !first);
+    cp_async4(LO + e, lo_g + gi, in && !first);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int e = tid; e < PLANE; e += CFG::NT) {
+    const int pr = e / NCOL, c = e % NCOL;
+    const int j = jb + pr - 1, i = ix0 + c;
+    if ((i == M - 1 && j >= 0 && j < M) || (j == M - 1 && i >= 0 && i < M))
+      hi[e] = far_field(pf, i * tb.h, j * tb.h, tau_new);
+    dB[e] = dA[e];
   }
   for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
@@ -361,10 +380,9 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
     const int j = jb + r0 + k;
     const bool pde = ig >= 0 && ig < M - 1 && j >= 0 && j < M - 1;
     invd[k] = pde ? inv_diag(d, ig, j) : 0.f;
-    const bool in = ig >= 0 && ig < M && j >= 0 && j < M;
-    lo[k] = (in && !first && pde) ? lo_g[(size_t)j * M + ig] : 0.f;
+    lo[k] = pde ? LO[(r0 + k) * NCOL + col] : 0.f;
     b[k] = 0.f;
-    dv[k] = (in && !first) ? dv_g[(size_t)j * M + ig] : 0.f;
+    dv[k] = dA[(r0 + k + 1) * NCOL + col];
   }
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
@@ -448,7 +466,7 @@ static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nst
   int rc = ensure(const_cast<bs_grid*>(g)->ws_fine, (size_t)std::min(n, kMaxItems) * 8 * MM * sizeof(float));
   if (rc) return rc;
   const size_t smem = (size_t)3 * CTileCfg::PLANE * sizeof(float) +
-                      (size_t)CTileCfg::BH * CTileCfg::NCOL * sizeof(float) + (size_t)CTileCfg::BH * sizeof(float4);
+                      (size_t)2 * CTileCfg::BH * CTileCfg::NCOL * sizeof(float) + (size_t)CTileCfg::BH * sizeof(float4);
   auto kern = fine_ctile_kernel<CTileCfg>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int base = 0; base < n; base += kMaxItems) {
