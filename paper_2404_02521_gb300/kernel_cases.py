@@ -13,6 +13,9 @@ workloads, one kernel each:
   solve256   one Parareal solve of that workload (rho = 0.7): payoff, initial coarse sweep,
              then per iteration the batched F launch and a correcting coarse sweep
   coarse512  coarse propagation of one 512x512 state, 4 steps (global-memory BiCGSTAB)
+  large1024  the large single solve: basket on 1024x1024, N = 128 slices of 1024 fine steps,
+             numerical G with 4 steps per slice on a 256x256 grid (bilinear resampling);
+             prints Parareal time to tolerance, iterations and serial fine stepping time
   pino128    the PINO coarse propagator on 64 states of 128x128 (random weights)
 """
 from __future__ import annotations
@@ -127,9 +130,42 @@ def case_pino128(bs, wl, torch):
     return run
 
 
+def case_large1024(bs, wl, torch):
+    import time
+    pb = wl.large_cfg4()
+    g = bs.Grid(pb.M, pb.xmax)
+    g.set_coarse(256)
+    U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+    state = {}
+
+    def run():
+        t0 = time.perf_counter()
+        rc, k, d = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM, pb.coarse_steps,
+                                     None, pb.tol, pb.N, U)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        state["solve"] = (rc, k, d, 1e3 * (t1 - t0))
+        if "serial" not in state:   # serial fine stepping once: N launches of one slice
+            S = torch.empty_like(U)
+            bs.bs_payoff(g, pb.params, S[0])
+            sl = pb.params.T / pb.N
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for n in range(pb.N):
+                bs.fine_propagate_batched(g, [pb.params], [S[n]], [S[n + 1]], [n * sl], [pb.dtau_fine],
+                                          pb.fine_steps)
+            torch.cuda.synchronize()
+            state["serial"] = 1e3 * (time.perf_counter() - t0)
+            state["err"] = float((U - S).abs().max() / S.abs().max())
+        rc, k, d, ms = state["solve"]
+        print(f"large1024: rc={rc} k={k} defects={['%.1e' % x for x in d]} parareal={ms:.0f} ms "
+              f"serial_fine={state['serial']:.0f} ms rel_diff_vs_serial={state['err']:.1e}", flush=True)
+    return run
+
+
 CASES = {"fine256": case_fine256, "coarse256": case_coarse256, "solve256": case_solve256,
          "tile1024": case_tile1024,
-         "coarse512": case_coarse512, "pino128": case_pino128}
+         "coarse512": case_coarse512, "pino128": case_pino128, "large1024": case_large1024}
 
 
 def main():
