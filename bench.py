@@ -141,13 +141,21 @@ def dist_setup():
 
 
 def barrier_max(x, world):
+    """Max of a per-rank value over all ranks (a tensor on the device the backend uses)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, t_max_ms):
+    """Units per second of the whole job: every rank processed units_per_rank_step per step
+    (weak scaling), and the job took the slowest rank's time."""
+    return world * steps * units_per_rank_step / (t_max_ms / 1e3)
 
 
 def barrier(world):
@@ -236,7 +244,7 @@ def gpu_arm(args, world, rank, local):
     phases = bs.bs_phase_stats(g)
     t_max_ms = barrier_max(total_ms, world)
     pts_per_step = sum(pb.M * pb.M * pb.N * pb.fine_steps for pb in problems)
-    value = world * args.steps * pts_per_step / (t_max_ms / 1e3)
+    value = whole_job_rate(pts_per_step, args.steps, world, t_max_ms)
 
     # coarse iteration counts: one more (untimed) solve per rho; the solves are deterministic,
     # so these are the timed solves' counts
@@ -309,7 +317,7 @@ def gpu_arm(args, world, rank, local):
         torch.cuda.synchronize()
         e2e_ms += 1e3 * (time.perf_counter() - t0)
     e2e_max = barrier_max(e2e_ms, world)
-    e2e_value = world * args.steps * pts_per_step / (e2e_max / 1e3)
+    e2e_value = whole_job_rate(pts_per_step, args.steps, world, e2e_max)
 
     # roofline of the dominant kernel by event-timed share
     pk, pk_kind = peaks()

@@ -131,6 +131,7 @@ class ImplicitEuler:
                  boundary: Optional[BoundaryFn] = None):
         self.M, self.xmax, self.p, self.dtau = M, xmax, params, dtau
         self.g = boundary if boundary is not None else dirichlet(params)
+        self._builtin_g = boundary is None
         self.X, self.Y = mesh(M, xmax)
         n = M - 1
         w = stencil_weights(M, xmax, params.sigma1, params.sigma2, params.rho, params.r)
@@ -161,8 +162,16 @@ class ImplicitEuler:
         self.lu = spla.splu(self.A)
 
     def boundary_values(self, tau: float) -> np.ndarray:
-        """g on the whole grid at time tau (only the far edges are used)."""
-        return np.asarray(self.g(self.X, self.Y, tau), dtype=np.float64)
+        """g at time tau; only the far edges i = M-1 and j = M-1 are used.  The built-in
+        closed forms act elementwise and are evaluated on those edges alone (the rest of the
+        returned grid is zero); a caller's boundary function gets the whole grid."""
+        if not self._builtin_g:
+            return np.asarray(self.g(self.X, self.Y, tau), dtype=np.float64)
+        M = self.M
+        out = np.zeros((M, M), dtype=np.float64)
+        out[M - 1, :] = np.asarray(self.g(self.X[M - 1, :], self.Y[M - 1, :], tau), dtype=np.float64)
+        out[:, M - 1] = np.asarray(self.g(self.X[:, M - 1], self.Y[:, M - 1], tau), dtype=np.float64)
+        return out
 
     def step(self, u: np.ndarray, tau_new: float) -> np.ndarray:
         """One implicit-Euler step from u^n (full [M][M] grid) to tau_new."""

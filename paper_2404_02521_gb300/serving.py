@@ -75,3 +75,9 @@ def fifo_latencies(arrivals_s, service_ms):
         end = start + service_ms[i]
         lat[i] = end - 1e3 * arrivals_s[i]
     return lat, end / 1e3
+
+
+def shard(n_requests: int, rank: int, world: int):
+    """Indices of the requests a replica serves when requests are partitioned across
+    world replicas by arrival order (round robin): disjoint, and together all of them."""
+    return list(range(rank, n_requests, world))
