@@ -148,6 +148,39 @@ int grid_sweeps(bs_grid* g, const bs_params& p, double dtau, int start) {
   return sweeps_for(g->q_val, start);
 }
 
+// Fine propagation of items whose Jacobi bound is too large for the sweep steppers: every
+// implicit step is solved by BiCGSTAB (the coarse solver), one cluster per state, in batched
+// SWEEP_PROP launches of states that share their parameters and step size.
+int launch_krylov_fine(bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
+  auto same = [](const ItemDesc& a, const ItemDesc& b) {
+    return a.s1 == b.s1 && a.s2 == b.s2 && a.rho == b.rho && a.r == b.r && a.K == b.K && a.w1 == b.w1 &&
+           a.w2 == b.w2 && a.K2 == b.K2 && a.cash == b.cash && a.payoff == b.payoff && a.dtau == b.dtau;
+  };
+  int i = 0;
+  while (i < n) {
+    SweepArgs a = {};
+    a.mode = SWEEP_PROP;
+    a.n_first = 0;
+    a.N = 1;
+    a.csteps = nsteps;
+    a.slice_len = 0.0;
+    a.status = g->status;
+    a.tol = g_opt.krylov_tol;
+    a.maxit = g_opt.krylov_maxit;
+    int j = i;
+    while (j < n && j - i < kMaxProp && same(items[i], items[j])) {
+      a.prop[j - i] = PropItem{items[j].in, items[j].out, items[j].tau0};
+      ++j;
+    }
+    a.nprop = j - i;
+    g->n_fine += 1;
+    int rc = launch_sweep(g, items[i], a, s);
+    if (rc) return rc;
+    i = j;
+  }
+  return BS_OK;
+}
+
 }  // namespace bsp
 
 using namespace bsp;
@@ -228,9 +261,6 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* co
     d.sweeps0 = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], START_COLD);
     d.sweepsx = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], START_EXTRAP);
     d.sweepsxl = grid_sweeps(const_cast<bs_grid*>(g), p[b], dtau[b], START_EXTRAP_LATE);
-    if (d.sweeps == 0)
-      return set_error(BS_ERR_ARG, "fine_propagate_batched: Jacobi contraction %.3f >= 0.8 for "
-                       "item %d; take smaller fine steps", g->q_val, b);
     items[(size_t)b] = d;
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -241,8 +271,16 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p, const float* co
                                     cudaMemcpyDeviceToDevice, s));
     return BS_OK;
   }
-  const_cast<bs_grid*>(g)->n_fine += fine_launches(g, items.data(), B, nsteps);
-  return launch_fine(g, items.data(), B, nsteps, s);
+  // Jacobi bound < 0.8: the sweep steppers; otherwise BiCGSTAB per step
+  std::vector<ItemDesc> jac, kry;
+  for (const ItemDesc& d : items) (d.sweeps > 0 ? jac : kry).push_back(d);
+  int rc = BS_OK;
+  if (!jac.empty()) {
+    const_cast<bs_grid*>(g)->n_fine += fine_launches(g, jac.data(), (int)jac.size(), nsteps);
+    if ((rc = launch_fine(g, jac.data(), (int)jac.size(), nsteps, s))) return rc;
+  }
+  if (!kry.empty()) rc = launch_krylov_fine(const_cast<bs_grid*>(g), kry.data(), (int)kry.size(), nsteps, s);
+  return rc;
 }
 
 int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_params* p,
@@ -461,8 +499,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   const int sweeps0 = grid_sweeps(g, *p, dtau_f, START_COLD);
   const int sweepsx = grid_sweeps(g, *p, dtau_f, START_EXTRAP);
   const int sweepsxl = grid_sweeps(g, *p, dtau_f, START_EXTRAP_LATE);
-  if (sweeps == 0)
-    return set_error(BS_ERR_ARG, "parareal_solve: Jacobi contraction %.3f >= 0.8; more fine steps needed", g->q_val);
+  const bool krylov_f = sweeps == 0;   // Jacobi bound >= 0.8: F by BiCGSTAB per step
   const size_t part_bytes = pino ? pino_partials_bytes(M, N) : 0;
   rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1) + part_bytes);
   if (rc) return rc;
@@ -542,10 +579,14 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
       items[(size_t)(n - k)] = d;
     }
     if ((rc = tf.begin(s))) return rc;
-    rc = launch_fine(g, items.data(), B, fine_steps, s);
+    if (krylov_f) {
+      rc = launch_krylov_fine(g, items.data(), B, fine_steps, s);
+    } else {
+      rc = launch_fine(g, items.data(), B, fine_steps, s);
+      g->n_fine += fine_launches(g, items.data(), B, fine_steps);
+    }
     if (rc) return rc;
     if ((rc = tf.end(s))) return rc;
-    g->n_fine += fine_launches(g, items.data(), B, fine_steps);
     a.mode = SWEEP_ITER;
     a.n_first = k;
     if ((rc = tc.begin(s))) return rc;

@@ -379,9 +379,12 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   int kit = 0;   // BiCGSTAB iterations run by this kernel (parity of the v halo buffers)
   bool failed = false;
 
+  // batched PROP: this cluster's state
+  const bool batched = a.mode == SWEEP_PROP && a.nprop > 0;
+  const PropItem pit = batched ? a.prop[blockIdx.y] : PropItem{a.in, a.out, d.tau0};
   // initial state of the first slice (own rows and halo rows)
   const float* src;
-  if (a.mode == SWEEP_PROP) src = a.in;
+  if (a.mode == SWEEP_PROP) src = pit.in;
   else if (a.mode == SWEEP_INIT) src = a.U;
   else src = a.Gold + (size_t)a.n_first * MM;   // ITER: G(u_k) is unchanged -> reuse G_old_k
   band_load<CFG>(u, src, M, jbase, tid);
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
     const bool skip_g = (a.mode == SWEEP_ITER && n == a.n_first);
     if (!skip_g) {
       for (int cstep = 0; cstep < a.csteps; ++cstep) {
-        const double tau_new = d.tau0 + a.slice_len * n + (cstep + 1) * d.dtau;
+        const double tau_new = pit.tau0 + a.slice_len * n + (cstep + 1) * d.dtau;
         band_far_field<CFG>(u, pu, pf, (float)tau_new, h, M, jbase, tid);
         cluster_barrier(cluster, C);
         if (nhist >= 2) {
@@ -576,7 +579,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const int j = jbase + r0 + k;
-          if (j < M) a.out[(size_t)j * M + col] = u[(r0 + k + 1) * NCOL + col];
+          if (j < M) pit.out[(size_t)j * M + col] = u[(r0 + k + 1) * NCOL + col];
         }
       }
     } else if (a.mode == SWEEP_INIT) {
@@ -661,7 +664,7 @@ static int launch_sweep_k(const SweepParams& sp, cudaStream_t s) {
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (sp.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(sp.sh.C, 1, 1);
+  cfg.gridDim = dim3(sp.sh.C, sp.a.mode == SWEEP_PROP && sp.a.nprop > 0 ? sp.a.nprop : 1, 1);
   cfg.blockDim = dim3(CFG::NT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -728,7 +731,15 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   cg::cluster_group cluster = cg::this_cluster();
   const ItemDesc& d = gp.d;
   const SweepArgs& a = gp.a;
-  const GlobalVecs& w = gp.w;
+  const bool batched = a.mode == SWEEP_PROP && a.nprop > 0;
+  const PropItem pit = batched ? a.prop[blockIdx.y] : PropItem{a.in, a.out, d.tau0};
+  // per-state workspace of a batched PROP launch
+  GlobalVecs w = gp.w;
+  if (batched) {
+    const size_t off = (size_t)blockIdx.y * 10 * (size_t)gp.M * gp.M;
+    w.u += off; w.x += off; w.xp += off; w.r += off; w.rh += off;
+    w.p += off; w.v += off; w.s += off; w.t += off; w.id += off;
+  }
   const int M = gp.M, C = gp.C;
   const int rank = C > 1 ? (int)cluster.block_rank() : 0;
   const int tid = threadIdx.x;
@@ -752,7 +763,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
     w.id[e] = (i < M - 1 && j < M - 1) ? inv_diag(d, i, j) : 0.f;
     w.x[e] = 0.f;
     w.xp[e] = 0.f;
-    const float* src = a.mode == SWEEP_PROP ? a.in : a.mode == SWEEP_INIT ? a.U : a.Gold + (size_t)a.n_first * MM;
+    const float* src = a.mode == SWEEP_PROP ? pit.in : a.mode == SWEEP_INIT ? a.U : a.Gold + (size_t)a.n_first * MM;
     w.u[e] = src[e];
   }
   barrier();
@@ -761,7 +772,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
     const bool skip_g = (a.mode == SWEEP_ITER && n == a.n_first);
     if (!skip_g) {
       for (int cstep = 0; cstep < a.csteps; ++cstep) {
-        const float tau_new = (float)(d.tau0 + a.slice_len * n + (cstep + 1) * d.dtau);
+        const float tau_new = (float)(pit.tau0 + a.slice_len * n + (cstep + 1) * d.dtau);
         // initial guess 2 d_{m-1} - d_{m-2} (see the band kernel); x holds d_{m-1}
         const bool extrap = nhist >= 2;
         for (size_t e = e0 + tid; e < e1; e += kGThreads) {
@@ -865,7 +876,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
       }
     }
     if (a.mode == SWEEP_PROP) {
-      for (size_t e = e0 + tid; e < e1; e += kGThreads) a.out[e] = w.u[e];
+      for (size_t e = e0 + tid; e < e1; e += kGThreads) pit.out[e] = w.u[e];
     } else {
       double nr[2] = {0.0, 0.0};
       float* Un = a.U + (size_t)(n + 1) * MM;
@@ -915,7 +926,8 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
 static int launch_sweep_global(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s) {
   const int M = g->M;
   const size_t MM = (size_t)M * M;
-  int rc = ensure(const_cast<bs_grid*>(g)->ws_coarse, 10 * MM * sizeof(float));
+  const int nst = a.mode == SWEEP_PROP && a.nprop > 0 ? a.nprop : 1;
+  int rc = ensure(const_cast<bs_grid*>(g)->ws_coarse, (size_t)nst * 10 * MM * sizeof(float));
   if (rc) return rc;
   GSweepParams gp;
   gp.d = d;
@@ -932,7 +944,7 @@ static int launch_sweep_global(const bs_grid* g, const ItemDesc& d, const SweepA
       if (e != cudaSuccess) { cudaGetLastError(); continue; }
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, 1, 1);
+    cfg.gridDim = dim3(C, nst, 1);
     cfg.blockDim = dim3(kGThreads, 1, 1);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

@@ -250,6 +250,15 @@ int launch_payoff(const bs_grid* g, const ItemDesc& d, float* u, cudaStream_t s)
 int grid_sweeps(bs_grid* g, const bs_params& p, double dtau, int start = START_WARM);
 // Coarse numerical propagation / Parareal serial sweep (see coarse.cu).
 enum { SWEEP_PROP = 0, SWEEP_INIT = 1, SWEEP_ITER = 2 };
+// Independent states propagated by one batched SWEEP_PROP launch (one cluster each): the
+// Krylov fine propagator for steps whose Jacobi bound is too large.
+constexpr int kMaxProp = 64;
+struct PropItem {
+  const float* in;
+  float* out;
+  double tau0;
+};
+
 struct SweepArgs {
   int mode;
   int n_first, N;
@@ -265,8 +274,12 @@ struct SweepArgs {
   int* status;
   double tol;           // relative residual of the Krylov solve
   int maxit;
+  int nprop;            // SWEEP_PROP: > 0 -> cluster blockIdx.y propagates prop[blockIdx.y]
+  PropItem prop[kMaxProp];
 };
 int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
+// F by BiCGSTAB per implicit step for items whose Jacobi bound is >= 0.8 (capi.cu)
+int launch_krylov_fine(bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s);
 int coarse_cached_variant(int device, int M);   // tuned (or default) variant, no allocation
 // Numerical G on the grid's coarse grid with bilinear resampling (resampled.cu).
 int resampled_propagate(bs_grid* g, const ItemDesc& d, const float* in, float* out, double tau0, int nsteps,

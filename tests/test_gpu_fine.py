@@ -185,13 +185,36 @@ def test_long_chain_compensated_state(bs):
 
 
 def test_bad_step_is_rejected(bs):
-    import torch
     g = bs.Grid(64, 4.0)
     u = to_gpu(np.zeros((64, 64)))
     with pytest.raises(bs.BSError):
-        bs.fine_propagate_batched(g, [PARAMS[0]], [u], [u], [0.0], [1.0], 3)   # q >= 0.8
-    with pytest.raises(bs.BSError):
         bs.fine_propagate_batched(g, [PARAMS[0]], [u], [u], [0.0], [-1e-3], 3)
+    with pytest.raises(bs.BSError):
+        bs.fine_propagate_batched(g, [PARAMS[0]], [u], [u], [0.0], [0.0], 3)
+
+
+# BiCGSTAB stops each step at a relative residual of 1e-6 of the Jacobi-scaled system; over a
+# few steps the result stays within 2e-5 of max|V| (the coarse propagator's bound).
+KRYLOV_TOL = 2e-5
+
+
+@pytest.mark.parametrize("M,pi", [(64, 1), (100, 0), (300, 2)])
+def test_krylov_fine_matches_oracle(bs, M, pi):
+    # steps whose Jacobi bound is >= 0.8 are solved by BiCGSTAB, one cluster per state; two
+    # states with different start times share a batched launch, a third with other
+    # parameters gets its own
+    import torch
+    p, q = PARAMS[pi], PARAMS[(pi + 1) % len(PARAMS)]
+    dtau = 1.0 / 256
+    g = bs.Grid(M, 4.0)
+    assert bs.bs_fine_sweeps(g, p, dtau) == 0 and bs.bs_fine_sweeps(g, q, dtau) == 0
+    u0 = start_state(M, 4.0, p, "payoff")
+    uin = to_gpu(u0)
+    outs = [torch.empty_like(uin) for _ in range(3)]
+    bs.fine_propagate_batched(g, [p, p, q], [uin, uin, uin], outs, [0.1, 0.3, 0.1], [dtau] * 3, 3)
+    torch.cuda.synchronize()
+    for o, pp, t0 in zip(outs, [p, p, q], [0.1, 0.3, 0.1]):
+        assert rel_err(to_np(o), oracle_fine(M, 4.0, pp, u0, t0, dtau, 3)) <= KRYLOV_TOL
 
 
 def test_payoff_kernel(bs):

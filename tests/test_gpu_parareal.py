@@ -168,6 +168,23 @@ def test_full_size_parareal_each_variant(bs, variant):
     assert float((U - U2).abs().max() / U2.abs().max()) <= pb.tol
 
 
+def test_parareal_with_krylov_fine(bs):
+    # fine steps too large for Jacobi: F runs BiCGSTAB per step (batched over the slices);
+    # K = N still reproduces serial fine stepping bitwise, and tol 1e-4 converges
+    import torch
+    pb = wl.Problem("kry", 64, 4.0, 6, 8, 1, wl.Params(0.25, 0.35, 0.7, 0.03, 1.0, payoff=wl.EXCHANGE))
+    g = bs.Grid(pb.M, pb.xmax)
+    assert bs.bs_fine_sweeps(g, pb.params, pb.dtau_fine) == 0
+    rc, k, _, U = gpu_parareal(bs, pb, 0.0, pb.N)
+    S = gpu_serial_fine(bs, pb)
+    assert k == pb.N and torch.equal(U, S)
+    serial = fd.serial_fine(pb)
+    assert rel_err(to_np(S), serial) <= 3 * COARSE_TOL
+    rc, k, defects, U = gpu_parareal(bs, pb, 1e-4, pb.N)
+    assert rc == 0 and k < pb.N
+    assert rel_err(to_np(U), serial) <= 1e-3
+
+
 def test_maxiter_status(bs):
     pb = cfg_small(wl.BASKET, M=40, N=6, fine=24, coarse=1)
     rc, k, defects, _ = gpu_parareal(bs, pb, 1e-14, 2)
