@@ -223,6 +223,7 @@ int bs_grid_destroy(bs_grid* g) {
   if (g->ws_fine.ptr) cudaFree(g->ws_fine.ptr);
   if (g->ws_coarse.ptr) cudaFree(g->ws_coarse.ptr);
   if (g->ws_rs.ptr) cudaFree(g->ws_rs.ptr);
+  pipe_destroy(g);
   if (g->coarse_grid) bs_grid_destroy(g->coarse_grid);
   delete g;
   return BS_OK;
@@ -339,6 +340,9 @@ int bs_set_option(int option, double value) {
       if (!(value == std::floor(value) && value >= 2.0 && value <= 1e9))
         return set_error(BS_ERR_ARG, "BS_OPT_EXTRAP_START must be an integer >= 2");
       g_opt.extrap_start = (int)value;
+      return BS_OK;
+    case BS_OPT_PIPELINE:
+      g_opt.pipeline = value != 0.0;
       return BS_OK;
     case BS_OPT_EXTRAP_LATE:
       if (!(value == std::floor(value) && value >= 2.0 && value <= 1e9))
@@ -500,6 +504,12 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   const int sweepsx = grid_sweeps(g, *p, dtau_f, START_EXTRAP);
   const int sweepsxl = grid_sweeps(g, *p, dtau_f, START_EXTRAP_LATE);
   const bool krylov_f = sweeps == 0;   // Jacobi bound >= 0.8: F by BiCGSTAB per step
+  // numerical G on this grid: F overlapped with the chunked coarse sweep (Krylov F of grids
+  // beyond one cluster shares the coarse solver's global workspace and stays sequential)
+  if (!pino && !(g->coarse_M > 0 && g->coarse_M != g->M) && g_opt.pipeline && pipeline_chunk(N) > 0 &&
+      !(krylov_f && g->M > 256))
+    return parareal_pipelined(g, p, N, fine_steps, coarse_steps, tol, Kmax, u_out, user_u0, k_done,
+                              defect_hist, s);
   const size_t part_bytes = pino ? pino_partials_bytes(M, N) : 0;
   rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1) + part_bytes);
   if (rc) return rc;

@@ -383,10 +383,14 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   const bool batched = a.mode == SWEEP_PROP && a.nprop > 0;
   const PropItem pit = batched ? a.prop[blockIdx.y] : PropItem{a.in, a.out, d.tau0};
   // initial state of the first slice (own rows and halo rows)
+  // slices of this launch (a chunk of the sweep, or all of it)
+  const int n_lo = a.n_end > 0 ? a.n_begin : a.n_first;
+  const int n_hi = a.n_end > 0 ? a.n_end : (a.mode == SWEEP_PROP ? a.n_first + 1 : a.N);
   const float* src;
   if (a.mode == SWEEP_PROP) src = pit.in;
-  else if (a.mode == SWEEP_INIT) src = a.U;
-  else src = a.Gold + (size_t)a.n_first * MM;   // ITER: G(u_k) is unchanged -> reuse G_old_k
+  else if (a.mode == SWEEP_INIT) src = a.U + (size_t)n_lo * MM;
+  else if (n_lo == a.n_first) src = a.Gold + (size_t)a.n_first * MM;   // G(u_k) unchanged: G_old_k
+  else src = a.U + (size_t)n_lo * MM;                                    // corrected by the chunk before
   band_load<CFG>(u, src, M, jbase, tid);
   cluster_barrier(cluster, C);   // also publishes the mbarrier initialisation
 
@@ -397,8 +401,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
 #pragma unroll
   for (int k = 0; k < K; ++k) xw[k] = 0.f;
   int nhist = 0;
-  const int n_end = (a.mode == SWEEP_PROP) ? a.n_first + 1 : a.N;
-  for (int n = a.n_first; n < n_end; ++n) {
+  for (int n = n_lo; n < n_hi; ++n) {
     const bool skip_g = (a.mode == SWEEP_ITER && n == a.n_first);
     if (!skip_g) {
       for (int cstep = 0; cstep < a.csteps; ++cstep) {
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
     atomicMax(a.status + 1, iters_max);
     atomicAdd(a.status + 2, iters_total);
     atomicAdd(a.status + 3, nsolves);
-    if (a.mode == SWEEP_ITER) {
+    if (a.mode == SWEEP_ITER && n_hi == a.N) {
       double num = 0.0, den = 0.0;
       for (int n = 1; n <= a.N; ++n) {
         den = fmax(den, a.norms[2 * n]);
@@ -758,17 +761,21 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   bool failed = false;
   auto barrier = [&]() { __threadfence(); cluster_barrier(cluster, C); };
 
+  const int n_lo = a.n_end > 0 ? a.n_begin : a.n_first;
+  const int n_hi = a.n_end > 0 ? a.n_end : (a.mode == SWEEP_PROP ? a.n_first + 1 : a.N);
   for (size_t e = e0 + tid; e < e1; e += kGThreads) {
     const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
     w.id[e] = (i < M - 1 && j < M - 1) ? inv_diag(d, i, j) : 0.f;
     w.x[e] = 0.f;
     w.xp[e] = 0.f;
-    const float* src = a.mode == SWEEP_PROP ? pit.in : a.mode == SWEEP_INIT ? a.U : a.Gold + (size_t)a.n_first * MM;
+    const float* src = a.mode == SWEEP_PROP   ? pit.in
+                       : a.mode == SWEEP_INIT ? a.U + (size_t)n_lo * MM
+                       : n_lo == a.n_first    ? a.Gold + (size_t)a.n_first * MM
+                                              : a.U + (size_t)n_lo * MM;
     w.u[e] = src[e];
   }
   barrier();
-  const int n_end = (a.mode == SWEEP_PROP) ? a.n_first + 1 : a.N;
-  for (int n = a.n_first; n < n_end; ++n) {
+  for (int n = n_lo; n < n_hi; ++n) {
     const bool skip_g = (a.mode == SWEEP_ITER && n == a.n_first);
     if (!skip_g) {
       for (int cstep = 0; cstep < a.csteps; ++cstep) {
@@ -912,7 +919,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
     atomicMax(a.status + 1, iters_max);
     atomicAdd(a.status + 2, iters_total);
     atomicAdd(a.status + 3, nsolves);
-    if (a.mode == SWEEP_ITER) {
+    if (a.mode == SWEEP_ITER && n_hi == a.N) {
       double num = 0.0, den = 0.0;
       for (int n = 1; n <= a.N; ++n) {
         den = fmax(den, a.norms[2 * n]);

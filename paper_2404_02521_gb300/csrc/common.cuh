@@ -201,6 +201,7 @@ struct Options {
   double jacobi_target_extrap_late = 1.0 / 16.0;  // ... from step extrap_late on: 2^-4
   int extrap_start = 2;                           // first extrapolated step of a launch
   int extrap_late = 16;                           // first step with the late target
+  int pipeline = 1;                               // parareal_solve overlaps F with the sweep
   double krylov_tol = 1e-6;
   int krylov_maxit = 400;
   int phase_timing = 0;
@@ -233,6 +234,7 @@ struct bs_grid {
   int coarse_M = 0;            // numerical G on an Mc x Mc grid with resampling (0: this grid)
   bs_grid* coarse_grid = nullptr;   // that grid (created on first use)
   bsp::Workspace ws_rs;        // resampling buffers and defect partials
+  void* pipe = nullptr;        // pipelined driver: second stream and events (pipeline.cu)
   // cached contraction
   double q_key[6];
   double q_val;
@@ -276,6 +278,10 @@ struct SweepArgs {
   int maxit;
   int nprop;            // SWEEP_PROP: > 0 -> cluster blockIdx.y propagates prop[blockIdx.y]
   PropItem prop[kMaxProp];
+  // INIT / ITER in chunks: with n_end > 0 the launch runs slices n_begin .. n_end-1 only,
+  // starting from U[n_begin] (written by the chunk before) unless n_begin == n_first; the
+  // defect is formed by the launch that ends at N.  n_end == 0: the whole sweep.
+  int n_begin, n_end;
 };
 int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
 // F by BiCGSTAB per implicit step for items whose Jacobi bound is >= 0.8 (capi.cu)
@@ -286,6 +292,12 @@ int resampled_propagate(bs_grid* g, const ItemDesc& d, const float* in, float* o
                         cudaStream_t s);
 int resampled_sweep(bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
 int resampled_launches_per_slice();
+// Pipelined Parareal with the numerical G on the state grid (pipeline.cu).
+int pipeline_chunk(int N);   // slices per chunk, 0: too few slices to pipeline
+int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, int coarse_steps, double tol,
+                       int Kmax, float* u_out, bool user_u0, int* k_done, double* defect_hist,
+                       cudaStream_t s);
+void pipe_destroy(bs_grid* g);
 int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, int* chosen);
 // PINO coarse propagator (pino.cu)
 int pino_check(const bs_pino* net, int M);

@@ -185,6 +185,31 @@ def test_parareal_with_krylov_fine(bs):
     assert rel_err(to_np(U), serial) <= 1e-3
 
 
+@pytest.mark.parametrize("payoff", [wl.BASKET, wl.EXCHANGE])
+def test_pipelined_driver(bs, payoff):
+    # F overlapped with the chunked coarse sweep: the same iterations and defects as the
+    # phase-by-phase driver (G agrees to the Krylov tolerance), K = N reproduces serial fine
+    # stepping bitwise, and the first k+1 slices are exact after k iterations
+    import torch
+    pb = cfg_small(payoff, M=64, N=16, fine=64, coarse=2)
+    try:
+        bs.bs_set_option(bs.OPT_PIPELINE, 0)
+        rc0, k0, d0, U0 = gpu_parareal(bs, pb, 1e-4, pb.N)
+    finally:
+        bs.bs_set_option(bs.OPT_PIPELINE, 1)
+    rc1, k1, d1, U1 = gpu_parareal(bs, pb, 1e-4, pb.N)
+    assert rc0 == rc1 == 0 and k0 == k1
+    for a, b in zip(d0, d1):
+        assert abs(a - b) <= 1e-3 * b + 1e-6
+    assert float((U0 - U1).abs().max() / U0.abs().max()) <= 3 * COARSE_TOL
+    S = gpu_serial_fine(bs, pb)
+    rc, k, _, U = gpu_parareal(bs, pb, 0.0, pb.N)
+    assert k == pb.N and torch.equal(U, S)
+    for K in (1, 3, 7):
+        rc, k, _, U = gpu_parareal(bs, pb, 0.0, K)
+        assert k == K and torch.equal(U[: K + 1], S[: K + 1]), K
+
+
 def test_maxiter_status(bs):
     pb = cfg_small(wl.BASKET, M=40, N=6, fine=24, coarse=1)
     rc, k, defects, _ = gpu_parareal(bs, pb, 1e-14, 2)

@@ -29,11 +29,29 @@ def mix():
     return out
 
 
-def alone(bs, reqs, fine_steps):
+def alone(bs, reqs):
+    """Each request through a server on its own (nothing else on the device)."""
     import torch
     from paper_2404_02521_gb300 import serving
     outs = [torch.empty((r.M, r.M), device="cuda") for r in reqs]
-    serving.service_times(reqs, fine_steps, outs)
+    sv = bs.Server(1 << 30, 8)
+    for i, r in enumerate(reqs):
+        serving.replay(sv, [r], [0.0], [outs[i]])
+    sv.close()
+    return outs
+
+
+def plain(bs, reqs, fine_steps):
+    """Each request through parareal_solve, F and the sweep alternating (the algorithm the
+    server runs per request)."""
+    import torch
+    from paper_2404_02521_gb300 import serving
+    outs = [torch.empty((r.M, r.M), device="cuda") for r in reqs]
+    try:
+        bs.bs_set_option(bs.OPT_PIPELINE, 0)
+        serving.service_times(reqs, fine_steps, outs)
+    finally:
+        bs.bs_set_option(bs.OPT_PIPELINE, 1)
     return outs
 
 
@@ -51,9 +69,9 @@ def test_mix_equals_alone_bitwise(bs):
     assert all(r["status"] == 0 for r in res), res
     assert st["arena_used"] == 0 and st["fine_batches"] >= 1
     fs = [r["fine_steps"] for r in res]
-    ref = alone(bs, reqs, fs)
-    for r, a, b in zip(reqs, outs, ref):
+    for r, a, b, c in zip(reqs, outs, alone(bs, reqs), plain(bs, reqs, fs)):
         assert torch.equal(a, b), r.name
+        assert torch.equal(a, c), r.name
 
 
 def test_admission_waits_for_memory(bs):

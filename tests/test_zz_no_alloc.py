@@ -27,9 +27,13 @@ def test_noalloc_matches_parareal_solve_on_two_calls(bs):
     for pb in problems:
         g = bs.Grid(pb.M, pb.xmax)
         ref = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
-        rc0, k0, d0 = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM,
-                                        pb.coarse_steps, None, pb.tol, pb.N, ref)
-        torch.cuda.synchronize()
+        try:   # the no-allocation entry point runs F and the sweep as alternating phases
+            bs.bs_set_option(bs.OPT_PIPELINE, 0)
+            rc0, k0, d0 = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM,
+                                            pb.coarse_steps, None, pb.tol, pb.N, ref)
+            torch.cuda.synchronize()
+        finally:
+            bs.bs_set_option(bs.OPT_PIPELINE, 1)
         for _ in range(2):
             out = torch.full_like(ref, float("nan"))
             rc, k, d = bs.parareal_solve_noalloc(pb.M, pb.xmax, pb.params, pb.N, pb.fine_steps,
