@@ -55,8 +55,24 @@ struct Scal {
 __device__ __forceinline__ double* scal_tot(Scal* s, double) { return s->tot; }
 __device__ __forceinline__ float* scal_tot(Scal* s, float) { return s->totf; }
 
-// Jacobi-scaled operator A^ y = y - invd * (off-diagonal part of dtau R_h) y on the thread's
-// column strip; zero on non-interior nodes (invd = 0 and y = 0 there).
+// Jacobi-scaled operator at one node:
+//   (A^ y)_C = y_C - invd * (ce y_E + cw y_W + cs y_S + cn y_N + cg ((y_SE - y_NE) - (y_SW - y_NW)))
+// (N = row j-1, S = row j+1), with every rounding explicit, so that a halo row evaluated by a
+// neighbour equals bit for bit the same row evaluated by its owner.
+__device__ __forceinline__ float scaled_node(float nW, float nC, float nE, float cW, float cC, float cE, float sW,
+                                             float sC, float sE, float4 rc, float id, float ce, float cw,
+                                             float cgi) {
+  const float cg = cgi * rc.z;
+  float acc = ce * cE;
+  acc = fmaf(cw, cW, acc);
+  acc = fmaf(rc.x, sC, acc);
+  acc = fmaf(rc.y, nC, acc);
+  acc = fmaf(cg, (sE - nE) - (sW - nW), acc);
+  return fmaf(-id, acc, cC);
+}
+
+// A^ y on the thread's column strip (K rows; y has one halo row above the strip's band);
+// zero on non-interior nodes (invd = 0 and y = 0 there).
 template <class CFG>
 __device__ __forceinline__ void scaled_matvec(const float* __restrict__ y,
                                               const float4* __restrict__ rowc,
@@ -71,13 +87,20 @@ __device__ __forceinline__ void scaled_matvec(const float* __restrict__ y,
   for (int k = 0; k < K; ++k) {
     const int p = p0 + k;
     const float sW = y[(p + 1) * NCOL + il], sC = y[(p + 1) * NCOL + col], sE = y[(p + 1) * NCOL + ir];
-    const float4 rc = rowc[p - 1];
-    const float cg = cgi * rc.z;
-    out[k] = cC - ID[(p - 1) * NCOL + col] *
-                      (ce * cE + cw * cW + rc.x * sC + rc.y * nC + cg * ((sE - nE) - (sW - nW)));
+    out[k] = scaled_node(nW, nC, nE, cW, cC, cE, sW, sC, sE, rowc[p - 1], ID[(p - 1) * NCOL + col], ce, cw, cgi);
     nW = cW; nC = cC; nE = cE;
     cW = sW; cC = sC; cE = sE;
   }
+}
+
+// A^ y at one row; yrow points at the row's first column, the rows above and below are
+// yrow -+ ncol.
+__device__ __forceinline__ float scaled_row(const float* yrow, int ncol, int col, int il, int ir, float4 rc,
+                                            float id, float ce, float cw, float cgi) {
+  const float* n = yrow - ncol;
+  const float* s = yrow + ncol;
+  return scaled_node(n[il], n[col], n[ir], yrow[il], yrow[col], yrow[ir], s[il], s[col], s[ir], rc, id, ce, cw,
+                     cgi);
 }
 
 template <class T>
@@ -281,15 +304,53 @@ __device__ __forceinline__ void xround(Xchg& xs, const float (&v)[NV], float (&t
   ++xs.round;
 }
 
+// Q = M^{-1} y = 2 y - A^ y on the strip's own rows and, for the edge groups, on the halo row
+// next to the band (y has DH = 2 halo rows; Q one).  Outside the domain Q stays zero.
+template <class CFG, int DH>
+__device__ __forceinline__ void precond_apply(const float* __restrict__ y, float* __restrict__ Q,
+                                              const float4* __restrict__ rowc, const float* __restrict__ ID,
+                                              int col, int il, int ir, int r0, int grp, float ce, float cw,
+                                              float cgi, bool has_up, bool has_down, float4 rc_top, float id_top,
+                                              float4 rc_bot, float id_bot) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH;
+  float ay[K];
+  scaled_matvec<CFG>(y + (DH - 1) * NCOL, rowc, ID, col, il, ir, r0, ce, cw, cgi, ay);
+#pragma unroll
+  for (int k = 0; k < K; ++k) Q[(r0 + k + 1) * NCOL + col] = fmaf(2.f, y[(r0 + k + DH) * NCOL + col], -ay[k]);
+  if (grp == 0 && has_up) {
+    const float* yr = y + (DH - 1) * NCOL;
+    Q[col] = fmaf(2.f, yr[col], -scaled_row(yr, NCOL, col, il, ir, rc_top, id_top, ce, cw, cgi));
+  }
+  if (grp == CFG::G - 1 && has_down) {
+    const float* yr = y + (BH + DH) * NCOL;
+    Q[(BH + 1) * NCOL + col] = fmaf(2.f, yr[col], -scaled_row(yr, NCOL, col, il, ir, rc_bot, id_bot, ce, cw, cgi));
+  }
+}
+
 // Shared-memory layout of sweep_band_kernel (floats first, every array a multiple of 16 B).
+// The polynomial preconditioner (POLY) needs the p and s planes with two halo rows on each
+// side and one more plane; quadratic extrapolation (QUAD) one more own-row plane.  Each is
+// used where it fits in the 227 KB of a CTA (POLY first: it saves more).
 template <class CFG>
 struct SweepSmem {
   static constexpr int NCOL = CFG::NCOL, BH = CFG::BH, PLANE = CFG::PLANE, NW = CFG::NW;
-  static constexpr size_t u = 0, P = u + PLANE, S = P + PLANE;          // planes (with halo rows)
-  static constexpr size_t RH = S + PLANE, ID = RH + BH * NCOL, XP = ID + BH * NCOL;   // own rows
-  static constexpr size_t VH = XP + BH * NCOL;   // [2 parity][2: top, bottom][NCOL] v halo rows
-  static constexpr size_t TH = VH + 4 * NCOL;    // [2: top, bottom][NCOL] t halo rows
-  static constexpr size_t KSLOT = TH + 2 * NCOL; // [2][kMaxCluster][4] exchange partials
+  static constexpr size_t TAIL_BYTES = 2 * kMaxCluster * 4 * 8 + NW * 4 * 8 + 16 + sizeof(Scal);
+  static constexpr size_t floats(int dh, bool q, bool quad) {
+    return PLANE + 2 * (size_t)(BH + 2 * dh) * NCOL + (q ? PLANE : 0) + (3 + (quad ? 1 : 0)) * (size_t)BH * NCOL +
+           6 * (size_t)dh * NCOL + 2 * kMaxCluster * 4 + NW * 4 + 4 * BH;
+  }
+  static constexpr bool fits(size_t f) { return f * 4 + TAIL_BYTES <= 227 * 1024; }
+  static constexpr bool POLY = fits(floats(2, true, false));
+  static constexpr int DH = POLY ? 2 : 1;   // halo rows of the p and s planes
+  static constexpr bool QUAD = fits(floats(DH, POLY, true));
+  static constexpr int DPLANE = (BH + 2 * DH) * NCOL;
+  static constexpr size_t u = 0, P = u + PLANE, S = P + DPLANE;         // u: one halo row; p, s: DH
+  static constexpr size_t Q = S + DPLANE;        // preconditioned direction, one halo row (POLY only)
+  static constexpr size_t RH = Q + (POLY ? PLANE : 0), ID = RH + BH * NCOL, XP = ID + BH * NCOL;   // own rows
+  static constexpr size_t XQ = XP + BH * NCOL;   // d_{m-3}, own rows (QUAD only)
+  static constexpr size_t VH = XQ + (QUAD ? BH * NCOL : 0);   // [2 parity][top DH, bottom DH rows][NCOL] v halo
+  static constexpr size_t TH = VH + 4 * DH * NCOL;   // [top DH, bottom DH rows][NCOL] t halo rows
+  static constexpr size_t KSLOT = TH + 2 * DH * NCOL;   // [2][kMaxCluster][4] exchange partials
   static constexpr size_t KWP = KSLOT + 2 * kMaxCluster * 4;   // [NW][4]
   static constexpr size_t ROWC = KWP + NW * 4;   // float4 [BH]: cs, cn, (float)j, 0
   static constexpr size_t FLOATS = ROWC + 4 * BH;
@@ -298,12 +359,31 @@ struct SweepSmem {
   static constexpr size_t MB_B = WPART_B + NW * 4 * 8, SCAL_B = MB_B + 16;
   static constexpr size_t BYTES = SCAL_B + sizeof(Scal);
   static_assert(FLOATS % 4 == 0, "16-byte alignment of the double arrays");
+  static_assert(FLOATS == floats(DH, POLY, QUAD), "layout and fit test agree");
+  static_assert(CFG::K >= DH, "the edge groups send DH rows");
 };
+
+// Halo targets of a plane with DH halo rows on each side: own rows 0..DH-1 mirror into rows
+// BH+DH.. of rank-1's plane, own rows BH-DH..BH-1 into rows 0.. of rank+1's plane.
+template <class CFG, int DH>
+__device__ __forceinline__ HaloPush deep_push(cg::cluster_group& cl, float* plane, int rank, int C) {
+  HaloPush h;
+  h.prev_bottom = rank > 0 ? cl.map_shared_rank(plane, rank - 1) + (CFG::BH + DH) * CFG::NCOL : nullptr;
+  h.next_top = rank < C - 1 ? cl.map_shared_rank(plane, rank + 1) : nullptr;
+  return h;
+}
+template <class CFG, int DH>
+__device__ __forceinline__ void deep_store(float* plane, const HaloPush& h, int r, int c, float v) {
+  plane[(r + DH) * CFG::NCOL + c] = v;
+  if (r < DH && h.prev_bottom) h.prev_bottom[r * CFG::NCOL + c] = v;
+  if (r >= CFG::BH - DH && h.next_top) h.next_top[(r - (CFG::BH - DH)) * CFG::NCOL + c] = v;
+}
 
 template <class CFG>
 __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_constant__ SweepParams sp) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, G = CFG::G;
   using L = SweepSmem<CFG>;
+  constexpr int DH = L::DH;
   cg::cluster_group cluster = cg::this_cluster();
   const ItemDesc& d = sp.d;
   const SweepArgs& a = sp.a;
@@ -320,11 +400,15 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* fs = reinterpret_cast<float*>(smem_raw);
   float* u = fs + L::u;      // state w / u          [PLANE]
-  float* P = fs + L::P;      // search direction p   [PLANE]
-  float* S = fs + L::S;      // s                    [PLANE]
+  float* P = fs + L::P;      // search direction p   [DPLANE]: own row r at plane row r + DH
+  float* S = fs + L::S;      // s                    [DPLANE]
+  float* Q = fs + L::Q;      // M^{-1} p, M^{-1} s   [PLANE] (L::POLY)
+  const float* P1 = P + (DH - 1) * NCOL;   // p and s seen with one halo row
+  const float* S1 = S + (DH - 1) * NCOL;
   float* RH = fs + L::RH;    // shadow residual r^   [BH*NCOL]
   float* ID = fs + L::ID;    // inverse diagonal     [BH*NCOL]
   float* XP = fs + L::XP;    // increment before xw  [BH*NCOL]
+  float* XQ = fs + L::XQ;    // the one before that  [BH*NCOL] (L::QUAD)
   float* VH = fs + L::VH;
   float* TH = fs + L::TH;
   float4* rowc = reinterpret_cast<float4*>(fs + L::ROWC);
@@ -334,12 +418,12 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   Scal* sc = reinterpret_cast<Scal*>(smem_raw + L::SCAL_B);
 
   const HaloPush pu = halo_push<CFG>(cluster, u, rank, C);
-  const HaloPush pP = halo_push<CFG>(cluster, P, rank, C);
+  const HaloPush pP = deep_push<CFG, DH>(cluster, P, rank, C);
   const bool has_up = rank > 0, has_down = rank < C - 1;
-  // receivers of this thread's halo stores (v and t rows): group 0 sends band row 0 to the
-  // bottom halo of rank-1, group G-1 sends band row BH-1 to the top halo of rank+1
+  // receivers of this thread's halo stores (v and t rows): group 0 sends band rows 0..DH-1 to
+  // the bottom halo of rank-1, group G-1 sends band rows BH-DH..BH-1 to the top halo of rank+1
   const bool send_up = grp == 0 && has_up, send_down = grp == G - 1 && has_down;
-  const uint32_t halo_bytes = (uint32_t)((has_up ? 1 : 0) + (has_down ? 1 : 0)) * NCOL * 4;
+  const uint32_t halo_bytes = (uint32_t)((has_up ? 1 : 0) + (has_down ? 1 : 0)) * DH * NCOL * 4;
 
   for (int e = tid; e < BH * NCOL; e += CFG::NT) {
     const int r = e / NCOL, c = e % NCOL;
@@ -347,10 +431,12 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
     ID[e] = (j < M - 1 && c < M - 1) ? inv_diag(d, c, j) : 0.f;
     RH[e] = 0.f;
   }
-  for (int e = tid; e < CFG::PLANE; e += CFG::NT) {
+  for (int e = tid; e < L::DPLANE; e += CFG::NT) {
     P[e] = 0.f; S[e] = 0.f;
   }
-  for (int e = tid; e < 6 * NCOL; e += CFG::NT) VH[e] = 0.f;   // VH and TH
+  if (L::POLY)
+    for (int e = tid; e < CFG::PLANE; e += CFG::NT) Q[e] = 0.f;
+  for (int e = tid; e < 6 * DH * NCOL; e += CFG::NT) VH[e] = 0.f;   // VH and TH
   for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
     row_coefs(d, jbase + r, cs, cn, gj);
@@ -372,6 +458,21 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   column_coefs(d, col, ce, cw, cgi);
   const int il = col > 0 ? col - 1 : 0;
   const int ir = col + 1 < NCOL ? col + 1 : col;
+  // coefficients of the halo rows next to the band (rows jbase-1 and jbase+BH), where the
+  // edge groups evaluate the preconditioner
+  float4 rc_top = make_float4(0.f, 0.f, 0.f, 0.f), rc_bot = rc_top;
+  float id_top = 0.f, id_bot = 0.f;
+  if (L::POLY) {
+    const int jt = jbase - 1, jb = jbase + BH;
+    if (grp == 0 && has_up) {
+      row_coefs(d, jt, rc_top.x, rc_top.y, rc_top.z);
+      id_top = (jt < M - 1 && col < M - 1) ? inv_diag(d, col, jt) : 0.f;
+    }
+    if (grp == G - 1 && has_down) {
+      row_coefs(d, jb, rc_bot.x, rc_bot.y, rc_bot.z);
+      id_bot = (jb < M - 1 && col < M - 1) ? inv_diag(d, col, jb) : 0.f;
+    }
+  }
   const float rdt = d.rdt;
   const float tol = (float)a.tol;
   int round = 0;
@@ -394,10 +495,12 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   band_load<CFG>(u, src, M, jbase, tid);
   cluster_barrier(cluster, C);   // also publishes the mbarrier initialisation
 
-  // Initial guess of each solve: the linear extrapolation 2 d_{m-1} - d_{m-2} of the two
-  // previous coarse increments (d_{m-1} after one step, 0 at the start); the increments of
-  // consecutive steps vary smoothly, and this start saves about a quarter of the iterations.
-  float xw[K];   // d_{m-1}; XP holds d_{m-2} (own rows)
+  // Initial guess of each solve: the extrapolation of the previous coarse increments --
+  // quadratic 3 d_{m-1} - 3 d_{m-2} + d_{m-3} where the third history plane fits in shared
+  // memory, else linear 2 d_{m-1} - d_{m-2} (d_{m-1} after one step, 0 at the start).  The
+  // increments of consecutive steps vary smoothly: the linear start saves about 30% of the
+  // BiCGSTAB iterations against the previous increment, the quadratic one 30% more.
+  float xw[K];   // d_{m-1}; XP holds d_{m-2}, XQ d_{m-3} (own rows)
 #pragma unroll
   for (int k = 0; k < K; ++k) xw[k] = 0.f;
   int nhist = 0;
@@ -408,11 +511,21 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         const double tau_new = pit.tau0 + a.slice_len * n + (cstep + 1) * d.dtau;
         band_far_field<CFG>(u, pu, pf, (float)tau_new, h, M, jbase, tid);
         cluster_barrier(cluster, C);
-        if (nhist >= 2) {
+        if (L::QUAD && nhist >= 3) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int e = (r0 + k) * NCOL + col;
+            const float d2 = XP[e], d3 = XQ[e];
+            XQ[e] = d2;
+            XP[e] = xw[k];
+            xw[k] = 3.f * (xw[k] - d2) + d3;
+          }
+        } else if (nhist >= 2) {
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             const int e = (r0 + k) * NCOL + col;
             const float dprev = XP[e];
+            if (L::QUAD) XQ[e] = dprev;
             XP[e] = xw[k];
             xw[k] = 2.f * xw[k] - dprev;
           }
@@ -451,9 +564,9 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             }
           }
 #pragma unroll
-          for (int k = 0; k < K; ++k) band_store<CFG>(P, pP, r0 + k, col, x[k]);
+          for (int k = 0; k < K; ++k) deep_store<CFG, DH>(P, pP, r0 + k, col, x[k]);
           cluster_barrier(cluster, C);
-          scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+          scaled_matvec<CFG>(P1, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             rr[k] -= vv[k];
@@ -465,7 +578,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
                               [tol](Scal* s) { KrylovFin::start(s, tol); });
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            band_store<CFG>(P, pP, r0 + k, col, rr[k]);
+            deep_store<CFG, DH>(P, pP, r0 + k, col, rr[k]);
             RH[(r0 + k) * NCOL + col] = rr[k];
           }
           cluster_barrier(cluster, C);
@@ -475,22 +588,47 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
           bool fail = false;
           // r on the halo rows (kept by the threads that own those columns of the edge groups;
           // the P halo rows hold r here)
-          float rh_top = grp == 0 ? P[col] : 0.f;
-          float rh_bot = grp == G - 1 ? P[(BH + 1) * NCOL + col] : 0.f;
+          float rh_top[DH], rh_bot[DH];
+#pragma unroll
+          for (int t = 0; t < DH; ++t) {
+            rh_top[t] = grp == 0 ? P[t * NCOL + col] : 0.f;
+            rh_bot[t] = grp == G - 1 ? P[(BH + DH + t) * NCOL + col] : 0.f;
+          }
           // BiCGSTAB iterations with two exchange rounds each.  The halo rows of s and p are
           // computed locally from r, v and t on the halo rows (v and t arrive with the rounds),
           // so the matrix-vector products need no cluster barrier.
+          //
+          // POLY: right preconditioning with M^{-1} = 2I - A^, the first two terms of the
+          // Neumann series of A^{-1} (A^ = I - (off-diagonal part), so M^{-1} A^ is closer to
+          // I): v = A^ M^{-1} p, t = A^ M^{-1} s, x += alpha M^{-1} p + omega M^{-1} s.  It
+          // halves the iterations for one more stencil evaluation per product; M^{-1} y on the
+          // row next to the band needs y two rows into the halo, so p, s, v and t keep two
+          // halo rows.
           while (!conv && it < a.maxit) {
             ++it;
             const int par = kit & 1;
-            float* vh_top = VH + (2 * par) * NCOL;
-            float* vh_bot = VH + (2 * par + 1) * NCOL;
-            // v = A^ p ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
-            scaled_matvec<CFG>(P, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+            float* vh_top = VH + (2 * par) * DH * NCOL;
+            float* vh_bot = vh_top + DH * NCOL;
+            // v = A^ p (POLY: A^ M^{-1} p) ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
+            if constexpr (L::POLY) {
+              precond_apply<CFG, DH>(P, Q, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
+                                     rc_top, id_top, rc_bot, id_bot);
+              __syncthreads();
+              scaled_matvec<CFG>(Q, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+            } else {
+              scaled_matvec<CFG>(P1, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+            }
             {
               const uint32_t mb = smem_addr(xs.mb + (xs.round & 1));
-              if (send_up) st_async_f32(cluster_addr(smem_addr(vh_bot + col), rank - 1), vv[0], cluster_addr(mb, rank - 1));
-              if (send_down) st_async_f32(cluster_addr(smem_addr(vh_top + col), rank + 1), vv[K - 1], cluster_addr(mb, rank + 1));
+#pragma unroll
+              for (int t = 0; t < DH; ++t) {
+                if (send_up)
+                  st_async_f32(cluster_addr(smem_addr(vh_bot + t * NCOL + col), rank - 1), vv[t],
+                               cluster_addr(mb, rank - 1));
+                if (send_down)
+                  st_async_f32(cluster_addr(smem_addr(vh_top + t * NCOL + col), rank + 1), vv[K - DH + t],
+                               cluster_addr(mb, rank + 1));
+              }
             }
             float p1[2] = {0.f, 0.f};
 #pragma unroll
@@ -506,21 +644,44 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             const float af = rho / ta[0];
             // s = r - alpha v, own rows and halo rows
 #pragma unroll
-            for (int k = 0; k < K; ++k) S[(r0 + k + 1) * NCOL + col] = fmaf(-af, vv[k], rr[k]);
-            if (grp == 0) S[col] = has_up ? fmaf(-af, vh_top[col], rh_top) : 0.f;
-            if (grp == G - 1) S[(BH + 1) * NCOL + col] = has_down ? fmaf(-af, vh_bot[col], rh_bot) : 0.f;
+            for (int k = 0; k < K; ++k) S[(r0 + k + DH) * NCOL + col] = fmaf(-af, vv[k], rr[k]);
+#pragma unroll
+            for (int t = 0; t < DH; ++t) {
+              if (grp == 0) S[t * NCOL + col] = has_up ? fmaf(-af, vh_top[t * NCOL + col], rh_top[t]) : 0.f;
+              if (grp == G - 1)
+                S[(BH + DH + t) * NCOL + col] = has_down ? fmaf(-af, vh_bot[t * NCOL + col], rh_bot[t]) : 0.f;
+            }
+            if constexpr (L::POLY) {
+              // x += alpha M^{-1} p while Q still holds it (own entries: no other thread writes them)
+#pragma unroll
+              for (int k = 0; k < K; ++k) x[k] = fmaf(af, Q[(r0 + k + 1) * NCOL + col], x[k]);
+            }
             __syncthreads();
-            // t = A^ s ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
-            scaled_matvec<CFG>(S, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
+            // t = A^ s (POLY: A^ M^{-1} s) ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
+            if constexpr (L::POLY) {
+              precond_apply<CFG, DH>(S, Q, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
+                                     rc_top, id_top, rc_bot, id_bot);
+              __syncthreads();
+              scaled_matvec<CFG>(Q, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
+            } else {
+              scaled_matvec<CFG>(S1, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
+            }
             {
               const uint32_t mb = smem_addr(xs.mb + (xs.round & 1));
-              if (send_up) st_async_f32(cluster_addr(smem_addr(TH + NCOL + col), rank - 1), tt[0], cluster_addr(mb, rank - 1));
-              if (send_down) st_async_f32(cluster_addr(smem_addr(TH + col), rank + 1), tt[K - 1], cluster_addr(mb, rank + 1));
+#pragma unroll
+              for (int t = 0; t < DH; ++t) {
+                if (send_up)
+                  st_async_f32(cluster_addr(smem_addr(TH + (DH + t) * NCOL + col), rank - 1), tt[t],
+                               cluster_addr(mb, rank - 1));
+                if (send_down)
+                  st_async_f32(cluster_addr(smem_addr(TH + t * NCOL + col), rank + 1), tt[K - DH + t],
+                               cluster_addr(mb, rank + 1));
+              }
             }
             float p2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const float sv = S[(r0 + k + 1) * NCOL + col], rh = RH[(r0 + k) * NCOL + col];
+              const float sv = S[(r0 + k + DH) * NCOL + col], rh = RH[(r0 + k) * NCOL + col];
               p2[0] = fmaf(tt[k], sv, p2[0]);
               p2[1] = fmaf(tt[k], tt[k], p2[1]);
               p2[2] = fmaf(rh, sv, p2[2]);
@@ -535,22 +696,28 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             if (of == 0.f || rho == 0.f) fail = true;
             else bf = (rho_new / rho) * (af / of);
             rho = rho_new;
-            // x += alpha p + omega s ;  r = s - omega t ;  p = r + beta (p - omega v)
+            // x += alpha p + omega s (POLY: omega M^{-1} s) ;  r = s - omega t ;  p = r + beta (p - omega v)
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const int idx = (r0 + k + 1) * NCOL + col;
+              const int idx = (r0 + k + DH) * NCOL + col;
               const float sv = S[idx], pv = P[idx];
-              x[k] += af * pv + of * sv;
+              if constexpr (L::POLY) x[k] = fmaf(of, Q[(r0 + k + 1) * NCOL + col], x[k]);
+              else x[k] += af * pv + of * sv;
               rr[k] = fmaf(-of, tt[k], sv);
-              P[idx] = rr[k] + bf * (pv - of * vv[k]);
+              P[idx] = fmaf(bf, fmaf(-of, vv[k], pv), rr[k]);
             }
-            if (grp == 0) {
-              rh_top = has_up ? fmaf(-of, TH[col], S[col]) : 0.f;
-              P[col] = has_up ? rh_top + bf * (P[col] - of * vh_top[col]) : 0.f;
-            }
-            if (grp == G - 1) {
-              rh_bot = has_down ? fmaf(-of, TH[NCOL + col], S[(BH + 1) * NCOL + col]) : 0.f;
-              P[(BH + 1) * NCOL + col] = has_down ? rh_bot + bf * (P[(BH + 1) * NCOL + col] - of * vh_bot[col]) : 0.f;
+#pragma unroll
+            for (int t = 0; t < DH; ++t) {
+              if (grp == 0) {
+                float* pp = P + t * NCOL + col;
+                rh_top[t] = has_up ? fmaf(-of, TH[t * NCOL + col], S[t * NCOL + col]) : 0.f;
+                *pp = has_up ? fmaf(bf, fmaf(-of, vh_top[t * NCOL + col], *pp), rh_top[t]) : 0.f;
+              }
+              if (grp == G - 1) {
+                float* pp = P + (BH + DH + t) * NCOL + col;
+                rh_bot[t] = has_down ? fmaf(-of, TH[(DH + t) * NCOL + col], S[(BH + DH + t) * NCOL + col]) : 0.f;
+                *pp = has_down ? fmaf(bf, fmaf(-of, vh_bot[t * NCOL + col], *pp), rh_bot[t]) : 0.f;
+              }
             }
             __syncthreads();
             ++kit;
@@ -566,7 +733,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         ++nsolves;
 #pragma unroll
         for (int k = 0; k < K; ++k) xw[k] = x[k];
-        nhist = nhist < 2 ? nhist + 1 : 2;
+        nhist = nhist < 3 ? nhist + 1 : 3;
         // u^{m+1} = w + d (d = 0 off the PDE rows, whose values already hold g(tau_new))
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -695,8 +862,9 @@ struct GCfg {
 };
 
 struct GlobalVecs {
-  float *u, *x, *xp, *r, *rh, *p, *v, *s, *t, *id;
+  float *u, *x, *xp, *xq, *r, *rh, *p, *v, *s, *t, *id;
 };
+constexpr int kGlobalVecs = 11;
 
 struct GSweepParams {
   ItemDesc d;
@@ -739,8 +907,8 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   // per-state workspace of a batched PROP launch
   GlobalVecs w = gp.w;
   if (batched) {
-    const size_t off = (size_t)blockIdx.y * 10 * (size_t)gp.M * gp.M;
-    w.u += off; w.x += off; w.xp += off; w.r += off; w.rh += off;
+    const size_t off = (size_t)blockIdx.y * kGlobalVecs * (size_t)gp.M * gp.M;
+    w.u += off; w.x += off; w.xp += off; w.xq += off; w.r += off; w.rh += off;
     w.p += off; w.v += off; w.s += off; w.t += off; w.id += off;
   }
   const int M = gp.M, C = gp.C;
@@ -768,6 +936,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
     w.id[e] = (i < M - 1 && j < M - 1) ? inv_diag(d, i, j) : 0.f;
     w.x[e] = 0.f;
     w.xp[e] = 0.f;
+    w.xq[e] = 0.f;
     const float* src = a.mode == SWEEP_PROP   ? pit.in
                        : a.mode == SWEEP_INIT ? a.U + (size_t)n_lo * MM
                        : n_lo == a.n_first    ? a.Gold + (size_t)a.n_first * MM
@@ -780,14 +949,15 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
     if (!skip_g) {
       for (int cstep = 0; cstep < a.csteps; ++cstep) {
         const float tau_new = (float)(pit.tau0 + a.slice_len * n + (cstep + 1) * d.dtau);
-        // initial guess 2 d_{m-1} - d_{m-2} (see the band kernel); x holds d_{m-1}
-        const bool extrap = nhist >= 2;
+        // initial guess 3 d_{m-1} - 3 d_{m-2} + d_{m-3} (see the band kernel); x holds d_{m-1}
         for (size_t e = e0 + tid; e < e1; e += kGThreads) {
           const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
           if (i == M - 1 || j == M - 1) w.u[e] = far_field(pf, i * gp.h, j * gp.h, tau_new);
-          const float xv = w.x[e];
-          if (extrap) w.x[e] = 2.f * xv - w.xp[e];
-          w.xp[e] = xv;
+          const float d1 = w.x[e], d2 = w.xp[e];
+          if (nhist >= 3) w.x[e] = 3.f * (d1 - d2) + w.xq[e];
+          else if (nhist == 2) w.x[e] = 2.f * d1 - d2;
+          w.xq[e] = d2;
+          w.xp[e] = d1;
         }
         barrier();
         int it = 0;
@@ -877,7 +1047,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
         iters_max = it > iters_max ? it : iters_max;
         iters_total += it;
         ++nsolves;
-        nhist = nhist < 2 ? nhist + 1 : 2;
+        nhist = nhist < 3 ? nhist + 1 : 3;
         for (size_t e = e0 + tid; e < e1; e += kGThreads) w.u[e] += w.x[e];
         barrier();
       }
@@ -934,14 +1104,14 @@ static int launch_sweep_global(const bs_grid* g, const ItemDesc& d, const SweepA
   const int M = g->M;
   const size_t MM = (size_t)M * M;
   const int nst = a.mode == SWEEP_PROP && a.nprop > 0 ? a.nprop : 1;
-  int rc = ensure(const_cast<bs_grid*>(g)->ws_coarse, (size_t)nst * 10 * MM * sizeof(float));
+  int rc = ensure(const_cast<bs_grid*>(g)->ws_coarse, (size_t)nst * kGlobalVecs * MM * sizeof(float));
   if (rc) return rc;
   GSweepParams gp;
   gp.d = d;
   gp.a = a;
   float* base = (float*)g->ws_coarse.ptr;
-  gp.w = GlobalVecs{base, base + MM, base + 2 * MM, base + 3 * MM, base + 4 * MM, base + 5 * MM,
-                    base + 6 * MM, base + 7 * MM, base + 8 * MM, base + 9 * MM};
+  gp.w = GlobalVecs{base,          base + MM,     base + 2 * MM, base + 3 * MM, base + 4 * MM, base + 5 * MM,
+                    base + 6 * MM, base + 7 * MM, base + 8 * MM, base + 9 * MM, base + 10 * MM};
   gp.M = M;
   gp.h = (float)(g->xmax / (M - 1));
   for (int C : {16, 8}) {
