@@ -184,7 +184,10 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  *  BS_OPT_COARSE_VARIANT  -1 (default): the coarse sweep of grids with M <= 256 uses the band
  *                        variant measured fastest for that M (bs_coarse_variant); k >= 0:
  *                        always variant k (it must fit the grid, else the launch fails with
- *                        BS_ERR_ARG).  Variants differ only in work split and reduction order.
+ *                        BS_ERR_ARG).  Variants differ in work split and reduction order
+ *                        and, where their shared memory allows, use the polynomial
+ *                        preconditioner and quadratic initial-guess extrapolation (all solve
+ *                        the same systems to the same Krylov tolerance).
  * Returns BS_OK or BS_ERR_ARG for an unknown option or an out-of-range value. */
 enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
        BS_OPT_KRYLOV_MAXIT = 3, BS_OPT_PHASE_TIMING = 4, BS_OPT_JACOBI_TARGET_COLD = 5,

@@ -414,7 +414,7 @@ int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* v
     return BS_OK;
   }
   if (g->coarse_variant < 0) {
-    rc = coarse_autotune(g, make_item(*p, 0.0, dtau_coarse), (cudaStream_t)stream, 4, nullptr);
+    rc = coarse_autotune(g, make_item(*p, 0.0, dtau_coarse), (cudaStream_t)stream, kAutotuneSteps, nullptr);
     if (rc) return rc;
   }
   *variant = g->coarse_variant;
@@ -506,7 +506,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   const bool krylov_f = sweeps == 0;   // Jacobi bound >= 0.8: F by BiCGSTAB per step
   // numerical G on this grid: F overlapped with the chunked coarse sweep (Krylov F of grids
   // beyond one cluster shares the coarse solver's global workspace and stays sequential)
-  if (!pino && !(g->coarse_M > 0 && g->coarse_M != g->M) && g_opt.pipeline && pipeline_chunk(N) > 0 &&
+  if (!pino && !(g->coarse_M > 0 && g->coarse_M != g->M) && g_opt.pipeline && pipeline_eligible(N) &&
       !(krylov_f && g->M > 256))
     return parareal_pipelined(g, p, N, fine_steps, coarse_steps, tol, Kmax, u_out, user_u0, k_done,
                               defect_hist, s);

@@ -103,6 +103,29 @@ __device__ __forceinline__ float scaled_row(const float* yrow, int ncol, int col
                      cgi);
 }
 
+// scaled_matvec with the strip's own values y_C taken from registers (c[k] equals the plane's
+// own row r0 + k): the vertical neighbours inside the strip come from registers too, so each
+// row loads only its west and east neighbours (and the strip's first and last rows one more).
+template <class CFG>
+__device__ __forceinline__ void scaled_matvec_rc(const float* __restrict__ y, const float (&c)[CFG::K],
+                                                 const float4* __restrict__ rowc,
+                                                 const float* __restrict__ ID, int col, int il, int ir, int r0,
+                                                 float ce, float cw, float cgi, float (&out)[CFG::K]) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K;
+  const int p0 = r0 + 1;
+  float nW = y[(p0 - 1) * NCOL + il], nC = y[(p0 - 1) * NCOL + col], nE = y[(p0 - 1) * NCOL + ir];
+  float cW = y[p0 * NCOL + il], cC = c[0], cE = y[p0 * NCOL + ir];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int p = p0 + k;
+    const float sW = y[(p + 1) * NCOL + il], sE = y[(p + 1) * NCOL + ir];
+    const float sC = k + 1 < K ? c[k + 1 < K ? k + 1 : k] : y[(p + 1) * NCOL + col];
+    out[k] = scaled_node(nW, nC, nE, cW, cC, cE, sW, sC, sE, rowc[p - 1], ID[(p - 1) * NCOL + col], ce, cw, cgi);
+    nW = cW; nC = cC; nE = cE;
+    cW = sW; cC = sC; cE = sE;
+  }
+}
+
 template <class T>
 __device__ __forceinline__ T warp_butterfly(T x) {
 #pragma unroll
@@ -305,18 +328,22 @@ __device__ __forceinline__ void xround(Xchg& xs, const float (&v)[NV], float (&t
 }
 
 // Q = M^{-1} y = 2 y - A^ y on the strip's own rows and, for the edge groups, on the halo row
-// next to the band (y has DH = 2 halo rows; Q one).  Outside the domain Q stays zero.
+// next to the band (y has DH = 2 halo rows, its own values also in yc; Q has one halo row).
+// The own rows of Q are also returned in q.  Outside the domain Q stays zero.
 template <class CFG, int DH>
-__device__ __forceinline__ void precond_apply(const float* __restrict__ y, float* __restrict__ Q,
+__device__ __forceinline__ void precond_apply(const float* __restrict__ y, const float (&yc)[CFG::K],
+                                              float* __restrict__ Q, float (&q)[CFG::K],
                                               const float4* __restrict__ rowc, const float* __restrict__ ID,
                                               int col, int il, int ir, int r0, int grp, float ce, float cw,
                                               float cgi, bool has_up, bool has_down, float4 rc_top, float id_top,
                                               float4 rc_bot, float id_bot) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH;
-  float ay[K];
-  scaled_matvec<CFG>(y + (DH - 1) * NCOL, rowc, ID, col, il, ir, r0, ce, cw, cgi, ay);
+  scaled_matvec_rc<CFG>(y + (DH - 1) * NCOL, yc, rowc, ID, col, il, ir, r0, ce, cw, cgi, q);
 #pragma unroll
-  for (int k = 0; k < K; ++k) Q[(r0 + k + 1) * NCOL + col] = fmaf(2.f, y[(r0 + k + DH) * NCOL + col], -ay[k]);
+  for (int k = 0; k < K; ++k) {
+    q[k] = fmaf(2.f, yc[k], -q[k]);
+    Q[(r0 + k + 1) * NCOL + col] = q[k];
+  }
   if (grp == 0 && has_up) {
     const float* yr = y + (DH - 1) * NCOL;
     Q[col] = fmaf(2.f, yr[col], -scaled_row(yr, NCOL, col, il, ir, rc_top, id_top, ce, cw, cgi));
@@ -533,7 +560,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
 #pragma unroll
           for (int k = 0; k < K; ++k) XP[(r0 + k) * NCOL + col] = xw[k];
         }
-        float x[K], rr[K], vv[K], tt[K];
+        // per thread: x, r (s after the first round of an iteration), v, t and p of the strip
+        float x[K], rr[K], vv[K], tt[K], pk[K];
         int it = 0;
         bool conv = false;
         // A breakdown (a zero denominator in alpha, omega or beta) restarts the solve from
@@ -580,6 +608,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
           for (int k = 0; k < K; ++k) {
             deep_store<CFG, DH>(P, pP, r0 + k, col, rr[k]);
             RH[(r0 + k) * NCOL + col] = rr[k];
+            pk[k] = rr[k];
           }
           cluster_barrier(cluster, C);
           float rho = sc->rho;
@@ -611,12 +640,13 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             float* vh_bot = vh_top + DH * NCOL;
             // v = A^ p (POLY: A^ M^{-1} p) ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
             if constexpr (L::POLY) {
-              precond_apply<CFG, DH>(P, Q, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
+              float qk[K];
+              precond_apply<CFG, DH>(P, pk, Q, qk, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
                                      rc_top, id_top, rc_bot, id_bot);
               __syncthreads();
-              scaled_matvec<CFG>(Q, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+              scaled_matvec_rc<CFG>(Q, qk, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
             } else {
-              scaled_matvec<CFG>(P1, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+              scaled_matvec_rc<CFG>(P1, pk, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
             }
             {
               const uint32_t mb = smem_addr(xs.mb + (xs.round & 1));
@@ -642,29 +672,30 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             if (ta[1] <= stop2) { conv = true; break; }
             if (ta[0] == 0.f) { fail = true; break; }
             const float af = rho / ta[0];
-            // s = r - alpha v, own rows and halo rows
+            // s = r - alpha v (rr holds s from here on), own rows and halo rows
 #pragma unroll
-            for (int k = 0; k < K; ++k) S[(r0 + k + DH) * NCOL + col] = fmaf(-af, vv[k], rr[k]);
+            for (int k = 0; k < K; ++k) {
+              if constexpr (L::POLY) x[k] = fmaf(af, Q[(r0 + k + 1) * NCOL + col], x[k]);   // x += alpha M^{-1} p
+              else x[k] = fmaf(af, pk[k], x[k]);
+              rr[k] = fmaf(-af, vv[k], rr[k]);
+              S[(r0 + k + DH) * NCOL + col] = rr[k];
+            }
 #pragma unroll
             for (int t = 0; t < DH; ++t) {
               if (grp == 0) S[t * NCOL + col] = has_up ? fmaf(-af, vh_top[t * NCOL + col], rh_top[t]) : 0.f;
               if (grp == G - 1)
                 S[(BH + DH + t) * NCOL + col] = has_down ? fmaf(-af, vh_bot[t * NCOL + col], rh_bot[t]) : 0.f;
             }
-            if constexpr (L::POLY) {
-              // x += alpha M^{-1} p while Q still holds it (own entries: no other thread writes them)
-#pragma unroll
-              for (int k = 0; k < K; ++k) x[k] = fmaf(af, Q[(r0 + k + 1) * NCOL + col], x[k]);
-            }
             __syncthreads();
             // t = A^ s (POLY: A^ M^{-1} s) ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
             if constexpr (L::POLY) {
-              precond_apply<CFG, DH>(S, Q, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
+              float qk[K];
+              precond_apply<CFG, DH>(S, rr, Q, qk, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
                                      rc_top, id_top, rc_bot, id_bot);
               __syncthreads();
-              scaled_matvec<CFG>(Q, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
+              scaled_matvec_rc<CFG>(Q, qk, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
             } else {
-              scaled_matvec<CFG>(S1, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
+              scaled_matvec_rc<CFG>(S1, rr, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
             }
             {
               const uint32_t mb = smem_addr(xs.mb + (xs.round & 1));
@@ -681,10 +712,10 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             float p2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const float sv = S[(r0 + k + DH) * NCOL + col], rh = RH[(r0 + k) * NCOL + col];
-              p2[0] = fmaf(tt[k], sv, p2[0]);
+              const float rh = RH[(r0 + k) * NCOL + col];
+              p2[0] = fmaf(tt[k], rr[k], p2[0]);
               p2[1] = fmaf(tt[k], tt[k], p2[1]);
-              p2[2] = fmaf(rh, sv, p2[2]);
+              p2[2] = fmaf(rh, rr[k], p2[2]);
               p2[3] = fmaf(rh, tt[k], p2[3]);
             }
             float tb[4];
@@ -696,15 +727,14 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             if (of == 0.f || rho == 0.f) fail = true;
             else bf = (rho_new / rho) * (af / of);
             rho = rho_new;
-            // x += alpha p + omega s (POLY: omega M^{-1} s) ;  r = s - omega t ;  p = r + beta (p - omega v)
+            // x += omega s (POLY: omega M^{-1} s) ;  r = s - omega t ;  p = r + beta (p - omega v)
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const int idx = (r0 + k + DH) * NCOL + col;
-              const float sv = S[idx], pv = P[idx];
               if constexpr (L::POLY) x[k] = fmaf(of, Q[(r0 + k + 1) * NCOL + col], x[k]);
-              else x[k] += af * pv + of * sv;
-              rr[k] = fmaf(-of, tt[k], sv);
-              P[idx] = fmaf(bf, fmaf(-of, vv[k], pv), rr[k]);
+              else x[k] = fmaf(of, rr[k], x[k]);
+              rr[k] = fmaf(-of, tt[k], rr[k]);
+              pk[k] = fmaf(bf, fmaf(-of, vv[k], pk[k]), rr[k]);
+              P[(r0 + k + DH) * NCOL + col] = pk[k];
             }
 #pragma unroll
             for (int t = 0; t < DH; ++t) {
@@ -827,9 +857,29 @@ static size_t sweep_smem_bytes() {
   return SweepSmem<CFG>::BYTES;
 }
 
+// The shared memory a CTA may claim on the current device (0 if the query fails).
+static size_t smem_optin_bytes() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (size_t)v;
+}
+
 template <class CFG>
 static int launch_sweep_k(const SweepParams& sp, cudaStream_t s) {
-  const size_t smem = sweep_smem_bytes<CFG>();
+  // A single system (the serial sweep, one PROP state) claims all of each SM's shared memory,
+  // so that no CTA of a concurrent kernel (the fine propagator of the pipelined driver) shares
+  // its SMs: the sweep is the serial critical path, and an SM shared with a stencil kernel
+  // issues its iterations up to a third slower.  Batched PROP packs its clusters as usual.
+  const bool batched = sp.a.mode == SWEEP_PROP && sp.a.nprop > 0;
+  size_t smem = sweep_smem_bytes<CFG>();
+  if (!batched) {
+    static const size_t optin = smem_optin_bytes();
+    if (optin > smem) smem = optin;
+  }
   auto kern = sweep_band_kernel<CFG>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (sp.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -1100,6 +1150,41 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   }
 }
 
+static cudaLaunchConfig_t global_launch_config(int C, int nst, cudaStream_t s, cudaLaunchAttribute (&attr)[1]) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, nst, 1);
+  cfg.blockDim = dim3(kGThreads, 1, 1);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Cluster size of the global-memory sweep: 16 CTAs where the device can hold such a cluster,
+// else 8 (0: neither).
+static int global_cluster_ctas(int) {
+  for (int C : {16, 8}) {
+    if (C > 8 &&
+        cudaFuncSetAttribute(sweep_global_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = global_launch_config(C, 1, nullptr, attr);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, sweep_global_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    return C;
+  }
+  return 0;
+}
+
 static int launch_sweep_global(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s) {
   const int M = g->M;
   const size_t MM = (size_t)M * M;
@@ -1114,32 +1199,13 @@ static int launch_sweep_global(const bs_grid* g, const ItemDesc& d, const SweepA
                     base + 6 * MM, base + 7 * MM, base + 8 * MM, base + 9 * MM, base + 10 * MM};
   gp.M = M;
   gp.h = (float)(g->xmax / (M - 1));
-  for (int C : {16, 8}) {
-    gp.C = C;
-    if (C > 8) {
-      cudaError_t e = cudaFuncSetAttribute(sweep_global_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) { cudaGetLastError(); continue; }
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, nst, 1);
-    cfg.blockDim = dim3(kGThreads, 1, 1);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, sweep_global_kernel, &cfg) != cudaSuccess || nclusters < 1) {
-      cudaGetLastError();
-      continue;
-    }
-    BS_CUDA_TRY(cudaLaunchKernelEx(&cfg, sweep_global_kernel, gp));
-    return BS_OK;
-  }
-  return set_error(BS_ERR_CUDA, "coarse propagator: no cluster shape available for M=%d", M);
+  const int C = global_cluster_ctas(M);
+  if (C == 0) return set_error(BS_ERR_CUDA, "coarse propagator: no cluster shape available for M=%d", M);
+  gp.C = C;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = global_launch_config(C, nst, s, attr);
+  BS_CUDA_TRY(cudaLaunchKernelEx(&cfg, sweep_global_kernel, gp));
+  return BS_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1156,8 +1222,10 @@ struct CoarseVariant {
 };
 static const CoarseVariant kCoarseVariants[] = {
     {32, 256, 4, true},   {32, 128, 2, false},  {64, 512, 8, true},   {64, 256, 4, false},
-    {128, 512, 16, true}, {128, 512, 4, false}, {256, 512, 16, true}, {256, 512, 8, false}};
+    {128, 512, 16, true}, {128, 512, 4, false}, {256, 512, 16, true}, {256, 512, 8, false},
+    {256, 256, 16, false}, {128, 256, 8, false}};
 constexpr int kNumCoarseVariants = (int)(sizeof(kCoarseVariants) / sizeof(kCoarseVariants[0]));
+static_assert(kNumCoarseVariants == 10, "launch_variant and variant_launchable list every variant");
 
 static int variant_ncol(int M) {
   return M <= 32 ? 32 : M <= 64 ? 64 : M <= 128 ? 128 : M <= 256 ? 256 : 0;
@@ -1190,6 +1258,8 @@ static int launch_variant(int v, SweepParams sp, cudaStream_t s) {
     case 5: return launch_sweep_k<BandCfg<128, 512, 4>>(sp, s);
     case 6: return launch_sweep_k<BandCfg<256, 512, 16>>(sp, s);
     case 7: return launch_sweep_k<BandCfg<256, 512, 8>>(sp, s);
+    case 8: return launch_sweep_k<BandCfg<256, 256, 16>>(sp, s);
+    case 9: return launch_sweep_k<BandCfg<128, 256, 8>>(sp, s);
   }
   return set_error(BS_ERR_ARG, "coarse propagator: no band variant %d", v);
 }
@@ -1236,6 +1306,8 @@ static bool variant_launchable(int v, int M) {
     case 5: return cluster_fits<BandCfg<128, 512, 4>>(sh);
     case 6: return cluster_fits<BandCfg<256, 512, 16>>(sh);
     case 7: return cluster_fits<BandCfg<256, 512, 8>>(sh);
+    case 8: return cluster_fits<BandCfg<256, 256, 16>>(sh);
+    case 9: return cluster_fits<BandCfg<128, 256, 8>>(sh);
   }
   return false;
 }
@@ -1319,13 +1391,9 @@ int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, in
   return BS_OK;
 }
 
-int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s) {
-  SweepParams sp;
-  sp.d = d;
-  sp.a = a;
-  sp.sh = g->shape;
-  sp.h = (float)(g->xmax / (g->M - 1));
-  if (variant_ncol(g->M) == 0) return launch_sweep_global(g, d, a, s);
+// The band variant the coarse sweep of g runs: forced by the option, else measured once per
+// grid size (from the cache while a stream is being captured).
+static int resolve_variant(const bs_grid* g, const ItemDesc& d, cudaStream_t s, int* v) {
   bs_grid* gm = const_cast<bs_grid*>(g);
   if (g_opt.coarse_variant < 0 && gm->coarse_variant < 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1333,13 +1401,38 @@ int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaSt
     if (capturing) {
       gm->coarse_variant = coarse_cached_variant(g->device, g->M);
     } else {
-      int rc = coarse_autotune(gm, d, s, 4, nullptr);
+      int rc = coarse_autotune(gm, d, s, kAutotuneSteps, nullptr);
       if (rc) return rc;
     }
   }
-  const int v = g_opt.coarse_variant >= 0 ? g_opt.coarse_variant : gm->coarse_variant;
-  if (v < 0 || v >= kNumCoarseVariants || !variant_fits(v, g->M))
-    return set_error(BS_ERR_ARG, "coarse propagator: band variant %d does not fit M=%d", v, g->M);
+  *v = g_opt.coarse_variant >= 0 ? g_opt.coarse_variant : gm->coarse_variant;
+  if (*v < 0 || *v >= kNumCoarseVariants || !variant_fits(*v, g->M))
+    return set_error(BS_ERR_ARG, "coarse propagator: band variant %d does not fit M=%d", *v, g->M);
+  return BS_OK;
+}
+
+int coarse_cluster_ctas(const bs_grid* g, const ItemDesc& d, cudaStream_t s, int* ctas) {
+  if (variant_ncol(g->M) == 0) {
+    *ctas = global_cluster_ctas(g->M);
+    return BS_OK;
+  }
+  int v = -1;
+  int rc = resolve_variant(g, d, s, &v);
+  if (rc) return rc;
+  *ctas = variant_shape(v, g->M).C;
+  return BS_OK;
+}
+
+int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s) {
+  SweepParams sp;
+  sp.d = d;
+  sp.a = a;
+  sp.sh = g->shape;
+  sp.h = (float)(g->xmax / (g->M - 1));
+  if (variant_ncol(g->M) == 0) return launch_sweep_global(g, d, a, s);
+  int v = -1;
+  int rc = resolve_variant(g, d, s, &v);
+  if (rc) return rc;
   sp.sh.M = g->M;
   return launch_variant(v, sp, s);
 }

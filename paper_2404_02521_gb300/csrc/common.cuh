@@ -293,11 +293,18 @@ int resampled_propagate(bs_grid* g, const ItemDesc& d, const float* in, float* o
 int resampled_sweep(bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStream_t s);
 int resampled_launches_per_slice();
 // Pipelined Parareal with the numerical G on the state grid (pipeline.cu).
-int pipeline_chunk(int N);   // slices per chunk, 0: too few slices to pipeline
+// Pipelined driver: whether N slices are enough to pipeline, and the slices per chunk.
+bool pipeline_eligible(int N);
+int pipeline_chunk(bs_grid* g, const ItemDesc& dc, int N, cudaStream_t s, int* S);
+int fine_cluster_capacity(const bs_grid* g);   // fine band clusters the device runs at once (0: unknown)
+int coarse_cluster_ctas(const bs_grid* g, const ItemDesc& d, cudaStream_t s, int* ctas);
 int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, int coarse_steps, double tol,
                        int Kmax, float* u_out, bool user_u0, int* k_done, double* defect_hist,
                        cudaStream_t s);
 void pipe_destroy(bs_grid* g);
+// coarse steps of each timed tuning solve: past the cold start from the payoff, so that the
+// extrapolated initial guesses of the steady state weigh in
+constexpr int kAutotuneSteps = 16;
 int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, int* chosen);
 // PINO coarse propagator (pino.cu)
 int pino_check(const bs_pino* net, int M);

@@ -555,6 +555,48 @@ static int launch_band(const FineBatch& fb, cudaStream_t s) {
   return BS_OK;
 }
 
+// Clusters of the fine band kernel that the device runs at once (0 if unknown: cluster tiles).
+template <class CFG>
+static int band_capacity(const BandShape& sh) {
+  const size_t smem = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
+                      (size_t)CFG::BH * sizeof(float4);
+  auto kern = fine_band_kernel<CFG>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      (sh.C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sh.C, 1, 1);
+  cfg.blockDim = dim3(CFG::NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = sh.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int fine_cluster_capacity(const bs_grid* g) {
+  const BandShape sh = g->shape;
+  if (sh.C < 1 || sh.C > kMaxCluster) return 0;
+  switch (sh.ncol) {
+    case 32: return band_capacity<BandCfg<32, 256, 4>>(sh);
+    case 64: return band_capacity<BandCfg<64, 512, 8>>(sh);
+    case 128: return band_capacity<BandCfg<128, 512, 16>>(sh);
+    case 256: return band_capacity<BandCfg<256, 512, 16>>(sh);
+  }
+  return 0;
+}
+
 int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
   const BandShape sh = g->shape;
   if (sh.C < 1 || sh.C > kMaxCluster) return launch_ctiles(g, items, n, nsteps, s);

@@ -81,7 +81,28 @@ static int timing_pair(PipeState* ps, cudaEvent_t* a, cudaEvent_t* b) {
   return BS_OK;
 }
 
-int pipeline_chunk(int N) { return N < 8 ? 0 : (N + 3) / 4; }
+bool pipeline_eligible(int N) { return N >= 8; }
+
+// Slices per chunk.  An F chunk should run in one wave beside the sweep's cluster: the fine
+// clusters the device holds at once, less those the coarse cluster displaces (its CTAs over
+// the fine cluster's, rounded up: both take whole SMs of one GPC).  A chunk that spills into a
+// second wave, or an F wave that leaves no GPC for the sweep's cluster, stalls the sweep --
+// on the 256 x 256 workload chunks of 16 slices took 65 ms per solve, chunks of 12 took 47.
+// At most a quarter of the slices, so that F starts early and the sweep drains soon.
+int pipeline_chunk(bs_grid* g, const ItemDesc& dc, int N, cudaStream_t s, int* S) {
+  int quarter = (N + 3) / 4;
+  const int cap = fine_cluster_capacity(g);
+  if (cap > 0) {
+    int cc = 0;
+    int rc = coarse_cluster_ctas(g, dc, s, &cc);
+    if (rc) return rc;
+    const int cf = g->shape.C;
+    const int wave = cap - (cc + cf - 1) / cf;
+    if (wave >= 1 && wave < quarter) quarter = wave;
+  }
+  *S = quarter;
+  return BS_OK;
+}
 
 int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, int coarse_steps, double tol,
                        int Kmax, float* u_out, bool user_u0, int* k_done, double* defect_hist,
@@ -95,9 +116,12 @@ int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, in
   const int sweepsx = grid_sweeps(g, *p, dtau_f, START_EXTRAP);
   const int sweepsxl = grid_sweeps(g, *p, dtau_f, START_EXTRAP_LATE);
   const bool krylov_f = sweeps == 0;
-  const int S = pipeline_chunk(N);
+  const ItemDesc dc = make_item(*p, 0.0, slice / coarse_steps);
+  int S = 0;
+  int rc = pipeline_chunk(g, dc, N, caller, &S);
+  if (rc) return rc;
   const int chunks = (N + S - 1) / S;
-  int rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1));
+  rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1));
   if (rc) return rc;
   float* Fb = (float*)g->ws_par.ptr;
   float* Gold = Fb + (size_t)N * MM;
@@ -113,7 +137,6 @@ int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, in
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_fine, t_coarse;
 
   BS_CUDA_TRY(cudaMemsetAsync(g->status, 0, kStatusWords * sizeof(int), s));
-  const ItemDesc dc = make_item(*p, 0.0, slice / coarse_steps);
   if (!user_u0) {
     if ((rc = launch_payoff(g, dc, u_out, s))) return rc;
     g->n_other += 1;

@@ -170,7 +170,7 @@ static int class_setup(bs_server* sv, const bs_request& r) {
   // one measurement of the coarse band variant per grid size, before any request uses it
   if (r.M <= 256 && g_opt.coarse_variant < 0) {
     const int cs = r.coarse_steps > 0 ? r.coarse_steps : 1;
-    rc = coarse_autotune(g, make_item(r.p, 0.0, r.p.T / r.N / cs), s, 4, nullptr);
+    rc = coarse_autotune(g, make_item(r.p, 0.0, r.p.T / r.N / cs), s, kAutotuneSteps, nullptr);
     if (rc) {
       cudaStreamDestroy(s);
       bs_grid_destroy(g);
