@@ -173,11 +173,15 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  *  BS_OPT_JACOBI_TARGET_EXTRAP_LATE  the extrapolated-start target from BS_OPT_EXTRAP_LATE on
  *                        (default 2^-4)
  *  BS_OPT_PIPELINE       1 (default): parareal_solve with the numerical G on the state grid
- *                        and N >= 8 splits each coarse sweep into four slice chunks and runs F
- *                        for a chunk on a second stream as soon as the sweep has produced its
- *                        input states (F of the next iteration speculatively, before the
- *                        defect is known); 0: F and the sweep alternate as whole phases
- *  BS_OPT_KRYLOV_TOL     relative residual at which a coarse BiCGSTAB solve stops (1e-6)
+ *                        and N >= 8 splits each coarse sweep into chunks of consecutive
+ *                        slices (as many as F runs in one wave beside the sweep's cluster, at
+ *                        most a quarter of them) and runs F for a chunk on a second stream as
+ *                        soon as the sweep has produced its input states (F of the next
+ *                        iteration speculatively, before the defect is known); 0: F and the
+ *                        sweep alternate as whole phases
+ *  BS_OPT_KRYLOV_TOL     relative residual at which a coarse BiCGSTAB solve (numerical G) stops
+ *                        (1e-5; G need only be a deterministic approximation of F)
+ *  BS_OPT_FINE_KRYLOV_TOL  ... a fine BiCGSTAB step (F for step sizes beyond Jacobi) stops (1e-6)
  *  BS_OPT_KRYLOV_MAXIT   iteration cap of a coarse BiCGSTAB solve (default 400)
  *  BS_OPT_PHASE_TIMING   1: parareal_solve brackets its fine and coarse launches with CUDA
  *                        events on the caller's stream (read back by bs_phase_stats); 0: off
@@ -192,7 +196,8 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
 enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
        BS_OPT_KRYLOV_MAXIT = 3, BS_OPT_PHASE_TIMING = 4, BS_OPT_JACOBI_TARGET_COLD = 5,
        BS_OPT_COARSE_VARIANT = 6, BS_OPT_JACOBI_TARGET_EXTRAP = 7, BS_OPT_EXTRAP_START = 8,
-       BS_OPT_EXTRAP_LATE = 9, BS_OPT_JACOBI_TARGET_EXTRAP_LATE = 10, BS_OPT_PIPELINE = 11 };
+       BS_OPT_EXTRAP_LATE = 9, BS_OPT_JACOBI_TARGET_EXTRAP_LATE = 10, BS_OPT_PIPELINE = 11,
+       BS_OPT_FINE_KRYLOV_TOL = 12 };
 int bs_set_option(int option, double value);
 
 /* Numerical coarse propagator on a coarser grid (the resolution change of Sec. 4.4 applied to

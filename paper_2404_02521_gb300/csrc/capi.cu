@@ -165,7 +165,7 @@ int launch_krylov_fine(bs_grid* g, const ItemDesc* items, int n, int nsteps, cud
     a.csteps = nsteps;
     a.slice_len = 0.0;
     a.status = g->status;
-    a.tol = g_opt.krylov_tol;
+    a.tol = g_opt.fine_krylov_tol;
     a.maxit = g_opt.krylov_maxit;
     int j = i;
     while (j < n && j - i < kMaxProp && same(items[i], items[j])) {
@@ -365,6 +365,10 @@ int bs_set_option(int option, double value) {
     case BS_OPT_KRYLOV_TOL:
       if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_KRYLOV_TOL must be in (0, 1)");
       g_opt.krylov_tol = value;
+      return BS_OK;
+    case BS_OPT_FINE_KRYLOV_TOL:
+      if (!(value > 0.0 && value < 1.0)) return set_error(BS_ERR_ARG, "BS_OPT_FINE_KRYLOV_TOL must be in (0, 1)");
+      g_opt.fine_krylov_tol = value;
       return BS_OK;
     case BS_OPT_PHASE_TIMING:
       g_opt.phase_timing = value != 0.0;

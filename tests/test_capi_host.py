@@ -81,3 +81,17 @@ def test_server_rejects_bad_arguments(lib):
     assert lib.bs_server_poll(None, None, 0, C.byref(n)) == _lib.BS_ERR_ARG
     assert lib.bs_server_progress(None, None, None) == _lib.BS_ERR_ARG
     assert lib.bs_server_destroy(None) == 0
+
+
+def test_options_are_range_checked(lib):
+    # the coarse (G) and fine (F) Krylov tolerances are separate options, each in (0, 1);
+    # an unknown option index is rejected
+    from paper_2404_02521_gb300 import _lib
+    lib.bs_set_option.argtypes = [C.c_int, C.c_double]
+    lib.bs_set_option.restype = C.c_int
+    for opt, default in [(_lib.OPT_KRYLOV_TOL, 1e-5), (_lib.OPT_FINE_KRYLOV_TOL, 1e-6)]:
+        assert lib.bs_set_option(opt, 0.0) != 0
+        assert lib.bs_set_option(opt, 1.0) != 0
+        assert lib.bs_set_option(opt, 3e-6) == 0
+        assert lib.bs_set_option(opt, default) == 0
+    assert lib.bs_set_option(99, 1.0) != 0

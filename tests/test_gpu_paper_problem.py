@@ -81,7 +81,10 @@ def test_parareal_converges_to_the_fine_solution(bs, golden, coarse_steps):
 def test_paper_step_sizes_parareal_matches_oracle(bs):
     # the paper's configuration: three fine substeps per 0.1-slice and one coarse step
     # (Sec. 4.1).  Both are too large for Jacobi sweeps on this grid, so F and G are BiCGSTAB
-    # solves; the GPU Parareal takes the oracle's iteration count and defects.
+    # solves; the GPU Parareal takes the oracle's iteration count and defects.  The oracle's G
+    # is an exact solve, so G's solves run to 1e-6 here: at the default 1e-5 the iteration
+    # count is the same but on this very stiff coarse step (dtau sigma^2 i^2 ~ 800) the
+    # smallest defect moves by 10%.
     import torch
     with open(os.path.join(HERE, "golden", "cash_or_nothing301_paper_steps.json")) as f:
         gd = json.load(f)
@@ -91,11 +94,13 @@ def test_paper_step_sizes_parareal_matches_oracle(bs):
     U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
     try:
         bs.bs_set_option(bs.OPT_KRYLOV_MAXIT, 20000)
+        bs.bs_set_option(bs.OPT_KRYLOV_TOL, 1e-6)
         rc, k, defects = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM, 1, None, 1e-4,
                                            pb.N, U)
         torch.cuda.synchronize()
     finally:
         bs.bs_set_option(bs.OPT_KRYLOV_MAXIT, 400)
+        bs.bs_set_option(bs.OPT_KRYLOV_TOL, 1e-5)
     assert rc == 0 and k == gd["parareal_k"]
     for a, b in zip(defects, gd["parareal_defects"]):
         assert abs(a - b) <= 2e-2 * b + 1e-6
