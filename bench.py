@@ -74,9 +74,11 @@ def fine_flops_per_point_launch(m0, m1, mx, mxl, steps):
 
 
 # Algorithmic FLOPs of one BiCGSTAB iteration per node of the coarse solve: two Jacobi-scaled
-# 9-point products (15 FLOP each: 4 FMA, 1 multiply, 3 add, and the scaled subtraction), six
-# dot-product terms (12) and the vector updates s, x, r, p (13).
+# 9-point products (15 FLOP each: 4 FMA, 2 multiplies, 3 adds), six dot-product terms (12) and
+# the vector updates s, x, r, p (13).  Band variants with the polynomial preconditioner
+# M^{-1} = 2I - A^ evaluate two more scaled products and 2 y - A^ y twice (+34).
 COARSE_FLOPS_PER_NODE_ITER = 55
+COARSE_FLOPS_POLY_EXTRA = 34
 
 
 class ClockSampler:
@@ -334,11 +336,12 @@ def gpu_arm(args, world, rank, local):
     peak_fp32 = fp32_peak_tflops(sm_max)
     fine_tflops = fine_flops / (phases["fine_ms"] / 1e3) / 1e12 if phases["fine_ms"] > 0 else 0.0
     # coarse: the timed region ran args.steps x the counted solves
-    coarse_flops = args.steps * krylov_iters * M * M * COARSE_FLOPS_PER_NODE_ITER
-    coarse_tflops = coarse_flops / (phases["coarse_ms"] / 1e3) / 1e12 if phases["coarse_ms"] > 0 else 0.0
     variant = bs.bs_coarse_variant(g, pb0.params, pb0.dtau_coarse)
-    # CTAs of the coarse cluster at M = 256: band variant 7 holds 16 rows per CTA, 6 holds 32
-    cluster_ctas = -(-M // 16) if variant == 7 else -(-M // 32)
+    vinfo = bs.bs_coarse_variant_info(variant, M)
+    cluster_ctas = vinfo["ctas"]
+    flops_node_iter = COARSE_FLOPS_PER_NODE_ITER + (COARSE_FLOPS_POLY_EXTRA if vinfo["poly"] else 0)
+    coarse_flops = args.steps * krylov_iters * M * M * flops_node_iter
+    coarse_tflops = coarse_flops / (phases["coarse_ms"] / 1e3) / 1e12 if phases["coarse_ms"] > 0 else 0.0
     iter_us = 1e3 * phases["coarse_ms"] / max(1, args.steps * krylov_iters)
     kernels = {
         "fine_band_kernel": {"ms_total": phases["fine_ms"], "launches": phases["fine_launches"],
@@ -353,6 +356,9 @@ def gpu_arm(args, world, rank, local):
                               "achieved_tflops": coarse_tflops, "peak_tflops": peak_fp32,
                               "frac": coarse_tflops / peak_fp32,
                               "band_variant": variant, "cluster_ctas": cluster_ctas,
+                              "polynomial_preconditioner": vinfo["poly"],
+                              "quadratic_extrapolation": vinfo["quad"],
+                              "flops_per_node_iter": flops_node_iter,
                               "frac_of_cluster_sms": coarse_tflops / (peak_fp32 * cluster_ctas / 152),
                               "krylov_iters_per_solve": krylov_iters / len(problems),
                               "implicit_solves_per_solve": krylov_solves / len(problems),

@@ -231,6 +231,15 @@ int bs_fine_steps_for(int M, const bs_params* p, int N, int min_steps, double qm
 int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* variant,
                       bs_stream stream);
 
+/* Shape and solver features of band variant `variant` on an M x M grid (M <= 256, the
+ * variant's column count must cover M): *ctas = CTAs of its cluster, *threads = threads per
+ * CTA, *rows = rows per thread, *poly = 1 if it applies the polynomial preconditioner
+ * M^{-1} = 2I - A^ (two more scaled 9-point products per BiCGSTAB iteration), *quad = 1 if its
+ * initial guesses extrapolate quadratically.  Both features are used where the variant's
+ * shared memory holds their extra planes.  Any output pointer may be NULL.  Host-only.
+ * Returns BS_OK or BS_ERR_ARG (unknown variant, or one that does not fit M). */
+int bs_coarse_variant_info(int variant, int M, int* ctas, int* threads, int* rows, int* poly, int* quad);
+
 /* Diagnostics of the coarse solves enqueued on this grid since the last parareal_solve or
  * bs_grid_stats call: the largest BiCGSTAB iteration count, whether any solve hit its cap,
  * the summed iteration count and the number of implicit-Euler solves.  Any output pointer

@@ -23,7 +23,7 @@ COARSE_NUM, COARSE_PINO = 0, 1
 EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
-           "bs_coarse_variant", "bs_server_create", "bs_server_submit", "bs_server_progress",
+           "bs_coarse_variant", "bs_coarse_variant_info", "bs_server_create", "bs_server_submit", "bs_server_progress",
            "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for",
            "bs_grid_set_coarse"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
@@ -102,6 +102,7 @@ def load(path: Optional[str] = None):
     lib.bs_set_option.argtypes = [i, d]
     lib.bs_grid_stats.argtypes = [vp, P(i), P(i), P(i), P(i)]
     lib.bs_coarse_variant.argtypes = [vp, P(bs_params), d, P(i), vp]
+    lib.bs_coarse_variant_info.argtypes = [i, i, P(i), P(i), P(i), P(i), P(i)]
     lib.bs_server_create.argtypes = [P(bs_server_config), P(vp)]
     lib.bs_server_submit.argtypes = [vp, P(bs_request), P(C.c_longlong)]
     lib.bs_server_progress.argtypes = [vp, P(i), P(i)]
@@ -255,6 +256,15 @@ def bs_coarse_variant(g: Grid, p, dtau_coarse: float, stream=None) -> int:
     v = C.c_int(-1)
     check(load().bs_coarse_variant(g.h, C.byref(bp), float(dtau_coarse), C.byref(v), _stream(stream)))
     return v.value
+
+
+def bs_coarse_variant_info(variant: int, M: int) -> dict:
+    """Cluster CTAs, threads per CTA, rows per thread and solver features (polynomial
+    preconditioner, quadratic extrapolation) of a band variant on an M x M grid (host-only)."""
+    v = [C.c_int(0) for _ in range(5)]
+    check(load().bs_coarse_variant_info(int(variant), int(M), *[C.byref(x) for x in v]))
+    return {"ctas": v[0].value, "threads": v[1].value, "rows": v[2].value, "poly": bool(v[3].value),
+            "quad": bool(v[4].value)}
 
 
 def bs_grid_stats(g: Grid, detail: bool = False):

@@ -405,6 +405,10 @@ int bs_fine_steps_for(int M, const bs_params* p, int N, int min_steps, double qm
   return set_error(BS_ERR_ARG, "bs_fine_steps_for: no step count up to 2^20 reaches q <= %g", qmax);
 }
 
+int bs_coarse_variant_info(int variant, int M, int* ctas, int* threads, int* rows, int* poly, int* quad) {
+  return coarse_variant_info(variant, M, ctas, threads, rows, poly, quad);
+}
+
 int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* variant,
                       bs_stream stream) {
   if (!g || !variant) return set_error(BS_ERR_ARG, "bs_coarse_variant: NULL argument");

@@ -1411,6 +1411,37 @@ static int resolve_variant(const bs_grid* g, const ItemDesc& d, cudaStream_t s, 
   return BS_OK;
 }
 
+template <class CFG>
+static void variant_features(int* poly, int* quad) {
+  *poly = SweepSmem<CFG>::POLY ? 1 : 0;
+  *quad = SweepSmem<CFG>::QUAD ? 1 : 0;
+}
+
+int coarse_variant_info(int v, int M, int* ctas, int* threads, int* rows, int* poly, int* quad) {
+  if (v < 0 || v >= kNumCoarseVariants || M < 2 || !variant_fits(v, M))
+    return set_error(BS_ERR_ARG, "bs_coarse_variant_info: no band variant %d for M=%d", v, M);
+  const BandShape sh = variant_shape(v, M);
+  int pl = 0, qd = 0;
+  switch (v) {
+    case 0: variant_features<BandCfg<32, 256, 4>>(&pl, &qd); break;
+    case 1: variant_features<BandCfg<32, 128, 2>>(&pl, &qd); break;
+    case 2: variant_features<BandCfg<64, 512, 8>>(&pl, &qd); break;
+    case 3: variant_features<BandCfg<64, 256, 4>>(&pl, &qd); break;
+    case 4: variant_features<BandCfg<128, 512, 16>>(&pl, &qd); break;
+    case 5: variant_features<BandCfg<128, 512, 4>>(&pl, &qd); break;
+    case 6: variant_features<BandCfg<256, 512, 16>>(&pl, &qd); break;
+    case 7: variant_features<BandCfg<256, 512, 8>>(&pl, &qd); break;
+    case 8: variant_features<BandCfg<256, 256, 16>>(&pl, &qd); break;
+    case 9: variant_features<BandCfg<128, 256, 8>>(&pl, &qd); break;
+  }
+  if (ctas) *ctas = sh.C;
+  if (threads) *threads = kCoarseVariants[v].nt;
+  if (rows) *rows = kCoarseVariants[v].k;
+  if (poly) *poly = pl;
+  if (quad) *quad = qd;
+  return BS_OK;
+}
+
 int coarse_cluster_ctas(const bs_grid* g, const ItemDesc& d, cudaStream_t s, int* ctas) {
   if (variant_ncol(g->M) == 0) {
     *ctas = global_cluster_ctas(g->M);

@@ -304,6 +304,7 @@ bool pipeline_eligible(int N);
 int pipeline_chunk(bs_grid* g, const ItemDesc& dc, int N, cudaStream_t s, int* S);
 int fine_cluster_capacity(const bs_grid* g);   // fine band clusters the device runs at once (0: unknown)
 int coarse_cluster_ctas(const bs_grid* g, const ItemDesc& d, cudaStream_t s, int* ctas);
+int coarse_variant_info(int v, int M, int* ctas, int* threads, int* rows, int* poly, int* quad);
 int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, int coarse_steps, double tol,
                        int Kmax, float* u_out, bool user_u0, int* k_done, double* defect_hist,
                        cudaStream_t s);

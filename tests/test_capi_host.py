@@ -95,3 +95,17 @@ def test_options_are_range_checked(lib):
         assert lib.bs_set_option(opt, 3e-6) == 0
         assert lib.bs_set_option(opt, default) == 0
     assert lib.bs_set_option(99, 1.0) != 0
+
+
+def test_coarse_variant_info(lib):
+    # host-only query of a band variant: its cluster at M = 256 and whether its shared memory
+    # holds the polynomial preconditioner's planes (the 16-row variants do, 32-row ones not)
+    from paper_2404_02521_gb300 import _lib
+    v8 = _lib.bs_coarse_variant_info(8, 256)
+    assert v8 == {"ctas": 16, "threads": 256, "rows": 16, "poly": True, "quad": True}
+    v6 = _lib.bs_coarse_variant_info(6, 256)
+    assert v6["ctas"] == 8 and not v6["poly"]
+    assert _lib.bs_coarse_variant_info(9, 100)["ctas"] == 7
+    for bad in [(8, 100), (10, 256), (-1, 64), (0, 300)]:
+        with pytest.raises(_lib.BSError):
+            _lib.bs_coarse_variant_info(*bad)
