@@ -902,9 +902,10 @@ static int launch_sweep_k(const SweepParams& sp, cudaStream_t s) {
 // ---------------------------------------------------------------------------------------
 // Grids beyond one cluster's shared memory (M > 256): the same BiCGSTAB and Parareal sweep
 // with the vectors in a global workspace.  One cluster of CG CTAs owns the system; CTA rank
-// handles rows [rank*BHg, rank*BHg + BHg).  Stencil operands written by other CTAs are read
-// with ld.global.cg (L2, never a stale L1 line); the cluster barrier's release/acquire
-// orders them.
+// handles rows [rank*BHg, rank*BHg + BHg).  Each stencil pass stages its operand rows (R rows
+// of the band plus one halo row on each side) in shared memory once, so every value crosses
+// L2 once rather than nine times; the rows written by other CTAs are read with ld.global.cg
+// (L2, never a stale L1 line), ordered by the cluster barrier's release/acquire.
 // ---------------------------------------------------------------------------------------
 constexpr int kGThreads = 1024;
 struct GCfg {
@@ -912,9 +913,9 @@ struct GCfg {
 };
 
 struct GlobalVecs {
-  float *u, *x, *xp, *xq, *r, *rh, *p, *v, *s, *t, *id;
+  float *u, *x, *xp, *xq, *r, *rh, *p, *v, *s, *t, *id, *q;   // q: M^{-1} p, then M^{-1} s
 };
-constexpr int kGlobalVecs = 11;
+constexpr int kGlobalVecs = 12;
 
 struct GSweepParams {
   ItemDesc d;
@@ -924,28 +925,90 @@ struct GSweepParams {
   float h;
 };
 
-__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
-
-// A^ y at node (i, j) (PDE rows only), y read through L2.
-__device__ __forceinline__ float g_matvec(const float* y, const float* id, int M, int i, int j,
-                                          float ce, float cw, float cs, float cn, float cg) {
-  const size_t e = (size_t)j * M + i;
-  const float* r0 = y + e - M;
-  const float* r2 = y + e + M;
-  const float yc = ldcg(y + e);
-  const float yw = i > 0 ? ldcg(y + e - 1) : 0.f, ye = ldcg(y + e + 1);
-  const float yn = j > 0 ? ldcg(r0) : 0.f, ys = ldcg(r2);
-  const float ynw = (i > 0 && j > 0) ? ldcg(r0 - 1) : 0.f, yne = j > 0 ? ldcg(r0 + 1) : 0.f;
-  const float ysw = i > 0 ? ldcg(r2 - 1) : 0.f, yse = ldcg(r2 + 1);
-  return yc - id[e] * (ce * ye + cw * yw + cs * ys + cn * yn + cg * ((yse - yne) - (ysw - ynw)));
-}
-
 __device__ __forceinline__ void g_coefs(const ItemDesc& d, int i, int j, float& ce, float& cw,
                                         float& cs, float& cn, float& cg) {
   float cgi, gj;
   column_coefs(d, i, ce, cw, cgi);
   row_coefs(d, j, cs, cn, gj);
   cg = cgi * gj;
+}
+
+// Shared-memory tiles of the stencil passes: rows ra-1 .. rb of an M-column vector with row
+// stride S = M + 8; column c sits at index c + 4, so columns -1 and M read the zero pads and
+// 16-byte copies land aligned.  Rows outside the grid are zero.
+constexpr int kTilePad = 4;
+__host__ __device__ inline int g_tile_stride(int M) { return M + 2 * kTilePad; }
+
+__device__ __forceinline__ void g_stage(const float* __restrict__ y, float* __restrict__ tile, int M, int ra, int rb) {
+  const int S = g_tile_stride(M);
+  const int rows = rb - ra + 2;   // ra-1 .. rb
+  if ((M & 3) == 0) {
+    const int q = M >> 2;
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < rows * q; idx += kGThreads) {
+      const int r = idx / q, c4 = idx - r * q;
+      const int j = ra - 1 + r;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j >= 0 && j < M) v = __ldcg(reinterpret_cast<const float4*>(y + (size_t)j * M) + c4);
+      *reinterpret_cast<float4*>(tile + r * S + kTilePad + 4 * c4) = v;
+    }
+  } else {
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < rows * M; idx += kGThreads) {
+      const int r = idx / M, c = idx - r * M;
+      const int j = ra - 1 + r;
+      tile[r * S + kTilePad + c] = (j >= 0 && j < M) ? __ldcg(y + (size_t)j * M + c) : 0.f;
+    }
+  }
+}
+
+// A^ y at node (i, j) from a tile whose first row is ra - 1.
+__device__ __forceinline__ float g_tile_matvec(const float* tile, int S, int ra, int i, int j, float id, float ce,
+                                               float cw, float cs, float cn, float cg) {
+  const float* c = tile + (j - ra + 1) * S + kTilePad + i;
+  const float yc = c[0], yw = c[-1], ye = c[1];
+  const float yn = c[-S], ys = c[S], ynw = c[-S - 1], yne = c[-S + 1], ysw = c[S - 1], yse = c[S + 1];
+  return yc - id * (ce * ye + cw * yw + cs * ys + cn * yn + cg * ((yse - yne) - (ysw - ynw)));
+}
+
+// Rows of a band per staged pass: two tiles of R + 2 rows in the dynamic shared memory.
+__host__ __device__ inline int g_tile_rows(int M, int BHg, size_t smem_bytes) {
+  const int fit = (int)(smem_bytes / (2 * sizeof(float) * (size_t)g_tile_stride(M))) - 2;
+  return fit < BHg ? (fit > 0 ? fit : 1) : BHg;
+}
+constexpr size_t kGTileBytes = 200 * 1024;   // dynamic shared memory of the global sweep
+
+// Visits the nodes e = b0 + tid, b0 + tid + kGThreads, ... < b1 as f(e, i, j), stepping (i, j)
+// instead of dividing e by M at every node (a 64-bit division is a long instruction sequence).
+template <class F>
+__device__ __forceinline__ void g_nodes(size_t b0, size_t b1, int M, F f) {
+  const int step_j = kGThreads / M, step_i = kGThreads - step_j * M;
+  size_t e = b0 + threadIdx.x;
+  int j = (int)(e / (size_t)M), i = (int)(e - (size_t)j * M);
+  for (; e < b1; e += kGThreads) {
+    f(e, i, j);
+    i += step_i;
+    j += step_j;
+    if (i >= M) {
+      i -= M;
+      ++j;
+    }
+  }
+}
+
+// One stencil pass over the CTA's rows j0..j1-1: stage y0 (and y1) tile by tile, then run
+// body(e, i, j, ra) for every node of the tile's rows (ra: the tile's first own row).
+template <class Body>
+__device__ __forceinline__ void g_pass(const float* y0, const float* y1, float* t0, float* t1, int M, int j0, int j1,
+                                       int R, Body body) {
+  for (int ra = j0; ra < j1; ra += R) {
+    const int rb = min(j1, ra + R);
+    g_stage(y0, t0, M, ra, rb);
+    if (y1) g_stage(y1, t1, M, ra, rb);
+    __syncthreads();
+    g_nodes((size_t)ra * M, (size_t)rb * M, M, [&](size_t e, int i, int j) { body(e, i, j, ra); });
+    __syncthreads();   // the tiles are restaged next
+  }
 }
 
 __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid_constant__ GSweepParams gp) {
@@ -959,7 +1022,7 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   if (batched) {
     const size_t off = (size_t)blockIdx.y * kGlobalVecs * (size_t)gp.M * gp.M;
     w.u += off; w.x += off; w.xp += off; w.xq += off; w.r += off; w.rh += off;
-    w.p += off; w.v += off; w.s += off; w.t += off; w.id += off;
+    w.p += off; w.v += off; w.s += off; w.t += off; w.id += off; w.q += off;
   }
   const int M = gp.M, C = gp.C;
   const int rank = C > 1 ? (int)cluster.block_rank() : 0;
@@ -975,24 +1038,30 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
   __shared__ double wpart[GCfg::NW * 4];
   __shared__ Scal scs;
   Scal* sc = &scs;
+  extern __shared__ __align__(16) float gtiles[];
+  const int S = g_tile_stride(M);
+  const int R = g_tile_rows(M, BHg, kGTileBytes);
+  float* T0 = gtiles;
+  float* T1 = gtiles + (R + 2) * S;
+  for (int idx = tid; idx < 2 * (R + 2) * S; idx += kGThreads) gtiles[idx] = 0.f;   // pads stay zero
   int round = 0, iters_max = 0, iters_total = 0, nsolves = 0, nhist = 0;
   bool failed = false;
   auto barrier = [&]() { __threadfence(); cluster_barrier(cluster, C); };
 
   const int n_lo = a.n_end > 0 ? a.n_begin : a.n_first;
   const int n_hi = a.n_end > 0 ? a.n_end : (a.mode == SWEEP_PROP ? a.n_first + 1 : a.N);
-  for (size_t e = e0 + tid; e < e1; e += kGThreads) {
-    const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+  g_nodes(e0, e1, M, [&](size_t e, int i, int j) {
     w.id[e] = (i < M - 1 && j < M - 1) ? inv_diag(d, i, j) : 0.f;
     w.x[e] = 0.f;
     w.xp[e] = 0.f;
     w.xq[e] = 0.f;
+    w.q[e] = 0.f;
     const float* src = a.mode == SWEEP_PROP   ? pit.in
                        : a.mode == SWEEP_INIT ? a.U + (size_t)n_lo * MM
                        : n_lo == a.n_first    ? a.Gold + (size_t)a.n_first * MM
                                               : a.U + (size_t)n_lo * MM;
     w.u[e] = src[e];
-  }
+  });
   barrier();
   for (int n = n_lo; n < n_hi; ++n) {
     const bool skip_g = (a.mode == SWEEP_ITER && n == a.n_first);
@@ -1000,15 +1069,14 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
       for (int cstep = 0; cstep < a.csteps; ++cstep) {
         const float tau_new = (float)(pit.tau0 + a.slice_len * n + (cstep + 1) * d.dtau);
         // initial guess 3 d_{m-1} - 3 d_{m-2} + d_{m-3} (see the band kernel); x holds d_{m-1}
-        for (size_t e = e0 + tid; e < e1; e += kGThreads) {
-          const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+        g_nodes(e0, e1, M, [&](size_t e, int i, int j) {
           if (i == M - 1 || j == M - 1) w.u[e] = far_field(pf, i * gp.h, j * gp.h, tau_new);
           const float d1 = w.x[e], d2 = w.xp[e];
           if (nhist >= 3) w.x[e] = 3.f * (d1 - d2) + w.xq[e];
           else if (nhist == 2) w.x[e] = 2.f * d1 - d2;
           w.xq[e] = d2;
           w.xp[e] = d1;
-        }
+        });
         barrier();
         int it = 0;
         // restart from the current iterate after a breakdown (see the band kernel)
@@ -1016,61 +1084,86 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
           if (attempt > 0) barrier();   // the other CTAs' last x updates are visible
           // b^ = D^{-1} dtau R_h w ;  r = b^ - A^ x (x = previous increment)
           float part[2] = {0.f, 0.f};
-          for (size_t e = e0 + tid; e < e1; e += kGThreads) {
-            const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+          g_pass(w.u, w.x, T0, T1, M, j0, j1, R, [&](size_t e, int i, int j, int ra) {
             float bh = 0.f, rr = 0.f;
             if (i < M - 1 && j < M - 1) {
               float ce, cw, cs, cn, cg;
               g_coefs(d, i, j, ce, cw, cs, cn, cg);
-              const float* y = w.u;
-              const float c = ldcg(y + e);
-              const float yw = i > 0 ? ldcg(y + e - 1) : 0.f, ye = ldcg(y + e + 1);
-              const float yn = j > 0 ? ldcg(y + e - M) : 0.f, ys = ldcg(y + e + M);
-              const float ynw = (i > 0 && j > 0) ? ldcg(y + e - M - 1) : 0.f, yne = j > 0 ? ldcg(y + e - M + 1) : 0.f;
-              const float ysw = i > 0 ? ldcg(y + e + M - 1) : 0.f, yse = ldcg(y + e + M + 1);
+              const float* y = T0 + (j - ra + 1) * S + kTilePad + i;
+              const float c = y[0], yw = y[-1], ye = y[1], yn = y[-S], ys = y[S];
+              const float ynw = y[-S - 1], yne = y[-S + 1], ysw = y[S - 1], yse = y[S + 1];
               const float b = ce * (ye - c) - cw * (c - yw) + cs * (ys - c) - cn * (c - yn) +
                               cg * ((yse - yne) - (ysw - ynw)) - rdt * c;
-              bh = b * w.id[e];
-              rr = bh - g_matvec(w.x, w.id, M, i, j, ce, cw, cs, cn, cg);
+              const float id = w.id[e];
+              bh = b * id;
+              rr = bh - g_tile_matvec(T1, S, ra, i, j, id, ce, cw, cs, cn, cg);
             }
             w.r[e] = rr;
             w.rh[e] = rr;
             part[0] = fmaf(bh, bh, part[0]);
             part[1] = fmaf(rr, rr, part[1]);
-          }
+          });
           cluster_sum<GCfg, 2>(cluster, part, slots, wpart, sc, round, rank, C,
                                [tol](Scal* s) { KrylovFin::start(s, tol); });
           for (size_t e = e0 + tid; e < e1; e += kGThreads) w.p[e] = w.r[e];
           barrier();
+          // Right-preconditioned with M^{-1} = 2I - A^ (see the band kernel): v = A^ M^{-1} p,
+          // t = A^ M^{-1} s, x += alpha M^{-1} p + omega M^{-1} s.  Each preconditioner
+          // application reads its operand's neighbours, hence one more barrier before the
+          // product that reads q.
           while (!sc->conv && it < a.maxit) {
             ++it;
+            g_pass(w.p, nullptr, T0, T1, M, j0, j1, R, [&](size_t e, int i, int j, int ra) {
+              float qv = 0.f;
+              if (i < M - 1 && j < M - 1) {
+                float ce, cw, cs, cn, cg;
+                g_coefs(d, i, j, ce, cw, cs, cn, cg);
+                qv = fmaf(2.f, T0[(j - ra + 1) * S + kTilePad + i],
+                          -g_tile_matvec(T0, S, ra, i, j, w.id[e], ce, cw, cs, cn, cg));
+              }
+              w.q[e] = qv;
+            });
+            barrier();
             float p1[2] = {0.f, 0.f};
-            for (size_t e = e0 + tid; e < e1; e += kGThreads) {
-              const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+            g_pass(w.q, nullptr, T0, T1, M, j0, j1, R, [&](size_t e, int i, int j, int ra) {
               float vv = 0.f;
               if (i < M - 1 && j < M - 1) {
                 float ce, cw, cs, cn, cg;
                 g_coefs(d, i, j, ce, cw, cs, cn, cg);
-                vv = g_matvec(w.p, w.id, M, i, j, ce, cw, cs, cn, cg);
+                vv = g_tile_matvec(T0, S, ra, i, j, w.id[e], ce, cw, cs, cn, cg);
               }
               w.v[e] = vv;
               const float rr = w.r[e];
               p1[0] = fmaf(w.rh[e], vv, p1[0]);
               p1[1] = fmaf(rr, rr, p1[1]);
-            }
+            });
+            // every CTA has read its neighbours' q before this reduction's barrier
             cluster_sum<GCfg, 2>(cluster, p1, slots, wpart, sc, round, rank, C, [](Scal* s) { KrylovFin::alpha(s); });
             if (sc->conv || sc->fail) break;
             const float af = sc->af;
-            for (size_t e = e0 + tid; e < e1; e += kGThreads) w.s[e] = fmaf(-af, w.v[e], w.r[e]);
+            for (size_t e = e0 + tid; e < e1; e += kGThreads) {
+              w.x[e] = fmaf(af, w.q[e], w.x[e]);
+              w.s[e] = fmaf(-af, w.v[e], w.r[e]);
+            }
+            barrier();
+            g_pass(w.s, nullptr, T0, T1, M, j0, j1, R, [&](size_t e, int i, int j, int ra) {
+              float qv = 0.f;
+              if (i < M - 1 && j < M - 1) {
+                float ce, cw, cs, cn, cg;
+                g_coefs(d, i, j, ce, cw, cs, cn, cg);
+                qv = fmaf(2.f, T0[(j - ra + 1) * S + kTilePad + i],
+                          -g_tile_matvec(T0, S, ra, i, j, w.id[e], ce, cw, cs, cn, cg));
+              }
+              w.q[e] = qv;
+            });
             barrier();
             float p2[4] = {0.f, 0.f, 0.f, 0.f};
-            for (size_t e = e0 + tid; e < e1; e += kGThreads) {
-              const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+            g_pass(w.q, nullptr, T0, T1, M, j0, j1, R, [&](size_t e, int i, int j, int ra) {
               float tt = 0.f;
               if (i < M - 1 && j < M - 1) {
                 float ce, cw, cs, cn, cg;
                 g_coefs(d, i, j, ce, cw, cs, cn, cg);
-                tt = g_matvec(w.s, w.id, M, i, j, ce, cw, cs, cn, cg);
+                tt = g_tile_matvec(T0, S, ra, i, j, w.id[e], ce, cw, cs, cn, cg);
               }
               w.t[e] = tt;
               const float sv = w.s[e], rh = w.rh[e];
@@ -1078,15 +1171,15 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
               p2[1] = fmaf(tt, tt, p2[1]);
               p2[2] = fmaf(rh, sv, p2[2]);
               p2[3] = fmaf(rh, tt, p2[3]);
-            }
+            });
             cluster_sum<GCfg, 4>(cluster, p2, slots, wpart, sc, round, rank, C, [](Scal* s) { KrylovFin::omega(s); });
             const float of = sc->of, bf = sc->bf;
             for (size_t e = e0 + tid; e < e1; e += kGThreads) {
               const float sv = w.s[e], pv = w.p[e], tt = w.t[e];
-              w.x[e] += af * pv + of * sv;
+              w.x[e] = fmaf(of, w.q[e], w.x[e]);
               const float rr = fmaf(-of, tt, sv);
               w.r[e] = rr;
-              w.p[e] = rr + bf * (pv - of * w.v[e]);
+              w.p[e] = fmaf(bf, fmaf(-of, w.v[e], pv), rr);
             }
             if (sc->fail) break;
             barrier();
@@ -1154,6 +1247,7 @@ static cudaLaunchConfig_t global_launch_config(int C, int nst, cudaStream_t s, c
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C, nst, 1);
   cfg.blockDim = dim3(kGThreads, 1, 1);
+  cfg.dynamicSmemBytes = kGTileBytes;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = C;
@@ -1167,6 +1261,11 @@ static cudaLaunchConfig_t global_launch_config(int C, int nst, cudaStream_t s, c
 // Cluster size of the global-memory sweep: 16 CTAs where the device can hold such a cluster,
 // else 8 (0: neither).
 static int global_cluster_ctas(int) {
+  if (cudaFuncSetAttribute(sweep_global_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGTileBytes) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   for (int C : {16, 8}) {
     if (C > 8 &&
         cudaFuncSetAttribute(sweep_global_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
@@ -1195,12 +1294,15 @@ static int launch_sweep_global(const bs_grid* g, const ItemDesc& d, const SweepA
   gp.d = d;
   gp.a = a;
   float* base = (float*)g->ws_coarse.ptr;
-  gp.w = GlobalVecs{base,          base + MM,     base + 2 * MM, base + 3 * MM, base + 4 * MM, base + 5 * MM,
-                    base + 6 * MM, base + 7 * MM, base + 8 * MM, base + 9 * MM, base + 10 * MM};
+  gp.w = GlobalVecs{base,          base + MM,     base + 2 * MM, base + 3 * MM, base + 4 * MM,  base + 5 * MM,
+                    base + 6 * MM, base + 7 * MM, base + 8 * MM, base + 9 * MM, base + 10 * MM, base + 11 * MM};
   gp.M = M;
   gp.h = (float)(g->xmax / (M - 1));
   const int C = global_cluster_ctas(M);
   if (C == 0) return set_error(BS_ERR_CUDA, "coarse propagator: no cluster shape available for M=%d", M);
+  const int R = g_tile_rows(M, (M + C - 1) / C, kGTileBytes);
+  if ((size_t)2 * (R + 2) * g_tile_stride(M) * sizeof(float) > kGTileBytes)
+    return set_error(BS_ERR_ARG, "coarse propagator: M=%d exceeds the global solver's tile size", M);
   gp.C = C;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = global_launch_config(C, nst, s, attr);
