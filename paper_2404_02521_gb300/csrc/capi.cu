@@ -124,7 +124,7 @@ __global__ void payoff_kernel(PayoffF pf, float* u, int M, float h) {
   const size_t n = (size_t)M * M;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+    const int j = (int)((unsigned)e / (unsigned)M), i = (int)(e - (size_t)j * M);
     u[e] = payoff_value(pf, i * h, j * h);
   }
 }

@@ -319,7 +319,7 @@ __global__ void pino_restrict_kernel(const PinoState* st, float* ump, int Mp) {
   const size_t P = (size_t)Mp * Mp;
   const float ratio = (float)(s.M - 1) / (float)(Mp - 1);
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / Mp), i = (int)(e - (size_t)j * Mp);
+    const int j = (int)((unsigned)e / (unsigned)Mp), i = (int)(e - (size_t)j * Mp);
     ump[(size_t)b * P + e] = (s.M == Mp) ? s.in[e] : bilinear(s.in, s.M, i * ratio, j * ratio);
   }
 }
@@ -332,7 +332,7 @@ __global__ void pino_lift_kernel(const PinoState* st, const float* ump, const fl
   const size_t P = (size_t)Mp * Mp;
   const float hp = s.h * (float)(s.M - 1) / (float)(Mp - 1);   // network grid spacing
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / Mp), i = (int)(e - (size_t)j * Mp);
+    const int j = (int)((unsigned)e / (unsigned)Mp), i = (int)(e - (size_t)j * Mp);
     const float a[9] = {ump[(size_t)b * P + e], i * hp, j * hp, s.tau, s.dtau, s.s1, s.s2, s.rho, s.r};
     __align__(16) bf16 h[32];
     for (int o = 0; o < C; ++o) {
@@ -368,7 +368,7 @@ __global__ void pino_apply_kernel(const PinoState* st, const float* wout, int Mp
   double n0 = 0.0, n1 = 0.0;
   const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (e < MM) {
-    const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+    const int j = (int)((unsigned)e / (unsigned)M), i = (int)(e - (size_t)j * M);
     float g;
     if (aa.mode == PAPPLY_ITER_SKIP) {
       g = aa.Gold[e];

@@ -32,7 +32,7 @@ __global__ void rs_restrict_kernel(const float* __restrict__ u, int M, float* __
   const size_t P = (size_t)Mc * Mc;
   const float ratio = (float)(M - 1) / (float)(Mc - 1);
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / Mc), i = (int)(e - (size_t)j * Mc);
+    const int j = (int)((unsigned)e / (unsigned)Mc), i = (int)(e - (size_t)j * Mc);
     uc[e] = rs_bilinear(u, M, i * ratio, j * ratio);
   }
 }
@@ -56,7 +56,7 @@ __global__ void rs_apply_kernel(const __grid_constant__ RsApply a) {
   double n0 = 0.0, n1 = 0.0;
   const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (e < MM) {
-    const int j = (int)(e / M), i = (int)(e - (size_t)j * M);
+    const int j = (int)((unsigned)e / (unsigned)M), i = (int)(e - (size_t)j * M);
     float g;
     if (a.mode == RS_ITER_SKIP) {
       g = a.Gold[e];
