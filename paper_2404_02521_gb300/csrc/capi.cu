@@ -81,18 +81,17 @@ double jacobi_contraction(int M, const bs_params& p, double dtau) {
 
 Options g_opt;
 
-// Sweeps so that q^m <= target (at least 3: the first sweep forms b, the last applies d, and
-// the far-field update sits between them).
+// Sweeps so that q^m <= target (at least 2: the first sweep forms b, the last applies d).
 int sweeps_for(double q, int start) {
   if (!(q < 0.8)) return 0;
   if (g_opt.fine_sweeps > 0) return g_opt.fine_sweeps;
-  if (q <= 0.0) return 3;
+  if (q <= 0.0) return 2;
   const double target = start == START_COLD          ? g_opt.jacobi_target_cold
                         : start == START_EXTRAP      ? g_opt.jacobi_target_extrap
                         : start == START_EXTRAP_LATE ? g_opt.jacobi_target_extrap_late
                                                      : g_opt.jacobi_target;
   int m = (int)std::ceil(std::log(target) / std::log(q));
-  return m < 3 ? 3 : m;
+  return m < 2 ? 2 : m;
 }
 
 // Band shapes of the cluster-resident kernels (NCOL columns, NT threads, K rows per thread,
@@ -324,8 +323,8 @@ int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_pa
 int bs_set_option(int option, double value) {
   switch (option) {
     case BS_OPT_FINE_SWEEPS:
-      if (!(value == 0.0 || (value >= 3.0 && value <= 256.0)))
-        return set_error(BS_ERR_ARG, "BS_OPT_FINE_SWEEPS must be 0 or in [3, 256]");
+      if (!(value == 0.0 || (value >= 2.0 && value <= 256.0)))
+        return set_error(BS_ERR_ARG, "BS_OPT_FINE_SWEEPS must be 0 or in [2, 256]");
       g_opt.fine_sweeps = (int)value;
       return BS_OK;
     case BS_OPT_JACOBI_TARGET:

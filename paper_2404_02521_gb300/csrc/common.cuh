@@ -198,7 +198,7 @@ struct Options {
   double jacobi_target = 1.0 / 1024.0;            // warm-started steps: q^m <= 2^-10
   double jacobi_target_cold = 1.0 / 4194304.0;    // first step of a launch: q^m <= 2^-22
   double jacobi_target_extrap = 1.0 / 64.0;       // extrapolated starts: q^m <= 2^-6
-  double jacobi_target_extrap_late = 1.0 / 16.0;  // ... from step extrap_late on: 2^-4
+  double jacobi_target_extrap_late = 0.15;        // ... from step extrap_late on
   int extrap_start = 2;                           // first extrapolated step of a launch
   int extrap_late = 16;                           // first step with the late target
   int pipeline = 1;                               // parareal_solve overlaps F with the sweep

@@ -91,9 +91,10 @@ __device__ __forceinline__ float next_guess(float v, float* dp, int e, bool extr
 // the rows just outside the strip (other row groups or the halo copies of the neighbouring
 // CTAs) and are updated after it, so the barrier latency overlaps the interior work.
 // The thread's own column of the old increment is in dv[].  FIRST also evaluates
-// b = dtau R_h w from hi; LAST also applies the increment to (hi, lo) and leaves the next
-// step's initial guess (next_guess) in wr and dv[].  Nodes that are not PDE rows have
-// invd = 0 and write a zero increment.
+// b = dtau R_h w from hi; LAST also applies the increment to (hi, lo) of the PDE nodes and
+// leaves the next step's initial guess (next_guess) in wr and dv[].  Nodes that are not PDE
+// rows have invd = 0 and write a zero increment; LAST leaves their hi (Dirichlet data) to the
+// far-field update, which may follow it directly.
 template <class CFG, bool FIRST, bool LAST>
 __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* __restrict__ wr,
                                            float* hi, const HaloPush& wr_push,
@@ -141,7 +142,7 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
     dv[k] = g;
     nW = cW; nE = cE;
     cW = sW; cE = sE;
-    if (LAST) hi[p * NCOL + col] = two_sum_update(hi[p * NCOL + col], v, lo[k]);
+    if (LAST && invd[k] != 0.f) hi[p * NCOL + col] = two_sum_update(hi[p * NCOL + col], v, lo[k]);
   }
   if (clustered) cl_wait();
   {  // last strip row: north = old row K-2 (window), south = plane row p0+K
@@ -158,7 +159,7 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
     const float g = LAST ? next_guess(v, dp, (r0 + k) * NCOL + col, extrap) : v;
     band_store<CFG>(wr, wr_push, p - 1, col, g);
     dv[k] = g;
-    if (LAST) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[k]));
+    if (LAST && invd[k] != 0.f) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[k]));
   }
   {  // first strip row: north = plane row p0-1, south = old row 1
     const int p = p0;
@@ -175,7 +176,7 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
     const float g = LAST ? next_guess(v, dp, r0 * NCOL + col, extrap) : v;
     band_store<CFG>(wr, wr_push, p - 1, col, g);
     dv[0] = g;
-    if (LAST) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[0]));
+    if (LAST && invd[0] != 0.f) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[0]));
   }
 }
 
@@ -256,8 +257,9 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
       else
         fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir,
                                       r0, ce, cw, cgi, rdt, clustered);
-      // After the first sweep has read hi, move the far-field data to the next step (the
-      // last sweep, at least one barrier later, leaves those nodes unchanged).
+      // After the first sweep has read hi (every CTA has: the second sweep waited on the
+      // cluster barrier), move the far-field data to the next step; the last sweep -- this
+      // one when a step has two sweeps -- writes only PDE nodes.
       if (s == 1 && step + 1 < fb.nsteps)
         band_far_field<CFG>(hi, hi_push, pf, (float)(d.tau0 + (step + 2) * d.dtau), h, M, jbase, tid);
       par ^= 1;
