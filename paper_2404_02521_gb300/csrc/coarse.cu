@@ -33,11 +33,18 @@ namespace bsp {
 
 constexpr int kKrylovAttempts = 3;   // BiCGSTAB starts per implicit step (restarts on breakdown)
 
+constexpr int kMaxBandRows = 256;   // rows of the largest band-variant grid, padding included
+
 struct SweepParams {
   ItemDesc d;       // dtau = coarse step
   SweepArgs a;
   BandShape sh;
   float h;
+  // Row coefficients {cs, cn, (float)j, 0} of every band row, in the launch's constant
+  // parameter space: the rows of a strip are the same for a whole warp (for a whole CTA in
+  // one-group variants), so the stencil reads them as uniform constant loads rather than
+  // shared-memory loads.  Owner and neighbour read the same values (halo rows included).
+  float4 rowc[kMaxBandRows];
 };
 
 // BiCGSTAB scalar state shared by a CTA (identical in every CTA of the cluster).  The
@@ -364,7 +371,7 @@ struct SweepSmem {
   static constexpr size_t TAIL_BYTES = 2 * kMaxCluster * 4 * 8 + NW * 4 * 8 + 16 + sizeof(Scal);
   static constexpr size_t floats(int dh, bool q, bool quad) {
     return PLANE + 2 * (size_t)(BH + 2 * dh) * NCOL + (q ? PLANE : 0) + (3 + (quad ? 1 : 0)) * (size_t)BH * NCOL +
-           6 * (size_t)dh * NCOL + 2 * kMaxCluster * 4 + NW * 4 + 4 * BH;
+           6 * (size_t)dh * NCOL + 2 * kMaxCluster * 4 + NW * 4;
   }
   static constexpr bool fits(size_t f) { return f * 4 + TAIL_BYTES <= 227 * 1024; }
   static constexpr bool POLY = fits(floats(2, true, false));
@@ -379,8 +386,7 @@ struct SweepSmem {
   static constexpr size_t TH = VH + 4 * DH * NCOL;   // [top DH, bottom DH rows][NCOL] t halo rows
   static constexpr size_t KSLOT = TH + 2 * DH * NCOL;   // [2][kMaxCluster][4] exchange partials
   static constexpr size_t KWP = KSLOT + 2 * kMaxCluster * 4;   // [NW][4]
-  static constexpr size_t ROWC = KWP + NW * 4;   // float4 [BH]: cs, cn, (float)j, 0
-  static constexpr size_t FLOATS = ROWC + 4 * BH;
+  static constexpr size_t FLOATS = KWP + NW * 4;
   // doubles after the floats: slots [2][kMaxCluster][4], wpart [NW][4]; then mbarriers, Scal
   static constexpr size_t SLOTS_B = FLOATS * 4, WPART_B = SLOTS_B + 2 * kMaxCluster * 4 * 8;
   static constexpr size_t MB_B = WPART_B + NW * 4 * 8, SCAL_B = MB_B + 16;
@@ -417,8 +423,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   const int M = sp.sh.M, C = sp.sh.C;
   const int rank = C > 1 ? (int)cluster.block_rank() : 0;
   const int tid = threadIdx.x;
-  const int col = tid % NCOL, grp = tid / NCOL;
-  const int r0 = grp * K;
+  const int col = tid % NCOL, grp = G == 1 ? 0 : tid / NCOL;
+  const int r0 = grp * K;   // a compile-time 0 in one-group variants: uniform row indices
   const int jbase = rank * BH;
   const size_t MM = (size_t)M * M;
   const float h = sp.h;
@@ -438,7 +444,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   float* XQ = fs + L::XQ;    // the one before that  [BH*NCOL] (L::QUAD)
   float* VH = fs + L::VH;
   float* TH = fs + L::TH;
-  float4* rowc = reinterpret_cast<float4*>(fs + L::ROWC);
+  const float4* rowc = sp.rowc + jbase;   // own band rows (index r0 + k)
   double* slots = reinterpret_cast<double*>(smem_raw + L::SLOTS_B);
   double* wpart = reinterpret_cast<double*>(smem_raw + L::WPART_B);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::MB_B);
@@ -464,11 +470,6 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   if (L::POLY)
     for (int e = tid; e < CFG::PLANE; e += CFG::NT) Q[e] = 0.f;
   for (int e = tid; e < 6 * DH * NCOL; e += CFG::NT) VH[e] = 0.f;   // VH and TH
-  for (int r = tid; r < BH; r += CFG::NT) {
-    float cs, cn, gj;
-    row_coefs(d, jbase + r, cs, cn, gj);
-    rowc[r] = make_float4(cs, cn, gj, 0.f);   // gj = (float)j exactly
-  }
   if (tid == 0) {
     mbar_init(mbar, 1);
     mbar_init(mbar + 1, 1);
@@ -492,11 +493,11 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   if (L::POLY) {
     const int jt = jbase - 1, jb = jbase + BH;
     if (grp == 0 && has_up) {
-      row_coefs(d, jt, rc_top.x, rc_top.y, rc_top.z);
+      rc_top = sp.rowc[jt];
       id_top = (jt < M - 1 && col < M - 1) ? inv_diag(d, col, jt) : 0.f;
     }
     if (grp == G - 1 && has_down) {
-      row_coefs(d, jb, rc_bot.x, rc_bot.y, rc_bot.z);
+      rc_bot = sp.rowc[jb];
       id_bot = (jb < M - 1 && col < M - 1) ? inv_diag(d, col, jb) : 0.f;
     }
   }
@@ -866,6 +867,16 @@ static size_t smem_optin_bytes() {
     return 0;
   }
   return (size_t)v;
+}
+
+// {cs, cn, (float)j, 0} of rows 0..kMaxBandRows-1 from the item's host-rounded constants, in
+// double and rounded once (the same on every host).
+static void fill_row_coefs(SweepParams& sp) {
+  const double ay = sp.d.ay, my = sp.d.my;
+  for (int j = 0; j < kMaxBandRows; ++j) {
+    const double b = ay * ((double)j * j), n = my * j;
+    sp.rowc[j] = make_float4((float)(b + n), (float)(b - n), (float)j, 0.f);
+  }
 }
 
 template <class CFG>
@@ -1351,6 +1362,7 @@ static bool variant_fits(int v, int M) {
 
 static int launch_variant(int v, SweepParams sp, cudaStream_t s) {
   sp.sh = variant_shape(v, sp.sh.M);
+  fill_row_coefs(sp);
   switch (v) {
     case 0: return launch_sweep_k<BandCfg<32, 256, 4>>(sp, s);
     case 1: return launch_sweep_k<BandCfg<32, 128, 2>>(sp, s);
