@@ -40,7 +40,7 @@ enum {
   BS_ERR_ARG = -1,      /* invalid argument (NULL pointer, size, unsupported combination) */
   BS_ERR_CUDA = -2,     /* a CUDA runtime call failed; message has the CUDA error string */
   BS_ERR_NOCONV = -3,   /* an inner Krylov solve hit its iteration cap */
-  BS_ERR_MAXITER = -4,  /* Parareal reached Kmax without meeting tol (results still valid) */
+  BS_ERR_MAXITER = -4,  /* Parareal reached Kmax < N without meeting tol (results still valid) */
   BS_ERR_OOM = -5,      /* device allocation failed */
   BS_ERR_FILE = -6      /* weight file missing, truncated or malformed */
 };
@@ -137,8 +137,9 @@ int pino_destroy(bs_pino* net);
  *  k_done       host int: iterations performed
  *  defect_hist  host double[Kmax] (may be NULL): delta_k per iteration
  * Synchronous (returns after the stream has drained).
- * Returns BS_OK on convergence, BS_ERR_MAXITER if tol was not met within Kmax (u_out then
- * holds the last iterate), BS_ERR_NOCONV if a coarse Krylov solve failed. */
+ * Returns BS_OK on convergence (delta_k <= tol, or k_done = N: after N iterations every slice
+ * is serial fine stepping exactly), BS_ERR_MAXITER if tol was not met within Kmax < N (u_out
+ * then holds the last iterate), BS_ERR_NOCONV if a coarse Krylov solve failed. */
 int parareal_solve(const bs_grid* g, const bs_params* p, int N, int fine_steps,
                    int coarse_kind, int coarse_steps, const bs_pino* net, double tol,
                    int Kmax, float* u_out, int* k_done, double* defect_hist,

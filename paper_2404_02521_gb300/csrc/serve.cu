@@ -331,7 +331,7 @@ static int progress(bs_server* sv) {
         sl.result = BS_ERR_CUDA;
       } else if (st) {
         sl.result = BS_ERR_NOCONV;
-      } else if (sl.defect <= sl.r.tol) {
+      } else if (sl.defect <= sl.r.tol || sl.k >= sl.r.N) {   // k = N: every slice is exact
         sl.result = BS_OK;
       } else if (sl.k >= sl.r.Kmax) {
         sl.result = BS_ERR_MAXITER;

@@ -250,3 +250,6 @@ def test_maxiter_status(bs):
     pb = cfg_small(wl.BASKET, M=40, N=6, fine=24, coarse=1)
     rc, k, defects, _ = gpu_parareal(bs, pb, 1e-14, 2)
     assert rc == -4 and k == 2 and len(defects) == 2
+    # K = N: every slice is exact, so the solve has converged whatever the last defect
+    rc, k, defects, _ = gpu_parareal(bs, pb, 1e-14, pb.N)
+    assert rc == 0 and k == pb.N and len(defects) == pb.N
