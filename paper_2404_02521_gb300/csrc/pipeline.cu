@@ -87,7 +87,8 @@ bool pipeline_eligible(int N) { return N >= 8; }
 // clusters the device holds at once, less those the coarse cluster displaces (its CTAs over
 // the fine cluster's, rounded up: both take whole SMs of one GPC).  A chunk that spills into a
 // second wave, or an F wave that leaves no GPC for the sweep's cluster, stalls the sweep --
-// on the 256 x 256 workload chunks of 16 slices took 65 ms per solve, chunks of 12 took 47.
+// on the 256 x 256 workload chunks of 16 slices took 60 ms per solve, of 12 slices 48, and the
+// 13 of this rule 44.
 // At most a quarter of the slices, so that F starts early and the sweep drains soon.
 int pipeline_chunk(bs_grid* g, const ItemDesc& dc, int N, cudaStream_t s, int* S) {
   int quarter = (N + 3) / 4;
