@@ -78,28 +78,6 @@ __device__ __forceinline__ float scaled_node(float nW, float nC, float nE, float
   return fmaf(-id, acc, cC);
 }
 
-// A^ y on the thread's column strip (K rows; y has one halo row above the strip's band);
-// zero on non-interior nodes (invd = 0 and y = 0 there).
-template <class CFG>
-__device__ __forceinline__ void scaled_matvec(const float* __restrict__ y,
-                                              const float4* __restrict__ rowc,
-                                              const float* __restrict__ ID, int col, int il,
-                                              int ir, int r0, float ce, float cw,
-                                              float cgi, float (&out)[CFG::K]) {
-  constexpr int NCOL = CFG::NCOL, K = CFG::K;
-  const int p0 = r0 + 1;
-  float nW = y[(p0 - 1) * NCOL + il], nC = y[(p0 - 1) * NCOL + col], nE = y[(p0 - 1) * NCOL + ir];
-  float cW = y[p0 * NCOL + il], cC = y[p0 * NCOL + col], cE = y[p0 * NCOL + ir];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int p = p0 + k;
-    const float sW = y[(p + 1) * NCOL + il], sC = y[(p + 1) * NCOL + col], sE = y[(p + 1) * NCOL + ir];
-    out[k] = scaled_node(nW, nC, nE, cW, cC, cE, sW, sC, sE, rowc[p - 1], ID[(p - 1) * NCOL + col], ce, cw, cgi);
-    nW = cW; nC = cC; nE = cE;
-    cW = sW; cC = sC; cE = sE;
-  }
-}
-
 // A^ y at one row; yrow points at the row's first column, the rows above and below are
 // yrow -+ ncol.
 __device__ __forceinline__ float scaled_row(const float* yrow, int ncol, int col, int il, int ir, float4 rc,
@@ -334,6 +312,12 @@ __device__ __forceinline__ void xround(Xchg& xs, const float (&v)[NV], float (&t
   ++xs.round;
 }
 
+// v with its sign flipped where bit k of `bits` is set: the product with the shadow residual
+// r^ = sign(r_0) of row k.
+__device__ __forceinline__ float signed_by(float v, uint32_t bits, int k) {
+  return __int_as_float(__float_as_int(v) ^ (int)((bits >> k) << 31));
+}
+
 // Q = M^{-1} y = 2 y - A^ y on the strip's own rows and, for the edge groups, on the halo row
 // next to the band (y has DH = 2 halo rows, its own values also in yc; Q has one halo row).
 // The own rows of Q are also returned in q.  Outside the domain Q stays zero.
@@ -370,7 +354,7 @@ struct SweepSmem {
   static constexpr int NCOL = CFG::NCOL, BH = CFG::BH, PLANE = CFG::PLANE, NW = CFG::NW;
   static constexpr size_t TAIL_BYTES = 2 * kMaxCluster * 4 * 8 + NW * 4 * 8 + 16 + sizeof(Scal);
   static constexpr size_t floats(int dh, bool q, bool quad) {
-    return PLANE + 2 * (size_t)(BH + 2 * dh) * NCOL + (q ? PLANE : 0) + (3 + (quad ? 1 : 0)) * (size_t)BH * NCOL +
+    return PLANE + 2 * (size_t)(BH + 2 * dh) * NCOL + (q ? PLANE : 0) + (2 + (quad ? 1 : 0)) * (size_t)BH * NCOL +
            6 * (size_t)dh * NCOL + 2 * kMaxCluster * 4 + NW * 4;
   }
   static constexpr bool fits(size_t f) { return f * 4 + TAIL_BYTES <= 227 * 1024; }
@@ -380,7 +364,7 @@ struct SweepSmem {
   static constexpr int DPLANE = (BH + 2 * DH) * NCOL;
   static constexpr size_t u = 0, P = u + PLANE, S = P + DPLANE;         // u: one halo row; p, s: DH
   static constexpr size_t Q = S + DPLANE;        // preconditioned direction, one halo row (POLY only)
-  static constexpr size_t RH = Q + (POLY ? PLANE : 0), ID = RH + BH * NCOL, XP = ID + BH * NCOL;   // own rows
+  static constexpr size_t ID = Q + (POLY ? PLANE : 0), XP = ID + BH * NCOL;   // own rows
   static constexpr size_t XQ = XP + BH * NCOL;   // d_{m-3}, own rows (QUAD only)
   static constexpr size_t VH = XQ + (QUAD ? BH * NCOL : 0);   // [2 parity][top DH, bottom DH rows][NCOL] v halo
   static constexpr size_t TH = VH + 4 * DH * NCOL;   // [top DH, bottom DH rows][NCOL] t halo rows
@@ -438,7 +422,6 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   float* Q = fs + L::Q;      // M^{-1} p, M^{-1} s   [PLANE] (L::POLY)
   const float* P1 = P + (DH - 1) * NCOL;   // p and s seen with one halo row
   const float* S1 = S + (DH - 1) * NCOL;
-  float* RH = fs + L::RH;    // shadow residual r^   [BH*NCOL]
   float* ID = fs + L::ID;    // inverse diagonal     [BH*NCOL]
   float* XP = fs + L::XP;    // increment before xw  [BH*NCOL]
   float* XQ = fs + L::XQ;    // the one before that  [BH*NCOL] (L::QUAD)
@@ -452,6 +435,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
 
   const HaloPush pu = halo_push<CFG>(cluster, u, rank, C);
   const HaloPush pP = deep_push<CFG, DH>(cluster, P, rank, C);
+  const HaloPush pS = deep_push<CFG, DH>(cluster, S, rank, C);
+  static_assert(K <= 32, "one sign bit per strip row");
   const bool has_up = rank > 0, has_down = rank < C - 1;
   // receivers of this thread's halo stores (v and t rows): group 0 sends band rows 0..DH-1 to
   // the bottom halo of rank-1, group G-1 sends band rows BH-DH..BH-1 to the top halo of rank+1
@@ -462,7 +447,6 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
     const int r = e / NCOL, c = e % NCOL;
     const int j = jbase + r;
     ID[e] = (j < M - 1 && c < M - 1) ? inv_diag(d, c, j) : 0.f;
-    RH[e] = 0.f;
   }
   for (int e = tid; e < L::DPLANE; e += CFG::NT) {
     P[e] = 0.f; S[e] = 0.f;
@@ -570,8 +554,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         for (int attempt = 0; attempt < kKrylovAttempts; ++attempt) {
           // a restart rewrites the neighbours' P halo rows: they must have left the iteration
           if (attempt > 0) cluster_barrier(cluster, C);
-          // b^ = D^{-1} dtau R_h w;  x = initial guess;  r = r^ = p = b^ - A^ x
-          float part[2] = {0.f, 0.f};
+          // b^ = D^{-1} dtau R_h w;  x = initial guess;  r = p = b^ - A^ x;  r^ = sign(r)
+          float bb_part = 0.f, rabs_part = 0.f;
           {
             const int p0 = r0 + 1;
             float nW = u[(p0 - 1) * NCOL + il], nC = u[(p0 - 1) * NCOL + col], nE = u[(p0 - 1) * NCOL + ir];
@@ -587,34 +571,35 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
                                cg * ((sE - nE) - (sW - nW)) - rdt * cC;
               const float bh = bb * ID[(p - 1) * NCOL + col];
               x[k] = xw[k]; rr[k] = bh; vv[k] = 0.f; tt[k] = 0.f;
-              part[0] = fmaf(bh, bh, part[0]);
+              bb_part = fmaf(bh, bh, bb_part);
               nW = cW; nC = cC; nE = cE;
               cW = sW; cC = sC; cE = sE;
             }
           }
+          // x goes through the s plane (free until the first iteration writes s), so that p can
+          // take r right after the product without a reduction in between
 #pragma unroll
-          for (int k = 0; k < K; ++k) deep_store<CFG, DH>(P, pP, r0 + k, col, x[k]);
+          for (int k = 0; k < K; ++k) deep_store<CFG, DH>(S, pS, r0 + k, col, x[k]);
           cluster_barrier(cluster, C);
-          scaled_matvec<CFG>(P1, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+          scaled_matvec_rc<CFG>(S1, x, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+          // The shadow residual r^ = sign(r_0) (+1 where r_0 = 0): its dot products need no
+          // loads, only the thread's K sign bits, and (r^, r_0) = sum |r_0| > 0.  On the CPU
+          // model of the workload it takes the iterations of r^ = r_0.
+          uint32_t rsign = 0;
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             rr[k] -= vv[k];
-            part[1] = fmaf(rr[k], rr[k], part[1]);
-          }
-          // every CTA has finished reading P before the barrier inside the reduction below;
-          // P is rewritten only after it
-          cluster_sum<CFG, 2>(cluster, part, slots, wpart, sc, round, rank, C,
-                              [tol](Scal* s) { KrylovFin::start(s, tol); });
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
+            rsign |= (rr[k] < 0.f ? 1u : 0u) << k;
+            rabs_part += fabsf(rr[k]);
             deep_store<CFG, DH>(P, pP, r0 + k, col, rr[k]);
-            RH[(r0 + k) * NCOL + col] = rr[k];
             pk[k] = rr[k];
           }
           cluster_barrier(cluster, C);
-          float rho = sc->rho;
-          const float stop2 = sc->stop2;
-          conv = sc->conv != 0;
+          // rho = (r^, r_0), the stopping threshold and the start test arrive with the first
+          // exchange round (the first iteration's)
+          float rho = 0.f, stop2 = 0.f;
+          bool first = true;
+          conv = false;
           bool fail = false;
           // r on the halo rows (kept by the threads that own those columns of the edge groups;
           // the P halo rows hold r here)
@@ -664,11 +649,28 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             float p1[2] = {0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              p1[0] = fmaf(RH[(r0 + k) * NCOL + col], vv[k], p1[0]);
+              p1[0] += signed_by(vv[k], rsign, k);
               p1[1] = fmaf(rr[k], rr[k], p1[1]);
             }
-            float ta[2];
-            xround<CFG, 2>(xs, p1, ta, rank, C, halo_bytes);
+            float ta[4];
+            if (first) {
+              // the first round also carries (b^, b^) and (r^, r_0)
+              const float p1x[4] = {p1[0], p1[1], bb_part, rabs_part};
+              xround<CFG, 4>(xs, p1x, ta, rank, C, halo_bytes);
+              first = false;
+              stop2 = tol * tol * ta[2];
+              rho = ta[3];
+              if (!xs.dead && (ta[1] <= stop2 || !(ta[2] > 1e-30f))) {   // the guess already solves it
+                --it;
+                conv = true;
+                break;
+              }
+            } else {
+              float t2[2];
+              xround<CFG, 2>(xs, p1, t2, rank, C, halo_bytes);
+              ta[0] = t2[0];
+              ta[1] = t2[1];
+            }
             if (xs.dead) { conv = true; break; }
             if (ta[1] <= stop2) { conv = true; break; }
             if (ta[0] == 0.f) { fail = true; break; }
@@ -713,11 +715,10 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             float p2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-              const float rh = RH[(r0 + k) * NCOL + col];
               p2[0] = fmaf(tt[k], rr[k], p2[0]);
               p2[1] = fmaf(tt[k], tt[k], p2[1]);
-              p2[2] = fmaf(rh, rr[k], p2[2]);
-              p2[3] = fmaf(rh, tt[k], p2[3]);
+              p2[2] += signed_by(rr[k], rsign, k);
+              p2[3] += signed_by(tt[k], rsign, k);
             }
             float tb[4];
             xround<CFG, 4>(xs, p2, tb, rank, C, halo_bytes);
