@@ -90,17 +90,20 @@ int bs_payoff(const bs_grid* g, const bs_params* p, float* u, bs_stream stream);
  * eq. (fd), the PDE row itself on x = 0 and y = 0 (its coefficients vanish there), and
  * far-field Dirichlet data g(x, y, tau^{m+1}) on x = xmax and y = xmax (exchange: Margrabe;
  * basket: max(w1 x + w2 y - K e^{-r tau}, 0); one-asset: Black-Scholes call; cash-or-nothing:
- * eq. solution).  Each implicit system is solved in FP32 by weighted-Jacobi sweeps whose
- * count follows from the Gershgorin contraction of the system; the state is carried as a
+ * eq. solution).  Each implicit system is solved in FP32 by Jacobi sweeps whose count
+ * follows from the Gershgorin contraction q of the system (q < 0.8), or, for items with
+ * q >= 0.8, by BiCGSTAB per step to BS_OPT_FINE_KRYLOV_TOL; the state is carried as a
  * compensated (hi, lo) float pair across steps and rounded to float on output.
  *
  *  p[B], tau0[B], dtau[B]  host arrays (per-item parameters)
  *  u_in[B], u_out[B]       host arrays of device pointers to float[M*M]; u_out[b] may
  *                          equal u_in[b] (in place)
  *  nsteps >= 0, 1 <= B
- * Results for an item do not depend on B or on the other items.  Asynchronous.
- * Errors: BS_ERR_ARG (NULL, B < 1, dtau <= 0, contraction >= 0.8 -- Jacobi does not
- * apply), BS_ERR_CUDA. */
+ * Results for an item do not depend on B or on the other items.  Asynchronous: only
+ * enqueues kernels, so after one call with the same grid and batch it can be captured into
+ * a CUDA graph.
+ * Errors: BS_ERR_ARG (NULL, B < 1, dtau <= 0), BS_ERR_CUDA.  A BiCGSTAB step that hits its
+ * iteration cap is reported by the next synchronous call on this grid as BS_ERR_NOCONV. */
 int fine_propagate_batched(const bs_grid* g, const bs_params* p,
                            const float* const* u_in, float* const* u_out,
                            const double* tau0, const double* dtau, int nsteps, int B,
@@ -113,7 +116,9 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p,
  *    single precision, Sec. 4.1).  net must be NULL.
  *  kind = BS_COARSE_PINO: one evaluation of the PINO (Sec. 3.4-3.5) mapping u(tau0) and
  *    the interval (tau0, tau0 + dtau_slice) to u(tau0 + dtau_slice); nsteps is ignored.
- * u_in, u_out: device float[M*M] (may alias).  Asynchronous.
+ * u_in, u_out: device float[M*M] (may alias).  Asynchronous: only enqueues kernels, so
+ * after one call on this grid (which picks the band variant) it can be captured into a CUDA
+ * graph.
  * Errors: BS_ERR_ARG, BS_ERR_CUDA.  A Krylov solve that hits its iteration cap is reported
  * by the next synchronous call on this grid as BS_ERR_NOCONV. */
 int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_params* p,
