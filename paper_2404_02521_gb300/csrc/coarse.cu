@@ -785,7 +785,10 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
         }
       }
     } else if (a.mode == SWEEP_INIT) {
-      double nr[1] = {0.0};
+      // The norms: each thread adds its K nodes in FP32, the sum over threads and CTAs is
+      // FP64 (FP64 runs at a small fraction of the FP32 rate on this part; per-node FP64
+      // arithmetic took a few microseconds per slice on the 16 SMs of the cluster).
+      float nf = 0.f;
       if (col < M) {
         float* Un = a.U + (size_t)(n + 1) * MM;
         float* Gn = a.Gold + (size_t)n * MM;
@@ -796,18 +799,20 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             const float g = u[(r0 + k + 1) * NCOL + col];
             Un[(size_t)j * M + col] = g;
             Gn[(size_t)j * M + col] = g;
-            nr[0] = fma((double)g, (double)g, nr[0]);
+            nf = fmaf(g, g, nf);
           }
         }
       }
+      double nr[1] = {(double)nf};
       double* norms = a.norms;
       const int slot_n = n + 1;
       cluster_sum<CFG, 1>(cluster, nr, slots, wpart, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
         if (rank == 0) { norms[2 * slot_n] = s->tot[0]; norms[2 * slot_n + 1] = 0.0; }
       });
     } else {
-      // correction u_{n+1} = F_n + (G_new - G_old_n) and defect partials
-      double nr[2] = {0.0, 0.0};
+      // correction u_{n+1} = F_n + (G_new - G_old_n) and defect partials (per thread in FP32:
+      // u_new - u_old of nearby values is exact, Sterbenz; over threads and CTAs in FP64)
+      float nf[2] = {0.f, 0.f};
       float* Un = a.U + (size_t)(n + 1) * MM;
       const float* Fn = a.Fb + (size_t)n * MM;
       float* Gn = a.Gold + (size_t)n * MM;
@@ -822,11 +827,12 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
           Un[gi] = unew;
           Gn[gi] = gnew;
           band_store<CFG>(u, pu, r0 + k, col, unew);
-          const double du = (double)unew - (double)uold;
-          nr[0] = fma((double)unew, (double)unew, nr[0]);
-          nr[1] = fma(du, du, nr[1]);
+          const float du = unew - uold;
+          nf[0] = fmaf(unew, unew, nf[0]);
+          nf[1] = fmaf(du, du, nf[1]);
         }
       }
+      double nr[2] = {(double)nf[0], (double)nf[1]};
       double* norms = a.norms;
       const int slot_n = n + 1;
       cluster_sum<CFG, 2>(cluster, nr, slots, wpart, sc, round, rank, C, [norms, slot_n, rank](Scal* s) {
@@ -1216,18 +1222,19 @@ __global__ void __launch_bounds__(kGThreads, 1) sweep_global_kernel(const __grid
       float* Gn = a.Gold + (size_t)n * MM;
       for (size_t e = e0 + tid; e < e1; e += kGThreads) {
         const float gnew = w.u[e];
+        // squares in FP32 (u_new - u_old of nearby values is exact), sums in FP64
         if (a.mode == SWEEP_INIT) {
           Un[e] = gnew;
           Gn[e] = gnew;
-          nr[0] = fma((double)gnew, (double)gnew, nr[0]);
+          nr[0] += (double)(gnew * gnew);
         } else {
           const float unew = Fn[e] + (gnew - Gn[e]);
-          const double du = (double)unew - (double)Un[e];
+          const float du = unew - Un[e];
           Un[e] = unew;
           Gn[e] = gnew;
           w.u[e] = unew;
-          nr[0] = fma((double)unew, (double)unew, nr[0]);
-          nr[1] = fma(du, du, nr[1]);
+          nr[0] += (double)(unew * unew);
+          nr[1] += (double)(du * du);
         }
       }
       double* norms = a.norms;

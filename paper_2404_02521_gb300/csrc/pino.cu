@@ -383,14 +383,15 @@ __global__ void pino_apply_kernel(const PinoState* st, const float* wout, int Mp
     } else if (aa.mode == PAPPLY_INIT) {
       aa.Unext[e] = g;
       aa.Gold[e] = g;
-      n0 = (double)g * (double)g;
+      n0 = (double)(g * g);
     } else {
+      // squares in FP32 (u_new - u_old of nearby values is exact), sums in FP64
       const float unew = aa.Fn[e] + (g - aa.Gold[e]);
-      const double du = (double)unew - (double)aa.Unext[e];
+      const float du = unew - aa.Unext[e];
       aa.Unext[e] = unew;
       aa.Gold[e] = g;
-      n0 = (double)unew * (double)unew;
-      n1 = du * du;
+      n0 = (double)(unew * unew);
+      n1 = (double)(du * du);
     }
   }
   if (aa.mode == PAPPLY_PROP) return;

@@ -70,14 +70,15 @@ __global__ void rs_apply_kernel(const __grid_constant__ RsApply a) {
     } else if (a.mode == RS_INIT) {
       a.Unext[e] = g;
       a.Gold[e] = g;
-      n0 = (double)g * (double)g;
+      n0 = (double)(g * g);
     } else {
+      // squares in FP32 (u_new - u_old of nearby values is exact), sums in FP64
       const float unew = a.Fn[e] + (g - a.Gold[e]);
-      const double du = (double)unew - (double)a.Unext[e];
+      const float du = unew - a.Unext[e];
       a.Unext[e] = unew;
       a.Gold[e] = g;
-      n0 = (double)unew * (double)unew;
-      n1 = du * du;
+      n0 = (double)(unew * unew);
+      n1 = (double)(du * du);
     }
   }
   if (a.mode == RS_PROP) return;

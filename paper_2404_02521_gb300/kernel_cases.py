@@ -17,6 +17,8 @@ workloads, one kernel each:
              numerical G with 4 steps per slice on a 256x256 grid (bilinear resampling);
              prints Parareal time to tolerance, iterations and serial fine stepping time
   pino128    the PINO coarse propagator on 64 states of 128x128 (random weights)
+  resample1024  Parareal to K = N = 4 on 1024x1024 basket states with numerical G on the 256x256
+             grid (bilinear restriction and prolongation kernels, 64 fine steps per slice)
 """
 from __future__ import annotations
 
@@ -163,9 +165,25 @@ def case_large1024(bs, wl, torch):
     return run
 
 
+def case_resample1024(bs, wl, torch):
+    # the large solve's coarse model at reduced length: 1024^2 basket states, numerical G on
+    # the 256^2 grid (restriction, coarse solve, prolongation with the correction and the
+    # defect norms), N = 4 slices of 64 fine steps at the large solve's fine step size
+    import dataclasses
+    base = wl.large_cfg4()
+    T = 4 * 64 * base.dtau_fine
+    p = dataclasses.replace(base.params, T=T)
+    M, N = base.M, 4
+    g = bs.Grid(M, base.xmax)
+    g.set_coarse(256)
+    U = torch.empty((N + 1, M, M), device="cuda")
+    return lambda: bs.parareal_solve(g, p, N, 64, bs.COARSE_NUM, base.coarse_steps, None, 0.0, N, U)
+
+
 CASES = {"fine256": case_fine256, "coarse256": case_coarse256, "solve256": case_solve256,
          "tile1024": case_tile1024,
-         "coarse512": case_coarse512, "pino128": case_pino128, "large1024": case_large1024}
+         "coarse512": case_coarse512, "pino128": case_pino128, "large1024": case_large1024,
+         "resample1024": case_resample1024}
 
 
 def main():
