@@ -49,13 +49,18 @@ struct RsApply {
   double* partials;     // Parareal: [blocks][2] sums of u^2 and du^2
 };
 
+// Blocks of the apply kernel: a grid-stride loop gives each thread several nodes, whose
+// squares it adds in FP32 before one FP64 reduction (one node per thread made the FP64
+// butterfly the bottleneck at this part's FP64 rate).
+constexpr int kRsApplyBlocks = 608;
+static int rs_apply_blocks(size_t MM) { return (int)std::min<size_t>((MM + 255) / 256, kRsApplyBlocks); }
+
 __global__ void rs_apply_kernel(const __grid_constant__ RsApply a) {
   const int M = a.M;
   const size_t MM = (size_t)M * M;
   const float ratio = (float)(a.Mc - 1) / (float)(M - 1);
-  double n0 = 0.0, n1 = 0.0;
-  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (e < MM) {
+  float s0 = 0.f, s1 = 0.f;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < MM; e += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)((unsigned)e / (unsigned)M), i = (int)(e - (size_t)j * M);
     float g;
     if (a.mode == RS_ITER_SKIP) {
@@ -70,18 +75,19 @@ __global__ void rs_apply_kernel(const __grid_constant__ RsApply a) {
     } else if (a.mode == RS_INIT) {
       a.Unext[e] = g;
       a.Gold[e] = g;
-      n0 = (double)(g * g);
+      s0 = fmaf(g, g, s0);
     } else {
-      // squares in FP32 (u_new - u_old of nearby values is exact), sums in FP64
+      // u_new - u_old of nearby values is exact in FP32
       const float unew = a.Fn[e] + (g - a.Gold[e]);
       const float du = unew - a.Unext[e];
       a.Unext[e] = unew;
       a.Gold[e] = g;
-      n0 = (double)(unew * unew);
-      n1 = (double)(du * du);
+      s0 = fmaf(unew, unew, s0);
+      s1 = fmaf(du, du, s1);
     }
   }
   if (a.mode == RS_PROP) return;
+  double n0 = s0, n1 = s1;
   __shared__ double r0[32], r1[32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -139,7 +145,7 @@ static int rs_ensure(bs_grid* g, int N, float** c_in, float** c_out, double** pa
     if (rc) return rc;
   }
   const size_t MM = (size_t)g->M * g->M, P = (size_t)Mc * Mc;
-  const size_t nblocks = (MM + 255) / 256;
+  const size_t nblocks = (size_t)rs_apply_blocks(MM);
   const size_t fbytes = ((2 * P * sizeof(float)) + 255) / 256 * 256;
   int rc = ensure(g->ws_rs, fbytes + (size_t)(N + 1) * nblocks * 2 * sizeof(double));
   if (rc) return rc;
@@ -194,7 +200,7 @@ int resampled_propagate(bs_grid* g, const ItemDesc& d, const float* in, float* o
   RsApply ra = rs_args(g, d, RS_PROP, tau0 + nsteps * d.dtau, c_out);
   ra.out = out;
   const size_t MM = (size_t)g->M * g->M;
-  rs_apply_kernel<<<(unsigned)((MM + 255) / 256), 256, 0, s>>>(ra);
+  rs_apply_kernel<<<rs_apply_blocks(MM), 256, 0, s>>>(ra);
   BS_CUDA_TRY(cudaGetLastError());
   return BS_OK;
 }
@@ -207,7 +213,7 @@ int resampled_sweep(bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStrea
   if (rc) return rc;
   const int M = g->M, Mc = g->coarse_M;
   const size_t MM = (size_t)M * M;
-  const int nblocks = (int)((MM + 255) / 256);
+  const int nblocks = rs_apply_blocks(MM);
   for (int n = a.n_first; n < a.N; ++n) {
     const bool skip = (a.mode == SWEEP_ITER && n == a.n_first);
     const float* un = a.U + (size_t)n * MM;
