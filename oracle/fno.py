@@ -4,7 +4,7 @@
 Test infrastructure only (see ``oracle/__init__``).  numpy.fft is used as a library
 primitive for the transforms; everything else is written out here.
 
-Architecture (readings recorded in the design doc):
+Architecture (where the paper leaves the sizes open, the width-32, 12 x 12-mode reading):
   input channels per node: u, x, y, tau_n, dtau, sigma1, sigma2, rho, r      (Sec. 3.5)
   lifting:   v = lift_w^T a + lift_b                        (pointwise, 9 -> width)
   L layers:  v = ReLU( K_l v + pw_w_l^T v + pw_b_l )
