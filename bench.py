@@ -8,7 +8,16 @@ of 512 implicit-Euler fine steps and 4 coarse steps, for each rho in {-0.5, 0, 0
           (sum over the step's solves of M*M*N*fine_steps / device time of the step)
   e2e     the same through parareal_solve with host buffers: the initial state is copied
           from pinned host memory and the price surface u_N read back inside the timed region
-  roofline, cpu_baseline, clocks, gpu_launches: see the README of the output keys below.
+  roofline      the coarse sweep or F, whichever has the larger event-timed share: algorithmic
+                FP32 FLOP per second against the FP32 peak of 152 SMs at the measured maximum
+                clock, with the DRAM bytes per launch from a committed ncu capture
+                (profiles/traffic.json) while the kernel's sources are unchanged
+  kernels       per-kernel event times, launches, rates and solver statistics
+  cpu_baseline  the FP64 oracle on one host core, bounded sample of the same workload
+  clocks        nvidia-smi SM clock samples and throttle reasons during the timed region
+  gpu_launches  the library's kernel launches inside the timed region (its own counters)
+  serving       the serving sample: the first requests of the seeded trace replayed through
+                the server at 0.8 of the measured one-at-a-time capacity (p50/p99 latency)
 
 --impl reference times the FP64 CPU oracle (oracle/) on the host cores on a bounded sample
 of the same workload, in the same unit.
