@@ -12,6 +12,8 @@ Modules
   parareal      textbook Parareal, eq. (parareal), with the defect norm
   fno           FP64 FNO / PINO forward (Sec. 3.4, 3.5)
   resample      bilinear resampling; the numerical coarse model on a coarser grid (Sec. 4.4)
+  fd_nd         eq. (bse_general) for n assets discretised like eq. (fd) (19-point stencil
+                at n = 3), implicit Euler by sparse LU
 
 Pinning: every function is checked by ``tests/test_oracle_*.py`` against facts
 the mathematics fixes (exactness of centred differences on x^a y^b, a, b <= 2,
