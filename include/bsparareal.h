@@ -109,6 +109,36 @@ int fine_propagate_batched(const bs_grid* g, const bs_params* p,
                            const double* tau0, const double* dtau, int nsteps, int B,
                            bs_stream stream);
 
+/* Three assets: eq. (bse_general) with n = 3 (the paper treats n = 2; its general form
+ * extends eq. (fd) to a 19-point stencil: second differences along each axis, four-point
+ * cross differences for each pair, centred first differences).  Grid: M nodes per axis
+ * including both ends on [0, xmax]^3, u[(k*M + j)*M + i] with i the index of asset 1. */
+typedef struct {
+  double sigma[3];   /* volatilities, > 0 */
+  double rho[3];     /* correlations rho_12, rho_13, rho_23 (a positive definite matrix) */
+  double r;          /* risk-free rate, >= 0 */
+  double strike;     /* K of the basket */
+  double w[3];       /* basket weights */
+  int payoff;        /* BS_PAYOFF_BASKET: max(w.x - K, 0), far faces max(w.x - K e^{-r tau}, 0);
+                        BS_PAYOFF_EXCHANGE: max(x_1 - x_2, 0), far faces Margrabe in (x_1, x_2) */
+  int reserved;      /* must be 0 */
+} bs_params3;
+
+/* The payoff of p on the M^3 grid into device float[M^3] u.  Asynchronous.
+ * Errors: BS_ERR_ARG (M outside [4, 128], invalid parameters, NULL), BS_ERR_CUDA. */
+int bs_payoff3(int M, double xmax, const bs_params3* p, float* u, bs_stream stream);
+
+/* F for three assets on B states at once: nsteps implicit-Euler steps of size dtau from
+ * tau0[b], (I - dtau R_h) u^{m+1} = u^m with the 19-point R_h and far-face Dirichlet data
+ * at tau^{m+1}; solved by Jacobi sweeps (count from the Gershgorin bound q of the system,
+ * q < 0.8) in FP32 with a compensated (hi, lo) state.  u_in[b], u_out[b]: device
+ * float[M^3] (may alias).  Allocates its workspace stream-ordered (5 M^3 floats per state).
+ * Asynchronous.  Results for a state do not depend on B or on the other states.
+ * Errors: BS_ERR_ARG (as bs_payoff3; NULL pointers, B < 1, dtau <= 0, q >= 0.8),
+ * BS_ERR_CUDA. */
+int fine_propagate3(int M, double xmax, const bs_params3* p, const float* const* u_in, float* const* u_out,
+                    const double* tau0, int B, double dtau, int nsteps, bs_stream stream);
+
 /* Coarse propagator G of Sec. 3.1 for one state.
  *  kind = BS_COARSE_NUM: nsteps implicit-Euler steps of size dtau_slice/nsteps with the
  *    same operator as F (Sec. 3.2: the numerical coarse model is the same discretisation

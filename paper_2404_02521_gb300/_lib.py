@@ -23,7 +23,7 @@ COARSE_NUM, COARSE_PINO = 0, 1
 EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
-           "bs_coarse_variant", "bs_coarse_variant_info", "bs_server_create", "bs_server_submit", "bs_server_progress",
+           "bs_coarse_variant", "bs_coarse_variant_info", "bs_payoff3", "fine_propagate3", "bs_server_create", "bs_server_submit", "bs_server_progress",
            "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for",
            "bs_grid_set_coarse"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
@@ -43,6 +43,12 @@ class bs_params(C.Structure):
                 ("r", C.c_double), ("T", C.c_double), ("strike", C.c_double),
                 ("w1", C.c_double), ("w2", C.c_double), ("payoff", C.c_int),
                 ("reserved", C.c_int), ("strike2", C.c_double), ("cash", C.c_double)]
+
+
+class bs_params3(C.Structure):
+    _fields_ = [("sigma", C.c_double * 3), ("rho", C.c_double * 3), ("r", C.c_double),
+                ("strike", C.c_double), ("w", C.c_double * 3), ("payoff", C.c_int),
+                ("reserved", C.c_int)]
 
 
 class bs_server_config(C.Structure):
@@ -103,6 +109,8 @@ def load(path: Optional[str] = None):
     lib.bs_grid_stats.argtypes = [vp, P(i), P(i), P(i), P(i)]
     lib.bs_coarse_variant.argtypes = [vp, P(bs_params), d, P(i), vp]
     lib.bs_coarse_variant_info.argtypes = [i, i, P(i), P(i), P(i), P(i), P(i)]
+    lib.bs_payoff3.argtypes = [i, d, P(bs_params3), vp, vp]
+    lib.fine_propagate3.argtypes = [i, d, P(bs_params3), P(vp), P(vp), P(d), i, d, i, vp]
     lib.bs_server_create.argtypes = [P(bs_server_config), P(vp)]
     lib.bs_server_submit.argtypes = [vp, P(bs_request), P(C.c_longlong)]
     lib.bs_server_progress.argtypes = [vp, P(i), P(i)]
@@ -135,6 +143,15 @@ def to_params(p) -> bs_params:
     return bs_params(float(p.sigma1), float(p.sigma2), float(p.rho), float(p.r), float(p.T),
                      float(p.strike), float(p.w1), float(p.w2), int(p.payoff), 0,
                      float(getattr(p, "strike2", 0.0)), float(getattr(p, "cash", 1.0)))
+
+
+def to_params3(p) -> bs_params3:
+    """From an object with sigma (3), rho (rho_12, rho_13, rho_23), r, strike, w (3), payoff."""
+    return bs_params3((C.c_double * 3)(*[float(v) for v in p.sigma]),
+                      (C.c_double * 3)(*[float(v) for v in p.rho]), float(p.r),
+                      float(getattr(p, "strike", 1.0)),
+                      (C.c_double * 3)(*[float(v) for v in getattr(p, "w", (1 / 3, 1 / 3, 1 / 3))]),
+                      int(p.payoff), 0)
 
 
 def _ptr(x) -> int:
@@ -190,6 +207,24 @@ def fine_propagate_batched(g: Grid, params: Sequence, u_in: Sequence, u_out: Seq
     dt = (C.c_double * B)(*[float(t) for t in dtau])
     return check(load().fine_propagate_batched(g.h, P, pin, pout, t0, dt, int(nsteps), B,
                                                _stream(stream)))
+
+
+def bs_payoff3(M: int, xmax: float, p, u, stream=None):
+    """Three-asset payoff into a device float[M^3] tensor."""
+    bp = to_params3(p)
+    return check(load().bs_payoff3(int(M), float(xmax), C.byref(bp), _ptr(u), _stream(stream)))
+
+
+def fine_propagate3(M: int, xmax: float, p, u_in: Sequence, u_out: Sequence, tau0: Sequence[float],
+                    dtau: float, nsteps: int, stream=None):
+    """F for three assets (19-point stencil) on len(u_in) states of M^3 nodes."""
+    bp = to_params3(p)
+    B = len(u_in)
+    pin = (C.c_void_p * B)(*[_ptr(x) for x in u_in])
+    pout = (C.c_void_p * B)(*[_ptr(x) for x in u_out])
+    t0 = (C.c_double * B)(*[float(t) for t in tau0])
+    return check(load().fine_propagate3(int(M), float(xmax), C.byref(bp), pin, pout, t0, B, float(dtau),
+                                        int(nsteps), _stream(stream)))
 
 
 def coarse_propagate(g: Grid, kind: int, net, p, u_in, u_out, tau0: float, dtau_slice: float,

@@ -1,0 +1,332 @@
+// F for three assets: eq. (bse_general) with n = 3, discretised like eq. (fd) (second
+// differences along each axis, four-point cross differences for each pair, centred first
+// differences: a 19-point stencil) and stepped by implicit Euler, for B states at once.
+//
+// A first, direct GPU path: the state and its increments live in global memory (L2 for the
+// grids this targets, M <= 128), one thread per node, one launch per Jacobi sweep.  Each
+// step solves (I - dtau R_h) d = dtau R_h u (increment form, far-face Dirichlet data already
+// at the new time level) by Jacobi sweeps whose count follows from the Gershgorin bound q of
+// the system (q < 0.8; the first step from d = 0 to q^m <= 2^-22, later steps from the
+// previous increment to q^m <= 2^-10, at least 2), and carries u as a compensated (hi, lo)
+// FP32 pair.  Stencil coefficients are products of host-rounded FP32 constants and exact
+// integer node indices (x_p = i_p h, so h cancels).
+//
+// Layout: u[(k*M + j)*M + i] with i the index of asset 1 (fastest), j of asset 2, k of
+// asset 3.  Nodes with an index M - 1 carry Dirichlet data; nodes with an index 0 carry the
+// PDE row itself (every coefficient that would reach index -1 is a multiple of that index).
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bsp {
+
+constexpr int kF3MaxItems = 32;
+constexpr int kF3Threads = 256;
+
+struct F3Item {
+  const float* in;
+  float* out;
+  float* hi;   // [M^3] state, high part
+  float* lo;   // [M^3] compensation
+  float* b;    // [M^3] dtau R_h u of the step
+  float* dA;   // [M^3] increment ping-pong
+  float* dB;
+  float tau0;
+};
+
+struct F3Coef {
+  float A[3];      // 1/2 sigma_p^2 dtau      (times i_p^2: diffusion weight of +-1 along p)
+  float D[3];      // 1/2 r dtau              (times i_p: drift weight, + on +1, - on -1)
+  float Cxy, Cxz, Cyz;   // 1/4 rho_pq sigma_p sigma_q dtau (times i_p i_q: cross weight)
+  float rdt;       // r dtau
+};
+
+struct F3Batch {
+  F3Item it[kF3MaxItems];
+  int n, M;
+  float h;
+  F3Coef c;
+  int kind;        // BS_PAYOFF_BASKET or BS_PAYOFF_EXCHANGE
+  float w[3], K;   // basket: max(w.x - K e^{-r tau}, 0) on the far faces
+  PayoffF ex;      // exchange: Margrabe in (x_1, x_2) on the far faces
+  float r;
+  float dtau;
+};
+
+__device__ __forceinline__ void f3_node(int e, int M, int& i, int& j, int& k) {
+  const int MM = M * M;
+  k = e / MM;
+  const int rem = e - k * MM;
+  j = rem / M;
+  i = rem - j * M;
+}
+
+__device__ __forceinline__ float f3_far_field(const F3Batch& fb, int i, int j, int k, float tau) {
+  const float x = i * fb.h, y = j * fb.h, z = k * fb.h;
+  if (fb.kind == BS_PAYOFF_BASKET)
+    return fmaxf(fb.w[0] * x + fb.w[1] * y + fb.w[2] * z - fb.K * expf(-fb.r * tau), 0.0f);
+  return far_field(fb.ex, x, y, tau);
+}
+
+// Off-diagonal part of dtau R_h applied to y at a PDE node (i, j, k <= M-2): the 18
+// neighbours; a neighbour at index -1 has weight 0 and is not read.
+__device__ __forceinline__ float f3_offdiag(const float* __restrict__ y, const F3Coef& c, int M, int i, int j,
+                                            int k) {
+  const int e = (k * M + j) * M + i;
+  const int sx = 1, sy = M, sz = M * M;
+  const float fi = (float)i, fj = (float)j, fk = (float)k;
+  const float ax = c.A[0] * (fi * fi), ay = c.A[1] * (fj * fj), az = c.A[2] * (fk * fk);
+  const float mx = c.D[0] * fi, my = c.D[1] * fj, mz = c.D[2] * fk;
+  float acc = (ax + mx) * __ldg(y + e + sx) + (ay + my) * __ldg(y + e + sy) + (az + mz) * __ldg(y + e + sz);
+  if (i > 0) acc = fmaf(ax - mx, __ldg(y + e - sx), acc);
+  if (j > 0) acc = fmaf(ay - my, __ldg(y + e - sy), acc);
+  if (k > 0) acc = fmaf(az - mz, __ldg(y + e - sz), acc);
+  // cross pairs: +(++ and --) - (+- and -+)
+  {
+    float s = __ldg(y + e + sx + sy);
+    if (i > 0 && j > 0) s += __ldg(y + e - sx - sy);
+    if (j > 0) s -= __ldg(y + e + sx - sy);
+    if (i > 0) s -= __ldg(y + e - sx + sy);
+    acc = fmaf(c.Cxy * (fi * fj), s, acc);
+  }
+  {
+    float s = __ldg(y + e + sx + sz);
+    if (i > 0 && k > 0) s += __ldg(y + e - sx - sz);
+    if (k > 0) s -= __ldg(y + e + sx - sz);
+    if (i > 0) s -= __ldg(y + e - sx + sz);
+    acc = fmaf(c.Cxz * (fi * fk), s, acc);
+  }
+  {
+    float s = __ldg(y + e + sy + sz);
+    if (j > 0 && k > 0) s += __ldg(y + e - sy - sz);
+    if (k > 0) s -= __ldg(y + e + sy - sz);
+    if (j > 0) s -= __ldg(y + e - sy + sz);
+    acc = fmaf(c.Cyz * (fj * fk), s, acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ float f3_diag(const F3Coef& c, int i, int j, int k) {
+  const float fi = (float)i, fj = (float)j, fk = (float)k;
+  return 1.0f + 2.0f * (c.A[0] * (fi * fi) + c.A[1] * (fj * fj) + c.A[2] * (fk * fk)) + c.rdt;
+}
+
+enum { F3_INIT = 0, F3_FACE = 1, F3_RHS = 2, F3_APPLY = 3, F3_OUT = 4 };
+
+// The pointwise phases of a step (one launch each): INIT copies u_in into (hi, lo = 0) and
+// zeroes the increment; FACE writes the far-face data at tau; RHS forms b = dtau R_h hi;
+// APPLY adds the increment to (hi, lo); OUT writes hi + lo.
+__global__ void __launch_bounds__(kF3Threads) f3_phase_kernel(const __grid_constant__ F3Batch fb, int phase,
+                                                              int step, int cur) {
+  const F3Item& it = fb.it[blockIdx.y];
+  const int M = fb.M, n3 = M * M * M;
+  const int e = blockIdx.x * kF3Threads + threadIdx.x;
+  if (e >= n3) return;
+  int i, j, k;
+  f3_node(e, M, i, j, k);
+  const bool pde = i < M - 1 && j < M - 1 && k < M - 1;
+  float* d = cur ? it.dB : it.dA;
+  switch (phase) {
+    case F3_INIT:
+      it.hi[e] = it.in[e];
+      it.lo[e] = 0.f;
+      it.dA[e] = 0.f;
+      it.dB[e] = 0.f;
+      break;
+    case F3_FACE:
+      if (!pde) {
+        it.hi[e] = f3_far_field(fb, i, j, k, it.tau0 + (step + 1) * fb.dtau);
+      }
+      break;
+    case F3_RHS:
+      it.b[e] = pde ? f3_offdiag(it.hi, fb.c, M, i, j, k) - (f3_diag(fb.c, i, j, k) - 1.0f) * it.hi[e] : 0.f;
+      break;
+    case F3_APPLY:
+      if (pde) {
+        const float h0 = it.hi[e], v = d[e];
+        const float s = h0 + v, bb = s - h0;
+        const float err = (h0 - (s - bb)) + (v - bb);
+        const float l = it.lo[e] + err;
+        const float hn = s + l;
+        it.lo[e] = l - (hn - s);
+        it.hi[e] = hn;
+      }
+      break;
+    case F3_OUT:
+      it.out[e] = it.hi[e] + it.lo[e];
+      break;
+  }
+}
+
+// One Jacobi sweep: d_new = (b + offdiag(d_old)) / diag at PDE nodes, 0 elsewhere.
+__global__ void __launch_bounds__(kF3Threads) f3_sweep_kernel(const __grid_constant__ F3Batch fb, int cur) {
+  const F3Item& it = fb.it[blockIdx.y];
+  const int M = fb.M, n3 = M * M * M;
+  const int e = blockIdx.x * kF3Threads + threadIdx.x;
+  if (e >= n3) return;
+  int i, j, k;
+  f3_node(e, M, i, j, k);
+  const float* din = cur ? it.dB : it.dA;
+  float* dout = cur ? it.dA : it.dB;
+  const bool pde = i < M - 1 && j < M - 1 && k < M - 1;
+  dout[e] = pde ? (it.b[e] + f3_offdiag(din, fb.c, M, i, j, k)) / f3_diag(fb.c, i, j, k) : 0.f;
+}
+
+// Gershgorin bound of I - dtau R_h over the PDE nodes: max of sum |off-diagonal| / diagonal.
+static double f3_contraction(int M, const bs_params3& p, double dtau) {
+  double q = 0.0;
+  const double rho[3][3] = {{1.0, p.rho[0], p.rho[1]}, {p.rho[0], 1.0, p.rho[2]}, {p.rho[1], p.rho[2], 1.0}};
+  for (int k = 0; k <= M - 2; ++k)
+    for (int j = 0; j <= M - 2; ++j)
+      for (int i = 0; i <= M - 2; ++i) {
+        const int id[3] = {i, j, k};
+        double off = 0.0, diag = 1.0 + dtau * p.r;
+        for (int a = 0; a < 3; ++a) {
+          const double dif = 0.5 * p.sigma[a] * p.sigma[a] * id[a] * id[a], drift = 0.5 * p.r * id[a];
+          off += std::fabs(dif + drift) + std::fabs(dif - drift);
+          diag += dtau * 2.0 * dif;
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int b = a + 1; b < 3; ++b)
+            off += 4.0 * std::fabs(0.25 * rho[a][b] * p.sigma[a] * p.sigma[b]) * id[a] * id[b];
+        q = std::fmax(q, dtau * off / diag);
+      }
+  return q;
+}
+
+static int f3_sweeps(double q, bool cold) {
+  const double target = cold ? 1.0 / 4194304.0 : 1.0 / 1024.0;
+  if (q <= 0.0) return 2;
+  const int m = (int)std::ceil(std::log(target) / std::log(q));
+  return m < 2 ? 2 : m;
+}
+
+static int f3_check(int M, double xmax, const bs_params3* p) {
+  if (!p) return set_error(BS_ERR_ARG, "params3 is NULL");
+  if (M < 4 || M > 128) return set_error(BS_ERR_ARG, "three-asset grid: M=%d out of [4, 128]", M);
+  if (!(xmax > 0.0)) return set_error(BS_ERR_ARG, "three-asset grid: xmax must be > 0");
+  for (int a = 0; a < 3; ++a) {
+    if (!(p->sigma[a] > 0.0)) return set_error(BS_ERR_ARG, "sigma must be > 0");
+    if (!(std::fabs(p->rho[a]) < 1.0)) return set_error(BS_ERR_ARG, "|rho| must be < 1");
+  }
+  // the correlation matrix must be positive definite (its determinant, the 2x2 minors are
+  // positive already)
+  const double r12 = p->rho[0], r13 = p->rho[1], r23 = p->rho[2];
+  if (!(1.0 - r12 * r12 - r13 * r13 - r23 * r23 + 2.0 * r12 * r13 * r23 > 0.0))
+    return set_error(BS_ERR_ARG, "the correlation matrix is not positive definite");
+  if (!(p->r >= 0.0)) return set_error(BS_ERR_ARG, "r must be >= 0");
+  if (p->payoff != BS_PAYOFF_BASKET && p->payoff != BS_PAYOFF_EXCHANGE)
+    return set_error(BS_ERR_ARG, "three-asset payoff must be BS_PAYOFF_BASKET or BS_PAYOFF_EXCHANGE");
+  if (p->reserved != 0) return set_error(BS_ERR_ARG, "bs_params3.reserved must be 0");
+  return BS_OK;
+}
+
+static F3Batch f3_batch(int M, double xmax, const bs_params3& p, double dtau) {
+  F3Batch fb = {};
+  fb.M = M;
+  fb.h = (float)(xmax / (M - 1));
+  for (int a = 0; a < 3; ++a) {
+    fb.c.A[a] = (float)(0.5 * p.sigma[a] * p.sigma[a] * dtau);
+    fb.c.D[a] = (float)(0.5 * p.r * dtau);
+    fb.w[a] = (float)p.w[a];
+  }
+  fb.c.Cxy = (float)(0.25 * p.rho[0] * p.sigma[0] * p.sigma[1] * dtau);
+  fb.c.Cxz = (float)(0.25 * p.rho[1] * p.sigma[0] * p.sigma[2] * dtau);
+  fb.c.Cyz = (float)(0.25 * p.rho[2] * p.sigma[1] * p.sigma[2] * dtau);
+  fb.c.rdt = (float)(p.r * dtau);
+  fb.kind = p.payoff;
+  fb.K = (float)p.strike;
+  fb.r = (float)p.r;
+  fb.dtau = (float)dtau;
+  fb.ex = PayoffF{};
+  fb.ex.kind = BS_PAYOFF_EXCHANGE;
+  fb.ex.s1 = (float)p.sigma[0];
+  fb.ex.s2 = (float)p.sigma[1];
+  fb.ex.rho = (float)p.rho[0];
+  fb.ex.r = (float)p.r;
+  return fb;
+}
+
+__global__ void f3_payoff_kernel(float* u, int M, float h, int kind, float w0, float w1, float w2, float K) {
+  const int n3 = M * M * M;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n3) return;
+  int i, j, k;
+  f3_node(e, M, i, j, k);
+  const float x = i * h, y = j * h, z = k * h;
+  u[e] = kind == BS_PAYOFF_BASKET ? fmaxf(w0 * x + w1 * y + w2 * z - K, 0.f) : fmaxf(x - y, 0.f);
+}
+
+}  // namespace bsp
+
+using namespace bsp;
+
+extern "C" {
+
+int bs_payoff3(int M, double xmax, const bs_params3* p, float* u, bs_stream stream) {
+  int rc = f3_check(M, xmax, p);
+  if (rc) return rc;
+  if (!u) return set_error(BS_ERR_ARG, "bs_payoff3: NULL state");
+  const int n3 = M * M * M;
+  f3_payoff_kernel<<<(n3 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+      u, M, (float)(xmax / (M - 1)), p->payoff, (float)p->w[0], (float)p->w[1], (float)p->w[2], (float)p->strike);
+  BS_CUDA_TRY(cudaGetLastError());
+  return BS_OK;
+}
+
+int fine_propagate3(int M, double xmax, const bs_params3* p, const float* const* u_in, float* const* u_out,
+                    const double* tau0, int B, double dtau, int nsteps, bs_stream stream) {
+  int rc = f3_check(M, xmax, p);
+  if (rc) return rc;
+  if (!u_in || !u_out || !tau0) return set_error(BS_ERR_ARG, "fine_propagate3: NULL argument");
+  if (B < 1 || nsteps < 0) return set_error(BS_ERR_ARG, "fine_propagate3: B=%d nsteps=%d", B, nsteps);
+  if (!(dtau > 0.0)) return set_error(BS_ERR_ARG, "fine_propagate3: dtau <= 0");
+  for (int b = 0; b < B; ++b)
+    if (!u_in[b] || !u_out[b]) return set_error(BS_ERR_ARG, "fine_propagate3: NULL state %d", b);
+  const double q = f3_contraction(M, *p, dtau);
+  if (!(q < 0.8))
+    return set_error(BS_ERR_ARG, "fine_propagate3: Jacobi bound %.3f >= 0.8 (take smaller steps)", q);
+  const int m0 = f3_sweeps(q, true), m1 = f3_sweeps(q, false);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n3 = (size_t)M * M * M;
+  const unsigned blocks = (unsigned)((n3 + kF3Threads - 1) / kF3Threads);
+  for (int base = 0; base < B; base += kF3MaxItems) {
+    const int nb = B - base < kF3MaxItems ? B - base : kF3MaxItems;
+    float* ws = nullptr;
+    BS_CUDA_TRY(cudaMallocAsync((void**)&ws, (size_t)nb * 5 * n3 * sizeof(float), s));
+    F3Batch fb = f3_batch(M, xmax, *p, dtau);
+    fb.n = nb;
+    for (int t = 0; t < nb; ++t) {
+      F3Item& it = fb.it[t];
+      float* w = ws + (size_t)t * 5 * n3;
+      it.in = u_in[base + t];
+      it.out = u_out[base + t];
+      it.hi = w;
+      it.lo = w + n3;
+      it.b = w + 2 * n3;
+      it.dA = w + 3 * n3;
+      it.dB = w + 4 * n3;
+      it.tau0 = (float)tau0[base + t];
+    }
+    const dim3 grid(blocks, nb);
+    f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_INIT, 0, 0);
+    int cur = 0;   // 0: the increment is in dA
+    for (int step = 0; step < nsteps; ++step) {
+      f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_FACE, step, cur);
+      f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_RHS, step, cur);
+      const int m = step == 0 ? m0 : m1;
+      for (int sw = 0; sw < m; ++sw) {
+        f3_sweep_kernel<<<grid, kF3Threads, 0, s>>>(fb, cur);
+        cur ^= 1;
+      }
+      f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_APPLY, step, cur);
+    }
+    f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_OUT, nsteps, cur);
+    BS_CUDA_TRY(cudaGetLastError());
+    BS_CUDA_TRY(cudaFreeAsync(ws, s));
+  }
+  return BS_OK;
+}
+
+}  // extern "C"

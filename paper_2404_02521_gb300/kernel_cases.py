@@ -19,6 +19,7 @@ workloads, one kernel each:
   pino128    the PINO coarse propagator on 64 states of 128x128 (random weights)
   resample1024  Parareal to K = N = 4 on 1024x1024 basket states with numerical G on the 256x256
              grid (bilinear restriction and prolongation kernels, 64 fine steps per slice)
+  fine3_64   three-asset F: 16 states of 64^3 nodes, 64 implicit steps (19-point stencil)
 """
 from __future__ import annotations
 
@@ -180,10 +181,23 @@ def case_resample1024(bs, wl, torch):
     return lambda: bs.parareal_solve(g, p, N, 64, bs.COARSE_NUM, base.coarse_steps, None, 0.0, N, U)
 
 
+def case_fine3_64(bs, wl, torch):
+    # three assets: 16 states of 64^3 nodes (a 3-asset basket), 64 implicit steps each
+    import types
+    p = types.SimpleNamespace(sigma=(0.3, 0.2, 0.25), rho=(0.5, -0.3, 0.2), r=0.05, strike=1.0,
+                              w=(0.4, 0.35, 0.25), payoff=wl.BASKET)
+    M, B, steps, dtau = 64, 16, 64, 1.0 / 4096
+    U = torch.empty((B, M, M, M), device="cuda")
+    bs.bs_payoff3(M, 4.0, p, U[0])
+    U[1:].copy_(U[0].expand(B - 1, M, M, M))
+    F = torch.empty_like(U)
+    return lambda: bs.fine_propagate3(M, 4.0, p, list(U), list(F), [0.01 * b for b in range(B)], dtau, steps)
+
+
 CASES = {"fine256": case_fine256, "coarse256": case_coarse256, "solve256": case_solve256,
          "tile1024": case_tile1024,
          "coarse512": case_coarse512, "pino128": case_pino128, "large1024": case_large1024,
-         "resample1024": case_resample1024}
+         "resample1024": case_resample1024, "fine3_64": case_fine3_64}
 
 
 def main():

@@ -110,3 +110,24 @@ def test_coarse_variant_info(lib):
     for bad in [(8, 100), (10, 256), (-1, 64), (0, 300)]:
         with pytest.raises(_lib.BSError):
             _lib.bs_coarse_variant_info(*bad)
+
+
+def test_three_asset_arguments_are_checked(lib):
+    # rejected on the host, before any device work
+    import types
+    from paper_2404_02521_gb300 import _lib
+    ok = types.SimpleNamespace(sigma=(0.3, 0.2, 0.25), rho=(0.5, -0.3, 0.2), r=0.05, strike=1.0,
+                               w=(0.4, 0.35, 0.25), payoff=0)
+    fake = [1 << 20]
+    bad = [
+        (3, ok, 0.001), (129, ok, 0.001),
+        (16, types.SimpleNamespace(**{**vars(ok), "rho": (0.9, 0.9, -0.9)}), 0.001),   # not positive definite
+        (16, types.SimpleNamespace(**{**vars(ok), "payoff": 2}), 0.001),               # one-asset call
+        (16, types.SimpleNamespace(**{**vars(ok), "sigma": (0.3, 0.0, 0.2)}), 0.001),
+        (64, ok, 1.0),                                                                  # Jacobi bound >= 0.8
+    ]
+    for M, p, dtau in bad:
+        with pytest.raises(_lib.BSError):
+            _lib.fine_propagate3(M, 4.0, p, fake, fake, [0.0], dtau, 1, stream=0)
+    with pytest.raises(_lib.BSError):
+        _lib.fine_propagate3(16, 4.0, ok, [], [], [], 0.001, 1, stream=0)

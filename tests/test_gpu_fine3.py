@@ -1,0 +1,89 @@
+"""Three-asset F (eq. bse_general with n = 3, 19-point stencil) against the n-asset oracle."""
+import types
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import closed_forms as cf
+from oracle import fd_nd
+from tests.gpu_util import FP32_FINE_TOL, rel_err
+
+pytestmark = pytest.mark.gpu
+
+XMAX = 4.0
+
+
+@pytest.fixture(scope="module")
+def bs():
+    import paper_2404_02521_gb300 as bs
+    bs.load()
+    return bs
+
+
+def params3(payoff):
+    return types.SimpleNamespace(sigma=(0.3, 0.2, 0.25), rho=(0.5, -0.3, 0.2), r=0.05, strike=1.0,
+                                 w=(0.4, 0.35, 0.25), payoff=payoff)
+
+
+def rho_matrix(p):
+    r12, r13, r23 = p.rho
+    return np.array([[1.0, r12, r13], [r12, 1.0, r23], [r13, r23, 1.0]])
+
+
+def oracle_boundary(p):
+    if p.payoff == wl.BASKET:
+        return lambda X, tau: np.maximum(p.w[0] * X[0] + p.w[1] * X[1] + p.w[2] * X[2]
+                                         - p.strike * np.exp(-p.r * tau), 0.0)
+    return lambda X, tau: cf.margrabe(X[0], X[1], p.sigma[0], p.sigma[1], p.rho[0], tau)
+
+
+def oracle_payoff(p, M):
+    X = fd_nd.coords(M, XMAX, 3)
+    if p.payoff == wl.BASKET:
+        return np.maximum(p.w[0] * X[0] + p.w[1] * X[1] + p.w[2] * X[2] - p.strike, 0.0)
+    return np.maximum(X[0] - X[1], 0.0)
+
+
+@pytest.mark.parametrize("payoff", [wl.BASKET, wl.EXCHANGE])
+def test_payoff3(bs, payoff):
+    import torch
+    p, M = params3(payoff), 13
+    u = torch.empty((M, M, M), device="cuda")
+    bs.bs_payoff3(M, XMAX, p, u)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(u.cpu().double().numpy(), oracle_payoff(p, M), rtol=1e-6, atol=1e-6)
+
+
+# M = 12 and 21: every node count is ragged against the 256-thread blocks
+@pytest.mark.parametrize("M", [12, 21])
+@pytest.mark.parametrize("payoff", [wl.BASKET, wl.EXCHANGE])
+def test_fine3_matches_oracle(bs, M, payoff):
+    import torch
+    p = params3(payoff)
+    dtau, nsteps = 0.004, 16
+    u0 = oracle_payoff(p, M)
+    ie = fd_nd.ImplicitEulerND(M, XMAX, p.sigma, rho_matrix(p), p.r, dtau, oracle_boundary(p))
+    tau0 = [0.0, 0.1]
+    uin = [torch.tensor(u0, dtype=torch.float32, device="cuda") for _ in tau0]
+    uout = [torch.empty_like(x) for x in uin]
+    bs.fine_propagate3(M, XMAX, p, uin, uout, tau0, dtau, nsteps)
+    torch.cuda.synchronize()
+    for t, out in zip(tau0, uout):
+        want = ie.propagate(u0, t, nsteps)
+        assert rel_err(out.cpu().double().numpy(), want) <= FP32_FINE_TOL, (t, M)
+
+
+def test_fine3_batch_invariance_and_in_place(bs):
+    import torch
+    p, M = params3(wl.EXCHANGE), 16
+    u0 = torch.tensor(oracle_payoff(p, M), dtype=torch.float32, device="cuda")
+    one = torch.empty_like(u0)
+    bs.fine_propagate3(M, XMAX, p, [u0], [one], [0.05], 0.004, 10)
+    many_in = [u0 * 1.5, u0, u0 * 0.5]
+    many_out = [torch.empty_like(u0) for _ in many_in]
+    bs.fine_propagate3(M, XMAX, p, many_in, many_out, [0.2, 0.05, 0.1], 0.004, 10)
+    inplace = u0.clone()
+    bs.fine_propagate3(M, XMAX, p, [inplace], [inplace], [0.05], 0.004, 10)
+    torch.cuda.synchronize()
+    assert torch.equal(one, many_out[1]) and torch.equal(one, inplace)
