@@ -139,6 +139,18 @@ int bs_payoff3(int M, double xmax, const bs_params3* p, float* u, bs_stream stre
 int fine_propagate3(int M, double xmax, const bs_params3* p, const float* const* u_in, float* const* u_out,
                     const double* tau0, int B, double dtau, int nsteps, bs_stream stream);
 
+/* Parareal (eq. parareal) for three assets on [0, T] with N slices: F = fine_steps implicit
+ * steps per slice, G = coarse_steps steps of the same three-asset scheme (its Jacobi bound
+ * must stay below 0.8); iterate until delta_k <= tol (reading c5, FP64 norms) or k = Kmax.
+ *  u_out        device float[(N+1)*M^3]: u_0 (the payoff) .. u_N on return
+ *  k_done       host int: iterations performed;  defect_hist  host double[Kmax] or NULL
+ * Synchronous.  Returns BS_OK (converged, or k_done = N: every slice exact), BS_ERR_MAXITER
+ * (tol not met within Kmax < N), BS_ERR_ARG (as fine_propagate3, or N, steps, Kmax out of
+ * range), BS_ERR_CUDA. */
+int parareal_solve3(int M, double xmax, const bs_params3* p, double T, int N, int fine_steps,
+                    int coarse_steps, double tol, int Kmax, float* u_out, int* k_done,
+                    double* defect_hist, bs_stream stream);
+
 /* Coarse propagator G of Sec. 3.1 for one state.
  *  kind = BS_COARSE_NUM: nsteps implicit-Euler steps of size dtau_slice/nsteps with the
  *    same operator as F (Sec. 3.2: the numerical coarse model is the same discretisation

@@ -87,3 +87,49 @@ def test_fine3_batch_invariance_and_in_place(bs):
     bs.fine_propagate3(M, XMAX, p, [inplace], [inplace], [0.05], 0.004, 10)
     torch.cuda.synchronize()
     assert torch.equal(one, many_out[1]) and torch.equal(one, inplace)
+
+
+def serial_fine3(bs, p, M, T, N, fine_steps):
+    import torch
+    U = torch.empty((N + 1, M, M, M), device="cuda")
+    bs.bs_payoff3(M, XMAX, p, U[0])
+    sl = T / N
+    for n in range(N):
+        bs.fine_propagate3(M, XMAX, p, [U[n]], [U[n + 1]], [n * sl], sl / fine_steps, fine_steps)
+    torch.cuda.synchronize()
+    return U
+
+
+@pytest.mark.parametrize("payoff", [wl.BASKET, wl.EXCHANGE])
+def test_parareal3_k_equals_n_is_serial_fine(bs, payoff):
+    # the Parareal invariant for three assets: K = N reproduces serial fine stepping bitwise
+    import torch
+    p, M, T, N, fs, cs = params3(payoff), 12, 0.05, 5, 12, 3
+    U = torch.empty((N + 1, M, M, M), device="cuda")
+    rc, k, defects = bs.parareal_solve3(M, XMAX, p, T, N, fs, cs, 0.0, N, U)
+    torch.cuda.synchronize()
+    assert rc == 0 and k == N and len(defects) == N
+    assert torch.equal(U, serial_fine3(bs, p, M, T, N, fs))
+
+
+def test_parareal3_matches_oracle_parareal(bs):
+    # to tol 1e-4: the oracle's iteration count (exact solves for F and G) and iterate, and
+    # within the tolerance of serial fine stepping
+    import torch
+    from oracle import parareal as opr
+    p, M, T, N, fs, cs = params3(wl.BASKET), 12, 0.2, 8, 24, 2
+    U = torch.empty((N + 1, M, M, M), device="cuda")
+    rc, k, defects = bs.parareal_solve3(M, XMAX, p, T, N, fs, cs, 1e-4, N, U)
+    torch.cuda.synchronize()
+    sl = T / N
+    ieF = fd_nd.ImplicitEulerND(M, XMAX, p.sigma, rho_matrix(p), p.r, sl / fs, oracle_boundary(p))
+    ieG = fd_nd.ImplicitEulerND(M, XMAX, p.sigma, rho_matrix(p), p.r, sl / cs, oracle_boundary(p))
+    Uo, ko, do, _ = opr.parareal(oracle_payoff(p, M), lambda u, n: ieF.propagate(u, n * sl, fs),
+                                 lambda u, n: ieG.propagate(u, n * sl, cs), N, 1e-4, N)
+    assert rc == 0 and k == ko and k < N
+    for a, b in zip(defects, do):
+        assert abs(a - b) <= 1e-2 * b + 1e-6
+    got = U.cpu().double().numpy()
+    assert rel_err(got, Uo) <= 1e-4
+    serial = serial_fine3(bs, p, M, T, N, fs).cpu().double().numpy()
+    assert rel_err(got, serial) <= 1e-3
