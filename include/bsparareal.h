@@ -139,14 +139,23 @@ int bs_payoff3(int M, double xmax, const bs_params3* p, float* u, bs_stream stre
 int fine_propagate3(int M, double xmax, const bs_params3* p, const float* const* u_in, float* const* u_out,
                     const double* tau0, int B, double dtau, int nsteps, bs_stream stream);
 
-/* Parareal (eq. parareal) for three assets on [0, T] with N slices: F = fine_steps implicit
- * steps per slice, G = coarse_steps steps of the same three-asset scheme (its Jacobi bound
- * must stay below 0.8); iterate until delta_k <= tol (reading c5, FP64 norms) or k = Kmax.
+/* G for three assets, one state: nsteps implicit-Euler steps of size dtau_slice/nsteps from
+ * tau0 with the 19-point operator, each solved by BiCGSTAB on the Jacobi-scaled increment
+ * system in FP32 to BS_OPT_KRYLOV_TOL (any step size).  Synchronous (the host checks
+ * convergence every iteration).  Errors: BS_ERR_ARG (as bs_payoff3, NULL, dtau_slice <= 0,
+ * nsteps < 1), BS_ERR_NOCONV (BS_OPT_KRYLOV_MAXIT reached), BS_ERR_CUDA. */
+int coarse_propagate3(int M, double xmax, const bs_params3* p, const float* u_in, float* u_out,
+                      double tau0, double dtau_slice, int nsteps, bs_stream stream);
+
+/* Parareal (eq. parareal) for three assets on [0, T] with N slices: F = fine_steps Jacobi
+ * steps per slice (fine_propagate3), G = coarse_steps steps of the same scheme solved by
+ * BiCGSTAB (coarse_propagate3); iterate until delta_k <= tol (reading c5, FP64 norms) or
+ * k = Kmax.
  *  u_out        device float[(N+1)*M^3]: u_0 (the payoff) .. u_N on return
  *  k_done       host int: iterations performed;  defect_hist  host double[Kmax] or NULL
  * Synchronous.  Returns BS_OK (converged, or k_done = N: every slice exact), BS_ERR_MAXITER
  * (tol not met within Kmax < N), BS_ERR_ARG (as fine_propagate3, or N, steps, Kmax out of
- * range), BS_ERR_CUDA. */
+ * range), BS_ERR_NOCONV (a coarse BiCGSTAB solve hit its cap), BS_ERR_CUDA. */
 int parareal_solve3(int M, double xmax, const bs_params3* p, double T, int N, int fine_steps,
                     int coarse_steps, double tol, int Kmax, float* u_out, int* k_done,
                     double* defect_hist, bs_stream stream);

@@ -23,7 +23,7 @@ COARSE_NUM, COARSE_PINO = 0, 1
 EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "fine_propagate_batched", "coarse_propagate", "pino_load", "pino_destroy",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
-           "bs_coarse_variant", "bs_coarse_variant_info", "bs_payoff3", "fine_propagate3", "parareal_solve3", "bs_server_create", "bs_server_submit", "bs_server_progress",
+           "bs_coarse_variant", "bs_coarse_variant_info", "bs_payoff3", "fine_propagate3", "coarse_propagate3", "parareal_solve3", "bs_server_create", "bs_server_submit", "bs_server_progress",
            "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for",
            "bs_grid_set_coarse"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
@@ -111,6 +111,7 @@ def load(path: Optional[str] = None):
     lib.bs_coarse_variant_info.argtypes = [i, i, P(i), P(i), P(i), P(i), P(i)]
     lib.bs_payoff3.argtypes = [i, d, P(bs_params3), vp, vp]
     lib.fine_propagate3.argtypes = [i, d, P(bs_params3), P(vp), P(vp), P(d), i, d, i, vp]
+    lib.coarse_propagate3.argtypes = [i, d, P(bs_params3), vp, vp, d, d, i, vp]
     lib.parareal_solve3.argtypes = [i, d, P(bs_params3), d, i, i, i, d, i, vp, P(i), P(d), vp]
     lib.bs_server_create.argtypes = [P(bs_server_config), P(vp)]
     lib.bs_server_submit.argtypes = [vp, P(bs_request), P(C.c_longlong)]
@@ -226,6 +227,14 @@ def fine_propagate3(M: int, xmax: float, p, u_in: Sequence, u_out: Sequence, tau
     t0 = (C.c_double * B)(*[float(t) for t in tau0])
     return check(load().fine_propagate3(int(M), float(xmax), C.byref(bp), pin, pout, t0, B, float(dtau),
                                         int(nsteps), _stream(stream)))
+
+
+def coarse_propagate3(M: int, xmax: float, p, u_in, u_out, tau0: float, dtau_slice: float, nsteps: int,
+                      stream=None):
+    """Three-asset G: nsteps BiCGSTAB-solved implicit steps over dtau_slice (synchronous)."""
+    bp = to_params3(p)
+    return check(load().coarse_propagate3(int(M), float(xmax), C.byref(bp), _ptr(u_in), _ptr(u_out),
+                                          float(tau0), float(dtau_slice), int(nsteps), _stream(stream)))
 
 
 def parareal_solve3(M: int, xmax: float, p, T: float, N: int, fine_steps: int, coarse_steps: int,

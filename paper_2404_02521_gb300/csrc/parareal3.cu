@@ -1,13 +1,13 @@
-// Parareal (eq. parareal) for three assets: F and G are both the three-asset implicit-Euler
-// propagator of fine3.cu, G with fewer, larger steps (the numerical coarse model of Sec. 3.2
-// for n = 3; it must keep the Jacobi bound below 0.8, which limits the coarse step).  The
-// iteration runs from the host: F on slices k..N-1 in one batched call, then the serial sweep
+// Parareal (eq. parareal) for three assets: F is the Jacobi-stepped three-asset propagator of
+// fine3.cu, G the same implicit scheme with fewer, larger steps solved by BiCGSTAB
+// (krylov3.cu; the numerical coarse model of Sec. 3.2 for n = 3).  The iteration runs from
+// the host: F on slices k..N-1 in one batched call, then the serial sweep
 // n = k..N-1 of G, the correction u_{n+1} = F_n + (G_new - G_old_n) and the FP64 defect
 // norms (reading c5), with G skipped on the exact slice n = k (G_old_k is unchanged).
 #include <cmath>
 #include <vector>
 
-#include "common.cuh"
+#include "fine3.cuh"
 
 namespace bsp {
 
@@ -93,10 +93,9 @@ extern "C" int parareal_solve3(int M, double xmax, const bs_params3* p, double T
   double* norms = partials + (size_t)nblocks * 2;
   std::vector<double> hnorms(2 * (size_t)(N + 1), 0.0);
   auto U = [&](int n) { return u_out + (size_t)n * n3; };
-  auto G = [&](int n, float* out) -> int {   // G(u_n) over slice n
-    const float* in = U(n);
-    const double t0 = n * slice;
-    return fine_propagate3(M, xmax, p, &in, &out, &t0, 1, dtg, coarse_steps, stream);
+  auto G = [&](int n, float* out) -> int {   // G(u_n) over slice n: BiCGSTAB per coarse step
+    return coarse_propagate3_krylov(M, xmax, *p, U(n), out, n * slice, dtg, coarse_steps, g_opt.krylov_tol,
+                                    g_opt.krylov_maxit, s);
   };
   auto correct = [&](int mode, int n) -> int {
     p3_correct_kernel<<<nblocks, kP3Threads, 0, s>>>(mode, n3, U(n + 1), Fb + (size_t)n * n3, Gnew,

@@ -131,3 +131,8 @@ def test_three_asset_arguments_are_checked(lib):
             _lib.fine_propagate3(M, 4.0, p, fake, fake, [0.0], dtau, 1, stream=0)
     with pytest.raises(_lib.BSError):
         _lib.fine_propagate3(16, 4.0, ok, [], [], [], 0.001, 1, stream=0)
+    # G (BiCGSTAB) takes any step size, but not a bad grid, NULL states or an empty slice
+    for M, p, u, dts, ns in [(3, ok, 1 << 20, 0.1, 1), (16, ok, 0, 0.1, 1), (16, ok, 1 << 20, 0.0, 1),
+                             (16, ok, 1 << 20, 0.1, 0)]:
+        with pytest.raises(_lib.BSError):
+            _lib.coarse_propagate3(M, 4.0, p, u, u, 0.0, dts, ns, stream=0)

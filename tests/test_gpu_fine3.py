@@ -12,6 +12,7 @@ from tests.gpu_util import FP32_FINE_TOL, rel_err
 pytestmark = pytest.mark.gpu
 
 XMAX = 4.0
+COARSE_TOL = 2e-5   # G against the oracle's exact solves, BiCGSTAB run to 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -19,6 +20,15 @@ def bs():
     import paper_2404_02521_gb300 as bs
     bs.load()
     return bs
+
+
+@pytest.fixture
+def tight_g(bs):
+    """G's BiCGSTAB solves run to a relative residual of 1e-6 during the test (the oracle's G is
+    an exact solve); the library default is 1e-5."""
+    bs.bs_set_option(bs.OPT_KRYLOV_TOL, 1e-6)
+    yield
+    bs.bs_set_option(bs.OPT_KRYLOV_TOL, 1e-5)
 
 
 def params3(payoff):
@@ -133,3 +143,53 @@ def test_parareal3_matches_oracle_parareal(bs):
     assert rel_err(got, Uo) <= 1e-4
     serial = serial_fine3(bs, p, M, T, N, fs).cpu().double().numpy()
     assert rel_err(got, serial) <= 1e-3
+
+
+# steps of 0.1 and 0.025 at M = 12 and 21: Jacobi bounds near 0.8 and above, where the fine
+# propagator refuses the step; BiCGSTAB solves them
+@pytest.mark.usefixtures("tight_g")
+@pytest.mark.parametrize("M,nsteps", [(12, 1), (21, 4)])
+@pytest.mark.parametrize("payoff", [wl.BASKET, wl.EXCHANGE])
+def test_coarse3_matches_oracle(bs, M, nsteps, payoff):
+    import torch
+    p, slice_len, tau0 = params3(payoff), 0.1, 0.05
+    u0 = oracle_payoff(p, M)
+    ie = fd_nd.ImplicitEulerND(M, XMAX, p.sigma, rho_matrix(p), p.r, slice_len / nsteps, oracle_boundary(p))
+    uin = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(uin)
+    bs.coarse_propagate3(M, XMAX, p, uin, out, tau0, slice_len, nsteps)
+    torch.cuda.synchronize()
+    assert rel_err(out.cpu().double().numpy(), ie.propagate(u0, tau0, nsteps)) <= COARSE_TOL
+
+
+def test_coarse3_zero_state_stays_zero(bs):
+    # the degenerate case: a zero state under a zero far field (a basket call struck far above
+    # the grid) gives b = 0 every step, and the increment must be exactly 0
+    import torch
+    p, M = params3(wl.BASKET), 12
+    p.strike = 1e6                       # the far-field call value is 0 everywhere on the grid
+    u = torch.zeros((M, M, M), device="cuda")
+    out = torch.full_like(u, 7.0)
+    bs.coarse_propagate3(M, XMAX, p, u, out, 0.0, 0.1, 3)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("payoff", [wl.BASKET, wl.EXCHANGE])
+def test_parareal3_stiff_coarse_matches_oracle_parareal(bs, payoff):
+    # one coarse step per slice of 0.1 (Jacobi bound near 0.8): G by BiCGSTAB at the library
+    # default tolerance; the oracle's iteration count, iterate within 1e-4
+    import torch
+    from oracle import parareal as opr
+    p, M, T, N, fs, cs = params3(payoff), 12, 0.4, 4, 25, 1
+    U = torch.empty((N + 1, M, M, M), device="cuda")
+    rc, k, defects = bs.parareal_solve3(M, XMAX, p, T, N, fs, cs, 1e-4, N, U)
+    torch.cuda.synchronize()
+    sl = T / N
+    ieF = fd_nd.ImplicitEulerND(M, XMAX, p.sigma, rho_matrix(p), p.r, sl / fs, oracle_boundary(p))
+    ieG = fd_nd.ImplicitEulerND(M, XMAX, p.sigma, rho_matrix(p), p.r, sl / cs, oracle_boundary(p))
+    Uo, ko, do, _ = opr.parareal(oracle_payoff(p, M), lambda u, n: ieF.propagate(u, n * sl, fs),
+                                 lambda u, n: ieG.propagate(u, n * sl, cs), N, 1e-4, N)
+    assert rc == 0 and k == ko
+    got = U.cpu().double().numpy()
+    assert rel_err(got, Uo) <= 1e-4
