@@ -4,8 +4,10 @@
 // The iteration is driven from the host: each BiCGSTAB iteration is a short chain of kernels
 // (products with the 19-point stencil, vector updates, block partial sums) and one-block
 // kernels that add the partials in a fixed order and update the scalars in device memory;
-// the host reads the convergence flag once per iteration.  Each step starts from the previous
-// step's increment; a breakdown restarts from the current iterate.
+// the host reads the convergence flag once per kK3Batch iterations: once the device sets
+// conv or fail, the kernels of the iterations still queued return at once.  Each step starts
+// from the previous step's increment; a breakdown restarts from the current iterate.
+#include <algorithm>
 #include <cmath>
 
 #include "fine3.cuh"
@@ -14,6 +16,7 @@ namespace bsp {
 
 constexpr int kK3Threads = 256;
 constexpr int kK3Attempts = 3;
+constexpr int kK3Batch = 4;   // iterations queued per host check
 
 struct K3Vecs {
   float *x, *r, *rh, *p, *v, *s, *t, *id, *b;   // x is the F3 item's increment buffer dA
@@ -22,6 +25,7 @@ struct K3Vecs {
 struct K3Scal {
   float rho, alpha, omega, beta, stop2;
   int conv, fail, zero;   // zero: b^ vanishes, the solution is d = 0
+  int pending;            // omega or rho vanished: finish this iteration, then stop
 };
 
 // block partial sums of up to 4 values: warp butterfly, then warp 0 over the warp sums
@@ -57,6 +61,7 @@ enum { K3_INIT = 0, K3_V = 1, K3_S = 2, K3_T = 3, K3_UPDATE = 4 };
 // p = r + beta (p - omega v), partial (r, r).
 __global__ void __launch_bounds__(kK3Threads) k3_phase_kernel(const __grid_constant__ F3Batch fb, K3Vecs w,
                                                               const K3Scal* sc, int phase, float* partials) {
+  if (phase != K3_INIT && (sc->conv || sc->fail)) return;   // uniform: the iteration is over
   const int M = fb.M, n3 = M * M * M;
   const int e = blockIdx.x * kK3Threads + threadIdx.x;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -117,6 +122,7 @@ enum { K3F_START = 0, K3F_ALPHA = 1, K3F_OMEGA = 2, K3F_CONV = 3 };
 // One thread adds the block partials in block order and updates the scalars.
 __global__ void k3_finish_kernel(const float* partials, int nblocks, K3Scal* sc, int mode, float tol) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (mode != K3F_START && (sc->conv || sc->fail)) return;
   float t[4] = {0.f, 0.f, 0.f, 0.f};
   for (int b = 0; b < nblocks; ++b)
     for (int q = 0; q < 4; ++q) t[q] += partials[4 * b + q];
@@ -127,6 +133,7 @@ __global__ void k3_finish_kernel(const float* partials, int nblocks, K3Scal* sc,
       sc->zero = !(t[0] > 1e-30f) ? 1 : 0;
       sc->conv = (t[1] <= sc->stop2 || sc->zero) ? 1 : 0;
       sc->fail = 0;
+      sc->pending = 0;
       break;
     case K3F_ALPHA:
       if (t[0] == 0.f) { sc->fail = 1; sc->alpha = 0.f; break; }
@@ -136,13 +143,14 @@ __global__ void k3_finish_kernel(const float* partials, int nblocks, K3Scal* sc,
       const float om = t[1] > 0.f ? t[0] / t[1] : 0.f;
       const float rho_new = t[2] - om * t[3];
       sc->omega = om;
-      if (om == 0.f || sc->rho == 0.f) { sc->fail = 1; sc->beta = 0.f; break; }
+      if (om == 0.f || sc->rho == 0.f) { sc->pending = 1; sc->beta = 0.f; break; }
       sc->beta = (rho_new / sc->rho) * (sc->alpha / om);
       sc->rho = rho_new;
       break;
     }
     case K3F_CONV:
       sc->conv = t[0] <= sc->stop2 ? 1 : 0;
+      if (sc->pending) sc->fail = 1;
       break;
   }
 }
@@ -191,7 +199,7 @@ int coarse_propagate3_krylov(int M, double xmax, const bs_params3& p, const floa
       k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_INIT, partials);
       finish(K3F_START);
       K3Scal h = {};
-      for (int itn = 0; itn <= maxit; ++itn) {
+      for (int itn = 0; itn <= maxit;) {
         if (cudaMemcpyAsync(&h, dsc, sizeof(K3Scal), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
           rc = cuda_error(cudaGetLastError(), "three-asset coarse BiCGSTAB");
@@ -204,13 +212,17 @@ int coarse_propagate3_krylov(int M, double xmax, const bs_params3& p, const floa
           break;
         }
         if (h.fail || itn == maxit) break;
-        k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_V, partials);
-        finish(K3F_ALPHA);
-        k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_S, partials);
-        k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_T, partials);
-        finish(K3F_OMEGA);
-        k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_UPDATE, partials);
-        finish(K3F_CONV);
+        const int nb = std::min(kK3Batch, maxit - itn);
+        for (int b = 0; b < nb; ++b) {
+          k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_V, partials);
+          finish(K3F_ALPHA);
+          k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_S, partials);
+          k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_T, partials);
+          finish(K3F_OMEGA);
+          k3_phase_kernel<<<grid, kK3Threads, 0, s>>>(fb, w, dsc, K3_UPDATE, partials);
+          finish(K3F_CONV);
+        }
+        itn += nb;
       }
       if (rc == BS_OK && !conv && !h.fail) break;   // the iteration cap, not a breakdown
     }
