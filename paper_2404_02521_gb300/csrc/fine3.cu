@@ -66,18 +66,129 @@ __global__ void __launch_bounds__(kF3Threads) f3_phase_kernel(const __grid_const
   }
 }
 
-// One Jacobi sweep: d_new = (b + offdiag(d_old)) / diag at PDE nodes, 0 elsewhere.
-__global__ void __launch_bounds__(kF3Threads) f3_sweep_kernel(const __grid_constant__ F3Batch fb, int cur) {
-  const F3Item& it = fb.it[blockIdx.y];
-  const int M = fb.M, n3 = M * M * M;
-  const int e = blockIdx.x * kF3Threads + threadIdx.x;
-  if (e >= n3) return;
-  int i, j, k;
-  f3_node(e, M, i, j, k);
-  const float* din = cur ? it.dB : it.dA;
-  float* dout = cur ? it.dA : it.dB;
-  const bool pde = i < M - 1 && j < M - 1 && k < M - 1;
-  dout[e] = pde ? (it.b[e] + f3_offdiag(din, fb.c, M, i, j, k)) / f3_diag(fb.c, i, j, k) : 0.f;
+// Halo tile of one block: kF3TileI x kF3TileJ columns and kF3PlanesPerBlock planes plus one
+// node on every side, i fastest.  Entries outside the grid are 0 (their weights are 0 too).
+constexpr int kHI = kF3TileI + 2, kHJ = kF3TileJ + 2, kHK = kF3PlanesPerBlock + 2;
+constexpr int kTileFloats = kHI * kHJ * kHK;
+
+// Off-diagonal part of dtau R_h at the node of tile index L (column coefficients precomputed;
+// no guards: a neighbour at index -1 is 0 in the tile and has weight 0).
+struct F3Col {
+  float wxp, wxm, wyp, wym, cxy, cxz, cyz;
+};
+__device__ __forceinline__ float f3_tile_offdiag(const float* t, int L, const F3Col& w, float az, float mz,
+                                                 float fk) {
+  constexpr int X = 1, Y = kHI, Z = kHI * kHJ;
+  float acc = w.wxp * t[L + X];
+  acc = fmaf(w.wxm, t[L - X], acc);
+  acc = fmaf(w.wyp, t[L + Y], acc);
+  acc = fmaf(w.wym, t[L - Y], acc);
+  acc = fmaf(az + mz, t[L + Z], acc);
+  acc = fmaf(az - mz, t[L - Z], acc);
+  acc = fmaf(w.cxy, (t[L + X + Y] + t[L - X - Y]) - (t[L + X - Y] + t[L - X + Y]), acc);
+  acc = fmaf(w.cxz * fk, (t[L + X + Z] + t[L - X - Z]) - (t[L + X - Z] + t[L - X + Z]), acc);
+  acc = fmaf(w.cyz * fk, (t[L + Y + Z] + t[L - Y - Z]) - (t[L + Y - Z] + t[L - Y + Z]), acc);
+  return acc;
+}
+
+// One Jacobi sweep: d_new = (b + offdiag(d_old)) / diag at PDE nodes, 0 elsewhere.  A block
+// stages its halo tile of d_old in shared memory (every load independent, coalesced along i),
+// then each thread walks its column (i, j) up through the block's planes.  The first sweep of
+// a step also stages the state and forms b = dtau R_h hi (RHS); the last one also adds its
+// increment to (hi, lo) (APPLY) and writes the far faces of step face_step (FACE; -1: none).
+// A step has at least two sweeps, so no launch both reads the state's neighbours and writes
+// the state.
+enum { F3S_FIRST = 1, F3S_LAST = 2 };
+template <int FLAGS>
+__global__ void __launch_bounds__(kF3TileI * kF3TileJ, 4) f3_sweep_kernel(const __grid_constant__ F3Batch fb,
+                                                                         int cur, int tiles_i, int face_step) {
+  constexpr bool first = FLAGS & F3S_FIRST, last = FLAGS & F3S_LAST;
+  __shared__ float sd[kTileFloats];
+  __shared__ float sh[first ? kTileFloats : 1];
+  const F3Item& it = fb.it[blockIdx.z];
+  const int M = fb.M;
+  const int tj = blockIdx.x / tiles_i;   // uniform per block
+  const int i0 = (blockIdx.x - tj * tiles_i) * kF3TileI, j0 = tj * kF3TileJ;
+  const int k0 = blockIdx.y * kF3PlanesPerBlock;
+  const float* __restrict__ din = cur ? it.dB : it.dA;
+  float* __restrict__ dout = cur ? it.dA : it.dB;
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  const int col = j * M + i, sz = M * M;
+  const bool active = i < M && j < M, pdecol = i < M - 1 && j < M - 1;
+  // the column's own operands for every plane, loaded with the tile (no load waits per plane)
+  float bq[kF3PlanesPerBlock], hq[last ? kF3PlanesPerBlock : 1], lq[last ? kF3PlanesPerBlock : 1];
+#pragma unroll
+  for (int kk = 0; kk < kF3PlanesPerBlock; ++kk) {
+    const int k = k0 + kk, e = k * sz + col;
+    const bool pde = pdecol && k < M - 1;
+    if (!first) bq[kk] = pde ? __ldg(it.b + e) : 0.f;
+    if (last) {
+      hq[kk] = pde ? it.hi[e] : 0.f;
+      lq[kk] = pde ? it.lo[e] : 0.f;
+    }
+  }
+  for (int q = threadIdx.y * kF3TileI + threadIdx.x; q < kTileFloats; q += kF3TileI * kF3TileJ) {
+    const int ck = q / (kHI * kHJ);
+    const int rem = q - ck * (kHI * kHJ);
+    const int bj = rem / kHI;
+    const int gi = i0 - 1 + (rem - bj * kHI), gj = j0 - 1 + bj, gk = k0 - 1 + ck;
+    const bool in = gi >= 0 && gi < M && gj >= 0 && gj < M && gk >= 0 && gk < M;
+    const int ge = (gk * M + gj) * M + gi;
+    sd[q] = in ? __ldg(din + ge) : 0.f;
+    if (first) sh[q] = in ? __ldg(it.hi + ge) : 0.f;
+  }
+  __syncthreads();   // the only barrier: threads outside the grid leave after it
+  if (!active) return;
+  const int k1 = min(k0 + kF3PlanesPerBlock, M);
+  const bool face = last && face_step >= 0;
+  const float tau_face = it.tau0 + (face_step + 1) * fb.dtau;
+  if (!pdecol) {   // far-face column: no unknowns
+    for (int k = k0; k < k1; ++k) {
+      dout[k * sz + col] = 0.f;
+      if (face) it.hi[k * sz + col] = f3_far_field(fb, i, j, k, tau_face);
+    }
+    return;
+  }
+  const F3Coef& c = fb.c;
+  const float fi = (float)i, fj = (float)j;
+  const float ax = c.A[0] * (fi * fi), ay = c.A[1] * (fj * fj);
+  const float mx = c.D[0] * fi, my = c.D[1] * fj;
+  const F3Col w = {ax + mx, ax - mx, ay + my, ay - my, c.Cxy * (fi * fj), c.Cxz * fi, c.Cyz * fj};
+  const float dxy = 1.0f + 2.0f * (ax + ay) + c.rdt;
+  const int L0 = (1 * kHJ + threadIdx.y + 1) * kHI + threadIdx.x + 1;   // tile index of plane k0
+#pragma unroll
+  for (int kk = 0; kk < kF3PlanesPerBlock; ++kk) {
+    const int k = k0 + kk;
+    if (k >= k1) break;
+    const int e = k * sz + col;
+    if (k == M - 1) {
+      dout[e] = 0.f;   // far face
+      if (face) it.hi[e] = f3_far_field(fb, i, j, k, tau_face);
+      break;
+    }
+    const int L = L0 + kk * (kHI * kHJ);
+    const float fk = (float)k;
+    const float az = c.A[2] * (fk * fk), mz = c.D[2] * fk;
+    const float diag = dxy + 2.0f * az;
+    float bv;
+    if (first) {   // RHS: b = offdiag(hi) - (diag - 1) hi
+      bv = f3_tile_offdiag(sh, L, w, az, mz, fk) - (diag - 1.0f) * sh[L];
+      it.b[e] = bv;
+    } else {
+      bv = bq[kk];
+    }
+    const float dn = (bv + f3_tile_offdiag(sd, L, w, az, mz, fk)) / diag;
+    dout[e] = dn;
+    if (last) {   // APPLY: compensated add of the increment
+      const float h0 = hq[kk];
+      const float sm = h0 + dn, bb = sm - h0;
+      const float err = (h0 - (sm - bb)) + (dn - bb);
+      const float l = lq[kk] + err;
+      const float hn = sm + l;
+      it.lo[e] = l - (hn - sm);
+      it.hi[e] = hn;
+    }
+  }
 }
 
 // Gershgorin bound of I - dtau R_h over the PDE nodes: max of sum |off-diagonal| / diagonal.
@@ -217,17 +328,25 @@ int fine_propagate3(int M, double xmax, const bs_params3* p, const float* const*
       it.tau0 = (float)tau0[base + t];
     }
     const dim3 grid(blocks, nb);
+    const int tiles_i = (M + kF3TileI - 1) / kF3TileI, tiles_j = (M + kF3TileJ - 1) / kF3TileJ;
+    const dim3 sgrid((unsigned)(tiles_i * tiles_j), (unsigned)((M + kF3PlanesPerBlock - 1) / kF3PlanesPerBlock),
+                     (unsigned)nb);
+    const dim3 sblock(kF3TileI, kF3TileJ);
     f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_INIT, 0, 0);
+    if (nsteps > 0) f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_FACE, 0, 0);
     int cur = 0;   // 0: the increment is in dA
     for (int step = 0; step < nsteps; ++step) {
-      f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_FACE, step, cur);
-      f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_RHS, step, cur);
-      const int m = step == 0 ? m0 : m1;
+      const int m = step == 0 ? m0 : m1;   // >= 2
       for (int sw = 0; sw < m; ++sw) {
-        f3_sweep_kernel<<<grid, kF3Threads, 0, s>>>(fb, cur);
+        const int face_step = step + 1 < nsteps ? step + 1 : -1;
+        if (sw == 0)
+          f3_sweep_kernel<F3S_FIRST><<<sgrid, sblock, 0, s>>>(fb, cur, tiles_i, face_step);
+        else if (sw == m - 1)
+          f3_sweep_kernel<F3S_LAST><<<sgrid, sblock, 0, s>>>(fb, cur, tiles_i, face_step);
+        else
+          f3_sweep_kernel<0><<<sgrid, sblock, 0, s>>>(fb, cur, tiles_i, face_step);
         cur ^= 1;
       }
-      f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_APPLY, step, cur);
     }
     f3_phase_kernel<<<grid, kF3Threads, 0, s>>>(fb, F3_OUT, nsteps, cur);
     BS_CUDA_TRY(cudaGetLastError());

@@ -10,6 +10,8 @@ namespace bsp {
 
 constexpr int kF3MaxItems = 32;
 constexpr int kF3Threads = 256;
+constexpr int kF3TileI = 32, kF3TileJ = 8;   // sweep kernel: columns per block
+constexpr int kF3PlanesPerBlock = 8;         // sweep kernel: planes of k per thread
 
 struct F3Item {
   const float* in;
