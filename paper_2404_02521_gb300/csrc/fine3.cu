@@ -66,6 +66,13 @@ __global__ void __launch_bounds__(kF3Threads) f3_phase_kernel(const __grid_const
   }
 }
 
+// Asynchronous 4-byte global -> shared copy (all of a thread's copies in flight at once);
+// with ok == false the destination is zero-filled and nothing is read.
+__device__ __forceinline__ void f3_cp_async4(float* dst, const float* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+
 // Halo tile of one block: kF3TileI x kF3TileJ columns and kF3PlanesPerBlock planes plus one
 // node on every side, i fastest.  Entries outside the grid are 0 (their weights are 0 too).
 constexpr int kHI = kF3TileI + 2, kHJ = kF3TileJ + 2, kHK = kF3PlanesPerBlock + 2;
@@ -92,7 +99,7 @@ __device__ __forceinline__ float f3_tile_offdiag(const float* t, int L, const F3
 }
 
 // One Jacobi sweep: d_new = (b + offdiag(d_old)) / diag at PDE nodes, 0 elsewhere.  A block
-// stages its halo tile of d_old in shared memory (every load independent, coalesced along i),
+// stages its halo tile of d_old in shared memory (asynchronous copies, coalesced along i),
 // then each thread walks its column (i, j) up through the block's planes.  The first sweep of
 // a step also stages the state and forms b = dtau R_h hi (RHS); the last one also adds its
 // increment to (hi, lo) (APPLY) and writes the far faces of step face_step (FACE; -1: none).
@@ -133,10 +140,11 @@ __global__ void __launch_bounds__(kF3TileI * kF3TileJ, 4) f3_sweep_kernel(const 
     const int bj = rem / kHI;
     const int gi = i0 - 1 + (rem - bj * kHI), gj = j0 - 1 + bj, gk = k0 - 1 + ck;
     const bool in = gi >= 0 && gi < M && gj >= 0 && gj < M && gk >= 0 && gk < M;
-    const int ge = (gk * M + gj) * M + gi;
-    sd[q] = in ? __ldg(din + ge) : 0.f;
-    if (first) sh[q] = in ? __ldg(it.hi + ge) : 0.f;
+    const int ge = in ? (gk * M + gj) * M + gi : 0;
+    f3_cp_async4(sd + q, din + ge, in);
+    if (first) f3_cp_async4(sh + q, it.hi + ge, in);
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();   // the only barrier: threads outside the grid leave after it
   if (!active) return;
   const int k1 = min(k0 + kF3PlanesPerBlock, M);
