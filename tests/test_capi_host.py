@@ -136,3 +136,13 @@ def test_three_asset_arguments_are_checked(lib):
                              (16, ok, 1 << 20, 0.1, 0)]:
         with pytest.raises(_lib.BSError):
             _lib.coarse_propagate3(M, 4.0, p, u, u, 0.0, dts, ns, stream=0)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no CPU fallback: a library that cannot be loaded is an error, not a slower path
+    import subprocess
+    import sys
+    code = ("import paper_2404_02521_gb300._lib as L\n"
+            f"L.load({str(tmp_path / 'absent.so')!r})\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=str(ROOT), capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 and "OSError" in r.stderr
