@@ -20,6 +20,7 @@ workloads, one kernel each:
   resample1024  Parareal to K = N = 4 on 1024x1024 basket states with numerical G on the 256x256
              grid (bilinear restriction and prolongation kernels, 64 fine steps per slice)
   fine3_64   three-asset F: 16 states of 64^3 nodes, 64 implicit steps (19-point stencil)
+  coarse3_64 three-asset G: one 64^3 basket state, 4 BiCGSTAB-solved steps of 0.025
 """
 from __future__ import annotations
 
@@ -194,10 +195,23 @@ def case_fine3_64(bs, wl, torch):
     return lambda: bs.fine_propagate3(M, 4.0, p, list(U), list(F), [0.01 * b for b in range(B)], dtau, steps)
 
 
+def case_coarse3_64(bs, wl, torch):
+    # three assets: G over one slice of 0.1 (4 implicit steps) on one 64^3 basket state
+    import types
+    p = types.SimpleNamespace(sigma=(0.3, 0.2, 0.25), rho=(0.5, -0.3, 0.2), r=0.05, strike=1.0,
+                              w=(0.4, 0.35, 0.25), payoff=wl.BASKET)
+    M = 64
+    u = torch.empty((M, M, M), device="cuda")
+    bs.bs_payoff3(M, 4.0, p, u)
+    out = torch.empty_like(u)
+    return lambda: bs.coarse_propagate3(M, 4.0, p, u, out, 0.0, 0.1, 4)
+
+
 CASES = {"fine256": case_fine256, "coarse256": case_coarse256, "solve256": case_solve256,
          "tile1024": case_tile1024,
          "coarse512": case_coarse512, "pino128": case_pino128, "large1024": case_large1024,
-         "resample1024": case_resample1024, "fine3_64": case_fine3_64}
+         "resample1024": case_resample1024, "fine3_64": case_fine3_64,
+         "coarse3_64": case_coarse3_64}
 
 
 def main():
