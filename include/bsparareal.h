@@ -141,8 +141,9 @@ int fine_propagate3(int M, double xmax, const bs_params3* p, const float* const*
 
 /* G for three assets, one state: nsteps implicit-Euler steps of size dtau_slice/nsteps from
  * tau0 with the 19-point operator, each solved by BiCGSTAB on the Jacobi-scaled increment
- * system in FP32 to BS_OPT_KRYLOV_TOL (any step size).  Synchronous (the host checks
- * convergence every iteration).  Errors: BS_ERR_ARG (as bs_payoff3, NULL, dtau_slice <= 0,
+ * system in FP32 to BS_OPT_KRYLOV_TOL (any step size).  u_in, u_out: device float[M^3] (may
+ * alias).  Allocates its workspace stream-ordered (12 M^3 floats).  Synchronous (the host
+ * checks convergence every four iterations).  Errors: BS_ERR_ARG (as bs_payoff3, NULL, dtau_slice <= 0,
  * nsteps < 1), BS_ERR_NOCONV (BS_OPT_KRYLOV_MAXIT reached), BS_ERR_CUDA. */
 int coarse_propagate3(int M, double xmax, const bs_params3* p, const float* u_in, float* u_out,
                       double tau0, double dtau_slice, int nsteps, bs_stream stream);
