@@ -75,6 +75,11 @@ typedef struct {
 /* Message describing the last failure on this host thread ("" if none). */
 const char* bs_last_error(void);
 
+/* Number of device allocations (cudaMalloc, cudaMallocAsync) and pinned host allocations the
+ * library has made in this process, into *count (a diagnostic: it lets a caller check that a
+ * call allocated nothing).  Host-only.  BS_ERR_ARG for a NULL pointer. */
+int bs_device_allocations(long long* count);
+
 /* Create a grid of M x M nodes on [0, xmax]^2 (4 <= M <= 4096, xmax > 0).  Selects the
  * device that is current on the calling thread.  *g receives the handle. */
 int bs_grid_create(int M, double xmax, bs_grid** g);
@@ -317,14 +322,23 @@ int bs_phase_stats(bs_grid* g, double* fine_ms, int* fine_launches, double* coar
  * code on a latency-critical pricing path where a device allocation (which may synchronise
  * the whole device and take milliseconds) is not allowed, or code embedded in a host
  * framework that owns all device memory through its own allocator.  The paper has no
- * counterpart to this entry point; it computes what parareal_solve computes with
- * coarse_kind = BS_COARSE_NUM (same kernels, same results), but takes the grid as M and xmax
- * instead of a bs_grid handle and keeps its scratch (fine and coarse slice buffers, norms,
- * status) in one fixed device array inside the library: about 32 MiB, held by every GPU that
- * loads the library until the process exits.  It calls no cudaMalloc, cudaFree or
- * allocating library routine.
- *  - Capacity: N * M * M <= 4,194,304 and N <= 1024 (for example N = 64 slices of 256 x 256);
- *    larger problems return BS_ERR_ARG with a message naming the limit.
+ * counterpart to this entry point.  It runs the phase-by-phase Parareal iteration of
+ * parareal_solve with coarse_kind = BS_COARSE_NUM and BS_OPT_PIPELINE = 0 (F on all open
+ * slices, then the serial coarse sweep), with the same kernels, but takes the grid as M and
+ * xmax instead of a bs_grid handle and keeps its scratch (fine and coarse slice buffers,
+ * norms, status) in one fixed device array inside the library: about 32 MiB, held by every
+ * GPU that loads the library until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine (bs_device_allocations does not move across a call).
+ *  - Capacity: N * M * M <= 4,194,304, N <= 1024 and M <= 256 (grids whose state fits one
+ *    thread-block cluster; for example N = 64 slices of 256 x 256); larger problems return
+ *    BS_ERR_ARG with a message naming the limit.  Use parareal_solve beyond these limits.
+ *  - The fine step must have a Jacobi bound below 0.8 (bs_fine_sweeps(...) > 0): F runs the
+ *    Jacobi stepper only; other steps return BS_ERR_ARG.
+ *  - The coarse sweep uses the band variant that bs_coarse_variant has measured for M in this
+ *    process (by a parareal_solve or coarse_propagate call on an M x M grid, or by
+ *    bs_coarse_variant), else the default variant for M; it never runs the autotuner (which
+ *    allocates).  With the same variant the iterates equal parareal_solve's bit for bit; with
+ *    another they agree within the coarse Krylov tolerance (variants add in other orders).
  *  - The caller still owns u_out (device float[(N+1)*M*M]); k_done and defect_hist as in
  *    parareal_solve.  Synchronous, same return codes as parareal_solve.
  *  - The first call on a device looks up the array's device address (which may also load the

@@ -1,5 +1,6 @@
 // C ABI of the Black-Scholes Parareal library: handles, argument checks, the payoff kernel
 // (K6) and the Parareal driver loop (eq. parareal, Sec. 3.1).
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -109,11 +110,16 @@ BandShape band_shape(int M) {
   return s;
 }
 
+static std::atomic<long long> g_dev_allocs{0};
+
+void note_device_alloc() { g_dev_allocs.fetch_add(1, std::memory_order_relaxed); }
+
 int ensure(Workspace& w, size_t bytes) {
   if (w.bytes >= bytes) return BS_OK;
   if (w.ptr) cudaFree(w.ptr);
   w.ptr = nullptr;
   w.bytes = 0;
+  note_device_alloc();
   BS_CUDA_TRY(cudaMalloc(&w.ptr, bytes));
   w.bytes = bytes;
   return BS_OK;
@@ -188,6 +194,12 @@ extern "C" {
 
 const char* bs_last_error(void) { return g_err; }
 
+int bs_device_allocations(long long* count) {
+  if (!count) return set_error(BS_ERR_ARG, "bs_device_allocations: NULL argument");
+  *count = g_dev_allocs.load(std::memory_order_relaxed);
+  return BS_OK;
+}
+
 int bs_grid_create(int M, double xmax, bs_grid** out) {
   g_err[0] = 0;
   if (!out) return set_error(BS_ERR_ARG, "bs_grid_create: out is NULL");
@@ -201,6 +213,8 @@ int bs_grid_create(int M, double xmax, bs_grid** out) {
   std::memset(g->q_key, 0, sizeof(g->q_key));
   g->q_val = 0.0;
   cudaError_t e = cudaGetDevice(&g->device);
+  note_device_alloc();
+  note_device_alloc();
   if (e == cudaSuccess) e = cudaMalloc(&g->status, kStatusWords * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->status, 0, kStatusWords * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->dscal, 8 * sizeof(double));

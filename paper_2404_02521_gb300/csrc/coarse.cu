@@ -1459,6 +1459,7 @@ int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, in
   int best = default_variant(M);
   float best_ms = 1e30f;
   int rc = BS_OK;
+  note_device_alloc();
   if (cudaMalloc(&buf, 2 * MM * sizeof(float)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess) {
     rc = cuda_error(cudaGetLastError(), "coarse_autotune");

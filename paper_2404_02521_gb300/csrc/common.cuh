@@ -220,6 +220,9 @@ struct Workspace {
   size_t bytes = 0;
 };
 int ensure(Workspace& w, size_t bytes);
+// Counts a device allocation made by the library (every cudaMalloc / cudaMallocAsync /
+// cudaMallocHost site calls it; read by bs_device_allocations).
+void note_device_alloc();
 
 }  // namespace bsp
 

@@ -16,6 +16,7 @@
 // an ulp of u are not lost over tens of thousands of steps; b is evaluated from hi.
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "band.cuh"
 
@@ -279,22 +280,26 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
 }
 
 // ---------------------------------------------------------------------------------------
-// Cluster tiles for grids that do not fit one cluster (M > 256): one implicit step per launch,
-// or several launches per step when its sweeps exceed the halo.  A cluster of C CTAs owns a
-// region of 256 columns x 32C rows (CTA `rank` holds rows 32 rank .. 32 rank + 31 in the band
-// layout of band.cuh, so the rows between its CTAs are exchanged over DSMEM every sweep like
-// the band stepper's).  Only the region's outer edges are cut: they hold values that are not
-// updated, and every sweep's result is exact one node further from them, so after H sweeps
-// an interior of I x I nodes at offset (H, H) matches a whole-grid sweep bit for bit (the
-// domain edges need no halo: zero coefficients at x = 0, y = 0, Dirichlet at the far edges).
-// The grid is covered by ntx^2 such interiors.  (hi, lo, increment, previous increment) of
-// every node go to the other half of a ping-pong workspace; the increment slot holds the
-// next step's initial guess (extrapolated from the third step on, as in the band stepper).
-// A launch runs sweeps [s_begin, s_end) of the step; it applies the increment only if the
-// item's step ends in it, and copies an item whose step has already ended.
+// Cluster tiles for grids that do not fit one cluster (M > 256), temporally blocked: one launch
+// runs several whole implicit steps on a region (or, when a step's sweeps exceed the halo, a
+// part of that step's sweeps).  A cluster of C CTAs owns a region of 256 columns x 32C rows
+// (CTA `rank` holds rows 32 rank .. 32 rank + 31 in the band layout of band.cuh, so the rows
+// between its CTAs are exchanged over DSMEM every sweep like the band stepper's).  Only the
+// region's outer edges are cut: they hold values that are not updated, and every sweep's
+// result is exact one node further from them -- the first sweep of a step forms b from hi one
+// node further in, the last one applies the increment where it is exact, so the state stays
+// exact as far in as the increment.  After a launch's H sweeps in all (over all its steps) an
+// interior of I x I nodes at offset (H, H) matches a whole-grid solve bit for bit (the domain
+// edges need no halo: zero coefficients at x = 0, y = 0, Dirichlet at the far edges).  The
+// grid is covered by ntx^2 such interiors.  (hi, lo, increment, previous increment) of every
+// node go to the other half of a ping-pong workspace between launches, so HBM carries
+// 32 bytes per node per launch and 32 / s per node-step for s steps per launch; the
+// increment slot holds the next step's initial guess (extrapolated from the third step on,
+// as in the band stepper).  Where M is a multiple of 4 the region origin is too, and the
+// region arrives as 16-byte asynchronous copies; otherwise as 4-byte ones.
 // ---------------------------------------------------------------------------------------
 typedef BandCfg<256, 512, 16> CTileCfg;
-constexpr int kCTileMaxHalo = 32;   // sweeps per launch; the interior keeps >= 192 x 192 nodes
+constexpr int kCTileMaxHalo = 24;   // sweeps per launch (a multiple of 4); interiors keep >= 208 nodes
 
 struct CTileBatch {
   ItemDesc it[kMaxItems];
@@ -303,11 +308,50 @@ struct CTileBatch {
   float h;
 };
 
+// Asynchronous 16-byte global -> shared copy (L2 only); ok == false zero-fills.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0)
+               : "memory");
+}
+
+// The far-field value g(x_i, y_j, tau), compiled once: the tile stepper sets a step's far-field
+// data at two places (when a launch starts, or between two steps of a launch, depending on the
+// launch plan), and separately inlined copies of far_field may contract their products into
+// fused multiply-adds differently, which would make a result depend on the plan.
+__device__ __noinline__ float ctile_g(const PayoffF& pf, int i, int j, float h, float tau) {
+  return far_field(pf, (float)i * h, (float)j * h, tau);
+}
+
+// Far-field data at tau on this thread's own region rows (the column i = M - 1 and the row
+// j = M - 1), mirrored into the neighbours' halo rows by band_store.  The region's cut halo
+// rows are left as they are (they are beyond the exact part).
 template <class CFG>
+__device__ __forceinline__ void ctile_far_field(float* hi, const HaloPush& hp, const PayoffF& pf, float tau,
+                                                float h, int M, int ig, int jrow0, int r0, int col) {
+  if (ig < 0 || ig >= M) return;
+  if (ig == M - 1) {
+#pragma unroll
+    for (int k = 0; k < CFG::K; ++k) {
+      const int j = jrow0 + k;
+      if (j >= 0 && j < M) band_store<CFG>(hi, hp, r0 + k, col, ctile_g(pf, ig, j, h, tau));
+    }
+  } else {
+    const int k = M - 1 - jrow0;
+    if (k >= 0 && k < CFG::K) band_store<CFG>(hi, hp, r0 + k, col, ctile_g(pf, ig, M - 1, h, tau));
+  }
+}
+
+// Launch of steps [step0, step0 + nstep) of every item; with nstep == 1 only the sweeps
+// [s_begin, s_end) of that step (the step is applied if it ends in this launch).  `first`:
+// the state comes from the items' inputs (no increments yet); `last`: the result goes to the
+// items' outputs instead of the workspace.
+template <class CFG, int VEC>
 __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_constant__ CTileBatch tb,
-                                                                int step, int first, int last, int par,
-                                                                int s_begin, int s_end) {
+                                                                int step0, int nstep, int first, int last,
+                                                                int par, int s_begin, int s_end) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, PLANE = CFG::PLANE;
+  static_assert(VEC == 1 || VEC == 4, "4-byte or 16-byte copies");
   cg::cluster_group cluster = cg::this_cluster();
   const int C = tb.C;
   const int rank = (int)cluster.block_rank();
@@ -315,7 +359,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   const int M = tb.M, H = tb.H, I = tb.I;
   const size_t MM = (size_t)M * M;
   const int tx = (int)blockIdx.y % tb.ntx, ty = (int)blockIdx.y / tb.ntx;
-  const int ix0 = tx * I - H, jy0 = ty * I - H;   // region origin
+  const int ix0 = tx * I - H, jy0 = ty * I - H;   // region origin (multiples of VEC)
   const int jb = jy0 + rank * BH;                 // row of this CTA's first own row
   float* ws = tb.ws + (size_t)blockIdx.z * 8 * MM;
   const float* hi_g = first ? d.in : ws + (size_t)(par * 4 + 0) * MM;
@@ -338,35 +382,38 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   float* DP = dB + PLANE;   // previous increment, own rows [BH*NCOL]
   float* LO = DP + BH * NCOL;   // compensation words, own rows [BH*NCOL]
   float4* rowc = reinterpret_cast<float4*>(LO + BH * NCOL);
-  const float tau_new = (float)(d.tau0 + (step + 1) * d.dtau);
   // Own rows and both halo rows of hi and of the increment (the halo rows between CTAs are
-  // the neighbours' own rows now and are kept current by DSMEM pushes during the sweeps),
-  // and the own rows of the previous increment and of lo: asynchronous 4-byte copies, all in
-  // flight at once, zero-filled outside the domain.
-  for (int e = tid; e < PLANE; e += CFG::NT) {
+  // the neighbours' own rows and are kept current by DSMEM pushes during the sweeps), and
+  // the own rows of the previous increment and of lo: asynchronous copies, all in flight at
+  // once, zero-filled outside the domain (with VEC = 4 a chunk lies wholly inside or outside:
+  // M and the region origin are multiples of 4).
+  for (int e = tid * VEC; e < PLANE; e += CFG::NT * VEC) {
     const int pr = e / NCOL, c = e % NCOL;
     const int j = jb + pr - 1, i = ix0 + c;
     const bool in = (i >= 0 && i < M && j >= 0 && j < M);
     const size_t gi = in ? (size_t)j * M + i : 0;
-    cp_async4(hi + e, hi_g + gi, in);
-    cp_async4(dA + e, dv_g + gi, in && !first);
+    if constexpr (VEC == 4) {
+      cp_async16(hi + e, hi_g + gi, in);
+      cp_async16(dA + e, dv_g + gi, in && !first);
+      cp_async16(dB + e, dv_g + gi, in && !first);
+    } else {
+      cp_async4(hi + e, hi_g + gi, in);
+      cp_async4(dA + e, dv_g + gi, in && !first);
+      cp_async4(dB + e, dv_g + gi, in && !first);
+    }
   }
-  for (int e = tid; e < BH * NCOL; e += CFG::NT) {
+  for (int e = tid * VEC; e < BH * NCOL; e += CFG::NT * VEC) {
     const int r = e / NCOL, c = e % NCOL;
     const int j = jb + r, i = ix0 + c;
     const bool in = (i >= 0 && i < M && j >= 0 && j < M);
     const size_t gi = in ? (size_t)j * M + i : 0;
-    cp_async4(DP + e, dp_g + gi, in && !first);
-    cp_async4(LO + e, lo_g + gi, in && !first);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  for (int e = tid; e < PLANE; e += CFG::NT) {
-    const int pr = e / NCOL, c = e % NCOL;
-    const int j = jb + pr - 1, i = ix0 + c;
-    if ((i == M - 1 && j >= 0 && j < M) || (j == M - 1 && i >= 0 && i < M))
-      hi[e] = far_field(pf, i * tb.h, j * tb.h, tau_new);
-    dB[e] = dA[e];
+    if constexpr (VEC == 4) {
+      cp_async16(DP + e, dp_g + gi, in && !first);
+      cp_async16(LO + e, lo_g + gi, in && !first);
+    } else {
+      cp_async4(DP + e, dp_g + gi, in && !first);
+      cp_async4(LO + e, lo_g + gi, in && !first);
+    }
   }
   for (int r = tid; r < BH; r += CFG::NT) {
     float cs, cn, gj;
@@ -376,6 +423,21 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   const int ig = ix0 + col;
   float ce = 0.f, cw = 0.f, cgi = 0.f;
   column_coefs(d, ig, ce, cw, cgi);
+  cp_async_wait_all();
+  __syncthreads();
+  // the far-field data of the first step on every plane row this thread covers (own rows and,
+  // for the edge groups, the halo row next to them), locally: the neighbours' halo rows are
+  // still being loaded
+  {
+    const float tau_new = (float)(d.tau0 + (step0 + 1) * d.dtau);
+    const int pa = grp == 0 ? 0 : r0 + 1, pb = grp == CFG::G - 1 ? BH + 1 : r0 + K;
+    if (ig >= 0 && ig < M) {
+      for (int pr = pa; pr <= pb; ++pr) {
+        const int j = jb + pr - 1;
+        if (j >= 0 && j < M && (ig == M - 1 || j == M - 1)) hi[pr * NCOL + col] = ctile_g(pf, ig, j, tb.h, tau_new);
+      }
+    }
+  }
   float dv[K], b[K], invd[K], lo[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -392,33 +454,45 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   const HaloPush hi_push = halo_push<CFG>(cluster, hi, rank, C);
   const HaloPush pA = halo_push<CFG>(cluster, dA, rank, C);
   const HaloPush pB = halo_push<CFG>(cluster, dB, rank, C);
-  const int m_item = step_sweeps(d, step);
-  const int nsw = max(0, min(s_end, m_item) - s_begin);
-  const bool commit = nsw > 0 && min(s_end, m_item) == m_item;
   cluster_barrier(cluster, C);   // every CTA's loads are done before the first push lands
 
   cl_arrive();
   int p = 0;
-  for (int s = 0; s < nsw; ++s) {
-    const float* rd = p ? dB : dA;
-    float* wr = p ? dA : dB;
-    const HaloPush& wp = p ? pA : pB;
-    const bool fst = s == 0, lst = commit && s == nsw - 1;
-    if (fst && lst)
-      fine_sweep<CFG, true, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                  cgi, rdt, true, DP, step + 1 >= d.xstart);
-    else if (fst)
-      fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                   cgi, rdt, true);
-    else if (lst)
-      fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                   cgi, rdt, true, DP, step + 1 >= d.xstart);
-    else
-      fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                    cgi, rdt, true);
-    p ^= 1;
-    cl_arrive();
-    __syncthreads();
+  for (int t = 0; t < nstep; ++t) {
+    const int step = step0 + t;
+    const int m_item = step_sweeps(d, step);
+    const int sa = nstep == 1 ? s_begin : 0;
+    const int sb = nstep == 1 ? min(s_end, m_item) : m_item;
+    const int nsw = max(0, sb - sa);
+    const bool commit = nsw > 0 && sb == m_item;
+    const bool extrap = step + 1 >= d.xstart;
+    for (int s = 0; s < nsw; ++s) {
+      const float* rd = p ? dB : dA;
+      float* wr = p ? dA : dB;
+      const HaloPush& wp = p ? pA : pB;
+      const bool fst = s == 0, lst = commit && s == nsw - 1;
+      if (fst && lst)
+        fine_sweep<CFG, true, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                    cgi, rdt, true, DP, extrap);
+      else if (fst)
+        fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                     cgi, rdt, true);
+      else if (lst)
+        fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                     cgi, rdt, true, DP, extrap);
+      else
+        fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                      cgi, rdt, true);
+      // After the second sweep of a step every CTA has passed the first one, which read hi:
+      // move the far-field data on to the next step of this launch (the last sweep writes
+      // only PDE nodes, so this may follow it directly).
+      if (s == 1 && t + 1 < nstep)
+        ctile_far_field<CFG>(hi, hi_push, pf, (float)(d.tau0 + (step + 2) * d.dtau), tb.h, M, ig, jb + r0, r0,
+                             col);
+      p ^= 1;
+      cl_arrive();
+      __syncthreads();
+    }
   }
   cl_wait();   // no CTA leaves while a neighbour may still store into it
 
@@ -452,9 +526,6 @@ __global__ void ctile_finish_kernel(const __grid_constant__ CTileBatch tb) {
   if (e < MM) d.out[e] = ws[4 * MM + e] + ws[5 * MM + e];
 }
 
-// Launches of one step whose largest sweep count is m: the step is split evenly.
-static int ctile_launches_per_step(int m) { return (m + kCTileMaxHalo - 1) / kCTileMaxHalo; }
-
 // The largest sweep count of any item in step `step`.
 static int max_step_sweeps(const ItemDesc* items, int n, int step) {
   int m = 1;
@@ -462,15 +533,77 @@ static int max_step_sweeps(const ItemDesc* items, int n, int step) {
   return m;
 }
 
+// One launch of the tile stepper: steps [step0, step0 + nstep), or sweeps [s0, s1) of step0
+// (nstep == 1), with H sweeps in all (the halo).
+struct CTileLaunch {
+  int step0, nstep, s0, s1, H;
+};
+
+// Launch plan: whole steps are packed into a launch while their sweeps (the largest count of
+// any item, step by step) add up to at most kCTileMaxHalo; a step with more sweeps than that is
+// split evenly over several launches.
+static void ctile_plan(const ItemDesc* items, int n, int nsteps, std::vector<CTileLaunch>& plan) {
+  plan.clear();
+  int step = 0;
+  while (step < nsteps) {
+    const int m = max_step_sweeps(items, n, step);
+    if (m > kCTileMaxHalo) {
+      const int nl = (m + kCTileMaxHalo - 1) / kCTileMaxHalo;
+      const int chunk = (m + nl - 1) / nl;
+      for (int l = 0; l < nl; ++l) {
+        const int s0 = l * chunk, s1 = std::min(m, s0 + chunk);
+        plan.push_back({step, 1, s0, s1, s1 - s0});
+      }
+      ++step;
+      continue;
+    }
+    int h = m, k = 1;
+    while (step + k < nsteps) {
+      const int mk = max_step_sweeps(items, n, step + k);
+      if (h + mk > kCTileMaxHalo) break;
+      h += mk;
+      ++k;
+    }
+    plan.push_back({step, k, 0, 1 << 30, h});
+    step += k;
+  }
+}
+
+// Region geometry of a launch with h sweeps: halo H (a multiple of 4 with 16-byte copies), ntx
+// interiors of I nodes per axis, clusters of C CTAs.
+static void ctile_geometry(int M, int h, bool vec, CTileBatch& tb) {
+  const int NC = CTileCfg::NCOL;
+  const int H = vec ? ((std::max(2, h) + 3) / 4) * 4 : std::max(2, h);
+  int ntx = (M + (NC - 2 * H) - 1) / (NC - 2 * H);
+  int I;
+  for (;; ++ntx) {
+    I = (M + ntx - 1) / ntx;
+    if (vec) I = ((I + 3) / 4) * 4;
+    if (I + 2 * H <= NC) break;
+  }
+  tb.H = H;
+  tb.I = I;
+  tb.ntx = ntx;
+  tb.C = (I + 2 * H + CTileCfg::BH - 1) / CTileCfg::BH;
+}
+
+static size_t ctile_smem() {
+  return (size_t)3 * CTileCfg::PLANE * sizeof(float) + (size_t)2 * CTileCfg::BH * CTileCfg::NCOL * sizeof(float) +
+         (size_t)CTileCfg::BH * sizeof(float4);
+}
+
 static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
   const int M = g->M;
   const size_t MM = (size_t)M * M;
   int rc = ensure(const_cast<bs_grid*>(g)->ws_fine, (size_t)std::min(n, kMaxItems) * 8 * MM * sizeof(float));
   if (rc) return rc;
-  const size_t smem = (size_t)3 * CTileCfg::PLANE * sizeof(float) +
-                      (size_t)2 * CTileCfg::BH * CTileCfg::NCOL * sizeof(float) + (size_t)CTileCfg::BH * sizeof(float4);
-  auto kern = fine_ctile_kernel<CTileCfg>;
+  const size_t smem = ctile_smem();
+  // 16-byte copies need M and every input state 16-byte aligned (the workspace is)
+  bool vec = M % 4 == 0;
+  for (int k = 0; k < n; ++k) vec = vec && ((uintptr_t)items[k].in % 16 == 0);
+  auto kern = vec ? fine_ctile_kernel<CTileCfg, 4> : fine_ctile_kernel<CTileCfg, 1>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  std::vector<CTileLaunch> plan;
   for (int base = 0; base < n; base += kMaxItems) {
     CTileBatch tb;
     tb.n = std::min(n - base, kMaxItems);
@@ -478,41 +611,32 @@ static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nst
     tb.ws = (float*)g->ws_fine.ptr;
     tb.M = M;
     tb.h = (float)(g->xmax / (M - 1));
+    ctile_plan(tb.it, tb.n, nsteps, plan);
     int par = 0;
-    bool pending_finish = false;
-    for (int step = 0; step < nsteps; ++step) {
-      const int m = max_step_sweeps(tb.it, tb.n, step);
-      const int nl = ctile_launches_per_step(m);
-      const int chunk = (m + nl - 1) / nl;
-      for (int l = 0; l < nl; ++l) {
-        const int s0 = l * chunk, s1 = std::min(m, s0 + chunk);
-        tb.H = std::max(2, s1 - s0);
-        tb.ntx = (M + (CTileCfg::NCOL - 2 * tb.H) - 1) / (CTileCfg::NCOL - 2 * tb.H);
-        tb.I = (M + tb.ntx - 1) / tb.ntx;
-        tb.C = (tb.I + 2 * tb.H + CTileCfg::BH - 1) / CTileCfg::BH;
-        const bool first = step == 0 && l == 0;
-        const bool final_launch = step == nsteps - 1 && l == nl - 1;
-        // A launch that reads u_in must not write u_out (they may alias): keep its result in
-        // the workspace and form u_out in a separate pass.
-        pending_finish = final_launch && first;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(tb.C, tb.ntx * tb.ntx, tb.n);
-        cfg.blockDim = dim3(CTileCfg::NT, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = tb.C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        BS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, tb, step, (int)first, (int)(final_launch && !first), par,
-                                       s0, s1));
-        par ^= 1;
-      }
+    const int nl = (int)plan.size();
+    for (int l = 0; l < nl; ++l) {
+      const CTileLaunch& L = plan[(size_t)l];
+      ctile_geometry(M, L.H, vec, tb);
+      const bool first = l == 0, final_launch = l == nl - 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(tb.C, tb.ntx * tb.ntx, tb.n);
+      cfg.blockDim = dim3(CTileCfg::NT, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = tb.C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      // A launch that reads u_in must not write u_out (they may alias): a single launch keeps
+      // its result in the workspace and u_out is formed in a separate pass.
+      BS_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, tb, L.step0, L.nstep, (int)first, (int)(final_launch && !first),
+                                     par, L.s0, L.s1));
+      par ^= 1;
     }
-    if (pending_finish) {
+    if (nl == 1) {
       ctile_finish_kernel<<<dim3((unsigned)((MM + 255) / 256), tb.n), 256, 0, s>>>(tb);
       BS_CUDA_TRY(cudaGetLastError());
     }
@@ -525,11 +649,11 @@ int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps) {
   if (g->shape.C >= 1 && g->shape.C <= kMaxCluster) return chunks;
   if (nsteps < 1) return 0;
   int total = 0;
+  std::vector<CTileLaunch> plan;
   for (int base = 0; base < n; base += kMaxItems) {
     const int nb = std::min(n - base, kMaxItems);
-    for (int step = 0; step < nsteps; ++step)
-      total += ctile_launches_per_step(max_step_sweeps(items + base, nb, step));
-    if (nsteps == 1 && ctile_launches_per_step(max_step_sweeps(items + base, nb, 0)) == 1) total += 1;
+    ctile_plan(items + base, nb, nsteps, plan);
+    total += (int)plan.size() + (plan.size() == 1 ? 1 : 0);
   }
   return total;
 }

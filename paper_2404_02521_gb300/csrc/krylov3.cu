@@ -163,6 +163,7 @@ int coarse_propagate3_krylov(int M, double xmax, const bs_params3& p, const floa
   const int nblocks = (int)((n3 + kK3Threads - 1) / kK3Threads);
   float* ws = nullptr;
   const size_t fl = 12 * n3 + (size_t)4 * nblocks;
+  note_device_alloc();
   BS_CUDA_TRY(cudaMallocAsync((void**)&ws, fl * sizeof(float) + sizeof(K3Scal), s));
   F3Batch fb = f3_batch(M, xmax, p, dtau);
   fb.n = 1;

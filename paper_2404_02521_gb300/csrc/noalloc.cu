@@ -70,14 +70,18 @@ extern "C" int parareal_solve_noalloc(int M, double xmax, const bs_params* p, in
                      (size_t)N * M * M, kNoAllocMaxNM2, kNoAllocMaxN);
   const BandShape shape = band_shape(M);
   if (shape.C < 1 || shape.C > kMaxCluster)
-    return set_error(BS_ERR_ARG, "parareal_solve_noalloc: grid M=%d not supported", M);
+    return set_error(BS_ERR_ARG,
+                     "parareal_solve_noalloc: M=%d exceeds the limit M <= 256 (grids that fit one "
+                     "thread-block cluster); use parareal_solve", M);
   const double slice = p->T / N;
   const double dtau_f = slice / fine_steps;
   const double q = jacobi_contraction(M, *p, dtau_f);
   const int sweeps = sweeps_for(q, START_WARM), sweeps0 = sweeps_for(q, START_COLD);
   const int sweepsx = sweeps_for(q, START_EXTRAP), sweepsxl = sweeps_for(q, START_EXTRAP_LATE);
   if (sweeps == 0)
-    return set_error(BS_ERR_ARG, "parareal_solve_noalloc: Jacobi contraction %.3f >= 0.8", q);
+    return set_error(BS_ERR_ARG,
+                     "parareal_solve_noalloc: the fine step's Jacobi bound %.3f is >= 0.8 (only the "
+                     "Jacobi stepper runs without allocation); use more fine steps or parareal_solve", q);
 
   unsigned char* base = nullptr;
   if ((rc = noalloc_scratch(&base))) return rc;

@@ -84,6 +84,7 @@ extern "C" int parareal_solve3(int M, double xmax, const bs_params3* p, double T
   const int nblocks = (int)std::min<size_t>((n3 + kP3Threads - 1) / kP3Threads, kP3Blocks);
   const size_t fbytes = ((2 * (size_t)N + 1) * n3 * sizeof(float) + 255) / 256 * 256;
   unsigned char* ws = nullptr;
+  note_device_alloc();
   BS_CUDA_TRY(cudaMallocAsync((void**)&ws, fbytes + (size_t)nblocks * 2 * sizeof(double) +
                                                (size_t)(N + 1) * 2 * sizeof(double), s));
   float* Fb = reinterpret_cast<float*>(ws);

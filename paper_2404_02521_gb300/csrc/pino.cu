@@ -68,6 +68,7 @@ struct bs_pino {
 namespace bsp {
 
 static int dev_alloc(void** p, size_t bytes) {
+  note_device_alloc();
   BS_CUDA_TRY(cudaMalloc(p, bytes));
   return BS_OK;
 }

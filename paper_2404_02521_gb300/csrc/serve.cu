@@ -390,6 +390,7 @@ int bs_server_create(const bs_server_config* cfg, bs_server** out) {
   bs_server* sv = new bs_server();
   sv->cfg = *cfg;
   cudaError_t e = cudaGetDevice(&sv->device);
+  note_device_alloc();
   if (e == cudaSuccess) e = cudaMalloc(&sv->arena_base, cfg->hbm_budget_bytes);
   if (e != cudaSuccess) {
     delete sv;
@@ -400,6 +401,8 @@ int bs_server_create(const bs_server_config* cfg, bs_server** out) {
   for (Slot& sl : sv->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    note_device_alloc();
+    note_device_alloc();
     if (e == cudaSuccess) e = cudaMallocHost(&sl.h_defect, sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&sl.h_status, sizeof(int));
   }

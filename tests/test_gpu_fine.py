@@ -67,6 +67,26 @@ def test_fine_tiles_match_oracle(bs, M, pi):
     assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
 
 
+@pytest.mark.parametrize("M,pi,nsteps", [(300, 1, 40), (301, 2, 40), (516, 0, 24)])
+def test_tile_temporal_blocking_matches_oracle(bs, M, pi, nsteps):
+    # several whole implicit steps per tile launch (the halo grows with the launch's sweeps):
+    # long enough to reach the late two- and three-sweep steps; M = 301 runs the 4-byte copy
+    # path (M not a multiple of 4), M = 300 and 516 the 16-byte one
+    import torch
+    p = PARAMS[pi]
+    dtau = dtau_for(M, p)
+    u0 = start_state(M, 4.0, p, "random", seed=M + nsteps)
+    g = bs.Grid(M, 4.0)
+    uin = to_gpu(u0)
+    out = torch.empty_like(uin)
+    bs.fine_propagate_batched(g, [p], [uin], [out], [0.05], [dtau], nsteps)
+    inplace = uin.clone()
+    bs.fine_propagate_batched(g, [p], [inplace], [inplace], [0.05], [dtau], nsteps)
+    torch.cuda.synchronize()
+    assert torch.equal(out, inplace)
+    assert rel_err(to_np(out), oracle_fine(M, 4.0, p, u0, 0.05, dtau, nsteps)) <= FP32_FINE_TOL
+
+
 def test_tile_step_split_over_launches(bs):
     # the cold first step needs more sweeps than one tile launch's halo holds: it runs as
     # two launches (the first leaves the increment unapplied); an item with fewer sweeps in
