@@ -1,23 +1,28 @@
 """Benchmark: Parareal time-to-tolerance vs serial fine stepping on one GB300.
 
-One step = Parareal (eq. parareal, numerical coarse model) to tol 1e-4 on the exchange
-option workload: 256x256 nodes on [0,4]^2, sigma1=0.25, sigma2=0.35, r=0.03, T=1, N=64 slices
-of 512 implicit-Euler fine steps and 4 coarse steps, for each rho in {-0.5, 0, 0.7}.
+One step = one Parareal solve (eq. parareal) to tol 1e-4 of the large single solve: a basket
+call max(0.5 x + 0.5 y - 1, 0) on a 1024 x 1024 grid over [0,4]^2 (sigma1=0.3, sigma2=0.2,
+rho=0.5, r=0.05, T=1), N=128 slices of 1024 implicit-Euler fine steps (FP32, temporally
+blocked cluster tiles), FP64 defect norms, numerical coarse model with 4 steps per slice on
+the 256 x 256 grid (bilinear restriction and prolongation).
 
   value   serial-fine-equivalent grid-point updates per second delivered by Parareal
-          (sum over the step's solves of M*M*N*fine_steps / device time of the step)
+          (M*M*N*fine_steps per solve / device time of the solve)
   e2e     the same through parareal_solve with host buffers: the initial state is copied
           from pinned host memory and the price surface u_N read back inside the timed region
-  roofline      the coarse sweep or F, whichever has the larger event-timed share: algorithmic
-                FP32 FLOP per second against the FP32 peak of 152 SMs at the measured maximum
-                clock, with the DRAM bytes per launch from a committed ncu capture
+  roofline      the fine stepper (the dominant kernel): algorithmic FP32 FLOP per second
+                against the FP32 peak of the device's SMs at the measured maximum clock,
+                with its DRAM bytes per launch from a committed ncu capture
                 (profiles/traffic.json) while the kernel's sources are unchanged
-  kernels       per-kernel event times, launches, rates and solver statistics
-  cpu_baseline  the FP64 oracle on one host core, bounded sample of the same workload
+  kernels       per-kernel event times, launches, rates and sweep counts
+  exchange256   the 256 x 256 exchange-option workload (N=64 x 512 fine steps, rho in
+                {-0.5, 0, 0.7}): time to tolerance, serial fine, coarse-sweep statistics
+  cpu_baseline  the FP64 oracle on one host core, a bounded sample of the large solve's
+                serial fine stepping (one sparse LU factorisation, then implicit steps)
   clocks        nvidia-smi SM clock samples and throttle reasons during the timed region
   gpu_launches  the library's kernel launches inside the timed region (its own counters)
-  serving       the serving sample: the first requests of the seeded trace replayed through
-                the server at 0.8 of the measured one-at-a-time capacity (p50/p99 latency)
+  serving       the serving sample: requests of the seeded trace replayed through the server
+                (p50/p99 latency, solves/s against one request at a time)
 
 --impl reference times the FP64 CPU oracle (oracle/) on the host cores on a bounded sample
 of the same workload, in the same unit.
@@ -56,17 +61,22 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 issue peak of the fine stepper's bound: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA)
-# x the maximum SM clock.
-def fp32_peak_tflops(sm_mhz):
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def sm_count(dev_index=0):
+    """Streaming multiprocessors of the device (queried, not assumed)."""
+    import torch
+    return int(torch.cuda.get_device_properties(dev_index).multi_processor_count)
+
+
+# FP32 peak of an ALU-bound kernel: SMs x 128 FP32 lanes x 2 FLOP (FMA) x the maximum SM clock.
+def fp32_peak_tflops(sm_mhz, sms):
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # Algorithmic FLOPs of one fine point-step with m Jacobi sweeps: each sweep is the 9-point
 # update (5 FMA + 3 add + 1 multiply = 14 FLOP), plus b = dtau R_h w (16 FLOP), the
 # compensated update (8 FLOP) and the next step's extrapolated guess (1 FMA = 2 FLOP) once
-# per step.  A launch of s steps takes m0 sweeps in its first (cold) step, m1 in the second
-# (warm start), mx in steps 2-15 and mxl after them (extrapolated starts).
+# per step.  A propagation of s steps takes m0 sweeps in its first (cold) step, m1 in the
+# second (warm start), mx in steps 2-15 and mxl after them (extrapolated starts).
 def fine_flops_per_point_step(m):
     return 14 * m + 26
 
@@ -82,12 +92,23 @@ def fine_flops_per_point_launch(m0, m1, mx, mxl, steps):
     return f
 
 
+def fine_sweeps_total(m0, m1, mx, mxl, steps):
+    t = 0
+    for step in range(steps):
+        t += m0 if step == 0 else m1 if step < EXTRAP_START else mx if step < EXTRAP_LATE else mxl
+    return t
+
+
 # Algorithmic FLOPs of one BiCGSTAB iteration per node of the coarse solve: two Jacobi-scaled
 # 9-point products (15 FLOP each: 4 FMA, 2 multiplies, 3 adds), six dot-product terms (12) and
 # the vector updates s, x, r, p (13).  Band variants with the polynomial preconditioner
 # M^{-1} = 2I - A^ evaluate two more scaled products and 2 y - A^ y twice (+34).
 COARSE_FLOPS_PER_NODE_ITER = 55
 COARSE_FLOPS_POLY_EXTRA = 34
+
+# Algorithmic HBM bytes of the fine stepper per grid point and launch: the state read and
+# written once in FP32 (8 B); a launch that blocks s steps moves 8 / s B per point-step.
+FINE_ALG_BYTES_PER_POINT_LAUNCH = 8
 
 
 class ClockSampler:
@@ -176,6 +197,8 @@ def barrier(world):
 
 
 KERNEL_SOURCES = {
+    "fine_ctile_kernel": ["paper_2404_02521_gb300/csrc/fine.cu", "paper_2404_02521_gb300/csrc/band.cuh",
+                          "paper_2404_02521_gb300/csrc/common.cuh"],
     "fine_band_kernel": ["paper_2404_02521_gb300/csrc/fine.cu", "paper_2404_02521_gb300/csrc/band.cuh",
                          "paper_2404_02521_gb300/csrc/common.cuh"],
     "sweep_band_kernel": ["paper_2404_02521_gb300/csrc/coarse.cu", "paper_2404_02521_gb300/csrc/band.cuh",
@@ -183,8 +206,9 @@ KERNEL_SOURCES = {
 }
 
 
-def traffic_for(kernel, source_files):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+def traffic_entry(kernel):
+    """The committed ncu figures of a kernel (profiles/traffic.json), if its sources are
+    unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -194,198 +218,230 @@ def traffic_for(kernel, source_files):
     if not ent:
         return None
     h = hashlib.sha256()
-    for s in source_files:
+    for s in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, s), "rb") as f:
             h.update(f.read())
     if ent.get("source_sha256") != h.hexdigest():
         return None
-    return ent.get("dram_bytes_per_launch_full")
+    return ent
 
 
-def gpu_arm(args, world, rank, local):
-    import numpy as np
+def timed(stream, fn):
+    """Device time of fn() in ms, CUDA events on the launching stream."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def large_arm(args, world, local):
+    """The headline: Parareal on the 1024 x 1024 basket (numerical G on 256 x 256)."""
     import torch
 
     import paper_2404_02521_gb300 as bs
 
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    bs.load()
+    stream = torch.cuda.current_stream(dev)
+    pb = wl.large_cfg4()
+    M, N = pb.M, pb.N
+    g = bs.Grid(M, pb.xmax)
+    g.set_coarse(256)
+    U = torch.empty((N + 1, M, M), device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    bs.bs_set_option(bs.OPT_PHASE_TIMING, 1)
+
+    def solve(flags=0):
+        rc, k, d = bs.parareal_solve(g, pb.params, N, pb.fine_steps, bs.COARSE_NUM | flags, pb.coarse_steps,
+                                     None, pb.tol, N, U, stream)
+        return k, d
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    bs.bs_phase_stats(g)
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, ks, defects = 0.0, [], None
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ms, (k, d) = timed(stream, solve)
+        total_ms += ms
+        ks.append(k)
+        defects = d
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    phases = bs.bs_phase_stats(g)
+    t_max_ms = barrier_max(total_ms, world)
+    pts_per_step = M * M * N * pb.fine_steps
+    value = whole_job_rate(pts_per_step, args.steps, world, t_max_ms)
+
+    # serial fine stepping on the same GPU: the N slices one after another
+    S = torch.empty((2, M, M), device=dev)
+    sl = pb.params.T / N
+
+    def serial():
+        bs.bs_payoff(g, pb.params, S[0])
+        for n in range(N):
+            bs.fine_propagate_batched(g, [pb.params], [S[n % 2]], [S[(n + 1) % 2]], [n * sl], [pb.dtau_fine],
+                                      pb.fine_steps, stream=stream)
+    serial_ms, _ = timed(stream, serial)
+    rel_diff = float((U[N] - S[N % 2]).abs().max() / S[N % 2].abs().max())
+    bs.bs_phase_stats(g)
+
+    # end to end through the C ABI with host buffers
+    bs.bs_payoff(g, pb.params, U[0])
+    torch.cuda.synchronize()
+    u0_host = U[0].cpu().pin_memory()
+    out_host = torch.empty((M, M), dtype=torch.float32).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        U[0].copy_(u0_host, non_blocking=True)
+        solve(bs.PARAREAL_USER_U0)
+        out_host.copy_(U[N], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+    e2e_value = whole_job_rate(pts_per_step, args.steps, world, barrier_max(e2e_ms, world))
+
+    # roofline of the fine stepper from the event-timed F launches of the timed solves
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    sms = sm_count(local)
+    peak = fp32_peak_tflops(sm_max, sms)
+    m0 = bs.bs_fine_sweeps(g, pb.params, pb.dtau_fine, bs.START_COLD)
+    m1 = bs.bs_fine_sweeps(g, pb.params, pb.dtau_fine, bs.START_WARM)
+    mx = bs.bs_fine_sweeps(g, pb.params, pb.dtau_fine, bs.START_EXTRAP)
+    mxl = bs.bs_fine_sweeps(g, pb.params, pb.dtau_fine, bs.START_EXTRAP_LATE)
+    # state-propagations of F in the timed solves: iteration k covers slices k..N-1
+    slices_f = sum(sum(N - kk for kk in range(k)) for k in ks)
+    fine_flops = slices_f * M * M * fine_flops_per_point_launch(m0, m1, mx, mxl, pb.fine_steps)
+    fine_s = phases["fine_ms"] / 1e3
+    achieved = fine_flops / fine_s / 1e12 if fine_s > 0 else 0.0
+    launches_f = max(1, phases["fine_launches"])
+    ms_per_launch = phases["fine_ms"] / launches_f
+    # Each F call splits its N - k states into chunks of at most 96 (one launch plan each), so
+    # a launch carries on average the states of the timed F calls over their chunks.
+    chunks = sum((N - kk + 95) // 96 for k in ks for kk in range(k))
+    avg_states = slices_f / max(1, chunks)
+    # DRAM bytes per launch: the committed capture's bytes per state and launch x avg_states
+    ent = traffic_entry("fine_ctile_kernel")
+    traffic = ent["dram_bytes_per_state_launch"] * avg_states if ent else None
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    alg_bytes_launch = avg_states * M * M * FINE_ALG_BYTES_PER_POINT_LAUNCH
+    roof = {"kernel": "fine_ctile_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": f"FP32 lanes x 2 x {sm_max:.0f} MHz of {sms} SMs ({pk_kind} max clock)"}
+    kernels = {
+        "fine_ctile_kernel": {
+            "ms_total": phases["fine_ms"], "launches": phases["fine_launches"], "ms_per_launch": ms_per_launch,
+            "states_per_launch": avg_states, "bound": "alu", "achieved_tflops": achieved, "peak_tflops": peak,
+            "frac": achieved / peak,
+            "sweeps_per_step": {"cold": m0, "warm": m1, "extrapolated": mx, "extrapolated_after_16": mxl},
+            "sweeps_per_slice": fine_sweeps_total(m0, m1, mx, mxl, pb.fine_steps),
+            "hbm_algorithmic_gbs": alg_bytes_launch / (ms_per_launch / 1e3) / 1e9,
+            "hbm_dram_gbs": (traffic / (ms_per_launch / 1e3) / 1e9) if traffic else None,
+            "hbm_peak_gbs": hbm_peak,
+        },
+        "coarse_resampled": {"ms_total": phases["coarse_ms"], "launches": phases["coarse_launches"],
+                             "note": "serial coarse sweep: restrict, BiCGSTAB on 256 x 256, prolong per slice"},
+    }
+    launches = phases["fine_launches"] + phases["coarse_launches"] + phases["other_launches"]
+    del U, S
+    return {
+        "value": value, "t_ms": t_max_ms, "ks": ks, "defects": defects, "serial_ms": serial_ms,
+        "rel_diff_vs_serial": rel_diff, "e2e": e2e_value, "roof": roof, "kernels": kernels, "clocks": clk,
+        "launches": launches, "h2d": M * M * 4, "d2h": M * M * 4,
+    }
+
+
+def exchange_arm(args, local):
+    """The 256 x 256 exchange-option workload (extra keys): Parareal to tol 1e-4 for each rho."""
+    import torch
+
+    import paper_2404_02521_gb300 as bs
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
     problems = [wl.exchange_cfg2(rho) for rho in wl.EXCHANGE_RHOS]
     pb0 = problems[0]
     M, N = pb0.M, pb0.N
     g = bs.Grid(M, pb0.xmax)
     U = torch.empty((N + 1, M, M), device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
     bs.bs_set_option(bs.OPT_PHASE_TIMING, 1)
 
-    def solve(pb):
-        rc, k, d = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM,
-                                     pb.coarse_steps, None, pb.tol, pb.N, U, stream)
-        return k
-
     def step():
-        return [solve(pb) for pb in problems]
+        ks = []
+        for pb in problems:
+            rc, k, d = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM, pb.coarse_steps,
+                                         None, pb.tol, pb.N, U, stream)
+            ks.append(k)
+        return ks
 
-    # warm-up
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     bs.bs_phase_stats(g)
-
-    # timed region: device events per step, L2 flushed between steps (outside the events)
-    clocks = ClockSampler(local)
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks.start()
-    total_ms = 0.0
-    ks = []
+    total_ms, ks = 0.0, []
     for _ in range(args.steps):
         flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ks.append(step())
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    barrier(world)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
+        ms, k = timed(stream, step)
+        total_ms += ms
+        ks.append(k)
     phases = bs.bs_phase_stats(g)
-    t_max_ms = barrier_max(total_ms, world)
-    pts_per_step = sum(pb.M * pb.M * pb.N * pb.fine_steps for pb in problems)
-    value = whole_job_rate(pts_per_step, args.steps, world, t_max_ms)
-
-    # coarse iteration counts: one more (untimed) solve per rho; the solves are deterministic,
-    # so these are the timed solves' counts
     krylov_iters = 0
-    krylov_solves = 0
-    for pb in problems:
-        solve(pb)
+    for pb in problems:   # one more (untimed) solve per rho: the solves are deterministic
+        bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM, pb.coarse_steps, None, pb.tol, pb.N,
+                          U, stream)
         _, _, tot, ns = bs.bs_grid_stats(g, detail=True)
         krylov_iters += tot
-        krylov_solves += ns
     bs.bs_phase_stats(g)
-
-    # fine stepper alone: every slice of every rho in one batched launch per rho
-    m_sweeps = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_WARM)
-    m_cold = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_COLD)
-    m_extrap = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_EXTRAP)
-    m_late = bs.bs_fine_sweeps(g, pb0.params, pb0.dtau_fine, bs.START_EXTRAP_LATE)
-    Fb = torch.empty((N, M, M), device=dev)
-    for pb in problems:
-        bs.bs_payoff(g, pb.params, U[0])
     sl = pb0.params.T / N
-    fine_ms = []
-    for pb in problems:
-        for n in range(1, N + 1):
-            U[n].copy_(U[0])
-        args_f = ([pb.params] * N, [U[n] for n in range(N)], [Fb[n] for n in range(N)],
-                  [n * sl for n in range(N)], [pb.dtau_fine] * N, pb.fine_steps)
-        bs.fine_propagate_batched(g, *args_f, stream=stream)
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bs.fine_propagate_batched(g, *args_f, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fine_ms.append(e0.elapsed_time(e1))
-    fine_rate = N * M * M * pb0.fine_steps / (statistics.mean(fine_ms) / 1e3)
-
-    # serial fine on the same GPU: one slice after another (what Parareal replaces)
     serial_ms = []
     for pb in problems:
-        bs.bs_payoff(g, pb.params, U[0])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for n in range(N):
-            bs.fine_propagate_batched(g, [pb.params], [U[n]], [U[n + 1]], [n * sl],
-                                      [pb.dtau_fine], pb.fine_steps, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        serial_ms.append(e0.elapsed_time(e1))
+        def serial():
+            bs.bs_payoff(g, pb.params, U[0])
+            for n in range(N):
+                bs.fine_propagate_batched(g, [pb.params], [U[n]], [U[n + 1]], [n * sl], [pb.dtau_fine],
+                                          pb.fine_steps, stream=stream)
+        ms, _ = timed(stream, serial)
+        serial_ms.append(ms)
     bs.bs_phase_stats(g)
-
-    # end-to-end through the C ABI with host buffers
-    u0_host = torch.empty((len(problems), M, M), dtype=torch.float32).pin_memory()
-    for q, pb in enumerate(problems):
-        bs.bs_payoff(g, pb.params, U[0])
-        torch.cuda.synchronize()
-        u0_host[q].copy_(U[0].cpu())
-    out_host = torch.empty((len(problems), M, M), dtype=torch.float32).pin_memory()
-    e2e_ms = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for q, pb in enumerate(problems):
-            U[0].copy_(u0_host[q], non_blocking=True)
-            bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps,
-                              bs.COARSE_NUM | bs.PARAREAL_USER_U0, pb.coarse_steps, None, pb.tol,
-                              pb.N, U, stream)
-            out_host[q].copy_(U[N], non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ms += 1e3 * (time.perf_counter() - t0)
-    e2e_max = barrier_max(e2e_ms, world)
-    e2e_value = whole_job_rate(pts_per_step, args.steps, world, e2e_max)
-
-    # roofline of the dominant kernel by event-timed share
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    fine_launch_ms = phases["fine_ms"] / max(1, phases["fine_launches"])
-    coarse_launch_ms = phases["coarse_ms"] / max(1, phases["coarse_launches"])
-    k_tot = sum(sum(k) for k in ks)
-    # fine launches in the timed region: iteration k covers slices k..N-1
-    fine_pt_launches = 0
-    for kl in ks:
-        for k in kl:
-            fine_pt_launches += sum((N - kk) for kk in range(k)) * M * M
-    fine_flops = fine_pt_launches * fine_flops_per_point_launch(m_cold, m_sweeps, m_extrap, m_late, pb0.fine_steps)
-    peak_fp32 = fp32_peak_tflops(sm_max)
-    fine_tflops = fine_flops / (phases["fine_ms"] / 1e3) / 1e12 if phases["fine_ms"] > 0 else 0.0
-    # coarse: the timed region ran args.steps x the counted solves
+    sms = sm_count(local)
+    peak = fp32_peak_tflops(sm_max, sms)
     variant = bs.bs_coarse_variant(g, pb0.params, pb0.dtau_coarse)
     vinfo = bs.bs_coarse_variant_info(variant, M)
-    cluster_ctas = vinfo["ctas"]
     flops_node_iter = COARSE_FLOPS_PER_NODE_ITER + (COARSE_FLOPS_POLY_EXTRA if vinfo["poly"] else 0)
-    coarse_flops = args.steps * krylov_iters * M * M * flops_node_iter
-    coarse_tflops = coarse_flops / (phases["coarse_ms"] / 1e3) / 1e12 if phases["coarse_ms"] > 0 else 0.0
-    iter_us = 1e3 * phases["coarse_ms"] / max(1, args.steps * krylov_iters)
-    kernels = {
-        "fine_band_kernel": {"ms_total": phases["fine_ms"], "launches": phases["fine_launches"],
-                             "ms_per_launch": fine_launch_ms, "bound": "alu",
-                             "achieved_tflops": fine_tflops,
-                             "peak_tflops": peak_fp32,
-                             "frac": fine_tflops / peak_fp32,
-                             "sweeps_per_step": {"cold": m_cold, "warm": m_sweeps, "extrapolated": m_extrap,
-                                                 "extrapolated_after_16": m_late}},
-        "sweep_band_kernel": {"ms_total": phases["coarse_ms"], "launches": phases["coarse_launches"],
-                              "ms_per_launch": coarse_launch_ms, "bound": "alu",
-                              "achieved_tflops": coarse_tflops, "peak_tflops": peak_fp32,
-                              "frac": coarse_tflops / peak_fp32,
-                              "band_variant": variant, "cluster_ctas": cluster_ctas,
-                              "polynomial_preconditioner": vinfo["poly"],
-                              "quadratic_extrapolation": vinfo["quad"],
-                              "flops_per_node_iter": flops_node_iter,
-                              "frac_of_cluster_sms": coarse_tflops / (peak_fp32 * cluster_ctas / 152),
-                              "krylov_iters_per_solve": krylov_iters / len(problems),
-                              "implicit_solves_per_solve": krylov_solves / len(problems),
-                              "us_per_krylov_iter": iter_us,
-                              "note": "serial coarse sweep on one thread-block cluster: latency-bound"},
-    }
-    dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
-    kd = kernels[dominant]
-    roof = {"kernel": dominant, "bound": "alu", "achieved": kd["achieved_tflops"], "peak": peak_fp32,
-            "unit": "TFLOP/s", "frac": kd["frac"],
-            "traffic": traffic_for(dominant, KERNEL_SOURCES[dominant]),
-            "peak_source": f"FP32 lanes x 2 x {sm_max:.0f} MHz of 152 SMs ({pk_kind} max clock)"}
-    launches = phases["fine_launches"] + phases["coarse_launches"] + phases["other_launches"]
+    coarse_tflops = (args.steps * krylov_iters * M * M * flops_node_iter / (phases["coarse_ms"] / 1e3) / 1e12
+                     if phases["coarse_ms"] > 0 else 0.0)
+    per_solve = total_ms / (args.steps * len(problems))
+    pts = sum(pb.M * pb.M * pb.N * pb.fine_steps for pb in problems)
+    del U, flush
     return {
-        "value": value, "t_ms": t_max_ms, "ks": ks, "fine_rate": fine_rate, "fine_ms": fine_ms,
-        "serial_ms": serial_ms, "e2e": e2e_value, "roof": roof, "kernels": kernels, "clocks": clk,
-        "launches": launches, "sweeps": m_late, "sweeps_cold": m_cold, "pts_per_step": pts_per_step,
-        "h2d": len(problems) * M * M * 4, "d2h": len(problems) * M * M * 4,
+        "workload": "exchange256_N64_fine512_coarse4", "rho": list(wl.EXCHANGE_RHOS),
+        "value": args.steps * pts / (total_ms / 1e3), "unit": UNIT,
+        "time_to_tol_ms_per_solve": per_solve, "serial_fine_ms_per_solve": statistics.mean(serial_ms),
+        "speedup_vs_serial_fine": statistics.mean(serial_ms) / per_solve, "parareal_iterations": ks[-1],
+        "sweep_band_kernel": {
+            "ms_total": phases["coarse_ms"], "launches": phases["coarse_launches"], "bound": "alu",
+            "achieved_tflops": coarse_tflops, "peak_tflops": peak, "frac": coarse_tflops / peak,
+            "band_variant": variant, "cluster_ctas": vinfo["ctas"], "polynomial_preconditioner": vinfo["poly"],
+            "quadratic_extrapolation": vinfo["quad"], "flops_per_node_iter": flops_node_iter,
+            "krylov_iters_per_solve": krylov_iters / len(problems),
+            "us_per_krylov_iter": 1e3 * phases["coarse_ms"] / max(1, args.steps * krylov_iters),
+            "note": "serial coarse sweep on one thread-block cluster: latency-bound"},
+        "fine_band_kernel": {"ms_total": phases["fine_ms"], "launches": phases["fine_launches"]},
     }
 
 
@@ -445,19 +501,40 @@ def serving_run(args):
     }
 
 
+_ORACLE_CACHE = {}
+
+
 def oracle_sample(seconds_budget=15.0):
-    """Oracle serial fine on the first rho of the workload, as many steps as fit the budget."""
+    """The FP64 oracle's serial fine stepping of the large solve: one sparse LU factorisation
+    of the 1024 x 1024 implicit-Euler matrix (kept for later samples, as the oracle keeps it
+    for every step of a solve), then as many implicit steps as fit the budget.  Returns the
+    point-update rate of the steps, their count and time, and the factorisation time."""
     from oracle import fd
-    pb = wl.exchange_cfg2(wl.EXCHANGE_RHOS[0])
+    pb = wl.large_cfg4()
+    if "ie" not in _ORACLE_CACHE:
+        t0 = time.perf_counter()
+        _ORACLE_CACHE["ie"] = fd.ImplicitEuler(pb.M, pb.xmax, pb.params, pb.dtau_fine)
+        _ORACLE_CACHE["factor_s"] = time.perf_counter() - t0
+        _ORACLE_CACHE["u"] = fd.initial_state(pb.M, pb.xmax, pb.params)
+        _ORACLE_CACHE["step"] = 0
+    ie = _ORACLE_CACHE["ie"]
     t0 = time.perf_counter()
-    ie = fd.ImplicitEuler(pb.M, pb.xmax, pb.params, pb.dtau_fine)
-    u = fd.initial_state(pb.M, pb.xmax, pb.params)
     steps = 0
-    while time.perf_counter() - t0 < seconds_budget and steps < pb.N * pb.fine_steps:
-        u = ie.step(u, (steps + 1) * pb.dtau_fine)
+    while time.perf_counter() - t0 < seconds_budget:
+        s = _ORACLE_CACHE["step"]
+        _ORACLE_CACHE["u"] = ie.step(_ORACLE_CACHE["u"], (s + 1) * pb.dtau_fine)
+        _ORACLE_CACHE["step"] = s + 1
         steps += 1
     dt = time.perf_counter() - t0
-    return pb.M * pb.M * steps / dt, steps, dt
+    return pb.M * pb.M * steps / dt, steps, dt, _ORACLE_CACHE["factor_s"]
+
+
+def single_thread():
+    try:
+        from threadpoolctl import threadpool_limits
+        return threadpool_limits(1)
+    except Exception:
+        return None
 
 
 def reference_arm(args):
@@ -465,17 +542,13 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    try:
-        from threadpoolctl import threadpool_limits
-        ctx = threadpool_limits(1)
-    except Exception:
-        ctx = None
+    ctx = single_thread()
     budget = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(budget / 4)
-    vals, total_steps, total_s = [], 0, 0.0
+    vals, total_steps, total_s, factor_s = [], 0, 0.0, 0.0
     for _ in range(args.steps):
-        v, st, dt = oracle_sample(budget)
+        v, st, dt, factor_s = oracle_sample(budget)
         vals.append(v)
         total_steps += st
         total_s += dt
@@ -485,12 +558,11 @@ def reference_arm(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": "exchange256_N64_fine512_coarse4", "rho": list(wl.EXCHANGE_RHOS),
-                   "l2": "oracle runs on the CPU"},
+        "config": {"workload": "basket1024_N128_fine1024_coarse4_on256", "l2": "oracle runs on the CPU"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"FP64 sparse-LU serial fine stepping, rho={wl.EXCHANGE_RHOS[0]}, "
-                                   f"{total_steps} implicit steps of the 256x256 grid over "
-                                   f"{args.steps} steps"},
+                         "sample": f"FP64 sparse-LU serial fine stepping of the 1024x1024 basket "
+                                   f"(dtau = 1/131072): {total_steps} implicit steps over {args.steps} "
+                                   f"steps after one factorisation ({factor_s:.1f} s, not in the rate)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -504,6 +576,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-exchange", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.8)
     args = ap.parse_args()
@@ -511,47 +584,46 @@ def main():
         reference_arm(args)
         return
     world, rank, local = dist_setup()
-    r = gpu_arm(args, world, rank, local)
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2404_02521_gb300 as bs
+    bs.load()
+    r = large_arm(args, world, local)
+    ex = exchange_arm(args, local) if (not args.no_exchange and world == 1) else None
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        try:
-            from threadpoolctl import threadpool_limits
-            ctx = threadpool_limits(1)
-        except Exception:
-            ctx = None
-        v, st, dt = oracle_sample(15.0)
+        ctx = single_thread()
+        v, st, dt, factor_s = oracle_sample(15.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 sparse-LU serial fine stepping of the 256x256 exchange workload "
-                         f"(rho={wl.EXCHANGE_RHOS[0]}), first {st} of 32768 implicit steps, {dt:.1f} s"}
+               "sample": f"FP64 sparse-LU serial fine stepping of the 1024x1024 basket (dtau = 1/131072): "
+                         f"{st} of 131072 implicit steps in {dt:.1f} s after one factorisation "
+                         f"({factor_s:.1f} s, not in the rate)"}
     serving_res = None
     if not args.no_serving and world == 1:
         serving_res = serving_run(args)
-    ks = r["ks"]
-    mean_serial = statistics.mean(r["serial_ms"])
-    per_solve = r["t_ms"] / (args.steps * len(wl.EXCHANGE_RHOS))
+    per_solve = r["t_ms"] / args.steps
     out = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r["t_ms"] / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": per_solve, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "exchange256_N64_fine512_coarse4",
-                   "grid": 256, "slices": 64, "fine_steps": 512, "coarse_steps": 4,
-                   "coarse": "numerical (BiCGSTAB)", "rho": list(wl.EXCHANGE_RHOS), "tol": 1e-4,
+        "config": {"workload": "basket1024_N128_fine1024_coarse4_on256",
+                   "grid": 1024, "slices": 128, "fine_steps": 1024, "coarse_steps": 4, "coarse_grid": 256,
+                   "coarse": "numerical (BiCGSTAB) on 256x256 with bilinear resampling", "tol": 1e-4,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "flushed between timed steps (2x L2 buffer write)"},
+                   "l2": "flushed between timed steps (2x L2 buffer write); state 541 MB > L2"},
         "time_to_tol_ms_per_solve": per_solve,
-        "serial_fine_ms_per_solve": mean_serial,
-        "speedup_vs_serial_fine": mean_serial / per_solve,
-        "parareal_iterations": ks[-1],
-        "fine_pt_updates_per_s": r["fine_rate"],
-        "fine_sweeps_per_step": r["sweeps"],
-        "fine_sweeps_first_step": r["sweeps_cold"],
+        "serial_fine_ms_per_solve": r["serial_ms"],
+        "speedup_vs_serial_fine": r["serial_ms"] / per_solve,
+        "parareal_iterations": r["ks"][-1],
+        "defects": r["defects"],
+        "rel_diff_vs_serial_fine": r["rel_diff_vs_serial"],
         "roofline": r["roof"],
         "kernels": r["kernels"],
+        "exchange256": ex,
         "cpu_baseline": cpu,
-        "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
-                "d2h_bytes_per_step": r["d2h"]},
+        "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "serving": serving_res,

@@ -325,18 +325,28 @@ __device__ __noinline__ float ctile_g(const PayoffF& pf, int i, int j, float h, 
 
 // Far-field data at tau on this thread's own region rows (the column i = M - 1 and the row
 // j = M - 1), mirrored into the neighbours' halo rows by band_store.  The region's cut halo
-// rows are left as they are (they are beyond the exact part).
+// rows are left as they are (they are beyond the exact part).  The far column's K rows are
+// evaluated by K lanes of the warp that holds it, one row each, and handed to the owning
+// lane by shuffles (one thread evaluating all K would hold up its whole cluster at the next
+// barrier).  Every lane of a warp takes the same branches (a warp covers 32 columns of one
+// row group).
 template <class CFG>
 __device__ __forceinline__ void ctile_far_field(float* hi, const HaloPush& hp, const PayoffF& pf, float tau,
                                                 float h, int M, int ig, int jrow0, int r0, int col) {
-  if (ig < 0 || ig >= M) return;
-  if (ig == M - 1) {
+  static_assert(CFG::K <= 32 && (CFG::K & (CFG::K - 1)) == 0, "one lane per strip row");
+  const int lane = threadIdx.x & 31;
+  const int cfar = col + (M - 1 - ig);   // region column of i = M - 1
+  if (cfar >= col - lane && cfar < col - lane + 32) {
+    const int kq = lane & (CFG::K - 1), jq = jrow0 + kq;
+    const float gq = (lane < CFG::K && jq >= 0 && jq < M) ? ctile_g(pf, M - 1, jq, h, tau) : 0.f;
 #pragma unroll
     for (int k = 0; k < CFG::K; ++k) {
+      const float v = __shfl_sync(0xffffffffu, gq, k);
       const int j = jrow0 + k;
-      if (j >= 0 && j < M) band_store<CFG>(hi, hp, r0 + k, col, ctile_g(pf, ig, j, h, tau));
+      if (ig == M - 1 && j >= 0 && j < M) band_store<CFG>(hi, hp, r0 + k, col, v);
     }
-  } else {
+  }
+  if (ig >= 0 && ig < M - 1) {
     const int k = M - 1 - jrow0;
     if (k >= 0 && k < CFG::K) band_store<CFG>(hi, hp, r0 + k, col, ctile_g(pf, ig, M - 1, h, tau));
   }
@@ -427,15 +437,25 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   __syncthreads();
   // the far-field data of the first step on every plane row this thread covers (own rows and,
   // for the edge groups, the halo row next to them), locally: the neighbours' halo rows are
-  // still being loaded
+  // still being loaded.  As in ctile_far_field, the far column's rows are evaluated one per
+  // lane of the warp that holds it.
   {
     const float tau_new = (float)(d.tau0 + (step0 + 1) * d.dtau);
-    const int pa = grp == 0 ? 0 : r0 + 1, pb = grp == CFG::G - 1 ? BH + 1 : r0 + K;
-    if (ig >= 0 && ig < M) {
+    const int pa = grp == 0 ? 0 : r0 + 1, pb = grp == CFG::G - 1 ? BH + 1 : r0 + K;   // <= K + 1 rows
+    const int lane = tid & 31;
+    const int cfar = col + (M - 1 - ig);
+    if (cfar >= col - lane && cfar < col - lane + 32) {
+      const int jq = jb + pa + lane - 1;
+      const float gq = (pa + lane <= pb && jq >= 0 && jq < M) ? ctile_g(pf, M - 1, jq, tb.h, tau_new) : 0.f;
       for (int pr = pa; pr <= pb; ++pr) {
+        const float v = __shfl_sync(0xffffffffu, gq, pr - pa);
         const int j = jb + pr - 1;
-        if (j >= 0 && j < M && (ig == M - 1 || j == M - 1)) hi[pr * NCOL + col] = ctile_g(pf, ig, j, tb.h, tau_new);
+        if (ig == M - 1 && j >= 0 && j < M) hi[pr * NCOL + col] = v;
       }
+    }
+    if (ig >= 0 && ig < M - 1) {
+      const int pr = M - jb;   // plane row of j = M - 1
+      if (pr >= pa && pr <= pb) hi[pr * NCOL + col] = ctile_g(pf, ig, M - 1, tb.h, tau_new);
     }
   }
   float dv[K], b[K], invd[K], lo[K];

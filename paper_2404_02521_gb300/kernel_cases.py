@@ -8,8 +8,12 @@ workloads, one kernel each:
 
   fine256    F on all 64 slices of the 256x256 exchange workload, 512 steps (one launch)
   coarse256  the initial serial coarse sweep of that workload (64 slices x 4 BiCGSTAB steps)
-  tile1024   F on 48 slices of a 1024x1024 basket grid, 20 steps of the large-solve step size
-             (cluster tiles, a launch per step; 48 x 4 MB of state exceeds the 129 MB L2)
+  tile1024   F on 48 slices of a 1024x1024 basket grid, 40 steps of the large-solve step size
+             (temporally blocked cluster tiles; 48 x 4 MB of state exceeds the 129 MB L2).  The
+             launch plan of one call: the cold first step split over two launches, the warm
+             second step with the third, two extrapolated steps per launch up to step 14, then
+             four steps of five sweeps per launch (the twelfth launch, steps 23-26, is the
+             steady state of the large solve)
   solve256   one Parareal solve of that workload (rho = 0.7): payoff, initial coarse sweep,
              then per iteration the batched F launch and a correcting coarse sweep
   coarse512  coarse propagation of one 512x512 state, 4 steps (global-memory BiCGSTAB)
@@ -89,7 +93,7 @@ def case_solve256(bs, wl, torch):
 
 def case_tile1024(bs, wl, torch):
     p = wl.basket_cfg1().params
-    M, B, steps = 1024, 48, 20
+    M, B, steps = 1024, 48, 40
     g = bs.Grid(M, 4.0)
     U = torch.empty((B, M, M), device="cuda")
     bs.bs_payoff(g, p, U[0])

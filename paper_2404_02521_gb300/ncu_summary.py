@@ -5,9 +5,10 @@
     python -m paper_2404_02521_gb300.ncu_summary report <capture.ncu-rep>
         the headline counters of each captured launch (time, DRAM bytes and throughput,
         pipe utilisation, occupancy, the largest warp-stall reasons)
-    python -m paper_2404_02521_gb300.ncu_summary traffic <capture.ncu-rep> <kernel> <json> <src>...
-        record the DRAM bytes (read + write) per launch of <kernel> in <json>, with the
-        sha256 of the kernel's source files (a later source change invalidates the entry)
+    python -m paper_2404_02521_gb300.ncu_summary traffic <capture.ncu-rep> <kernel> <json> [--states S] <src>...
+        record the DRAM bytes (read + write) per launch of <kernel> in <json> (and per state
+        when the captured launches carried S states each), with the sha256 of the kernel's
+        source files (a later source change invalidates the entry)
 
 The launch list comes from `ncu --metrics gpu__time_duration.sum --csv --log-file`; a capture
 from `ncu --set full -o`.  Reading a capture runs `ncu -i <file> --page raw --csv`.
@@ -112,7 +113,7 @@ def sources_sha256(root: str, files) -> str:
     return h.hexdigest()
 
 
-def traffic(path: str, kernel: str, json_path: str, sources) -> dict:
+def traffic(path: str, kernel: str, json_path: str, sources, states: int = 0) -> dict:
     hdr, units, rows = _raw(path)
     ki = hdr.index("Kernel Name")
     sel = [r for r in rows if kernel in r[ki]]
@@ -133,6 +134,9 @@ def traffic(path: str, kernel: str, json_path: str, sources) -> dict:
     d[kernel] = {"dram_bytes_per_launch_full": sum(per) / len(per), "launches_captured": len(per),
                  "capture": os.path.basename(path), "sources": list(sources),
                  "source_sha256": sources_sha256(root, sources)}
+    if states > 0:
+        d[kernel]["states_per_launch_captured"] = states
+        d[kernel]["dram_bytes_per_state_launch"] = sum(per) / len(per) / states
     with open(json_path, "w") as f:
         json.dump(d, f, indent=1, sort_keys=True)
         f.write("\n")
@@ -145,7 +149,10 @@ def main(argv):
     elif len(argv) >= 2 and argv[0] == "report":
         print(report(argv[1]))
     elif len(argv) >= 5 and argv[0] == "traffic":
-        print(json.dumps(traffic(argv[1], argv[2], argv[3], argv[4:])))
+        rest, states = argv[4:], 0
+        if rest[:1] == ["--states"]:
+            states, rest = int(rest[1]), rest[2:]
+        print(json.dumps(traffic(argv[1], argv[2], argv[3], rest, states)))
     else:
         print(__doc__)
         return 2

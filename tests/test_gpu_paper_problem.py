@@ -78,6 +78,27 @@ def test_parareal_converges_to_the_fine_solution(bs, golden, coarse_steps):
     check_against_golden(U, golden, 1e-3)
 
 
+def test_paper_step_sizes_serial_fine_matches_oracle(bs):
+    # serial fine stepping with the paper's three substeps per 0.1-slice (Sec. 4.1): every step
+    # is too large for Jacobi sweeps, so F solves it by BiCGSTAB; held to the FP32 fine bound
+    # at the golden's sampled nodes of slices 1, 2, 5 and 10 (eq. fd, implicit Euler)
+    import torch
+    with open(os.path.join(HERE, "golden", "cash_or_nothing301_paper_steps.json")) as f:
+        gd = json.load(f)
+    pb = wl.paper_cash_or_nothing(N=gd["N"], fine_steps=gd["fine_steps"])
+    g = bs.Grid(pb.M, pb.xmax)
+    assert bs.bs_fine_sweeps(g, pb.params, pb.dtau_fine) == 0
+    U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+    bs.bs_payoff(g, pb.params, U[0])
+    sl = pb.params.T / pb.N
+    for n in range(pb.N):
+        bs.fine_propagate_batched(g, [pb.params], [U[n]], [U[n + 1]], [n * sl], [pb.dtau_fine],
+                                  pb.fine_steps)
+    torch.cuda.synchronize()
+    assert not bs.bs_grid_stats(g)[1]
+    check_against_golden(U, gd, FP32_FINE_TOL)
+
+
 def test_paper_step_sizes_parareal_matches_oracle(bs):
     # the paper's configuration: three fine substeps per 0.1-slice and one coarse step
     # (Sec. 4.1).  Both are too large for Jacobi sweeps on this grid, so F and G are BiCGSTAB

@@ -214,7 +214,7 @@ def test_parareal_with_krylov_fine(bs):
     S = gpu_serial_fine(bs, pb)
     assert k == pb.N and torch.equal(U, S)
     serial = fd.serial_fine(pb)
-    assert rel_err(to_np(S), serial) <= 3 * COARSE_TOL
+    assert rel_err(to_np(S), serial) <= FP32_FINE_TOL   # F by BiCGSTAB steps: the fine bound
     rc, k, defects, U = gpu_parareal(bs, pb, 1e-4, pb.N)
     assert rc == 0 and k < pb.N
     assert rel_err(to_np(U), serial) <= 1e-3

@@ -93,6 +93,76 @@ def test_pino_parareal_invariants(bs, weights):
     assert rel_err(to_np(S), fd.serial_fine(pb)) <= FP32_FINE_TOL
 
 
+def test_pino_parareal_matches_oracle_parareal(bs, tmp_path):
+    # GPU PINO-Parareal (eq. parareal with the BF16 tensor-core FNO as G) beside the textbook
+    # FP64 Parareal of the oracle with the FP64 FNO forward of the same weights, three
+    # iterations on 64 x 64 states (the network runs on its 128 x 128 grid: restriction and
+    # prolongation are part of G).  The projection weights are scaled down so that G is the
+    # identity plus a small network increment w, as a trained coarse model is.
+    import torch
+    from paper_2404_02521_gb300 import pino_io
+    from oracle import parareal as opr
+    arch = wl.PinoArch()
+    w = wl.pino_random_weights(arch, seed=23, spectral_scale=8.0)
+    w["proj2_w"] = 0.05 * w["proj2_w"]
+    w["proj2_b"] = np.float64(0.0)
+    path = str(tmp_path / "w.bin")
+    pino_io.write_weights(path, w, arch.in_channels, arch.width, arch.modes_x, arch.modes_y,
+                          arch.layers, arch.proj_hidden)
+    w32, _ = pino_io.read_weights(path)
+    net = bs.Pino(path)
+    pb = wl.Problem("pino64", 64, 4.0, 4, 128, 1, wl.basket_cfg1().params)   # Jacobi bound 0.6
+    K = 3
+    g = bs.Grid(pb.M, pb.xmax)
+    sl = pb.params.T / pb.N
+    Ug, dg = [], None
+    for k in range(K + 1):
+        U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+        rc, kd, d = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_PINO, 1, net,
+                                      0.0, k, U)
+        torch.cuda.synchronize()
+        assert kd == k
+        Ug.append(to_np(U))
+        dg = d
+    F = fd.SlicePropagator(pb.M, pb.xmax, pb.params, pb.N, pb.fine_steps)
+
+    def G(u, n):
+        return fno.pino_coarse(u, pb.xmax, n * sl, sl, pb.params, w32, arch.modes_x, arch.modes_y, Mp=128)
+
+    # the network increments on the GPU's inputs bound the BF16 error of one G evaluation
+    Gv = [[G(Ug[k][n], n) for n in range(pb.N)] for k in range(K + 1)]
+    wmax = max(float(np.max(np.abs(Gv[k][n] - Ug[k][n]))) for k in range(K + 1) for n in range(pb.N))
+    vmax = float(np.max(np.abs(Ug[K])))
+    eps_g = PINO_REL_TOL * wmax
+    # the initial sweep: u_{n+1}^0 = G(u_n^0)
+    for n in range(pb.N):
+        assert np.max(np.abs(Ug[0][n + 1] - Gv[0][n])) <= eps_g + FP32_FINE_TOL * vmax, n
+    # every iterate, slice by slice: u_{n+1}^k = F(u_n^{k-1}) + G(u_n^k) - G(u_n^{k-1}) on the
+    # GPU's own previous iterates, within two network errors and the FP32 fine bound
+    for k in range(1, K + 1):
+        assert np.array_equal(Ug[k][0], Ug[0][0])
+        for n in range(pb.N):
+            want = F(Ug[k - 1][n], n) + (Gv[k][n] - Gv[k - 1][n])
+            err = float(np.max(np.abs(Ug[k][n + 1] - want)))
+            assert err <= 2 * eps_g + FP32_FINE_TOL * vmax, (k, n, err / wmax)
+    # the defects are those of the GPU iterates (reading c5; the GPU sums squares in FP32 per
+    # block of 256 nodes and over blocks in FP64)
+    for k in range(1, K + 1):
+        num = max(float(np.linalg.norm(Ug[k][n] - Ug[k - 1][n])) for n in range(1, pb.N + 1))
+        den = max(float(np.linalg.norm(Ug[k][n])) for n in range(1, pb.N + 1))
+        assert abs(dg[k - 1] - num / den) <= 1e-4 * num / den, k
+    # against the oracle's own PINO-Parareal: each iterate is a chain of at most 2N + 1 network
+    # evaluations (and fine propagations, which do not amplify), so it stays within that many
+    # network errors; the defects agree to the same relative accuracy
+    u0 = Ug[0][0].astype(np.float64)
+    _, _, do, hist = opr.parareal(u0, F, G, pb.N, 0.0, K)
+    for k in range(K + 1):
+        err = float(np.max(np.abs(Ug[k] - hist[k])))
+        assert err <= (2 * pb.N + 1) * eps_g + FP32_FINE_TOL * vmax, (k, err / wmax)
+    for a, b in zip(dg, do):
+        assert abs(a - b) <= (2 * pb.N + 1) * PINO_REL_TOL * b, (a, b)
+
+
 def test_pino_load_rejects_bad_files(bs, tmp_path):
     p = tmp_path / "bad.bin"
     p.write_bytes(b"BSPINO01" + b"\0" * 16)
