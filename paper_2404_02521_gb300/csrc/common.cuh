@@ -198,7 +198,8 @@ struct Options {
   double jacobi_target = 1.0 / 1024.0;            // warm-started steps: q^m <= 2^-10
   double jacobi_target_cold = 1.0 / 4194304.0;    // first step of a launch: q^m <= 2^-22
   double jacobi_target_extrap = 1.0 / 64.0;       // extrapolated starts: q^m <= 2^-6
-  double jacobi_target_extrap_late = 0.15;        // ... from step extrap_late on
+  // ... from step extrap_late on: two sweeps (the structural minimum) wherever q <= 0.707
+  double jacobi_target_extrap_late = 0.5;
   int extrap_start = 2;                           // first extrapolated step of a launch
   int extrap_late = 16;                           // first step with the late target
   int pipeline = 1;                               // parareal_solve overlaps F with the sweep

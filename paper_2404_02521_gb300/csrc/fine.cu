@@ -91,17 +91,18 @@ __device__ __forceinline__ float next_guess(float v, float* dp, int e, bool extr
 // in the previous sweep; they are updated before the cluster wait.  The two end rows read
 // the rows just outside the strip (other row groups or the halo copies of the neighbouring
 // CTAs) and are updated after it, so the barrier latency overlaps the interior work.
-// The thread's own column of the old increment is in dv[].  FIRST also evaluates
+// The thread's own column of the old increment is in dv[]; lo[k] is the compensation word of
+// strip row k (registers, or shared memory through StripLo).  FIRST also evaluates
 // b = dtau R_h w from hi; LAST also applies the increment to (hi, lo) of the PDE nodes and
 // leaves the next step's initial guess (next_guess) in wr and dv[].  Nodes that are not PDE
 // rows have invd = 0 and write a zero increment; LAST leaves their hi (Dirichlet data) to the
 // far-field update, which may follow it directly.
-template <class CFG, bool FIRST, bool LAST>
+template <class CFG, bool FIRST, bool LAST, class LoT>
 __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* __restrict__ wr,
                                            float* hi, const HaloPush& wr_push,
                                            const HaloPush& hi_push, const float4* __restrict__ rowc,
                                            float (&dv)[CFG::K], float (&b)[CFG::K],
-                                           const float (&invd)[CFG::K], float (&lo)[CFG::K],
+                                           const float (&invd)[CFG::K], LoT& lo,
                                            int col, int il, int ir, int r0, float ce, float cw,
                                            float cgi, float rdt, bool clustered,
                                            float* dp = nullptr, bool extrap = false) {
@@ -180,6 +181,13 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
     if (LAST && invd[0] != 0.f) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[0]));
   }
 }
+
+// The compensation words of a thread's strip rows in a shared-memory plane of own rows.
+template <class CFG>
+struct StripLo {
+  float* p;   // the thread's entry of its first strip row
+  __device__ __forceinline__ float& operator[](int k) const { return p[k * CFG::NCOL]; }
+};
 
 template <class CFG>
 __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_constant__ FineBatch fb) {
@@ -315,40 +323,61 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src, bool ok
                : "memory");
 }
 
-// The far-field value g(x_i, y_j, tau), compiled once: the tile stepper sets a step's far-field
-// data at two places (when a launch starts, or between two steps of a launch, depending on the
-// launch plan), and separately inlined copies of far_field may contract their products into
-// fused multiply-adds differently, which would make a result depend on the plan.
-__device__ __noinline__ float ctile_g(const PayoffF& pf, int i, int j, float h, float tau) {
-  return far_field(pf, (float)i * h, (float)j * h, tau);
+// Far-field data of the launch's steps.  A launch evaluates g(x, y, tau) once per step for the
+// far-edge nodes it holds -- the column i = M - 1 on this CTA's plane rows and the row
+// j = M - 1 on the region's columns -- into a shared-memory table, at one place in the code
+// (an inlined far_field may contract its products into fused multiply-adds differently at
+// different call sites, which would make a result depend on the launch plan); the steps copy
+// their values from it.  The work is spread over the CTA's threads.
+constexpr int kCTileMaxSteps = kCTileMaxHalo / 2;   // steps have at least two sweeps
+template <class CFG>
+struct FarTable {
+  static constexpr int W = (CFG::BH + 2) + CFG::NCOL;   // far column rows, then far row columns
+  static constexpr int FLOATS = kCTileMaxSteps * W;
+};
+
+template <class CFG>
+__device__ __forceinline__ void far_table_fill(float* ff, const PayoffF& pf, const ItemDesc& d, int step0,
+                                               int nstep, float h, int M, int ix0, int jb, int tid) {
+  constexpr int W = FarTable<CFG>::W, PR = CFG::BH + 2;
+  const int cfar = M - 1 - ix0;          // region column of i = M - 1
+  const int pfar = M - jb;               // plane row of j = M - 1
+  const bool has_col = cfar >= 0 && cfar < CFG::NCOL, has_row = pfar >= 0 && pfar < PR;
+  if (!has_col && !has_row) return;
+  for (int e = tid; e < nstep * W; e += CFG::NT) {
+    const int t = e / W, q = e - t * W;
+    const float tau = (float)(d.tau0 + (step0 + t + 1) * d.dtau);
+    int i, j;
+    if (q < PR) {
+      if (!has_col) continue;
+      i = M - 1;
+      j = jb + q - 1;
+    } else {
+      if (!has_row) continue;
+      i = ix0 + (q - PR);
+      j = M - 1;
+    }
+    if (i >= 0 && i < M && j >= 0 && j < M) ff[e] = far_field(pf, (float)i * h, (float)j * h, tau);
+  }
 }
 
-// Far-field data at tau on this thread's own region rows (the column i = M - 1 and the row
-// j = M - 1), mirrored into the neighbours' halo rows by band_store.  The region's cut halo
-// rows are left as they are (they are beyond the exact part).  The far column's K rows are
-// evaluated by K lanes of the warp that holds it, one row each, and handed to the owning
-// lane by shuffles (one thread evaluating all K would hold up its whole cluster at the next
-// barrier).  Every lane of a warp takes the same branches (a warp covers 32 columns of one
-// row group).
+// Step t's far-field data on this thread's own region rows, mirrored into the neighbours'
+// halo rows by band_store.  The region's cut halo rows are left as they are (they are beyond
+// the exact part).
 template <class CFG>
-__device__ __forceinline__ void ctile_far_field(float* hi, const HaloPush& hp, const PayoffF& pf, float tau,
-                                                float h, int M, int ig, int jrow0, int r0, int col) {
-  static_assert(CFG::K <= 32 && (CFG::K & (CFG::K - 1)) == 0, "one lane per strip row");
-  const int lane = threadIdx.x & 31;
-  const int cfar = col + (M - 1 - ig);   // region column of i = M - 1
-  if (cfar >= col - lane && cfar < col - lane + 32) {
-    const int kq = lane & (CFG::K - 1), jq = jrow0 + kq;
-    const float gq = (lane < CFG::K && jq >= 0 && jq < M) ? ctile_g(pf, M - 1, jq, h, tau) : 0.f;
+__device__ __forceinline__ void ctile_far_field(float* hi, const HaloPush& hp, const float* ff, int t, int M,
+                                                int ig, int jrow0, int r0, int col) {
+  constexpr int W = FarTable<CFG>::W, PR = CFG::BH + 2;
+  const float* row = ff + t * W;
+  if (ig == M - 1) {
 #pragma unroll
     for (int k = 0; k < CFG::K; ++k) {
-      const float v = __shfl_sync(0xffffffffu, gq, k);
       const int j = jrow0 + k;
-      if (ig == M - 1 && j >= 0 && j < M) band_store<CFG>(hi, hp, r0 + k, col, v);
+      if (j >= 0 && j < M) band_store<CFG>(hi, hp, r0 + k, col, row[r0 + k + 1]);
     }
-  }
-  if (ig >= 0 && ig < M - 1) {
+  } else if (ig >= 0 && ig < M - 1) {
     const int k = M - 1 - jrow0;
-    if (k >= 0 && k < CFG::K) band_store<CFG>(hi, hp, r0 + k, col, ctile_g(pf, ig, M - 1, h, tau));
+    if (k >= 0 && k < CFG::K) band_store<CFG>(hi, hp, r0 + k, col, row[PR + col]);
   }
 }
 
@@ -391,7 +420,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   float* dB = dA + PLANE;
   float* DP = dB + PLANE;   // previous increment, own rows [BH*NCOL]
   float* LO = DP + BH * NCOL;   // compensation words, own rows [BH*NCOL]
-  float4* rowc = reinterpret_cast<float4*>(LO + BH * NCOL);
+  float* FF = LO + BH * NCOL;   // far-field table [kCTileMaxSteps][FarTable::W]
+  float4* rowc = reinterpret_cast<float4*>(FF + FarTable<CFG>::FLOATS);
   // Own rows and both halo rows of hi and of the increment (the halo rows between CTAs are
   // the neighbours' own rows and are kept current by DSMEM pushes during the sweeps), and
   // the own rows of the previous increment and of lo: asynchronous copies, all in flight at
@@ -430,6 +460,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
     row_coefs(d, jb + r, cs, cn, gj);
     rowc[r] = make_float4(cs, cn, gj, 0.f);   // gj = (float)j exactly
   }
+  far_table_fill<CFG>(FF, pf, d, step0, nstep, tb.h, M, ix0, jb, tid);
   const int ig = ix0 + col;
   float ce = 0.f, cw = 0.f, cgi = 0.f;
   column_coefs(d, ig, ce, cw, cgi);
@@ -437,34 +468,27 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   __syncthreads();
   // the far-field data of the first step on every plane row this thread covers (own rows and,
   // for the edge groups, the halo row next to them), locally: the neighbours' halo rows are
-  // still being loaded.  As in ctile_far_field, the far column's rows are evaluated one per
-  // lane of the warp that holds it.
+  // still being loaded
   {
-    const float tau_new = (float)(d.tau0 + (step0 + 1) * d.dtau);
-    const int pa = grp == 0 ? 0 : r0 + 1, pb = grp == CFG::G - 1 ? BH + 1 : r0 + K;   // <= K + 1 rows
-    const int lane = tid & 31;
-    const int cfar = col + (M - 1 - ig);
-    if (cfar >= col - lane && cfar < col - lane + 32) {
-      const int jq = jb + pa + lane - 1;
-      const float gq = (pa + lane <= pb && jq >= 0 && jq < M) ? ctile_g(pf, M - 1, jq, tb.h, tau_new) : 0.f;
+    const int pa = grp == 0 ? 0 : r0 + 1, pb = grp == CFG::G - 1 ? BH + 1 : r0 + K;
+    if (ig == M - 1) {
       for (int pr = pa; pr <= pb; ++pr) {
-        const float v = __shfl_sync(0xffffffffu, gq, pr - pa);
         const int j = jb + pr - 1;
-        if (ig == M - 1 && j >= 0 && j < M) hi[pr * NCOL + col] = v;
+        if (j >= 0 && j < M) hi[pr * NCOL + col] = FF[pr];
       }
-    }
-    if (ig >= 0 && ig < M - 1) {
+    } else if (ig >= 0 && ig < M - 1) {
       const int pr = M - jb;   // plane row of j = M - 1
-      if (pr >= pa && pr <= pb) hi[pr * NCOL + col] = ctile_g(pf, ig, M - 1, tb.h, tau_new);
+      if (pr >= pa && pr <= pb) hi[pr * NCOL + col] = FF[(BH + 2) + col];
     }
   }
-  float dv[K], b[K], invd[K], lo[K];
+  float dv[K], b[K], invd[K];
+  StripLo<CFG> lo{LO + r0 * NCOL + col};   // compensation words stay in shared memory
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int j = jb + r0 + k;
     const bool pde = ig >= 0 && ig < M - 1 && j >= 0 && j < M - 1;
     invd[k] = pde ? inv_diag(d, ig, j) : 0.f;
-    lo[k] = pde ? LO[(r0 + k) * NCOL + col] : 0.f;
+    if (!pde) lo[k] = 0.f;
     b[k] = 0.f;
     dv[k] = dA[(r0 + k + 1) * NCOL + col];
   }
@@ -506,9 +530,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
       // After the second sweep of a step every CTA has passed the first one, which read hi:
       // move the far-field data on to the next step of this launch (the last sweep writes
       // only PDE nodes, so this may follow it directly).
-      if (s == 1 && t + 1 < nstep)
-        ctile_far_field<CFG>(hi, hi_push, pf, (float)(d.tau0 + (step + 2) * d.dtau), tb.h, M, ig, jb + r0, r0,
-                             col);
+      if (s == 1 && t + 1 < nstep) ctile_far_field<CFG>(hi, hi_push, FF, t + 1, M, ig, jb + r0, r0, col);
       p ^= 1;
       cl_arrive();
       __syncthreads();
@@ -609,7 +631,7 @@ static void ctile_geometry(int M, int h, bool vec, CTileBatch& tb) {
 
 static size_t ctile_smem() {
   return (size_t)3 * CTileCfg::PLANE * sizeof(float) + (size_t)2 * CTileCfg::BH * CTileCfg::NCOL * sizeof(float) +
-         (size_t)CTileCfg::BH * sizeof(float4);
+         (size_t)FarTable<CTileCfg>::FLOATS * sizeof(float) + (size_t)CTileCfg::BH * sizeof(float4);
 }
 
 static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
