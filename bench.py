@@ -21,8 +21,13 @@ the 256 x 256 grid (bilinear restriction and prolongation).
                 serial fine stepping (one sparse LU factorisation, then implicit steps)
   clocks        nvidia-smi SM clock samples and throttle reasons during the timed region
   gpu_launches  the library's kernel launches inside the timed region (its own counters)
-  serving       the serving sample: requests of the seeded trace replayed through the server
-                (p50/p99 latency, solves/s against one request at a time)
+  serving       the serving sample: the first 200 requests of the seeded trace replayed through
+                the server at 1.5x the one-at-a-time capacity (p50/p99 latency, solves/s
+                against one request at a time)
+
+Under torchrun with N ranks each GPU solves its own copy of the workload (replicas, weak
+scaling; no data-path collective).  --slices instead partitions one solve's time slices over
+the ranks (paper_2404_02521_gb300/slices.py; strong scaling).
 
 --impl reference times the FP64 CPU oracle (oracle/) on the host cores on a bounded sample
 of the same workload, in the same unit.
@@ -363,6 +368,68 @@ def large_arm(args, world, local):
     }
 
 
+def slices_arm(args, world, rank, local):
+    """The large solve with its 128 time slices partitioned over the ranks (paper_2404_02521_gb300/
+    slices.py: contiguous slices per GPU, u_n handed on point to point in the serial sweep, one
+    FP64 all-reduce of the defect per iteration).  One solve per step for the whole job (strong
+    scaling); the time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2404_02521_gb300 as bs
+    from paper_2404_02521_gb300 import slices
+
+    pb = wl.large_cfg4()
+    g = bs.Grid(pb.M, pb.xmax)
+    g.set_coarse(256)
+    be = slices.GpuSlices(g, pb.params, pb.N, pb.fine_steps, pb.coarse_steps)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def solve():
+        if rank == 0:
+            be.initial()
+        return slices.parareal_partitioned(be, pb.N, pb.tol, pb.N)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms, ks = 0.0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k, d = solve()
+        torch.cuda.synchronize()
+        total_ms += 1e3 * (time.perf_counter() - t0)
+        ks.append(k)
+    barrier(world)
+    clk = clocks.stop()
+    t_max = barrier_max(total_ms, world)
+    pts = pb.M * pb.M * pb.N * pb.fine_steps
+    value = args.steps * pts / (t_max / 1e3)
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "basket1024_N128_fine1024_coarse4_on256", "grid": 1024, "slices": 128,
+                   "fine_steps": 1024, "coarse_grid": 256, "tol": 1e-4,
+                   "parallelism": f"time slices over {world} GPUs",
+                   "slices_per_gpu": [b - a for a, b in slices.partition(pb.N, world)],
+                   "l2": "flushed between timed steps (2x L2 buffer write); state 541 MB > L2"},
+        "time_to_tol_ms_per_solve": t_max / args.steps, "parareal_iterations": ks[-1],
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 16 * (pb.N + 1)},
+        "gpu_launches": None, "clocks": clk,
+        "note": "host-timed (the driver synchronises on each iteration's defect); value and e2e are the same "
+                "measurement: the initial state is formed on rank 0's GPU",
+    }
+
+
 def exchange_arm(args, local):
     """The 256 x 256 exchange-option workload (extra keys): Parareal to tol 1e-4 for each rho."""
     import torch
@@ -450,7 +517,8 @@ def serving_run(args):
     (seed 12345: basket/exchange 50/50, sigma ~ U[0.1,0.5], rho ~ U[-0.7,0.7],
     r ~ U[0,0.08], T ~ U[0.25,2], M in {64,128,256,512}, N in {16,32,64}; fine steps per slice
     64 doubled until the Jacobi bound is <= 0.7, one coarse step per slice, tol 1e-4).
-    Poisson arrivals at args.serve_load x the measured one-at-a-time capacity."""
+    Poisson arrivals at args.serve_load x the measured one-at-a-time capacity (above 1 the
+    queue grows, so the solves/s show what batching and overlap add)."""
     import numpy as np
     import torch
 
@@ -498,6 +566,8 @@ def serving_run(args):
         "parareal_iterations_mean": float(np.mean([r["iterations"] for r in res])),
         "results_max_rel_diff_vs_parareal_solve": diff,
         "fine_batches": stats["fine_batches"], "fine_slices_batched": stats["fine_items"],
+        "slices_per_fine_batch": stats["fine_items"] / max(1, stats["fine_batches"]),
+        "throughput_gain_vs_one_at_a_time": (n / makespan) / (n / fifo_span),
     }
 
 
@@ -577,8 +647,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-exchange", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--slices", action="store_true",
+                    help="partition one large solve's time slices over the ranks (strong scaling) "
+                         "instead of one independent solve per rank")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-load", type=float, default=1.5)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -588,6 +661,17 @@ def main():
     torch.cuda.set_device(local)
     import paper_2404_02521_gb300 as bs
     bs.load()
+    if args.slices:
+        import torch.distributed as dist
+        if not dist.is_initialized():   # the driver's collectives need a group, even of one
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", "29531")
+            dist.init_process_group("nccl", rank=rank, world_size=world)
+        out = slices_arm(args, world, rank, local)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        dist.destroy_process_group()
+        return
     r = large_arm(args, world, local)
     ex = exchange_arm(args, local) if (not args.no_exchange and world == 1) else None
     if rank != 0:

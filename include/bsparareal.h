@@ -207,6 +207,27 @@ int parareal_solve(const bs_grid* g, const bs_params* p, int N, int fine_steps,
                    int Kmax, float* u_out, int* k_done, double* defect_hist,
                    bs_stream stream);
 
+/* One serial coarse sweep of eq. (parareal) over the slices [n_begin, n_end) of a solve with N
+ * slices of [0, p->T], numerical G (coarse_steps implicit steps per slice, on the grid's
+ * coarse grid if bs_grid_set_coarse set one).  For drivers that partition the slices over
+ * several GPUs: each GPU sweeps its own contiguous range once it holds u_{n_begin} (the
+ * serial sweep's hand-off), and the Parareal defect is formed across GPUs from the norms.
+ *  k = -1: the initial sweep, U[n+1] = Gold[n] = G(U[n]);
+ *  k >= 0: iteration k, U[n+1] = Fb[n] + (G(U[n]) - Gold[n]), Gold[n] = G(U[n]) (reading c6),
+ *          with n_begin >= k; slice k's G is Gold[k] unchanged (u_k is exact after k
+ *          iterations), so for n_begin == k it is not recomputed.
+ *  U     device float[(N+1)*M*M], Fb and Gold device float[N*M*M]: full-size arrays indexed by
+ *        the global slice number; only U[n_begin .. n_end], Fb[n_begin .. n_end-1] and
+ *        Gold[n_begin .. n_end-1] are read or written.
+ *  norms device double[2*(N+1)]: for n in (n_begin, n_end], norms[2n] = ||U[n]||^2 and
+ *        norms[2n+1] = ||U[n]_new - U[n]_old||^2 (FP64 reductions; 0 for k = -1).  The defect of
+ *        iteration k is sqrt(max_{n > k} norms[2n+1]) / sqrt(max_{n >= 1} norms[2n]) over all
+ *        slices of all GPUs (reading c5).
+ * Asynchronous (enqueues kernels on `stream`).  Errors: BS_ERR_ARG (NULL, ranges), BS_ERR_CUDA;
+ * a coarse BiCGSTAB solve that hits its cap is reported by the next bs_grid_stats call. */
+int parareal_sweep_range(const bs_grid* g, const bs_params* p, int N, int coarse_steps, int k, int n_begin,
+                         int n_end, float* U, const float* Fb, float* Gold, double* norms, bs_stream stream);
+
 /* Number of Jacobi sweeps F uses per implicit step for these parameters and step size on
  * this grid, by how the step's solve starts: first_step = 1 for the first step of a launch
  * (zero increment), 0 for a step started from the previous increment (the second step; every

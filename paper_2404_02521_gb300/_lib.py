@@ -25,7 +25,7 @@ EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
            "bs_coarse_variant", "bs_coarse_variant_info", "bs_payoff3", "fine_propagate3", "coarse_propagate3", "parareal_solve3", "bs_server_create", "bs_server_submit", "bs_server_progress",
            "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for",
-           "bs_grid_set_coarse", "bs_device_allocations"]
+           "bs_grid_set_coarse", "bs_device_allocations", "parareal_sweep_range"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
 OPT_COARSE_VARIANT = 6
@@ -124,6 +124,7 @@ def load(path: Optional[str] = None):
     lib.bs_phase_stats.argtypes = [vp, P(d), P(i), P(d), P(i), P(i)]
     lib.parareal_solve_noalloc.argtypes = [i, d, P(bs_params), i, i, i, d, i, vp, P(i), P(d), vp]
     lib.bs_device_allocations.argtypes = [P(C.c_longlong)]
+    lib.parareal_sweep_range.argtypes = [vp, P(bs_params), i, i, i, i, i, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name != "bs_last_error":
             getattr(lib, name).restype = C.c_int
@@ -285,6 +286,16 @@ def parareal_solve_noalloc(M: int, xmax: float, p, N: int, fine_steps: int, coar
                                        C.byref(k), hist, _stream(stream))
     check(rc, allow=(BS_ERR_MAXITER,) if allow_maxiter else ())
     return rc, k.value, [hist[i] for i in range(k.value)]
+
+
+def parareal_sweep_range(g: Grid, p, N: int, coarse_steps: int, k: int, n_begin: int, n_end: int,
+                         U, Fb, Gold, norms, stream=None):
+    """The serial coarse sweep over slices [n_begin, n_end) (k = -1: the initial sweep)."""
+    bp = to_params(p)
+    return check(load().parareal_sweep_range(g.h, C.byref(bp), int(N), int(coarse_steps), int(k),
+                                             int(n_begin), int(n_end), _ptr(U),
+                                             _ptr(Fb) if Fb is not None else None, _ptr(Gold),
+                                             _ptr(norms), _stream(stream)))
 
 
 def bs_device_allocations() -> int:

@@ -434,6 +434,7 @@ int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* v
     *variant = g_opt.coarse_variant;
     return BS_OK;
   }
+  if (g->coarse_variant < 0) g->coarse_variant = coarse_tuned_variant(g->device, g->M);
   if (g->coarse_variant < 0) {
     rc = coarse_autotune(g, make_item(*p, 0.0, dtau_coarse), (cudaStream_t)stream, kAutotuneSteps, nullptr);
     if (rc) return rc;
@@ -496,6 +497,44 @@ struct PhaseTimer {
     if (e[1]) cudaEventDestroy(e[1]);
   }
 };
+
+int parareal_sweep_range(const bs_grid* gc, const bs_params* p, int N, int coarse_steps, int k, int n_begin,
+                         int n_end, float* U, const float* Fb, float* Gold, double* norms, bs_stream stream) {
+  bs_grid* g = const_cast<bs_grid*>(gc);
+  if (!g || !U || !Gold || !norms || (k >= 0 && !Fb))
+    return set_error(BS_ERR_ARG, "parareal_sweep_range: NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (N < 1 || coarse_steps < 1 || !(p->T > 0.0) || k < -1 || k >= N || n_begin < 0 || n_end > N ||
+      n_begin >= n_end || (k >= 0 && n_begin < k))
+    return set_error(BS_ERR_ARG, "parareal_sweep_range: N=%d coarse_steps=%d k=%d range [%d, %d)", N,
+                     coarse_steps, k, n_begin, n_end);
+  const double slice = p->T / N;
+  const ItemDesc dc = make_item(*p, 0.0, slice / coarse_steps);
+  SweepArgs a = {};
+  a.N = N;
+  a.csteps = coarse_steps;
+  a.slice_len = slice;
+  a.U = U;
+  a.Fb = Fb;
+  a.Gold = Gold;
+  a.norms = norms;
+  a.defect = g->dscal;   // scratch: the caller forms the defect from the norms
+  a.status = g->status;
+  a.tol = g_opt.krylov_tol;
+  a.maxit = g_opt.krylov_maxit;
+  a.mode = k < 0 ? SWEEP_INIT : SWEEP_ITER;
+  a.n_first = k < 0 ? 0 : k;
+  a.n_begin = n_begin;
+  a.n_end = n_end;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->coarse_M > 0 && g->coarse_M != g->M) {
+    g->n_coarse += (n_end - n_begin) * resampled_launches_per_slice() + 1;
+    return resampled_sweep(g, dc, a, s);
+  }
+  g->n_coarse += 1;
+  return launch_sweep(g, dc, a, s);
+}
 
 int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps, int coarse_kind,
                    int coarse_steps, const bs_pino* net, double tol, int Kmax, float* u_out,

@@ -1449,6 +1449,13 @@ int coarse_cached_variant(int device, int M) {
   return it != g_tuned.end() ? it->second : default_variant(M);
 }
 
+// The variant measured for (device, M) in this process, or -1 if none was measured yet.
+int coarse_tuned_variant(int device, int M) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find({device, M});
+  return it != g_tuned.end() ? it->second : -1;
+}
+
 // Times every launchable variant on a PROP solve of `steps` coarse steps from the payoff
 // state of d (best of three after one warm-up) and caches the fastest for (device, M).
 int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, int* chosen) {
@@ -1518,6 +1525,9 @@ int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, in
 // grid size (from the cache while a stream is being captured).
 static int resolve_variant(const bs_grid* g, const ItemDesc& d, cudaStream_t s, int* v) {
   bs_grid* gm = const_cast<bs_grid*>(g);
+  // one measurement per (device, M) for the whole process: every grid of that size then runs
+  // the same kernel and reduction order
+  if (g_opt.coarse_variant < 0 && gm->coarse_variant < 0) gm->coarse_variant = coarse_tuned_variant(g->device, g->M);
   if (g_opt.coarse_variant < 0 && gm->coarse_variant < 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool capturing = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;

@@ -297,6 +297,7 @@ int launch_sweep(const bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaSt
 // F by BiCGSTAB per implicit step for items whose Jacobi bound is >= 0.8 (capi.cu)
 int launch_krylov_fine(bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s);
 int coarse_cached_variant(int device, int M);   // tuned (or default) variant, no allocation
+int coarse_tuned_variant(int device, int M);    // tuned variant, -1 if none measured yet
 // Numerical G on the grid's coarse grid with bilinear resampling (resampled.cu).
 int resampled_propagate(bs_grid* g, const ItemDesc& d, const float* in, float* out, double tau0, int nsteps,
                         cudaStream_t s);

@@ -214,7 +214,10 @@ int resampled_sweep(bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStrea
   const int M = g->M, Mc = g->coarse_M;
   const size_t MM = (size_t)M * M;
   const int nblocks = rs_apply_blocks(MM);
-  for (int n = a.n_first; n < a.N; ++n) {
+  // slices of this call: the whole sweep, or the range [n_begin, n_end) (a partitioned sweep)
+  const int n_lo = a.n_end > 0 ? a.n_begin : a.n_first;
+  const int n_hi = a.n_end > 0 ? a.n_end : a.N;
+  for (int n = n_lo; n < n_hi; ++n) {
     const bool skip = (a.mode == SWEEP_ITER && n == a.n_first);
     const float* un = a.U + (size_t)n * MM;
     const double tau_n = n * a.slice_len;
@@ -232,8 +235,9 @@ int resampled_sweep(bs_grid* g, const ItemDesc& d, const SweepArgs& a, cudaStrea
     rs_apply_kernel<<<nblocks, 256, 0, s>>>(ra);
     BS_CUDA_TRY(cudaGetLastError());
   }
-  const int n_lo = a.mode == SWEEP_INIT ? 1 : a.n_first + 1;
-  rs_defect_kernel<<<1, 32, 0, s>>>(partials, nblocks, n_lo, a.N, a.n_first, a.norms, a.defect,
+  // norms of the slices this call wrote (and, for a whole sweep, the defect)
+  const int n_norm = a.n_end > 0 ? n_lo + 1 : (a.mode == SWEEP_INIT ? 1 : a.n_first + 1);
+  rs_defect_kernel<<<1, 32, 0, s>>>(partials, nblocks, n_norm, n_hi, a.n_first, a.norms, a.defect,
                                     a.mode == SWEEP_ITER ? 1 : 0);
   BS_CUDA_TRY(cudaGetLastError());
   return BS_OK;

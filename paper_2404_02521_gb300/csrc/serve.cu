@@ -167,8 +167,9 @@ static int class_setup(bs_server* sv, const bs_request& r) {
     bs_grid_destroy(g);
     return cuda_error(cudaGetLastError(), "bs_server: stream");
   }
-  // one measurement of the coarse band variant per grid size, before any request uses it
-  if (r.M <= 256 && g_opt.coarse_variant < 0) {
+  // one measurement of the coarse band variant per grid size and process, before any request
+  // uses it (a variant this process has already measured for M is kept)
+  if (r.M <= 256 && g_opt.coarse_variant < 0 && coarse_tuned_variant(sv->device, r.M) < 0) {
     const int cs = r.coarse_steps > 0 ? r.coarse_steps : 1;
     rc = coarse_autotune(g, make_item(r.p, 0.0, r.p.T / r.N / cs), s, kAutotuneSteps, nullptr);
     if (rc) {
@@ -350,7 +351,8 @@ static int progress(bs_server* sv) {
     for (Slot& sl : sv->slots)
       if (sl.phase == PH_FREE) { free_slot = &sl; break; }
     if (!free_slot) break;
-    const bs_request& r = sv->pending.front().second;
+    // a copy: pop_front below destroys the queued element (and may free its block)
+    const bs_request r = sv->pending.front().second;
     const size_t bytes = request_bytes(r);
     size_t off = 0;
     if (!sv->arena.alloc(bytes, &off)) break;   // wait for memory to free up

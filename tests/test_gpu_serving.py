@@ -110,3 +110,26 @@ def test_serving_result_is_parareal_solution(bs):
     assert res[0]["iterations"] == ko
     assert rel_err(to_np(out), Uo[6]) <= 6e-5
     assert rel_err(to_np(out), serial[6]) <= 1e-3
+
+
+def test_long_queue_admits_every_request_intact(bs):
+    # many more requests than slots, all queued at once: the pending queue is drained across
+    # many of its storage blocks, and every request must be admitted with its own parameters
+    # (its result equals the same request solved alone)
+    import torch
+    from paper_2404_02521_gb300 import serving
+    rng = np.random.default_rng(11)
+    reqs = []
+    for k in range(96):
+        p = wl.random_params(rng, wl.BASKET if k % 2 else wl.EXCHANGE, float(rng.uniform(0.25, 1.0)))
+        reqs.append(wl.Problem(f"q{k}", int(rng.choice([16, 24, 32])), 4.0, int(rng.choice([4, 6])), 0, 1, p))
+    outs = [torch.zeros((r.M, r.M), device="cuda") for r in reqs]
+    sv = bs.Server(1 << 28, 3)
+    res, _ = serving.replay(sv, reqs, [0.0] * len(reqs), outs)
+    st = sv.stats()
+    sv.close()
+    assert all(r is not None and r["status"] == 0 for r in res)
+    assert st["arena_used"] == 0
+    ref = alone(bs, reqs[::8])
+    for a, b in zip(outs[::8], ref):
+        assert torch.equal(a, b)
