@@ -106,10 +106,12 @@ def fine_sweeps_total(m0, m1, mx, mxl, steps):
 
 # Algorithmic FLOPs of one BiCGSTAB iteration per node of the coarse solve: two Jacobi-scaled
 # 9-point products (15 FLOP each: 4 FMA, 2 multiplies, 3 adds), six dot-product terms (12) and
-# the vector updates s, x, r, p (13).  Band variants with the polynomial preconditioner
-# M^{-1} = 2I - A^ evaluate two more scaled products and 2 y - A^ y twice (+34).
+# the vector updates s, x, r, p (13).  Band variants with the degree-1 polynomial
+# preconditioner M^{-1} = 2I - A^ evaluate two more scaled products and 2 y - A^ y twice (+34);
+# with the degree-2 one, M^{-1} y = y + E(1.5 y + E y), four more products, w = 2.5 y - A^ y
+# and (y + w) - A^ w twice (+68).
 COARSE_FLOPS_PER_NODE_ITER = 55
-COARSE_FLOPS_POLY_EXTRA = 34
+COARSE_FLOPS_POLY_EXTRA = {0: 0, 1: 34, 2: 68}
 
 # Algorithmic HBM bytes of the fine stepper per grid point and launch: the state read and
 # written once in FP32 (8 B); a launch that blocks s steps moves 8 / s B per point-step.
@@ -489,7 +491,7 @@ def exchange_arm(args, local):
     peak = fp32_peak_tflops(sm_max, sms)
     variant = bs.bs_coarse_variant(g, pb0.params, pb0.dtau_coarse)
     vinfo = bs.bs_coarse_variant_info(variant, M)
-    flops_node_iter = COARSE_FLOPS_PER_NODE_ITER + (COARSE_FLOPS_POLY_EXTRA if vinfo["poly"] else 0)
+    flops_node_iter = COARSE_FLOPS_PER_NODE_ITER + COARSE_FLOPS_POLY_EXTRA[vinfo["poly"]]
     coarse_tflops = (args.steps * krylov_iters * M * M * flops_node_iter / (phases["coarse_ms"] / 1e3) / 1e12
                      if phases["coarse_ms"] > 0 else 0.0)
     per_solve = total_ms / (args.steps * len(problems))
@@ -503,7 +505,7 @@ def exchange_arm(args, local):
         "sweep_band_kernel": {
             "ms_total": phases["coarse_ms"], "launches": phases["coarse_launches"], "bound": "alu",
             "achieved_tflops": coarse_tflops, "peak_tflops": peak, "frac": coarse_tflops / peak,
-            "band_variant": variant, "cluster_ctas": vinfo["ctas"], "polynomial_preconditioner": vinfo["poly"],
+            "band_variant": variant, "cluster_ctas": vinfo["ctas"], "polynomial_preconditioner_degree": vinfo["poly"],
             "quadratic_extrapolation": vinfo["quad"], "flops_per_node_iter": flops_node_iter,
             "krylov_iters_per_solve": krylov_iters / len(problems),
             "us_per_krylov_iter": 1e3 * phases["coarse_ms"] / max(1, args.steps * krylov_iters),

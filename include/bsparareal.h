@@ -275,7 +275,7 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  *                        variant measured fastest for that M (bs_coarse_variant); k >= 0:
  *                        always variant k (it must fit the grid, else the launch fails with
  *                        BS_ERR_ARG).  Variants differ in work split and reduction order
- *                        and, where their shared memory allows, use the polynomial
+ *                        and, where their shared memory allows, use a polynomial
  *                        preconditioner and quadratic initial-guess extrapolation (all solve
  *                        the same systems to the same Krylov tolerance).
  * Returns BS_OK or BS_ERR_ARG for an unknown option or an out-of-range value. */
@@ -319,11 +319,12 @@ int bs_coarse_variant(bs_grid* g, const bs_params* p, double dtau_coarse, int* v
 
 /* Shape and solver features of band variant `variant` on an M x M grid (M <= 256, the
  * variant's column count must cover M): *ctas = CTAs of its cluster, *threads = threads per
- * CTA, *rows = rows per thread, *poly = 1 if it applies the polynomial preconditioner
- * M^{-1} = 2I - A^ (two more scaled 9-point products per BiCGSTAB iteration), *quad = 1 if its
- * initial guesses extrapolate quadratically.  Both features are used where the variant's
- * shared memory holds their extra planes.  Any output pointer may be NULL.  Host-only.
- * Returns BS_OK or BS_ERR_ARG (unknown variant, or one that does not fit M). */
+ * CTA, *rows = rows per thread, *poly = the degree of its polynomial preconditioner (0: none;
+ * 1: M^{-1} = 2I - A^, two more scaled 9-point products per BiCGSTAB iteration; 2: M^{-1} =
+ * I + 1.5E + E^2 with E = I - A^, four more), *quad = 1 if its initial guesses extrapolate
+ * quadratically.  Each feature is used where the variant's shared memory holds its extra
+ * planes (and, for degree 2, its strips have at least three rows).  Any output pointer may be
+ * NULL.  Host-only.  Returns BS_OK or BS_ERR_ARG (unknown variant, or one that does not fit M). */
 int bs_coarse_variant_info(int variant, int M, int* ctas, int* threads, int* rows, int* poly, int* quad);
 
 /* Diagnostics of the coarse solves enqueued on this grid since the last parareal_solve or

@@ -336,11 +336,12 @@ def bs_coarse_variant(g: Grid, p, dtau_coarse: float, stream=None) -> int:
 
 
 def bs_coarse_variant_info(variant: int, M: int) -> dict:
-    """Cluster CTAs, threads per CTA, rows per thread and solver features (polynomial
-    preconditioner, quadratic extrapolation) of a band variant on an M x M grid (host-only)."""
+    """Cluster CTAs, threads per CTA, rows per thread and solver features (degree of the
+    polynomial preconditioner, 0 for none; quadratic extrapolation) of a band variant on an
+    M x M grid (host-only)."""
     v = [C.c_int(0) for _ in range(5)]
     check(load().bs_coarse_variant_info(int(variant), int(M), *[C.byref(x) for x in v]))
-    return {"ctas": v[0].value, "threads": v[1].value, "rows": v[2].value, "poly": bool(v[3].value),
+    return {"ctas": v[0].value, "threads": v[1].value, "rows": v[2].value, "poly": v[3].value,
             "quad": bool(v[4].value)}
 
 

@@ -345,26 +345,86 @@ __device__ __forceinline__ void precond_apply(const float* __restrict__ y, const
   }
 }
 
+// Q = M^{-1} y with the degree-2 Neumann polynomial M^{-1} = I + 1.5 E + E^2, E = I - A^,
+// evaluated as y + E w with w = 1.5 y + E y:  w = 2.5 y - A^ y,  Q = (y + w) - A^ w.  w goes to
+// the plane W (two halo rows each side; the edge groups evaluate them from y, which has
+// DH = 3 halo rows), then Q to its plane on the own rows and one halo row each side; the own
+// rows of Q are also returned in q.  Owner and neighbour evaluate a row with the same
+// operations in the same order (scaled_node, fmaf, then an add and a subtract), so a halo row
+// of W or Q equals its owner's row bit for bit and M^{-1} is the same operator on every CTA.
+// Outside the domain W and Q stay zero.
+template <class CFG>
+__device__ __forceinline__ void precond_apply2(const float* __restrict__ y, const float (&yc)[CFG::K],
+                                               float* __restrict__ W, float* __restrict__ Q, float (&q)[CFG::K],
+                                               const float4* __restrict__ rowc, const float* __restrict__ ID,
+                                               int col, int il, int ir, int r0, int grp, float ce, float cw,
+                                               float cgi, bool has_up, bool has_down, const float4 (&rc_top)[2],
+                                               const float (&id_top)[2], const float4 (&rc_bot)[2],
+                                               const float (&id_bot)[2]) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K, BH = CFG::BH, DH = 3;
+  float wk[K];
+  scaled_matvec_rc<CFG>(y + (DH - 1) * NCOL, yc, rowc, ID, col, il, ir, r0, ce, cw, cgi, wk);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    wk[k] = fmaf(2.5f, yc[k], -wk[k]);
+    W[(r0 + k + 2) * NCOL + col] = wk[k];
+  }
+  if (grp == 0 && has_up) {   // band rows -1 and -2 (W rows 1 and 0)
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float* yr = y + (DH - 1 - t) * NCOL;
+      W[(1 - t) * NCOL + col] = fmaf(2.5f, yr[col], -scaled_row(yr, NCOL, col, il, ir, rc_top[t], id_top[t], ce, cw, cgi));
+    }
+  }
+  if (grp == CFG::G - 1 && has_down) {   // band rows BH and BH + 1 (W rows BH + 2, BH + 3)
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const float* yr = y + (BH + DH + t) * NCOL;
+      W[(BH + 2 + t) * NCOL + col] = fmaf(2.5f, yr[col], -scaled_row(yr, NCOL, col, il, ir, rc_bot[t], id_bot[t], ce, cw, cgi));
+    }
+  }
+  __syncthreads();
+  scaled_matvec_rc<CFG>(W + NCOL, wk, rowc, ID, col, il, ir, r0, ce, cw, cgi, q);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    q[k] = (yc[k] + wk[k]) - q[k];
+    Q[(r0 + k + 1) * NCOL + col] = q[k];
+  }
+  if (grp == 0 && has_up) {
+    const float* wr = W + NCOL;
+    Q[col] = (y[(DH - 1) * NCOL + col] + wr[col]) - scaled_row(wr, NCOL, col, il, ir, rc_top[0], id_top[0], ce, cw, cgi);
+  }
+  if (grp == CFG::G - 1 && has_down) {
+    const float* wr = W + (BH + 2) * NCOL;
+    Q[(BH + 1) * NCOL + col] = (y[(BH + DH) * NCOL + col] + wr[col]) -
+                               scaled_row(wr, NCOL, col, il, ir, rc_bot[0], id_bot[0], ce, cw, cgi);
+  }
+}
+
 // Shared-memory layout of sweep_band_kernel (floats first, every array a multiple of 16 B).
-// The polynomial preconditioner (POLY) needs the p and s planes with two halo rows on each
-// side and one more plane; quadratic extrapolation (QUAD) one more own-row plane.  Each is
-// used where it fits in the 227 KB of a CTA (POLY first: it saves more).
+// The polynomial preconditioner needs the p and s planes with halo rows on each side as deep
+// as its degree plus one and one more plane (Q); the degree-2 polynomial (POLY2) also the plane
+// W with two halo rows, and strips of at least three rows (each edge group sends its DH rows);
+// quadratic extrapolation (QUAD) one more own-row plane.  Each is used where it fits in the
+// 227 KB of a CTA (the degree-2 polynomial first: it saves the most iterations).
 template <class CFG>
 struct SweepSmem {
   static constexpr int NCOL = CFG::NCOL, BH = CFG::BH, PLANE = CFG::PLANE, NW = CFG::NW;
   static constexpr size_t TAIL_BYTES = 2 * kMaxCluster * 4 * 8 + NW * 4 * 8 + 16 + sizeof(Scal);
-  static constexpr size_t floats(int dh, bool q, bool quad) {
-    return PLANE + 2 * (size_t)(BH + 2 * dh) * NCOL + (q ? PLANE : 0) + (2 + (quad ? 1 : 0)) * (size_t)BH * NCOL +
-           6 * (size_t)dh * NCOL + 2 * kMaxCluster * 4 + NW * 4;
+  static constexpr size_t floats(int dh, bool q, bool w, bool quad) {
+    return PLANE + 2 * (size_t)(BH + 2 * dh) * NCOL + (q ? PLANE : 0) + (w ? (size_t)(BH + 4) * NCOL : 0) +
+           (2 + (quad ? 1 : 0)) * (size_t)BH * NCOL + 6 * (size_t)dh * NCOL + 2 * kMaxCluster * 4 + NW * 4;
   }
   static constexpr bool fits(size_t f) { return f * 4 + TAIL_BYTES <= 227 * 1024; }
-  static constexpr bool POLY = fits(floats(2, true, false));
-  static constexpr int DH = POLY ? 2 : 1;   // halo rows of the p and s planes
-  static constexpr bool QUAD = fits(floats(DH, POLY, true));
+  static constexpr bool POLY2 = CFG::K >= 3 && fits(floats(3, true, true, false));
+  static constexpr bool POLY = POLY2 || fits(floats(2, true, false, false));
+  static constexpr int DH = POLY2 ? 3 : POLY ? 2 : 1;   // halo rows of the p and s planes
+  static constexpr bool QUAD = fits(floats(DH, POLY, POLY2, true));
   static constexpr int DPLANE = (BH + 2 * DH) * NCOL;
   static constexpr size_t u = 0, P = u + PLANE, S = P + DPLANE;         // u: one halo row; p, s: DH
   static constexpr size_t Q = S + DPLANE;        // preconditioned direction, one halo row (POLY only)
-  static constexpr size_t ID = Q + (POLY ? PLANE : 0), XP = ID + BH * NCOL;   // own rows
+  static constexpr size_t W = Q + (POLY ? PLANE : 0);   // degree-2 intermediate, two halo rows (POLY2)
+  static constexpr size_t ID = W + (POLY2 ? (size_t)(BH + 4) * NCOL : 0), XP = ID + BH * NCOL;   // own rows
   static constexpr size_t XQ = XP + BH * NCOL;   // d_{m-3}, own rows (QUAD only)
   static constexpr size_t VH = XQ + (QUAD ? BH * NCOL : 0);   // [2 parity][top DH, bottom DH rows][NCOL] v halo
   static constexpr size_t TH = VH + 4 * DH * NCOL;   // [top DH, bottom DH rows][NCOL] t halo rows
@@ -376,7 +436,7 @@ struct SweepSmem {
   static constexpr size_t MB_B = WPART_B + NW * 4 * 8, SCAL_B = MB_B + 16;
   static constexpr size_t BYTES = SCAL_B + sizeof(Scal);
   static_assert(FLOATS % 4 == 0, "16-byte alignment of the double arrays");
-  static_assert(FLOATS == floats(DH, POLY, QUAD), "layout and fit test agree");
+  static_assert(FLOATS == floats(DH, POLY, POLY2, QUAD), "layout and fit test agree");
   static_assert(CFG::K >= DH, "the edge groups send DH rows");
 };
 
@@ -420,6 +480,7 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   float* P = fs + L::P;      // search direction p   [DPLANE]: own row r at plane row r + DH
   float* S = fs + L::S;      // s                    [DPLANE]
   float* Q = fs + L::Q;      // M^{-1} p, M^{-1} s   [PLANE] (L::POLY)
+  float* W = fs + L::W;      // 2.5 y - A^ y          [(BH + 4) * NCOL] (L::POLY2)
   const float* P1 = P + (DH - 1) * NCOL;   // p and s seen with one halo row
   const float* S1 = S + (DH - 1) * NCOL;
   float* ID = fs + L::ID;    // inverse diagonal     [BH*NCOL]
@@ -453,6 +514,8 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   }
   if (L::POLY)
     for (int e = tid; e < CFG::PLANE; e += CFG::NT) Q[e] = 0.f;
+  if (L::POLY2)
+    for (int e = tid; e < (BH + 4) * NCOL; e += CFG::NT) W[e] = 0.f;
   for (int e = tid; e < 6 * DH * NCOL; e += CFG::NT) VH[e] = 0.f;   // VH and TH
   if (tid == 0) {
     mbar_init(mbar, 1);
@@ -472,17 +535,27 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
   const int ir = col + 1 < NCOL ? col + 1 : col;
   // coefficients of the halo rows next to the band (rows jbase-1 and jbase+BH), where the
   // edge groups evaluate the preconditioner
-  float4 rc_top = make_float4(0.f, 0.f, 0.f, 0.f), rc_bot = rc_top;
-  float id_top = 0.f, id_bot = 0.f;
+  // coefficients of the halo rows next to the band (rows jbase-1, jbase-2 and jbase+BH,
+  // jbase+BH+1), where the edge groups evaluate the preconditioner
+  float4 rc_top[2], rc_bot[2];
+  float id_top[2], id_bot[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    rc_top[t] = rc_bot[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    id_top[t] = id_bot[t] = 0.f;
+  }
   if (L::POLY) {
-    const int jt = jbase - 1, jb = jbase + BH;
-    if (grp == 0 && has_up) {
-      rc_top = sp.rowc[jt];
-      id_top = (jt < M - 1 && col < M - 1) ? inv_diag(d, col, jt) : 0.f;
-    }
-    if (grp == G - 1 && has_down) {
-      rc_bot = sp.rowc[jb];
-      id_bot = (jb < M - 1 && col < M - 1) ? inv_diag(d, col, jb) : 0.f;
+#pragma unroll
+    for (int t = 0; t < (L::POLY2 ? 2 : 1); ++t) {
+      const int jt = jbase - 1 - t, jb = jbase + BH + t;
+      if (grp == 0 && has_up) {
+        rc_top[t] = sp.rowc[jt];
+        id_top[t] = (jt < M - 1 && col < M - 1) ? inv_diag(d, col, jt) : 0.f;
+      }
+      if (grp == G - 1 && has_down) {
+        rc_bot[t] = sp.rowc[jb];
+        id_bot[t] = (jb < M - 1 && col < M - 1) ? inv_diag(d, col, jb) : 0.f;
+      }
     }
   }
   const float rdt = d.rdt;
@@ -625,10 +698,16 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             float* vh_top = VH + (2 * par) * DH * NCOL;
             float* vh_bot = vh_top + DH * NCOL;
             // v = A^ p (POLY: A^ M^{-1} p) ;  alpha = rho / (r^, v) ;  (r, r) for the stopping test
-            if constexpr (L::POLY) {
+            if constexpr (L::POLY2) {
+              float qk[K];
+              precond_apply2<CFG>(P, pk, W, Q, qk, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
+                                  rc_top, id_top, rc_bot, id_bot);
+              __syncthreads();
+              scaled_matvec_rc<CFG>(Q, qk, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
+            } else if constexpr (L::POLY) {
               float qk[K];
               precond_apply<CFG, DH>(P, pk, Q, qk, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
-                                     rc_top, id_top, rc_bot, id_bot);
+                                     rc_top[0], id_top[0], rc_bot[0], id_bot[0]);
               __syncthreads();
               scaled_matvec_rc<CFG>(Q, qk, rowc, ID, col, il, ir, r0, ce, cw, cgi, vv);
             } else {
@@ -691,10 +770,16 @@ __global__ void __launch_bounds__(CFG::NT, 1) sweep_band_kernel(const __grid_con
             }
             __syncthreads();
             // t = A^ s (POLY: A^ M^{-1} s) ;  omega = (t, s) / (t, t) ;  rho_new = (r^, s) - omega (r^, t)
-            if constexpr (L::POLY) {
+            if constexpr (L::POLY2) {
+              float qk[K];
+              precond_apply2<CFG>(S, rr, W, Q, qk, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
+                                  rc_top, id_top, rc_bot, id_bot);
+              __syncthreads();
+              scaled_matvec_rc<CFG>(Q, qk, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
+            } else if constexpr (L::POLY) {
               float qk[K];
               precond_apply<CFG, DH>(S, rr, Q, qk, rowc, ID, col, il, ir, r0, grp, ce, cw, cgi, has_up, has_down,
-                                     rc_top, id_top, rc_bot, id_bot);
+                                     rc_top[0], id_top[0], rc_bot[0], id_bot[0]);
               __syncthreads();
               scaled_matvec_rc<CFG>(Q, qk, rowc, ID, col, il, ir, r0, ce, cw, cgi, tt);
             } else {
@@ -1546,7 +1631,7 @@ static int resolve_variant(const bs_grid* g, const ItemDesc& d, cudaStream_t s, 
 
 template <class CFG>
 static void variant_features(int* poly, int* quad) {
-  *poly = SweepSmem<CFG>::POLY ? 1 : 0;
+  *poly = SweepSmem<CFG>::POLY2 ? 2 : SweepSmem<CFG>::POLY ? 1 : 0;
   *quad = SweepSmem<CFG>::QUAD ? 1 : 0;
 }
 

@@ -105,7 +105,7 @@ def pde_residual(u_new, u_old, dtau, prm, h):
     return (c - u_old[:, 1:-1, 1:-1]) / dtau - Ru
 
 
-def generate(M, N, fine_steps, n_problems, seed, device):
+def generate(M, N, fine_steps, n_problems, seed, device, rough=0.0):
     """Trajectories u_0..u_N of random problems from the library's fine propagator."""
     rng = np.random.default_rng(seed)
     g = bs.Grid(M, 4.0)
@@ -132,6 +132,9 @@ def generate(M, N, fine_steps, n_problems, seed, device):
     gen = torch.Generator(device="cpu").manual_seed(seed + 1)
     x = torch.linspace(0.0, 1.0, M, device=device)
     mask = ((1.0 - x).view(1, M) * (1.0 - x).view(M, 1))
+    edge = torch.ones(M, M, device=device)
+    edge[-1, :] = 0.0
+    edge[:, -1] = 0.0
     P0 = torch.empty((n_problems, N, M, M), device=device)
     P1 = torch.empty_like(P0)
     for k in range(n_problems):
@@ -139,6 +142,14 @@ def generate(M, N, fine_steps, n_problems, seed, device):
         amp = 0.05 * torch.rand(N, 1, 1, generator=gen).to(device)
         modes = torch.stack([torch.sin(math.pi * (a + 1) * x) for a in range(4)])   # [4][M]
         eta = torch.einsum("nab,ay,bx->nyx", coef, modes, modes) * mask / 4.0
+        if rough > 0.0:
+            # Rough perturbations as well (every other slice): white noise, which the fine
+            # propagator damps within a slice.  Parareal's coarse propagator must damp it too:
+            # a network that passes high-frequency error through unchanged (G ~ I beyond its
+            # retained modes) lets it accumulate along the slices instead of correcting it.
+            noise = torch.randn(N, M, M, generator=gen).to(device) * edge
+            odd = (torch.arange(N, device=device) % 2 == 1).view(N, 1, 1)
+            eta = torch.where(odd, rough * noise / 0.05, eta)
         scale = U[k, :N].abs().amax(dim=(1, 2)).view(N, 1, 1)
         P0[k] = U[k, :N] + amp * scale * eta
     for n in range(N):
@@ -160,6 +171,9 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--physics-weight", type=float, default=1e-4)
     ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--rough", type=float, default=0.0,
+                    help="relative size of the white-noise perturbations (0: smooth ones only)")
+    ap.add_argument("--lr", type=float, default=1e-3)
     args = ap.parse_args()
     dev = torch.device("cuda")
     torch.manual_seed(args.seed)
@@ -169,7 +183,7 @@ def main():
     sets = []
     for q, N in enumerate(int(v) for v in args.slices.split(",")):
         fine = max(1, int(round(1.0 / (N * args.fine_dtau))))
-        U, prm, P0, P1 = generate(M, N, fine, args.problems, args.seed + 7 * q, dev)
+        U, prm, P0, P1 = generate(M, N, fine, args.problems, args.seed + 7 * q, dev, args.rough)
         sets.append(dict(N=N, U=U, prm=prm, P0=P0, P1=P1, dtau=1.0 / N))
         print(f"data: {args.problems} trajectories x {N} slices of {fine} fine steps "
               f"({time.time() - t0:.1f} s)", flush=True)
@@ -177,7 +191,7 @@ def main():
     x = torch.arange(M, device=dev, dtype=torch.float32) * h
     Xg, Yg = x.view(1, M).expand(M, M), x.view(M, 1).expand(M, M)
     model = FNO().to(dev)
-    opt = torch.optim.Adam(model.parameters(), lr=1e-3)
+    opt = torch.optim.Adam(model.parameters(), lr=args.lr)
     sched = torch.optim.lr_scheduler.StepLR(opt, step_size=max(1, args.iters // 100), gamma=0.96)
     n_train = int(0.9 * args.problems)
     gen = torch.Generator(device="cpu").manual_seed(args.seed)

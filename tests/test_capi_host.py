@@ -99,13 +99,15 @@ def test_options_are_range_checked(lib):
 
 def test_coarse_variant_info(lib):
     # host-only query of a band variant: its cluster at M = 256 and which extra planes its
-    # shared memory holds (16-row bands: the preconditioner's and the third history plane;
-    # 32-row bands of 256 columns: the preconditioner's only)
+    # shared memory holds (16-row bands of 256 columns: the degree-2 preconditioner's and the
+    # third history plane; 32-row bands: the degree-1 preconditioner's only; strips of two
+    # rows: degree 1, which needs two halo rows, not three)
     from paper_2404_02521_gb300 import _lib
     v8 = _lib.bs_coarse_variant_info(8, 256)
-    assert v8 == {"ctas": 16, "threads": 256, "rows": 16, "poly": True, "quad": True}
+    assert v8 == {"ctas": 16, "threads": 256, "rows": 16, "poly": 2, "quad": True}
     v6 = _lib.bs_coarse_variant_info(6, 256)
-    assert v6["ctas"] == 8 and v6["poly"] and not v6["quad"]
+    assert v6["ctas"] == 8 and v6["poly"] == 1 and not v6["quad"]
+    assert _lib.bs_coarse_variant_info(1, 32)["poly"] == 1
     assert _lib.bs_coarse_variant_info(9, 100)["ctas"] == 7
     for bad in [(8, 100), (10, 256), (-1, 64), (0, 300)]:
         with pytest.raises(_lib.BSError):
