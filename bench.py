@@ -17,6 +17,8 @@ the 256 x 256 grid (bilinear restriction and prolongation).
   kernels       per-kernel event times, launches, rates and sweep counts
   exchange256   the 256 x 256 exchange-option workload (N=64 x 512 fine steps, rho in
                 {-0.5, 0, 0.7}): time to tolerance, serial fine, coarse-sweep statistics
+  coarse_models_128  the PINO network and the numerical G on 128 x 128 states, cost per state
+                at one and at 128 states per call
   cpu_baseline  the FP64 oracle on one host core, a bounded sample of the large solve's
                 serial fine stepping (one sparse LU factorisation, then implicit steps)
   clocks        nvidia-smi SM clock samples and throttle reasons during the timed region
@@ -432,6 +434,48 @@ def slices_arm(args, world, rank, local):
     }
 
 
+def coarse_models(local):
+    """The two coarse propagators on 128 x 128 basket states (the PINO workload's grid), per
+    state, one state per call (the serial sweep) and 128 states per call
+    (coarse_propagate_batched, as for concurrent solves): the PINO network (seeded random
+    weights of the reading's architecture -- cost only) against the numerical G's 4 implicit
+    steps."""
+    import tempfile
+
+    import torch
+
+    import paper_2404_02521_gb300 as bs
+    from paper_2404_02521_gb300 import pino_io
+
+    arch = wl.PinoArch()
+    w = wl.pino_random_weights(arch, seed=3)
+    fd_, path = tempfile.mkstemp(suffix=".bin")
+    os.close(fd_)
+    pino_io.write_weights(path, w, arch.in_channels, arch.width, arch.modes_x, arch.modes_y, arch.layers,
+                          arch.proj_hidden)
+    net = bs.Pino(path)
+    os.unlink(path)
+    pb = wl.pino_cfg3()
+    M = pb.M
+    g = bs.Grid(M, pb.xmax)
+    stream = torch.cuda.current_stream(torch.device("cuda", local))
+    u0 = torch.empty((M, M), device="cuda")
+    bs.bs_payoff(g, pb.params, u0)
+    out = {}
+    for B in (1, 128):
+        ins = [u0.clone() for _ in range(B)]
+        outs = [torch.empty_like(u0) for _ in range(B)]
+        for name, kind, nt, steps in (("pino", bs.COARSE_PINO, net, 1), ("numerical_4_steps", bs.COARSE_NUM, None, 4)):
+            def call():
+                bs.coarse_propagate_batched(g, kind, nt, [pb.params] * B, ins, outs, [0.25] * B, pb.params.T / pb.N,
+                                            steps, stream=stream)
+            for _ in range(3):
+                call()
+            ms, _ = timed(stream, lambda: [call() for _ in range(5)])
+            out[f"{name}_us_per_state_batch{B}"] = 1e3 * ms / 5 / B
+    return out
+
+
 def exchange_arm(args, local):
     """The 256 x 256 exchange-option workload (extra keys): Parareal to tol 1e-4 for each rho."""
     import torch
@@ -676,6 +720,7 @@ def main():
         return
     r = large_arm(args, world, local)
     ex = exchange_arm(args, local) if (not args.no_exchange and world == 1) else None
+    cm = coarse_models(local) if (not args.no_exchange and world == 1) else None
     if rank != 0:
         return
     cpu = None
@@ -708,6 +753,7 @@ def main():
         "roofline": r["roof"],
         "kernels": r["kernels"],
         "exchange256": ex,
+        "coarse_models_128": cm,
         "cpu_baseline": cpu,
         "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["launches"],

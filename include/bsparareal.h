@@ -182,6 +182,22 @@ int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_pa
                      const float* u_in, float* u_out, double tau0, double dtau_slice,
                      int nsteps, bs_stream stream);
 
+/* Coarse propagator G for B independent states at once (the same grid): as coarse_propagate
+ * for item b with p[b], u_in[b] -> u_out[b], starting at tau0[b], over dtau_slice.
+ *  kind = BS_COARSE_NUM: one thread-block cluster per state, one launch per run of
+ *    consecutive items with equal parameters (at most 64 states each); on a grid with a
+ *    coarse grid (bs_grid_set_coarse) the states are propagated one after another.
+ *  kind = BS_COARSE_PINO: the network on up to 128 states per launch chain (every GEMM of the
+ *    chain carries the states as extra rows or grid blocks); nsteps is ignored.
+ * For concurrent solves or requests whose coarse steps are due together (a slice of each).
+ * Results for an item do not depend on B or on the other items (bitwise).
+ *  p[B], u_in[B], u_out[B], tau0[B]  host arrays (u_in/u_out: device float[M*M], may alias)
+ * Asynchronous.  Errors: BS_ERR_ARG (NULL, B < 1, dtau_slice <= 0, nsteps < 1 for NUM, a
+ * network for NUM or none for PINO), BS_ERR_OOM, BS_ERR_CUDA. */
+int coarse_propagate_batched(const bs_grid* g, int kind, const bs_pino* net, const bs_params* p,
+                             const float* const* u_in, float* const* u_out, const double* tau0,
+                             double dtau_slice, int nsteps, int B, bs_stream stream);
+
 /* Load PINO weights (Sec. 3.5: FNO backbone with lifting, L Fourier layers, projection;
  * batch norm folded into the pointwise weights) from a little-endian file written by
  * paper_2404_02521_gb300/pino_train.py.  Weights are converted to BF16 on load.

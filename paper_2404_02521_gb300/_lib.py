@@ -25,7 +25,7 @@ EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
            "bs_coarse_variant", "bs_coarse_variant_info", "bs_payoff3", "fine_propagate3", "coarse_propagate3", "parareal_solve3", "bs_server_create", "bs_server_submit", "bs_server_progress",
            "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for",
-           "bs_grid_set_coarse", "bs_device_allocations", "parareal_sweep_range"]
+           "bs_grid_set_coarse", "bs_device_allocations", "parareal_sweep_range", "coarse_propagate_batched"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
 OPT_COARSE_VARIANT = 6
@@ -125,6 +125,7 @@ def load(path: Optional[str] = None):
     lib.parareal_solve_noalloc.argtypes = [i, d, P(bs_params), i, i, i, d, i, vp, P(i), P(d), vp]
     lib.bs_device_allocations.argtypes = [P(C.c_longlong)]
     lib.parareal_sweep_range.argtypes = [vp, P(bs_params), i, i, i, i, i, vp, vp, vp, vp, vp]
+    lib.coarse_propagate_batched.argtypes = [vp, i, vp, P(bs_params), P(vp), P(vp), P(d), d, i, i, vp]
     for name in EXPORTS:
         if name != "bs_last_error":
             getattr(lib, name).restype = C.c_int
@@ -286,6 +287,18 @@ def parareal_solve_noalloc(M: int, xmax: float, p, N: int, fine_steps: int, coar
                                        C.byref(k), hist, _stream(stream))
     check(rc, allow=(BS_ERR_MAXITER,) if allow_maxiter else ())
     return rc, k.value, [hist[i] for i in range(k.value)]
+
+
+def coarse_propagate_batched(g: Grid, kind: int, net, params: Sequence, u_in: Sequence, u_out: Sequence,
+                             tau0: Sequence[float], dtau_slice: float, nsteps: int = 1, stream=None):
+    """G on len(u_in) independent states at once (numerical: nsteps steps; PINO: the network)."""
+    B = len(u_in)
+    bp = (bs_params * B)(*[to_params(p) for p in params])
+    ins = (C.c_void_p * B)(*[_ptr(u) for u in u_in])
+    outs = (C.c_void_p * B)(*[_ptr(u) for u in u_out])
+    t0 = (C.c_double * B)(*[float(t) for t in tau0])
+    return check(load().coarse_propagate_batched(g.h, int(kind), net.h if net is not None else None, bp, ins, outs,
+                                                 t0, float(dtau_slice), int(nsteps), B, _stream(stream)))
 
 
 def parareal_sweep_range(g: Grid, p, N: int, coarse_steps: int, k: int, n_begin: int, n_end: int,

@@ -334,6 +334,67 @@ int coarse_propagate(const bs_grid* g, int kind, const bs_pino* net, const bs_pa
   return set_error(BS_ERR_ARG, "coarse_propagate: unknown kind %d", kind);
 }
 
+int coarse_propagate_batched(const bs_grid* g, int kind, const bs_pino* net, const bs_params* p,
+                             const float* const* u_in, float* const* u_out, const double* tau0,
+                             double dtau_slice, int nsteps, int B, bs_stream stream) {
+  if (!g || !p || !u_in || !u_out || !tau0) return set_error(BS_ERR_ARG, "coarse_propagate_batched: NULL argument");
+  if (B < 1) return set_error(BS_ERR_ARG, "coarse_propagate_batched: B=%d", B);
+  if (!(dtau_slice > 0.0)) return set_error(BS_ERR_ARG, "coarse_propagate_batched: dtau_slice <= 0");
+  for (int b = 0; b < B; ++b) {
+    int rc = check_params(&p[b]);
+    if (rc) return rc;
+    if (!u_in[b] || !u_out[b]) return set_error(BS_ERR_ARG, "coarse_propagate_batched: NULL state %d", b);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  bs_grid* gm = const_cast<bs_grid*>(g);
+  if (kind == BS_COARSE_PINO) {
+    std::vector<ItemDesc> items((size_t)B);
+    for (int b = 0; b < B; ++b) items[(size_t)b] = make_item(p[b], tau0[b], dtau_slice);
+    gm->n_coarse += ((B + 127) / 128) * pino_launches_per_step(const_cast<bs_pino*>(net));
+    return pino_propagate_batched(const_cast<bs_pino*>(net), g, items.data(), u_in, u_out, B, s);
+  }
+  if (kind != BS_COARSE_NUM) return set_error(BS_ERR_ARG, "coarse_propagate_batched: unknown kind %d", kind);
+  if (net) return set_error(BS_ERR_ARG, "coarse_propagate_batched: net must be NULL for BS_COARSE_NUM");
+  if (nsteps < 1) return set_error(BS_ERR_ARG, "coarse_propagate_batched: nsteps < 1");
+  if (g->coarse_M > 0 && g->coarse_M != g->M) {   // resampled G: state after state
+    for (int b = 0; b < B; ++b) {
+      gm->n_coarse += resampled_launches_per_slice();
+      int rc = resampled_propagate(gm, make_item(p[b], tau0[b], dtau_slice / nsteps), u_in[b], u_out[b], tau0[b],
+                                   nsteps, s);
+      if (rc) return rc;
+    }
+    return BS_OK;
+  }
+  // one cluster per state, one launch per run of consecutive states with the same parameters
+  auto same = [](const bs_params& a, const bs_params& b) {
+    return a.sigma1 == b.sigma1 && a.sigma2 == b.sigma2 && a.rho == b.rho && a.r == b.r && a.strike == b.strike &&
+           a.w1 == b.w1 && a.w2 == b.w2 && a.payoff == b.payoff && a.strike2 == b.strike2 && a.cash == b.cash;
+  };
+  int i = 0;
+  while (i < B) {
+    SweepArgs a = {};
+    a.mode = SWEEP_PROP;
+    a.n_first = 0;
+    a.N = 1;
+    a.csteps = nsteps;
+    a.slice_len = 0.0;
+    a.status = g->status;
+    a.tol = g_opt.krylov_tol;
+    a.maxit = g_opt.krylov_maxit;
+    int j = i;
+    while (j < B && j - i < kMaxProp && same(p[i], p[j])) {
+      a.prop[j - i] = PropItem{u_in[j], u_out[j], tau0[j]};
+      ++j;
+    }
+    a.nprop = j - i;
+    gm->n_coarse += 1;
+    int rc = launch_sweep(g, make_item(p[i], 0.0, dtau_slice / nsteps), a, s);
+    if (rc) return rc;
+    i = j;
+  }
+  return BS_OK;
+}
+
 int bs_set_option(int option, double value) {
   switch (option) {
     case BS_OPT_FINE_SWEEPS:

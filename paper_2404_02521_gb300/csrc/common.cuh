@@ -322,6 +322,8 @@ int coarse_autotune(bs_grid* g, const ItemDesc& d, cudaStream_t s, int steps, in
 int pino_check(const bs_pino* net, int M);
 int pino_propagate(bs_pino* net, const bs_grid* g, const ItemDesc& d, const float* in, float* out,
                    double tau0, double dtau, cudaStream_t s);
+int pino_propagate_batched(bs_pino* net, const bs_grid* g, const ItemDesc* items, const float* const* in,
+                           float* const* out, int B, cudaStream_t s);   // items[b].tau0, .dtau: the slice
 int pino_sweep(bs_pino* net, const bs_grid* g, const ItemDesc& d, const SweepArgs& a,
                double* partials, cudaStream_t s);
 size_t pino_partials_bytes(int M, int N);

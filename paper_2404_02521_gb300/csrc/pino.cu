@@ -537,6 +537,34 @@ int pino_propagate(bs_pino* net, const bs_grid* g, const ItemDesc& d, const floa
   return pino_run(net, *R, R->st, 1, g->M, aa, false, s);
 }
 
+// The PINO on B independent states at once (coarse_propagate_batched): one network launch
+// chain per chunk of at most kPinoBatch states (the mixing GEMM holds a chunk's states in one
+// 128-row tile).  A state's result does not depend on the others in its chunk: every output
+// row of every GEMM is its own dot product.
+constexpr int kPinoBatch = 128;
+int pino_propagate_batched(bs_pino* net, const bs_grid* g, const ItemDesc* items, const float* const* in,
+                           float* const* out, int B, cudaStream_t s) {
+  int rc = pino_check(net, g->M);
+  if (rc) return rc;
+  const int chunk = B < kPinoBatch ? B : kPinoBatch;
+  PinoRes* R;
+  if ((rc = ensure_res(net, network_grid(g->M), chunk, chunk, &R))) return rc;
+  std::vector<PinoState> sts((size_t)chunk);
+  for (int b0 = 0; b0 < B; b0 += kPinoBatch) {
+    const int nb = (B - b0) < kPinoBatch ? (B - b0) : kPinoBatch;
+    for (int i = 0; i < nb; ++i) {
+      const ItemDesc& d = items[b0 + i];
+      sts[(size_t)i] = make_state(d, in[b0 + i], out[b0 + i], g->M, g->xmax, d.tau0, d.dtau);
+    }
+    // stream-ordered after the previous chunk's kernels, which read the descriptors
+    BS_CUDA_TRY(cudaMemcpyAsync(R->st, sts.data(), (size_t)nb * sizeof(PinoState), cudaMemcpyHostToDevice, s));
+    ApplyArgs aa = {};
+    aa.mode = PAPPLY_PROP;
+    if ((rc = pino_run(net, *R, R->st, nb, g->M, aa, false, s))) return rc;
+  }
+  return BS_OK;
+}
+
 // One serial Parareal sweep with the PINO as G (mode SWEEP_INIT or SWEEP_ITER), on the same
 // buffers as the numerical sweep.  partials: [(N+1)][nblocks][2] doubles of workspace.
 int pino_sweep(bs_pino* net, const bs_grid* g, const ItemDesc& d, const SweepArgs& a,

@@ -253,3 +253,26 @@ def test_maxiter_status(bs):
     # K = N: every slice is exact, so the solve has converged whatever the last defect
     rc, k, defects, _ = gpu_parareal(bs, pb, 1e-14, pb.N)
     assert rc == 0 and k == pb.N and len(defects) == pb.N
+
+
+@pytest.mark.parametrize("M,Mc", [(64, 0), (300, 0), (128, 64)])
+def test_coarse_batched_equals_single(bs, M, Mc):
+    # numerical G on several states at once (one cluster each; a launch per run of equal
+    # parameters; on a coarse grid state after state) equals coarse_propagate per state
+    import torch
+    pA = wl.Params(0.25, 0.35, 0.7, 0.03, payoff=wl.EXCHANGE)
+    pB = wl.Params(0.3, 0.2, 0.5, 0.05, payoff=wl.BASKET)
+    ps = [pA, pA, pB, pA]
+    g = bs.Grid(M, 4.0)
+    if Mc:
+        g.set_coarse(Mc)
+    ins = [to_gpu(start_state(M, 4.0, p, "random", seed=k)) for k, p in enumerate(ps)]
+    outs = [torch.empty_like(u) for u in ins]
+    taus = [0.1, 0.2, 0.1, 0.3]
+    bs.coarse_propagate_batched(g, bs.COARSE_NUM, None, ps, ins, outs, taus, 1.0 / 64, 2)
+    torch.cuda.synchronize()
+    for k, p in enumerate(ps):
+        one = torch.empty_like(ins[k])
+        bs.coarse_propagate(g, bs.COARSE_NUM, None, p, ins[k], one, taus[k], 1.0 / 64, 2)
+        torch.cuda.synchronize()
+        assert torch.equal(one, outs[k]), k

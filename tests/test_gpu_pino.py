@@ -163,6 +163,28 @@ def test_pino_parareal_matches_oracle_parareal(bs, tmp_path):
         assert abs(a - b) <= (2 * pb.N + 1) * PINO_REL_TOL * b, (a, b)
 
 
+@pytest.mark.parametrize("M,B", [(96, 5), (128, 3), (64, 130)])
+def test_pino_batched_equals_single(bs, weights, M, B):
+    # several states through one network launch chain (B = 130: two chunks of at most 128)
+    # give each state's single-state result bit for bit
+    import torch
+    path, _, _ = weights
+    net = bs.Pino(path)
+    rng = np.random.default_rng(M + B)
+    ps = [wl.random_params(rng, wl.BASKET if b % 2 else wl.EXCHANGE) for b in range(B)]
+    ins = [to_gpu(start_state(M, 4.0, ps[b], "random", seed=b)) for b in range(B)]
+    outs = [torch.empty_like(u) for u in ins]
+    taus = [0.01 * b for b in range(B)]
+    g = bs.Grid(M, 4.0)
+    bs.coarse_propagate_batched(g, bs.COARSE_PINO, net, ps, ins, outs, taus, 1.0 / 64)
+    torch.cuda.synchronize()
+    for b in sorted({0, 1, B // 2, B - 1}):
+        one = torch.empty_like(ins[b])
+        bs.coarse_propagate(g, bs.COARSE_PINO, net, ps[b], ins[b], one, taus[b], 1.0 / 64, 1)
+        torch.cuda.synchronize()
+        assert torch.equal(one, outs[b]), b
+
+
 def test_pino_load_rejects_bad_files(bs, tmp_path):
     p = tmp_path / "bad.bin"
     p.write_bytes(b"BSPINO01" + b"\0" * 16)
