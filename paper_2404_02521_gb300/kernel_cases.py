@@ -21,6 +21,8 @@ workloads, one kernel each:
              numerical G with 4 steps per slice on a 256x256 grid (bilinear resampling);
              prints Parareal time to tolerance, iterations and serial fine stepping time
   pino128    the PINO coarse propagator on 64 states of 128x128 (random weights)
+  pino128b   the PINO on 128 states of 128x128 in one coarse_propagate_batched call (random
+             weights): the network's GEMM chain with the states as extra rows or blocks
   resample1024  Parareal to K = N = 4 on 1024x1024 basket states with numerical G on the 256x256
              grid (bilinear restriction and prolongation kernels, 64 fine steps per slice)
   fine3_64   three-asset F: 16 states of 64^3 nodes, 64 implicit steps (19-point stencil)
@@ -138,6 +140,30 @@ def case_pino128(bs, wl, torch):
     return run
 
 
+def case_pino128b(bs, wl, torch):
+    from paper_2404_02521_gb300 import pino_io
+    arch = wl.PinoArch()
+    w = wl.pino_random_weights(arch, seed=3)
+    fd, path = tempfile.mkstemp(suffix=".bin")
+    os.close(fd)
+    pino_io.write_weights(path, w, arch.in_channels, arch.width, arch.modes_x, arch.modes_y,
+                          arch.layers, arch.proj_hidden)
+    net = bs.Pino(path)
+    os.unlink(path)
+    pb = wl.pino_cfg3()
+    g = bs.Grid(pb.M, pb.xmax)
+    u0 = torch.empty((pb.M, pb.M), device="cuda")
+    bs.bs_payoff(g, pb.params, u0)
+    ins = [u0.clone() for _ in range(128)]
+    outs = [torch.empty_like(u0) for _ in range(128)]
+
+    def run():
+        bs.coarse_propagate_batched(g, bs.COARSE_PINO, net, [pb.params] * 128, ins, outs, [0.25] * 128,
+                                    pb.params.T / pb.N)
+    run.net = net
+    return run
+
+
 def case_large1024(bs, wl, torch):
     import time
     pb = wl.large_cfg4()
@@ -212,6 +238,7 @@ def case_coarse3_64(bs, wl, torch):
 
 
 CASES = {"fine256": case_fine256, "coarse256": case_coarse256, "solve256": case_solve256,
+         "pino128b": case_pino128b,
          "tile1024": case_tile1024,
          "coarse512": case_coarse512, "pino128": case_pino128, "large1024": case_large1024,
          "resample1024": case_resample1024, "fine3_64": case_fine3_64,
