@@ -274,13 +274,14 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  *                        (default 0.5: two sweeps, the structural minimum, wherever q <= 0.707;
  *                        at the 1024 x 1024 large-solve step, q = 0.63, the error against the FP64
  *                        oracle after 1024 steps is 6e-8 max|V| with two, three or five sweeps)
- *  BS_OPT_PIPELINE       1 (default): parareal_solve with the numerical G on the state grid
- *                        and N >= 8 splits each coarse sweep into chunks of consecutive
- *                        slices (as many as F runs in one wave beside the sweep's cluster, at
- *                        most a quarter of them) and runs F for a chunk on a second stream as
- *                        soon as the sweep has produced its input states (F of the next
- *                        iteration speculatively, before the defect is known); 0: F and the
- *                        sweep alternate as whole phases
+ *  BS_OPT_PIPELINE       1 (default): parareal_solve with the numerical G (on the state grid
+ *                        or on a coarse grid) and N >= 8 splits each coarse sweep into chunks
+ *                        of consecutive slices (as many as F runs in one wave beside the
+ *                        sweep's cluster, at most a quarter of them) and runs F for a chunk on
+ *                        a second stream as soon as the sweep has produced its input states
+ *                        (F of the next iteration speculatively, before the defect is known,
+ *                        where a state fits one cluster or from the second iteration on); 0: F
+ *                        and the sweep alternate as whole phases
  *  BS_OPT_KRYLOV_TOL     relative residual at which a coarse BiCGSTAB solve (numerical G) stops
  *                        (1e-5; G need only be a deterministic approximation of F)
  *  BS_OPT_FINE_KRYLOV_TOL  ... a fine BiCGSTAB step (F for step sizes beyond Jacobi) stops (1e-6)

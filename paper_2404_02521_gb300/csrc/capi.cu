@@ -627,8 +627,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   const bool krylov_f = sweeps == 0;   // Jacobi bound >= 0.8: F by BiCGSTAB per step
   // numerical G on this grid: F overlapped with the chunked coarse sweep (Krylov F of grids
   // beyond one cluster shares the coarse solver's global workspace and stays sequential)
-  if (!pino && !(g->coarse_M > 0 && g->coarse_M != g->M) && g_opt.pipeline && pipeline_eligible(N) &&
-      !(krylov_f && g->M > 256))
+  if (!pino && g_opt.pipeline && pipeline_eligible(N) && !(krylov_f && g->M > 256))
     return parareal_pipelined(g, p, N, fine_steps, coarse_steps, tol, Kmax, u_out, user_u0, k_done,
                               defect_hist, s);
   const size_t part_bytes = pino ? pino_partials_bytes(M, N) : 0;

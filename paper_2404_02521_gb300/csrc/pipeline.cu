@@ -1,4 +1,4 @@
-// Pipelined Parareal driver (numerical G on the state grid).
+// Pipelined Parareal driver (numerical G, on the state grid or on the grid's coarse grid).
 //
 // Eq. (parareal) needs F(u_n^k) only when the sweep of iteration k-1 has produced u_n^k, so F
 // and the serial coarse sweep need not alternate as whole phases.  Each sweep is split into
@@ -6,14 +6,21 @@
 // highest priority (so that a sweep chunk's 16-CTA cluster is placed before an F chunk that
 // becomes ready at the same moment); the F launch of a chunk goes to a low-priority stream
 // and waits (cudaStreamWaitEvent) for the sweep chunk that finished its input states.  Both
-// streams start after the caller's stream and the caller's stream waits for both at the end.  The sweep chunk of iteration k waits for the F chunk
-// of iteration k over the same slices.  F of iteration k+1 is launched before the host has
-// read the defect of iteration k (speculatively: it writes only the F workspace, and is
-// wasted if iteration k converged), so it runs on the SMs the 16-CTA coarse cluster leaves
-// free while the sweep continues.  All ordering is between whole kernels through stream
-// events; no kernel waits on another.  Results: the same Parareal iteration; the coarse
-// solves restart their extrapolated initial guesses at chunk boundaries, so G agrees with
-// the unchunked sweep to the Krylov tolerance, not bitwise.
+// streams start after the caller's stream and the caller's stream waits for both at the end.
+// The sweep chunk of iteration k waits for the F chunk of iteration k over the same slices.
+// The first input of F chunk c, u_{cS}, is the last state sweep chunk c-1 writes, and the next
+// sweep rewrites it while F chunk c may still be waiting for SMs; so each sweep chunk also
+// copies its last state into a snapshot (two sets, by iteration parity) that F chunk c reads.
+// F of iteration k+1 is launched before the host has read the defect of iteration k
+// (speculatively: it writes only the F workspace, and is wasted if iteration k converged), so
+// it runs on the SMs the 16-CTA coarse cluster leaves free while the sweep continues.  All ordering is between whole kernels through stream
+// events; no kernel waits on another.  Results: the same Parareal iteration; on the state grid
+// the coarse solves restart their extrapolated initial guesses at chunk boundaries, so G agrees
+// with the unchunked sweep to the Krylov tolerance, not bitwise; with G on a coarse grid every
+// slice's coarse solve starts afresh anyway, and the result is the phase-by-phase driver's bit
+// for bit.  F of the next iteration is speculated only where it is cheap (grids whose states
+// live in one cluster) or from the second iteration on: on the tiled grids one F pass is most
+// of a solve, and a solve that converges after one iteration would pay for a second.
 #include <vector>
 
 #include "common.cuh"
@@ -117,16 +124,24 @@ int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, in
   const int sweepsx = grid_sweeps(g, *p, dtau_f, START_EXTRAP);
   const int sweepsxl = grid_sweeps(g, *p, dtau_f, START_EXTRAP_LATE);
   const bool krylov_f = sweeps == 0;
+  const bool resampled = g->coarse_M > 0 && g->coarse_M != g->M;
+  const bool cheap_f = g->shape.C >= 1 && g->shape.C <= kMaxCluster;   // a state per cluster
   const ItemDesc dc = make_item(*p, 0.0, slice / coarse_steps);
   int S = 0;
   int rc = pipeline_chunk(g, dc, N, caller, &S);
   if (rc) return rc;
   const int chunks = (N + S - 1) / S;
-  rc = ensure(g->ws_par, sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1));
+  // F buffers, G_old, the slice norms, then two sets (by iteration parity) of chunk-boundary
+  // snapshots: snap[par][c] holds u_{cS} of the iterate that F of that parity reads
+  const size_t base = sizeof(float) * 2 * (size_t)N * MM + sizeof(double) * 2 * (N + 1);
+  const size_t snap_off = (base + 255) & ~(size_t)255;
+  rc = ensure(g->ws_par, snap_off + sizeof(float) * 2 * (size_t)chunks * MM);
   if (rc) return rc;
   float* Fb = (float*)g->ws_par.ptr;
   float* Gold = Fb + (size_t)N * MM;
   double* norms = (double*)(Gold + (size_t)N * MM);
+  float* snap = (float*)((unsigned char*)g->ws_par.ptr + snap_off);
+  auto snap_at = [&](int parity, int c) { return snap + ((size_t)parity * chunks + c) * MM; };
   PipeState* ps;
   if ((rc = pipe_state(g, chunks, &ps))) return rc;
   cudaStream_t sf = ps->sf, s = ps->ss;
@@ -171,9 +186,22 @@ int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, in
       a.n_first = k;
       a.n_begin = lo;
       a.n_end = hi;
-      int r = launch_sweep(g, dc, a, s);
+      int r;
+      if (resampled) {
+        r = resampled_sweep(g, dc, a, s);
+        g->n_coarse += (hi - lo) * resampled_launches_per_slice() + 1;
+      } else {
+        r = launch_sweep(g, dc, a, s);
+        g->n_coarse += 1;
+      }
       if (r) return r;
-      g->n_coarse += 1;
+      // u_hi is the first input of the next F chunk, which may not have read it yet when the
+      // next iteration's sweep chunk c overwrites it: that F chunk reads this copy instead
+      if (hi < N) {
+        const int par = mode == SWEEP_INIT ? 0 : (k + 1) & 1;
+        BS_CUDA_TRY(cudaMemcpyAsync(snap_at(par, c + 1), u_out + (size_t)hi * MM, sizeof(float) * MM,
+                                    cudaMemcpyDeviceToDevice, s));
+      }
       if (timing) {
         BS_CUDA_TRY(cudaEventRecord(t1, s));
         t_coarse.emplace_back(t0, t1);
@@ -193,7 +221,8 @@ int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, in
       items.clear();
       for (int n = lo; n < hi; ++n) {
         ItemDesc d = make_item(*p, n * slice, dtau_f);
-        d.in = u_out + (size_t)n * MM;
+        // u_{cS} is rewritten by this iteration's sweep chunk c-1 while k < cS
+        d.in = (n == c * S && c >= 1 && k < n) ? snap_at(k & 1, c) : u_out + (size_t)n * MM;
         d.out = Fb + (size_t)n * MM;
         d.sweeps = sweeps;
         d.sweeps0 = sweeps0;
@@ -236,7 +265,7 @@ int parareal_pipelined(bs_grid* g, const bs_params* p, int N, int fine_steps, in
     // The next iteration's F, before this iteration's defect is known -- unless the last
     // defect was already within 10 tol: then this iteration is likely the final one, and a
     // wasted F would only slow its sweep down (the two share the GPU).
-    f_launched = k + 1 < Kmax && prev_defect > 10.0 * tol;
+    f_launched = k + 1 < Kmax && prev_defect > 10.0 * tol && (cheap_f || k >= 1);
     if (f_launched && (rc = fine_chunks(k + 1))) return rc;
     double host = 0.0;
     int hstat = 0;

@@ -80,3 +80,31 @@ def test_set_coarse_rejects_bad_sizes(bs):
         g.set_coarse(65)
     g.set_coarse(64)   # same grid: plain coarse propagation
     g.set_coarse(0)
+
+
+@pytest.mark.parametrize("M,Mc,N", [(300, 100, 8), (128, 64, 12)])
+def test_pipelined_resampled_equals_phase_driver(bs, M, Mc, N):
+    # F chunks overlapped with the chunked coarse sweep on the coarse grid: every slice's
+    # coarse solve starts afresh, so the iteration is the phase-by-phase driver's bit for bit --
+    # to convergence, and after two fixed iterations, where an F chunk that read its first
+    # state after the next sweep had rewritten it would show in slice 3
+    import torch
+    pb = wl.Problem("rsp", M, 4.0, N, 64 if M == 128 else 96, 2, wl.basket_cfg1().params)
+    g = bs.Grid(pb.M, pb.xmax)
+    g.set_coarse(Mc)
+    for tol, K in ((1e-4, pb.N), (0.0, 2), (0.0, 3)):
+        out = []
+        for pipe in (0, 1):
+            U = torch.empty((pb.N + 1, pb.M, pb.M), device="cuda")
+            try:
+                bs.bs_set_option(bs.OPT_PIPELINE, pipe)
+                rc, k, d = bs.parareal_solve(g, pb.params, pb.N, pb.fine_steps, bs.COARSE_NUM, pb.coarse_steps,
+                                             None, tol, K, U)
+                torch.cuda.synchronize()
+            finally:
+                bs.bs_set_option(bs.OPT_PIPELINE, 1)
+            out.append((rc, k, d, U))
+        assert out[0][1] == out[1][1] and out[0][0] == out[1][0], (tol, K)
+        assert (out[0][0] == 0) if K == pb.N else (out[0][1] == K)
+        assert out[0][2] == out[1][2], (tol, K)
+        assert torch.equal(out[0][3], out[1][3]), (tol, K)
