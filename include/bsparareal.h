@@ -397,12 +397,15 @@ int parareal_solve_noalloc(int M, double xmax, const bs_params* p, int N, int fi
  * A server owns one device arena of hbm_budget_bytes.  Each admitted request keeps its whole
  * Parareal state in the arena -- U [N+1][M][M], F and G_old [N][M][M] in FP32 and 2(N+1) FP64
  * norms, request_bytes = (3N+1) M^2 * 4 + 16 (N+1), rounded up to 256 -- from admission to
- * completion.  Requests are admitted in submission order while one of max_active slots is
+ * completion (a PINO request also keeps its defect partials there, (N+1) ceil(M^2/256) x 16
+ * bytes).  Requests are admitted in submission order while one of max_active slots is
  * free and the arena has room (first fit); a request that does not fit waits.  Every
- * request runs the numerical-coarse Parareal of parareal_solve (eq. parareal; reading c5
- * stopping norm) on its own CUDA stream; the fine propagation of all requests due at the
- * same time is batched into one fine_propagate launch per (grid size, fine steps), and the
- * serial coarse sweeps of different requests overlap on their streams.  A request's result
+ * request runs the Parareal of parareal_solve (eq. parareal; reading c5 stopping norm) with
+ * its own coarse model -- numerical G on its grid, numerical G on a coarse grid, or the
+ * PINO -- on its own CUDA stream; the fine propagation of all requests due at the same time
+ * is batched into one fine_propagate launch per (grid size, fine steps), and the serial
+ * coarse sweeps of different requests overlap on their streams (PINO sweeps share the
+ * network's workspace and run one after another on one server stream).  A request's result
  * does not depend on what it was batched with: every slice of a fine launch is computed
  * independently, and each coarse sweep belongs to one request.
  *
@@ -430,6 +433,13 @@ typedef struct {
   int Kmax;                  /* iteration cap, 1..N */
   float* u_out;              /* [M*M] caller buffer (host or device) for u(T) = U[N]; it
                                 must stay valid until the request is reported done */
+  /* The coarse model (zero-initialised: the numerical G on the request's own grid). */
+  int coarse_kind;           /* BS_COARSE_NUM or BS_COARSE_PINO */
+  int coarse_M;              /* BS_COARSE_NUM only: 0 = G on the request's grid; 8..M = G on an
+                                coarse_M x coarse_M grid with bilinear resampling, the form
+                                bs_grid_set_coarse selects for parareal_solve */
+  const bs_pino* net;        /* BS_COARSE_PINO: the network (coarse_steps is then ignored);
+                                the caller keeps it loaded until the request is done */
 } bs_request;
 
 typedef struct {
@@ -454,8 +464,9 @@ typedef struct {
  * current device.  BS_ERR_ARG for a budget below 1 MiB or max_active outside 1..256. */
 int bs_server_create(const bs_server_config* cfg, bs_server** out);
 /* Queues a request (copied); *id identifies it in bs_server_poll.  Host-only.  BS_ERR_ARG
- * for invalid sizes or parameters, for explicit fine_steps whose Jacobi bound is >= 0.8, or
- * for a request larger than the whole arena. */
+ * for invalid sizes or parameters, for explicit fine_steps whose Jacobi bound is >= 0.8, for
+ * an unknown coarse_kind, a coarse_M outside {0} U [8, M], a PINO request without a network
+ * of the supported shape or with coarse_M set, or for a request larger than the whole arena. */
 int bs_server_submit(bs_server* s, const bs_request* r, long long* id);
 /* Advances the server without blocking (see above); *active and *pending (either may be
  * NULL) receive the numbers of admitted and waiting requests.  The first request of a grid

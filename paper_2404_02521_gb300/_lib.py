@@ -58,7 +58,8 @@ class bs_server_config(C.Structure):
 class bs_request(C.Structure):
     _fields_ = [("p", bs_params), ("M", C.c_int), ("xmax", C.c_double), ("N", C.c_int),
                 ("fine_steps", C.c_int), ("coarse_steps", C.c_int), ("tol", C.c_double),
-                ("Kmax", C.c_int), ("u_out", C.c_void_p)]
+                ("Kmax", C.c_int), ("u_out", C.c_void_p), ("coarse_kind", C.c_int), ("coarse_M", C.c_int),
+                ("net", C.c_void_p)]
 
 
 class bs_result(C.Structure):
@@ -398,7 +399,7 @@ class Pino:
 
 
 class Server:
-    """bs_server handle: continuous batching of Parareal requests (numerical coarse G)."""
+    """bs_server handle: continuous batching of Parareal requests (each with its coarse model)."""
 
     def __init__(self, hbm_budget_bytes: int, max_active: int = 32):
         cfg = bs_server_config(int(hbm_budget_bytes), int(max_active))
@@ -407,12 +408,14 @@ class Server:
         self.h = h
         self._keep = {}   # id -> output buffer kept alive until the request is done
 
-    def submit(self, p, M, xmax, N, u_out, fine_steps=0, coarse_steps=1, tol=1e-4, Kmax=None) -> int:
+    def submit(self, p, M, xmax, N, u_out, fine_steps=0, coarse_steps=1, tol=1e-4, Kmax=None,
+               coarse_kind=COARSE_NUM, coarse_M=0, net=None) -> int:
         r = bs_request(to_params(p), int(M), float(xmax), int(N), int(fine_steps), int(coarse_steps),
-                       float(tol), int(N if Kmax is None else Kmax), _ptr(u_out))
+                       float(tol), int(N if Kmax is None else Kmax), _ptr(u_out), int(coarse_kind),
+                       int(coarse_M), net.h if net is not None else None)
         rid = C.c_longlong(0)
         check(load().bs_server_submit(self.h, C.byref(r), C.byref(rid)))
-        self._keep[rid.value] = u_out
+        self._keep[rid.value] = (u_out, net)
         return rid.value
 
     def progress(self):

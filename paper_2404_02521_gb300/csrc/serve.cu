@@ -11,7 +11,11 @@
 // propagation is due at the same time are batched: their slices go into one
 // fine_propagate launch per grid size (the fine kernels treat every slice independently,
 // so a result does not depend on what it was batched with).  Coarse sweeps, serial within a
-// request, run on the request's own stream and overlap across requests.
+// request, run on the request's own stream and overlap across requests.  Each request
+// brings its coarse model: the numerical G on its grid or on a coarse grid (its own grid
+// object carries the coarse grid and its buffers), or the PINO, whose sweeps share the
+// network's workspace and so run in order on one server stream, ordered against the
+// request's stream by events.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -89,6 +93,7 @@ struct Slot {
   size_t off = 0, bytes = 0;
   float *U = nullptr, *Fb = nullptr, *Gold = nullptr;
   double* norms = nullptr;
+  double* partials = nullptr;    // PINO requests: the sweep's defect partials
   int k = 0, sweeps = 0, sweeps0 = 0, sweepsx = 0, sweepsxl = 0, result = BS_OK;
   double defect = 0.0, t_submit = 0.0;
 };
@@ -114,6 +119,7 @@ struct bs_server {
   std::map<int, cudaStream_t> batch_stream;         // M -> stream of its batched F launches
   std::vector<cudaEvent_t> batch_events;
   size_t next_batch_event = 0;
+  cudaStream_t pino_stream = nullptr;               // every PINO sweep, in order
   long long next_id = 1;
   std::mutex mu;
   // statistics
@@ -122,12 +128,46 @@ struct bs_server {
 
 namespace bsp {
 
-// Request state in the arena: U [N+1][M][M], F [N][M][M], G_old [N][M][M] (FP32) and the
-// per-slice norms [2(N+1)] (FP64).
-static size_t request_bytes(const bs_request& r) {
+// Request state in the arena: U [N+1][M][M], F [N][M][M], G_old [N][M][M] (FP32), the
+// per-slice norms [2(N+1)] (FP64) and, for a PINO request, the sweep's defect partials.
+static size_t state_bytes(const bs_request& r) {
   const size_t MM = (size_t)r.M * r.M;
-  const size_t f = ((size_t)(3 * r.N + 1) * MM * sizeof(float) + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
-  return f + sizeof(double) * 2 * (r.N + 1);
+  return ((size_t)(3 * r.N + 1) * MM * sizeof(float) + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+}
+static size_t norms_bytes(const bs_request& r) {
+  return (sizeof(double) * 2 * (r.N + 1) + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+}
+static size_t request_bytes(const bs_request& r) {
+  const size_t part = r.coarse_kind == BS_COARSE_PINO ? pino_partials_bytes(r.M, r.N) : 0;
+  return state_bytes(r) + (part ? norms_bytes(r) + part : sizeof(double) * 2 * (r.N + 1));
+}
+
+static cudaEvent_t batch_event(bs_server* sv);
+
+// One coarse sweep of a request (SweepArgs filled in by the caller) with its coarse model,
+// ordered after the work already on the request's stream; counts its launches.
+static int request_sweep(bs_server* sv, Slot& sl, const ItemDesc& dc, const SweepArgs& a) {
+  const bs_request& r = sl.r;
+  int rc;
+  if (r.coarse_kind == BS_COARSE_PINO) {
+    // the network's workspace (activations, slice descriptors) serves one sweep at a time
+    cudaEvent_t e0 = batch_event(sv);
+    BS_CUDA_TRY(cudaEventRecord(e0, sl.st));
+    BS_CUDA_TRY(cudaStreamWaitEvent(sv->pino_stream, e0, 0));
+    if ((rc = pino_sweep(const_cast<bs_pino*>(r.net), sl.g, dc, a, sl.partials, sv->pino_stream))) return rc;
+    cudaEvent_t e1 = batch_event(sv);
+    BS_CUDA_TRY(cudaEventRecord(e1, sv->pino_stream));
+    BS_CUDA_TRY(cudaStreamWaitEvent(sl.st, e1, 0));
+    sv->launches += (long long)(a.N - a.n_first) * pino_launches_per_step(r.net) + 1;
+  } else if (sl.g->coarse_M > 0) {
+    if ((rc = resampled_sweep(sl.g, dc, a, sl.st))) return rc;
+    sv->launches += (long long)(a.N - a.n_first) * resampled_launches_per_slice() + 1;
+  } else {
+    if ((rc = launch_sweep(sl.g, dc, a, sl.st))) return rc;
+    sv->launches += 1;
+  }
+  sv->coarse_sweeps += 1;
+  return BS_OK;
 }
 
 // 64 steps per slice, doubled until the Jacobi bound of a fine step is at most 0.7
@@ -198,9 +238,15 @@ static int admit(bs_server* sv, Slot& sl, long long id, const bs_request& r, dou
   sl.U = base;
   sl.Fb = base + (size_t)(r.N + 1) * MM;
   sl.Gold = sl.Fb + (size_t)r.N * MM;
-  const size_t fbytes = ((size_t)(3 * r.N + 1) * MM * sizeof(float) + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+  const size_t fbytes = state_bytes(r);
   sl.norms = reinterpret_cast<double*>(sv->arena_base + sl.off + fbytes);
+  sl.partials = r.coarse_kind == BS_COARSE_PINO
+                    ? reinterpret_cast<double*>(sv->arena_base + sl.off + fbytes + norms_bytes(r))
+                    : nullptr;
   if ((rc = take_grid(sv, r.M, r.xmax, &sl.g))) return rc;
+  // the numerical G's grid (a pooled grid keeps the coarse grid of its last request until
+  // this call changes it)
+  if ((rc = bs_grid_set_coarse(sl.g, r.coarse_kind == BS_COARSE_NUM ? r.coarse_M : 0))) return rc;
   const double slice = r.p.T / r.N;
   const double dtau_f = slice / r.fine_steps;
   sl.sweeps = grid_sweeps(sl.g, r.p, dtau_f, START_WARM);
@@ -224,10 +270,9 @@ static int admit(bs_server* sv, Slot& sl, long long id, const bs_request& r, dou
   a.status = sl.g->status;
   a.tol = g_opt.krylov_tol;
   a.maxit = g_opt.krylov_maxit;
-  if ((rc = launch_sweep(sl.g, dc, a, sl.st))) return rc;
+  if ((rc = request_sweep(sv, sl, dc, a))) return rc;
   BS_CUDA_TRY(cudaEventRecord(sl.ev, sl.st));
-  sv->launches += 2;
-  sv->coarse_sweeps += 1;
+  sv->launches += 1;   // the payoff
   sl.phase = PH_INIT;
   return BS_OK;
 }
@@ -303,12 +348,10 @@ static int launch_group(bs_server* sv, const std::vector<Slot*>& grp) {
     a.status = sl->g->status;
     a.tol = g_opt.krylov_tol;
     a.maxit = g_opt.krylov_maxit;
-    if ((rc = launch_sweep(sl->g, dc, a, sl->st))) return rc;
+    if ((rc = request_sweep(sv, *sl, dc, a))) return rc;
     BS_CUDA_TRY(cudaMemcpyAsync(sl->h_defect, sl->g->dscal, sizeof(double), cudaMemcpyDeviceToHost, sl->st));
     BS_CUDA_TRY(cudaMemcpyAsync(sl->h_status, sl->g->status, sizeof(int), cudaMemcpyDeviceToHost, sl->st));
     BS_CUDA_TRY(cudaEventRecord(sl->ev, sl->st));
-    sv->launches += 1;
-    sv->coarse_sweeps += 1;
     sl->phase = PH_G;
   }
   return BS_OK;
@@ -411,6 +454,7 @@ int bs_server_create(const bs_server_config* cfg, bs_server** out) {
   sv->batch_events.resize(64);
   for (auto& be : sv->batch_events)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&be, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->pino_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     bs_server_destroy(sv);
     return cuda_error(e, "bs_server_create");
@@ -427,7 +471,14 @@ int bs_server_submit(bs_server* sv, const bs_request* r, long long* id) {
       !(r->tol > 0.0) || r->Kmax < 1 || r->Kmax > r->N)
     return set_error(BS_ERR_ARG, "bs_server_submit: M=%d N=%d coarse_steps=%d Kmax=%d", r->M, r->N,
                      r->coarse_steps, r->Kmax);
+  if (r->coarse_kind != BS_COARSE_NUM && r->coarse_kind != BS_COARSE_PINO)
+    return set_error(BS_ERR_ARG, "bs_server_submit: unknown coarse_kind %d", r->coarse_kind);
+  if (r->coarse_M != 0 && (r->coarse_kind != BS_COARSE_NUM || r->coarse_M < 8 || r->coarse_M > r->M))
+    return set_error(BS_ERR_ARG, "bs_server_submit: coarse_M=%d needs the numerical G and 8 <= coarse_M <= M=%d",
+                     r->coarse_M, r->M);
+  if (r->coarse_kind == BS_COARSE_PINO && (rc = pino_check(r->net, r->M))) return rc;
   bs_request q = *r;
+  if (q.coarse_kind == BS_COARSE_PINO) q.coarse_steps = 1;
   if (q.fine_steps <= 0) q.fine_steps = auto_fine_steps(q);
   if (q.fine_steps <= 0 || !(jacobi_contraction(q.M, q.p, q.p.T / q.N / q.fine_steps) < 0.8))
     return set_error(BS_ERR_ARG, "bs_server_submit: fine steps give a Jacobi bound >= 0.8");
@@ -492,6 +543,7 @@ int bs_server_destroy(bs_server* sv) {
     for (bs_grid* g : kv.second) bs_grid_destroy(g);
   for (auto& kv : sv->class_grid) bs_grid_destroy(kv.second);
   for (auto& kv : sv->batch_stream) cudaStreamDestroy(kv.second);
+  if (sv->pino_stream) cudaStreamDestroy(sv->pino_stream);
   for (auto& be : sv->batch_events)
     if (be) cudaEventDestroy(be);
   if (sv->arena_base) cudaFree(sv->arena_base);

@@ -2,8 +2,10 @@
 and price the same requests one at a time with parareal_solve for comparison.
 
 A request here is any object with .params (workloads.Params-like), .M, .xmax, .N,
-.coarse_steps, .tol and an arrival time; fine steps per slice are chosen by the server's
-rule (64, doubled until the Jacobi bound of a fine step is at most 0.7) unless given.
+.coarse_steps, .tol and an arrival time, and optionally its coarse model: .coarse_kind
+(default numerical), .coarse_M (numerical G on that grid; default the request's own) and
+.net (a loaded Pino for the PINO G).  Fine steps per slice are chosen by the server's rule
+(64, doubled until the Jacobi bound of a fine step is at most 0.7) unless given.
 """
 from __future__ import annotations
 
@@ -30,7 +32,7 @@ def replay(server: "_lib.Server", reqs, arrivals_s, outputs, fine_steps=None, po
             r = reqs[i]
             fs = 0 if fine_steps is None else int(fine_steps[i])
             rid = server.submit(r.params, r.M, r.xmax, r.N, outputs[i], fine_steps=fs,
-                                coarse_steps=r.coarse_steps, tol=r.tol)
+                                coarse_steps=r.coarse_steps, tol=r.tol, **coarse_model(r))
             by_id[rid] = i
             nxt += 1
         server.progress()
@@ -42,22 +44,32 @@ def replay(server: "_lib.Server", reqs, arrivals_s, outputs, fine_steps=None, po
     return results, time.perf_counter() - t0
 
 
+def coarse_model(r) -> dict:
+    """The request's coarse model as Server.submit keywords."""
+    return {"coarse_kind": getattr(r, "coarse_kind", _lib.COARSE_NUM), "coarse_M": getattr(r, "coarse_M", 0),
+            "net": getattr(r, "net", None)}
+
+
 def service_times(reqs, fine_steps, outputs):
-    """Each request alone through parareal_solve (numerical G), back to back on the current
-    stream: device-synchronised wall time per request in ms, iterations and results."""
+    """Each request alone through parareal_solve (with its coarse model), back to back on the
+    current stream: device-synchronised wall time per request in ms, iterations and results."""
     import torch
     out = []
     grids = {}
     for i, r in enumerate(reqs):
-        key = (r.M, r.xmax)
+        cm = coarse_model(r)
+        key = (r.M, r.xmax, cm["coarse_M"])
         if key not in grids:
             grids[key] = _lib.Grid(r.M, r.xmax)
+            grids[key].set_coarse(cm["coarse_M"])
         g = grids[key]
         U = torch.empty((r.N + 1, r.M, r.M), device="cuda")
         torch.cuda.synchronize()
         t = time.perf_counter()
-        rc, k, _ = _lib.parareal_solve(g, r.params, r.N, int(fine_steps[i]), _lib.COARSE_NUM,
-                                       r.coarse_steps, None, r.tol, r.N, U, allow_maxiter=True)
+        pino = cm["coarse_kind"] == _lib.COARSE_PINO
+        rc, k, _ = _lib.parareal_solve(g, r.params, r.N, int(fine_steps[i]), cm["coarse_kind"],
+                                       1 if pino else r.coarse_steps, cm["net"], r.tol, r.N, U,
+                                       allow_maxiter=True)
         outputs[i].copy_(U[r.N])
         torch.cuda.synchronize()
         out.append({"ms": 1e3 * (time.perf_counter() - t), "iterations": k, "status": rc})

@@ -133,3 +133,56 @@ def test_long_queue_admits_every_request_intact(bs):
     ref = alone(bs, reqs[::8])
     for a, b in zip(outs[::8], ref):
         assert torch.equal(a, b)
+
+
+def test_coarse_models_mix_equals_alone(bs, tmp_path):
+    # requests with the numerical G on their own grid, the numerical G on a coarse grid and
+    # the PINO, all in one mix (the PINO sweeps of two requests share the network): each
+    # result equals the same request alone through the server and through parareal_solve's
+    # phase-by-phase driver with the same coarse model, bit for bit
+    import types
+
+    import torch
+    from paper_2404_02521_gb300 import pino_io, serving
+    arch = wl.PinoArch()
+    w = wl.pino_random_weights(arch, seed=23, spectral_scale=8.0)
+    w["proj2_w"] = 0.05 * w["proj2_w"]
+    w["proj2_b"] = np.float64(0.0)
+    path = str(tmp_path / "w.bin")
+    pino_io.write_weights(path, w, arch.in_channels, arch.width, arch.modes_x, arch.modes_y, arch.layers,
+                          arch.proj_hidden)
+    net = bs.Pino(path)
+    rng = np.random.default_rng(5)
+    specs = [(128, 8, bs.COARSE_NUM, 64), (64, 8, bs.COARSE_PINO, 0), (300, 4, bs.COARSE_NUM, 100),
+             (96, 6, bs.COARSE_NUM, 0), (128, 4, bs.COARSE_PINO, 0), (200, 8, bs.COARSE_NUM, 72)]
+    reqs = []
+    for k, (M, N, kind, Mc) in enumerate(specs):
+        p = wl.random_params(rng, wl.BASKET if k % 2 == 0 else wl.EXCHANGE, float(rng.uniform(0.25, 1.0)))
+        reqs.append(types.SimpleNamespace(name=f"cm{k}", params=p, M=M, xmax=4.0, N=N, coarse_steps=2, tol=1e-4,
+                                          coarse_kind=kind, coarse_M=Mc,
+                                          net=net if kind == bs.COARSE_PINO else None))
+    outs = [torch.zeros((r.M, r.M), device="cuda") for r in reqs]
+    sv = bs.Server(1 << 30, 8)
+    res, _ = serving.replay(sv, reqs, [0.0, 0.0, 0.0, 0.005, 0.005, 0.01], outs)
+    st = sv.stats()
+    sv.close()
+    assert all(r["status"] == 0 for r in res), res
+    assert st["arena_used"] == 0
+    fs = [r["fine_steps"] for r in res]
+    for r, a, b, c in zip(reqs, outs, alone(bs, reqs), plain(bs, reqs, fs)):
+        assert torch.equal(a, b), r.name
+        assert torch.equal(a, c), r.name
+
+
+def test_submit_rejects_bad_coarse_models(bs):
+    import torch
+    out = torch.zeros((64, 64), device="cuda")
+    p = wl.basket_cfg1().params
+    sv = bs.Server(1 << 26, 2)
+    try:
+        for kw in ({"coarse_kind": 7}, {"coarse_M": 4}, {"coarse_M": 65},
+                   {"coarse_kind": bs.COARSE_PINO}):   # the PINO without a network
+            with pytest.raises(bs.BSError):
+                sv.submit(p, 64, 4.0, 8, out, **kw)
+    finally:
+        sv.close()
