@@ -19,6 +19,8 @@ the 256 x 256 grid (bilinear restriction and prolongation).
                 {-0.5, 0, 0.7}): time to tolerance, serial fine, coarse-sweep statistics
   coarse_models_128  the PINO network and the numerical G on 128 x 128 states, cost per state
                 at one and at 128 states per call
+  coarse_models_1024 G of one slice of the large solve: the PINO on its 256 x 256 grid
+                (restricted and prolonged) against the numerical G on 256 x 256
   cpu_baseline  the FP64 oracle on one host core, a bounded sample of the large solve's
                 serial fine stepping (one sparse LU factorisation, then implicit steps)
   clocks        nvidia-smi SM clock samples and throttle reasons during the timed region
@@ -473,7 +475,28 @@ def coarse_models(local):
                 call()
             ms, _ = timed(stream, lambda: [call() for _ in range(5)])
             out[f"{name}_us_per_state_batch{B}"] = 1e3 * ms / 5 / B
-    return out
+    # the large solve's slice (1024 x 1024, dtau_slice = 1/128): the network on its 256 x 256
+    # grid with restriction and prolongation, against the numerical G's 4 steps on 256 x 256
+    pb4 = wl.large_cfg4()
+    g4 = bs.Grid(pb4.M, pb4.xmax)
+    u4 = torch.empty((pb4.M, pb4.M), device="cuda")
+    o4 = torch.empty_like(u4)
+    bs.bs_payoff(g4, pb4.params, u4)
+    out4 = {}
+    for name, kind, nt, steps, coarse in (("pino_net256", bs.COARSE_PINO, net, 1, 0),
+                                          ("numerical_4_steps_on256", bs.COARSE_NUM, None, 4, 256)):
+        g4.set_coarse(coarse)
+
+        def call4():
+            bs.coarse_propagate(g4, kind, nt, pb4.params, u4, o4, 0.25, pb4.params.T / pb4.N, steps,
+                                stream=stream)
+        for _ in range(3):
+            call4()
+        ms, _ = timed(stream, lambda: [call4() for _ in range(10)])
+        out4[f"{name}_us_per_slice"] = 1e3 * ms / 10
+    out4["note"] = ("G of one 1024 x 1024 slice of the large solve, as in its serial sweep; the PINO "
+                    "row is cost only (seeded random weights)")
+    return out, out4
 
 
 def exchange_arm(args, local):
@@ -720,7 +743,7 @@ def main():
         return
     r = large_arm(args, world, local)
     ex = exchange_arm(args, local) if (not args.no_exchange and world == 1) else None
-    cm = coarse_models(local) if (not args.no_exchange and world == 1) else None
+    cm, cm4 = coarse_models(local) if (not args.no_exchange and world == 1) else (None, None)
     if rank != 0:
         return
     cpu = None
@@ -754,6 +777,7 @@ def main():
         "kernels": r["kernels"],
         "exchange256": ex,
         "coarse_models_128": cm,
+        "coarse_models_1024": cm4,
         "cpu_baseline": cpu,
         "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["launches"],

@@ -5,7 +5,8 @@
 //
 // The CTA stages A and B from global memory into shared memory in the canonical no-swizzle
 // K-major layout (8 x 8 core matrices of 16-byte rows; consecutive core matrices along K are
-// 128 bytes apart, along M/N K*16 bytes apart), one thread issues K/16 MMAs of shape
+// 128 bytes apart, along M/N K*16 bytes apart) with 16-byte asynchronous copies that are all
+// in flight before the first is waited for, one thread issues K/16 MMAs of shape
 // 128 x N x 16, the commit arrives on an mbarrier, and each warp reads its 32 accumulator
 // rows back with tcgen05.ld and hands them to the epilogue in chunks of 16 columns.
 // Every wait is bounded; on time-out the CTA records an error and still frees its tensor
@@ -53,6 +54,14 @@ __device__ __forceinline__ int canon_idx(int r, int k, int K) {
 
 constexpr int kUmmaWaitIters = 1 << 22;
 
+// 16-byte global -> shared copy through the L2 (cp.async.cg); ok == false zero-fills the
+// destination and reads nothing.
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
+
 template <int N>
 struct TmemCols {
   static constexpr int value = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
@@ -77,19 +86,20 @@ __global__ void __launch_bounds__(128) umma_gemm(GemmA A, GemmB B, Epi epi, int*
   const int by = blockIdx.y, bz = blockIdx.z;
   const bf16* Ab = A.base + by * A.ystride;
   const bf16* Bb = B.base + by * B.ystride + bz * B.zstride;
+  // every 16-byte chunk of both operands as an asynchronous copy, all in flight at once
+  // (rows of A beyond nrows and columns beyond ka are zero-filled, nothing is read there)
   constexpr int KV = K / 8;
   for (int e = tid; e < 128 * KV; e += 128) {
     const int r = e / KV, kv = e - (e / KV) * KV;
     const int grow = row0 + r;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (grow < A.nrows && kv * 8 < A.ka) v = *reinterpret_cast<const uint4*>(Ab + (size_t)grow * A.lda + kv * 8);
-    *reinterpret_cast<uint4*>(sA + canon_idx(r, kv * 8, K)) = v;
+    const bool ok = grow < A.nrows && kv * 8 < A.ka;
+    cp_async_16(sA + canon_idx(r, kv * 8, K), ok ? Ab + (size_t)grow * A.lda + kv * 8 : Ab, ok);
   }
   for (int e = tid; e < N * KV; e += 128) {
     const int r = e / KV, kv = e - (e / KV) * KV;
-    *reinterpret_cast<uint4*>(sB + canon_idx(r, kv * 8, K)) =
-        *reinterpret_cast<const uint4*>(Bb + (size_t)r * K + kv * 8);
+    cp_async_16(sB + canon_idx(r, kv * 8, K), Bb + (size_t)r * K + kv * 8, true);
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   constexpr int NCOLS = TmemCols<N>::value;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)), "n"(NCOLS));

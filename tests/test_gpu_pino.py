@@ -42,7 +42,7 @@ def network_grid(M):
 
 
 @pytest.mark.parametrize("M,payoff", [(128, wl.BASKET), (256, wl.EXCHANGE), (96, wl.EXCHANGE),
-                                      (200, wl.BASKET), (64, wl.BASKET)])
+                                      (200, wl.BASKET), (64, wl.BASKET), (1024, wl.BASKET)])
 def test_pino_step_matches_oracle(bs, weights, M, payoff):
     import torch
     path, w, arch = weights
