@@ -182,6 +182,29 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
   }
 }
 
+// The commit of a step whose last sweep has already run as a FIRST sweep (its result is in
+// dv[] and in the own rows of the plane wr): the compensated update of hi by v = dv[k] and
+// the next step's initial guess into wr and dv[], with the band-edge rows mirrored into the
+// neighbours -- what a LAST sweep does after its Jacobi update.  The caller separates it from
+// that sweep by a block and cluster barrier: the sweep's right-hand side read hi around
+// every node, here hi is written.
+template <class CFG, class LoT>
+__device__ __forceinline__ void fine_commit(float* __restrict__ wr, const HaloPush& wr_push, float* hi,
+                                            const HaloPush& hi_push, float (&dv)[CFG::K],
+                                            const float (&invd)[CFG::K], LoT& lo, int col, int r0, float* dp,
+                                            bool extrap) {
+  constexpr int NCOL = CFG::NCOL, K = CFG::K;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int p = r0 + 1 + k;
+    const float v = dv[k];
+    const float g = next_guess(v, dp, (r0 + k) * NCOL + col, extrap);
+    band_store<CFG>(wr, wr_push, p - 1, col, g);
+    dv[k] = g;
+    if (invd[k] != 0.f) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[k]));
+  }
+}
+
 // The compensation words of a thread's strip rows in a shared-memory plane of own rows.
 template <class CFG>
 struct StripLo {
@@ -515,10 +538,17 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
       float* wr = p ? dA : dB;
       const HaloPush& wp = p ? pA : pB;
       const bool fst = s == 0, lst = commit && s == nsw - 1;
-      if (fst && lst)
-        fine_sweep<CFG, true, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                    cgi, rdt, true, DP, extrap);
-      else if (fst)
+      if (fst && lst) {
+        // A one-sweep piece that commits its step (an item whose step ends one sweep into a
+        // launch of a split step): the sweep forms b from hi, so hi is updated only after
+        // every thread of the cluster has passed it.
+        fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
+                                     cgi, rdt, true);
+        cl_arrive();
+        __syncthreads();
+        cl_wait();
+        fine_commit<CFG>(wr, wp, hi, hi_push, dv, invd, lo, col, r0, DP, extrap);
+      } else if (fst)
         fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
                                      cgi, rdt, true);
       else if (lst)

@@ -121,6 +121,42 @@ def test_tile_step_split_over_launches(bs):
     assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
 
 
+def test_tile_one_sweep_commit_in_split_step(bs):
+    # items of one batch with different step sizes: the batch's cold step takes 26 sweeps and
+    # runs as two launches of 13, and item B's takes 14, so B's step ends one sweep into the
+    # second launch -- a piece that forms b from hi and commits the step.  B equals its
+    # propagation alone bit for bit, and both items the oracle
+    import torch
+    M, xmax = 300, 4.0
+    p = PARAMS[0]
+    g = bs.Grid(M, xmax)
+
+    def dtau_with(m):
+        lo, hi = 1e-7, 1e-2
+        for _ in range(80):
+            mid = (lo * hi) ** 0.5
+            k = bs.bs_fine_sweeps(g, p, mid, first_step=True)
+            if k == m:
+                return mid
+            if k == 0 or k > m:
+                hi = mid
+            else:
+                lo = mid
+        raise AssertionError(f"no step size with {m} cold sweeps")
+
+    dA, dB = dtau_with(26), dtau_with(14)
+    u0 = start_state(M, xmax, p, "random", seed=5)
+    uin = to_gpu(u0)
+    outs = [torch.empty_like(uin) for _ in range(2)]
+    bs.fine_propagate_batched(g, [p, p], [uin, uin], outs, [0.1, 0.1], [dA, dB], 3)
+    alone = torch.empty_like(uin)
+    bs.fine_propagate_batched(g, [p], [uin], [alone], [0.1], [dB], 3)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[1], alone)
+    assert rel_err(to_np(outs[1]), oracle_fine(M, xmax, p, u0, 0.1, dB, 3)) <= FP32_FINE_TOL
+    assert rel_err(to_np(outs[0]), oracle_fine(M, xmax, p, u0, 0.1, dA, 3)) <= FP32_FINE_TOL
+
+
 def test_tile_batch_composition_invariance(bs):
     # a tile item's result does not depend on the halo width chosen for its batch (the
     # halo follows the largest sweep count in the launch)
