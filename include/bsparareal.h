@@ -295,12 +295,17 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  *                        and, where their shared memory allows, use a polynomial
  *                        preconditioner and quadratic initial-guess extrapolation (all solve
  *                        the same systems to the same Krylov tolerance).
+ *  BS_OPT_FINE_TILE      region layout of the fine stepper on grids with M > 256, which runs
+ *                        as overlapping cluster tiles: 0 (default) the layout that computes
+ *                        fewer nodes for M; 1 regions of 256 x 256 nodes (8 CTAs, up to 24
+ *                        sweeps per launch); 2 regions of 288 x 288 (9 CTAs, up to 16 sweeps).
+ *                        Both compute the same steps; results agree to FP32 rounding.
  * Returns BS_OK or BS_ERR_ARG for an unknown option or an out-of-range value. */
 enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
        BS_OPT_KRYLOV_MAXIT = 3, BS_OPT_PHASE_TIMING = 4, BS_OPT_JACOBI_TARGET_COLD = 5,
        BS_OPT_COARSE_VARIANT = 6, BS_OPT_JACOBI_TARGET_EXTRAP = 7, BS_OPT_EXTRAP_START = 8,
        BS_OPT_EXTRAP_LATE = 9, BS_OPT_JACOBI_TARGET_EXTRAP_LATE = 10, BS_OPT_PIPELINE = 11,
-       BS_OPT_FINE_KRYLOV_TOL = 12 };
+       BS_OPT_FINE_KRYLOV_TOL = 12, BS_OPT_FINE_TILE = 13 };
 int bs_set_option(int option, double value);
 
 /* Numerical coarse propagator on a coarser grid (the resolution change of Sec. 4.4 applied to

@@ -35,6 +35,7 @@ OPT_EXTRAP_LATE = 9
 OPT_JACOBI_TARGET_EXTRAP_LATE = 10
 OPT_PIPELINE = 11
 OPT_FINE_KRYLOV_TOL = 12
+OPT_FINE_TILE = 13
 PARAREAL_USER_U0 = 0x100
 
 

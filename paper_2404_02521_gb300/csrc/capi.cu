@@ -451,6 +451,11 @@ int bs_set_option(int option, double value) {
       if (!(value >= 1.0 && value <= 100000.0)) return set_error(BS_ERR_ARG, "BS_OPT_KRYLOV_MAXIT must be in [1, 1e5]");
       g_opt.krylov_maxit = (int)value;
       return BS_OK;
+    case BS_OPT_FINE_TILE:
+      if (!(value == 0.0 || value == 1.0 || value == 2.0))
+        return set_error(BS_ERR_ARG, "BS_OPT_FINE_TILE must be 0, 1 or 2");
+      g_opt.fine_tile = (int)value;
+      return BS_OK;
   }
   return set_error(BS_ERR_ARG, "bs_set_option: unknown option %d", option);
 }

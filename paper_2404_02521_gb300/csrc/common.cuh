@@ -213,6 +213,7 @@ struct Options {
   int krylov_maxit = 400;
   int phase_timing = 0;
   int coarse_variant = -1;   // >= 0: force this coarse band variant; -1: measured per grid size
+  int fine_tile = 0;         // region layout of the fine tiles (M > 256): 0 auto, 1 or 2 forced
 };
 extern Options g_opt;
 

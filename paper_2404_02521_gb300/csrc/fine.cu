@@ -15,7 +15,10 @@
 // pair (hi, lo): u = hi + lo, updated by an error-free two-sum, so that increments below half
 // an ulp of u are not lost over tens of thousands of steps; b is evaluated from hi.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "band.cuh"
@@ -329,8 +332,17 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
 // as in the band stepper).  Where M is a multiple of 4 the region origin is too, and the
 // region arrives as 16-byte asynchronous copies; otherwise as 4-byte ones.
 // ---------------------------------------------------------------------------------------
-typedef BandCfg<256, 512, 16> CTileCfg;
-constexpr int kCTileMaxHalo = 24;   // sweeps per launch (a multiple of 4); interiors keep >= 208 nodes
+// Two region layouts.  A: 256 columns x 256 rows (8 CTAs of 32 rows; 512 threads of one column
+// x 16 rows), at most 24 sweeps per launch, so interiors keep >= 208 nodes.  B: 288 x 288 (9
+// CTAs of 32 rows, a non-portable cluster size; 576 threads of one column x 16 rows), at most
+// 16 sweeps per launch, interiors of 256: 1024 x 1024 takes 4 x 4 regions instead of A's 5 x 5
+// (19% fewer nodes computed), 512 x 512 2 x 2 instead of 3 x 3.  The launch picks the layout
+// with less work in waves of co-resident clusters (tile_layout).  Both keep 16-row strips; A in 128 registers per
+// thread, B in 96 (a CTA of 576 threads is allocated registers for 20 warps).
+typedef BandCfg<256, 512, 16> CTileCfgA;
+typedef BandCfg<288, 576, 16> CTileCfgB;
+constexpr int kCTileMaxHalo = 24;    // layout A: sweeps per launch (a multiple of 4)
+constexpr int kCTileMaxHaloB = 16;   // layout B
 
 struct CTileBatch {
   ItemDesc it[kMaxItems];
@@ -614,13 +626,13 @@ struct CTileLaunch {
 // Launch plan: whole steps are packed into a launch while their sweeps (the largest count of
 // any item, step by step) add up to at most kCTileMaxHalo; a step with more sweeps than that is
 // split evenly over several launches.
-static void ctile_plan(const ItemDesc* items, int n, int nsteps, std::vector<CTileLaunch>& plan) {
+static void ctile_plan(const ItemDesc* items, int n, int nsteps, int hmax, std::vector<CTileLaunch>& plan) {
   plan.clear();
   int step = 0;
   while (step < nsteps) {
     const int m = max_step_sweeps(items, n, step);
-    if (m > kCTileMaxHalo) {
-      const int nl = (m + kCTileMaxHalo - 1) / kCTileMaxHalo;
+    if (m > hmax) {
+      const int nl = (m + hmax - 1) / hmax;
       const int chunk = (m + nl - 1) / nl;
       for (int l = 0; l < nl; ++l) {
         const int s0 = l * chunk, s1 = std::min(m, s0 + chunk);
@@ -632,7 +644,7 @@ static void ctile_plan(const ItemDesc* items, int n, int nsteps, std::vector<CTi
     int h = m, k = 1;
     while (step + k < nsteps) {
       const int mk = max_step_sweeps(items, n, step + k);
-      if (h + mk > kCTileMaxHalo) break;
+      if (h + mk > hmax) break;
       h += mk;
       ++k;
     }
@@ -643,8 +655,9 @@ static void ctile_plan(const ItemDesc* items, int n, int nsteps, std::vector<CTi
 
 // Region geometry of a launch with h sweeps: halo H (a multiple of 4 with 16-byte copies), ntx
 // interiors of I nodes per axis, clusters of C CTAs.
+template <class CFG>
 static void ctile_geometry(int M, int h, bool vec, CTileBatch& tb) {
-  const int NC = CTileCfg::NCOL;
+  const int NC = CFG::NCOL;
   const int H = vec ? ((std::max(2, h) + 3) / 4) * 4 : std::max(2, h);
   int ntx = (M + (NC - 2 * H) - 1) / (NC - 2 * H);
   int I;
@@ -656,25 +669,93 @@ static void ctile_geometry(int M, int h, bool vec, CTileBatch& tb) {
   tb.H = H;
   tb.I = I;
   tb.ntx = ntx;
-  tb.C = (I + 2 * H + CTileCfg::BH - 1) / CTileCfg::BH;
+  tb.C = (I + 2 * H + CFG::BH - 1) / CFG::BH;
 }
 
+template <class CFG>
 static size_t ctile_smem() {
-  return (size_t)3 * CTileCfg::PLANE * sizeof(float) + (size_t)2 * CTileCfg::BH * CTileCfg::NCOL * sizeof(float) +
-         (size_t)FarTable<CTileCfg>::FLOATS * sizeof(float) + (size_t)CTileCfg::BH * sizeof(float4);
+  return (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)2 * CFG::BH * CFG::NCOL * sizeof(float) +
+         (size_t)FarTable<CFG>::FLOATS * sizeof(float) + (size_t)CFG::BH * sizeof(float4);
 }
 
-static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
+// Clusters of C CTAs of a layout that the current device runs at once (0 if unknown),
+// measured once per device, layout and C through the occupancy API.
+template <class CFG>
+static int tile_capacity(int C) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, C});
+  if (it != cache.end()) return it->second;
+  const size_t smem = ctile_smem<CFG>();
+  auto kern = fine_ctile_kernel<CFG, 4>;
+  int n = 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(CFG::NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) ||
+      cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cache[{dev, C}] = n;
+  return n;
+}
+
+// The region layout of a launch batch of nb states (1 = A, 2 = B; BS_OPT_FINE_TILE forces
+// one): the one with less work per launch, counted as waves of clusters (states x regions
+// over the clusters the device holds at once) times the nodes of a region, B's nodes weighted
+// by kTileCostB; with an unknown capacity, the nodes of all regions.  A on a tie.  Both give
+// the same result bit for bit.  At 1024 x 1024 the device holds 15 clusters of 8 or of 9
+// CTAs: one state (25 A regions or 16 B regions, two waves either way) goes to A, eight or
+// more to B.
+constexpr double kTileCostB = 1.12;   // B's time per node over A's (more launches, 96 registers),
+                                      // from 64 states x 64 steps at 1024^2
+static int tile_layout(int M, int nb) {
+  if (g_opt.fine_tile == 1 || g_opt.fine_tile == 2) return g_opt.fine_tile;
+  CTileBatch ta, tb;
+  ctile_geometry<CTileCfgA>(M, kCTileMaxHalo, M % 4 == 0, ta);
+  ctile_geometry<CTileCfgB>(M, kCTileMaxHaloB, M % 4 == 0, tb);
+  const double ra = (double)CTileCfgA::NCOL * (ta.C * CTileCfgA::BH);   // nodes of a region
+  const double rb = (double)CTileCfgB::NCOL * (tb.C * CTileCfgB::BH);
+  const double ca = (double)nb * ta.ntx * ta.ntx, cb = (double)nb * tb.ntx * tb.ntx;   // clusters
+  const int capa = tile_capacity<CTileCfgA>(ta.C), capb = tile_capacity<CTileCfgB>(tb.C);
+  double wa = ca * ra, wb = cb * rb;
+  if (capa > 0 && capb > 0) {
+    wa = std::ceil(ca / capa) * ra;
+    wb = std::ceil(cb / capb) * rb;
+  }
+  wb *= kTileCostB;
+  return wb < wa ? 2 : 1;
+}
+
+template <class CFG>
+static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, int hmax, cudaStream_t s) {
   const int M = g->M;
   const size_t MM = (size_t)M * M;
   int rc = ensure(const_cast<bs_grid*>(g)->ws_fine, (size_t)std::min(n, kMaxItems) * 8 * MM * sizeof(float));
   if (rc) return rc;
-  const size_t smem = ctile_smem();
+  const size_t smem = ctile_smem<CFG>();
   // 16-byte copies need M and every input state 16-byte aligned (the workspace is)
   bool vec = M % 4 == 0;
   for (int k = 0; k < n; ++k) vec = vec && ((uintptr_t)items[k].in % 16 == 0);
-  auto kern = vec ? fine_ctile_kernel<CTileCfg, 4> : fine_ctile_kernel<CTileCfg, 1>;
+  auto kern = vec ? fine_ctile_kernel<CFG, 4> : fine_ctile_kernel<CFG, 1>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (CFG::NCOL / CFG::BH > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   std::vector<CTileLaunch> plan;
   for (int base = 0; base < n; base += kMaxItems) {
     CTileBatch tb;
@@ -683,16 +764,16 @@ static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nst
     tb.ws = (float*)g->ws_fine.ptr;
     tb.M = M;
     tb.h = (float)(g->xmax / (M - 1));
-    ctile_plan(tb.it, tb.n, nsteps, plan);
+    ctile_plan(tb.it, tb.n, nsteps, hmax, plan);
     int par = 0;
     const int nl = (int)plan.size();
     for (int l = 0; l < nl; ++l) {
       const CTileLaunch& L = plan[(size_t)l];
-      ctile_geometry(M, L.H, vec, tb);
+      ctile_geometry<CFG>(M, L.H, vec, tb);
       const bool first = l == 0, final_launch = l == nl - 1;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(tb.C, tb.ntx * tb.ntx, tb.n);
-      cfg.blockDim = dim3(CTileCfg::NT, 1, 1);
+      cfg.blockDim = dim3(CFG::NT, 1, 1);
       cfg.dynamicSmemBytes = smem;
       cfg.stream = s;
       cudaLaunchAttribute attr[1];
@@ -716,15 +797,22 @@ static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nst
   return BS_OK;
 }
 
+static int launch_ctiles(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
+  return tile_layout(g->M, std::min(n, kMaxItems)) == 2
+             ? launch_ctiles<CTileCfgB>(g, items, n, nsteps, kCTileMaxHaloB, s)
+             : launch_ctiles<CTileCfgA>(g, items, n, nsteps, kCTileMaxHalo, s);
+}
+
 int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps) {
   const int chunks = (n + kMaxItems - 1) / kMaxItems;
   if (g->shape.C >= 1 && g->shape.C <= kMaxCluster) return chunks;
   if (nsteps < 1) return 0;
+  const int hmax = tile_layout(g->M, std::min(n, kMaxItems)) == 2 ? kCTileMaxHaloB : kCTileMaxHalo;
   int total = 0;
   std::vector<CTileLaunch> plan;
   for (int base = 0; base < n; base += kMaxItems) {
     const int nb = std::min(n - base, kMaxItems);
-    ctile_plan(items + base, nb, nsteps, plan);
+    ctile_plan(items + base, nb, nsteps, hmax, plan);
     total += (int)plan.size() + (plan.size() == 1 ? 1 : 0);
   }
   return total;

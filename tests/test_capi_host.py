@@ -94,6 +94,10 @@ def test_options_are_range_checked(lib):
         assert lib.bs_set_option(opt, 1.0) != 0
         assert lib.bs_set_option(opt, 3e-6) == 0
         assert lib.bs_set_option(opt, default) == 0
+    for bad in (-1.0, 0.5, 3.0):
+        assert lib.bs_set_option(_lib.OPT_FINE_TILE, bad) != 0
+    for ok in (1.0, 2.0, 0.0):
+        assert lib.bs_set_option(_lib.OPT_FINE_TILE, ok) == 0
     assert lib.bs_set_option(99, 1.0) != 0
 
 

@@ -67,12 +67,23 @@ def test_fine_tiles_match_oracle(bs, M, pi):
     assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
 
 
+@pytest.fixture
+def tile_layout(bs):
+    """Force the fine tiles' region layout (1: 256 x 256 regions, 2: 288 x 288) for a test."""
+    def force(k):
+        bs.bs_set_option(bs.OPT_FINE_TILE, k)
+    yield force
+    bs.bs_set_option(bs.OPT_FINE_TILE, 0)
+
+
+@pytest.mark.parametrize("layout", [1, 2])
 @pytest.mark.parametrize("M,pi,nsteps", [(300, 1, 40), (301, 2, 40), (516, 0, 24)])
-def test_tile_temporal_blocking_matches_oracle(bs, M, pi, nsteps):
+def test_tile_temporal_blocking_matches_oracle(bs, tile_layout, M, pi, nsteps, layout):
     # several whole implicit steps per tile launch (the halo grows with the launch's sweeps):
     # long enough to reach the late two- and three-sweep steps; M = 301 runs the 4-byte copy
-    # path (M not a multiple of 4), M = 300 and 516 the 16-byte one
+    # path (M not a multiple of 4), M = 300 and 516 the 16-byte one; both region layouts
     import torch
+    tile_layout(layout)
     p = PARAMS[pi]
     dtau = dtau_for(M, p)
     u0 = start_state(M, 4.0, p, "random", seed=M + nsteps)
@@ -85,6 +96,28 @@ def test_tile_temporal_blocking_matches_oracle(bs, M, pi, nsteps):
     torch.cuda.synchronize()
     assert torch.equal(out, inplace)
     assert rel_err(to_np(out), oracle_fine(M, 4.0, p, u0, 0.05, dtau, nsteps)) <= FP32_FINE_TOL
+
+
+@pytest.mark.parametrize("M,pi,nsteps", [(300, 0, 40), (301, 1, 30), (516, 2, 24), (1024, 0, 20)])
+def test_tile_layouts_agree_bitwise(bs, tile_layout, M, pi, nsteps):
+    # the two region layouts (256 x 256 regions and up to 24 sweeps per launch, 288 x 288 and up
+    # to 16) compute every node of a region's exact part with the same operations in the same
+    # order from its global indices, and a launch boundary carries the state exactly, so they
+    # agree bit for bit though their launches and tiles differ
+    import torch
+    p = PARAMS[pi]
+    dtau = dtau_for(M, p)
+    u0 = to_gpu(start_state(M, 4.0, p, "random", seed=7 * M))
+    g = bs.Grid(M, 4.0)
+    outs = []
+    for layout in (1, 2):
+        tile_layout(layout)
+        out = torch.empty_like(u0)
+        bs.fine_propagate_batched(g, [p, p], [u0, u0], [out, torch.empty_like(u0)], [0.0, 0.1],
+                                  [dtau, dtau / 2], nsteps)
+        torch.cuda.synchronize()
+        outs.append(out)
+    assert torch.equal(outs[0], outs[1])
 
 
 def test_tile_step_split_over_launches(bs):
@@ -121,12 +154,14 @@ def test_tile_step_split_over_launches(bs):
     assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
 
 
-def test_tile_one_sweep_commit_in_split_step(bs):
+@pytest.mark.parametrize("layout", [1, 2])
+def test_tile_one_sweep_commit_in_split_step(bs, tile_layout, layout):
     # items of one batch with different step sizes: the batch's cold step takes 26 sweeps and
     # runs as two launches of 13, and item B's takes 14, so B's step ends one sweep into the
     # second launch -- a piece that forms b from hi and commits the step.  B equals its
-    # propagation alone bit for bit, and both items the oracle
+    # propagation alone bit for bit, and both items the oracle (both region layouts)
     import torch
+    tile_layout(layout)
     M, xmax = 300, 4.0
     p = PARAMS[0]
     g = bs.Grid(M, xmax)
