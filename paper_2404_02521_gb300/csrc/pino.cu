@@ -184,6 +184,7 @@ struct NoAcc {};
 struct EpiX1 {   // G1: rows (c, y), cols (kx, re/im) -> X1[b][c][kx][y][re/im]
   typedef NoAcc Acc;
   bf16* X1; int Mp, mx, C;
+  __device__ void prefetch(Acc&, int, int, int) const {}
   __device__ void begin(Acc&, int, int, int) const {}
   __device__ void end(Acc&, int, int, int) const {}
   __device__ void chunk(Acc&, int b, int, int row, int c0, const float* v) const {
@@ -201,6 +202,7 @@ struct EpiX1 {   // G1: rows (c, y), cols (kx, re/im) -> X1[b][c][kx][y][re/im]
 struct EpiX2 {   // G2: rows (c, kx), cols (q, re/im) -> X2[q*mx + kx][b][c][re/im]
   typedef NoAcc Acc;
   bf16* X2; int mx, MY, C, B;
+  __device__ void prefetch(Acc&, int, int, int) const {}
   __device__ void begin(Acc&, int, int, int) const {}
   __device__ void end(Acc&, int, int, int) const {}
   __device__ void chunk(Acc&, int b, int, int row, int c0, const float* v) const {
@@ -220,6 +222,7 @@ struct EpiX2 {   // G2: rows (c, kx), cols (q, re/im) -> X2[q*mx + kx][b][c][re/
 struct EpiY {    // G3 (blockIdx.y = mode): rows b, cols (o, re/im) -> Y[b][o][kx][q][re/im]
   typedef NoAcc Acc;
   bf16* Y; int mx, MY, C, B;
+  __device__ void prefetch(Acc&, int, int, int) const {}
   __device__ void begin(Acc&, int, int, int) const {}
   __device__ void end(Acc&, int, int, int) const {}
   __device__ void chunk(Acc&, int mode, int, int row, int c0, const float* v) const {
@@ -236,6 +239,7 @@ struct EpiY {    // G3 (blockIdx.y = mode): rows b, cols (o, re/im) -> Y[b][o][k
 struct EpiZ {    // G4 (blockIdx.z = 256-column chunk): rows (o, kx), cols (y, re/im) -> Z1[b][o][y][kx][re/im]
   typedef NoAcc Acc;
   bf16* Z1; int Mp, mx, C;
+  __device__ void prefetch(Acc&, int, int, int) const {}
   __device__ void begin(Acc&, int, int, int) const {}
   __device__ void end(Acc&, int, int, int) const {}
   __device__ void chunk(Acc&, int b, int z, int row, int c0, const float* v) const {
@@ -252,6 +256,7 @@ struct EpiZ {    // G4 (blockIdx.z = 256-column chunk): rows (o, kx), cols (y, r
 struct EpiSpec { // G5: rows (o, y), cols x -> spec[b][o][y][x] (FP32)
   typedef NoAcc Acc;
   float* spec; int Mp, C;
+  __device__ void prefetch(Acc&, int, int, int) const {}
   __device__ void begin(Acc&, int, int, int) const {}
   __device__ void end(Acc&, int, int, int) const {}
   __device__ void chunk(Acc&, int b, int, int row, int c0, const float* v) const {
@@ -262,18 +267,24 @@ struct EpiSpec { // G5: rows (o, y), cols x -> spec[b][o][y][x] (FP32)
   }
 };
 
+struct SpecAcc { float s[32]; };
 struct EpiAct {  // G6: rows pixels, cols o -> ReLU(W v + b + spec) into both activation layouts
-  typedef NoAcc Acc;
+  typedef SpecAcc Acc;   // the pixel's spectral outputs, loaded while the product runs (C = 32)
   bf16 *act_cp, *act_pc; const float* spec; const float* bias; int P, C;
+  __device__ void prefetch(Acc& a, int b, int, int p) const {
+    if (p >= P) return;
+#pragma unroll
+    for (int o = 0; o < 32; ++o) a.s[o] = spec[((size_t)b * C + o) * P + p];
+  }
   __device__ void begin(Acc&, int, int, int) const {}
   __device__ void end(Acc&, int, int, int) const {}
-  __device__ void chunk(Acc&, int b, int, int p, int c0, const float* v) const {
+  __device__ void chunk(Acc& a, int b, int, int p, int c0, const float* v) const {
     if (p >= P) return;
     __align__(16) bf16 h[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int o = c0 + q;
-      const float x = fmaxf(v[q] + bias[o] + spec[((size_t)b * C + o) * P + p], 0.f);
+      const float x = fmaxf(v[q] + bias[o] + a.s[o], 0.f);
       h[q] = __float2bfloat16(x);
       act_cp[((size_t)b * C + o) * P + p] = h[q];
     }
@@ -287,6 +298,7 @@ struct ProjAcc { float s; };
 struct EpiProj { // P: rows pixels, cols hidden -> w = sum_h ReLU(v + b1) w2[h] + b2
   typedef ProjAcc Acc;
   float* wout; const float* b1; const float* w2; float b2; int P;
+  __device__ void prefetch(Acc&, int, int, int) const {}
   __device__ void begin(Acc& a, int, int, int) const { a.s = 0.f; }
   __device__ void chunk(Acc& a, int, int, int, int c0, const float* v) const {
 #pragma unroll

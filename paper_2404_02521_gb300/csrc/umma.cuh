@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(128) umma_gemm(GemmA A, GemmB B, Epi epi, int*
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(mbar)));
   }
+  // loads of the epilogue that do not depend on the product, in flight while it runs
+  const int row = row0 + warp * 32 + lane;
+  typename Epi::Acc acc;
+  epi.prefetch(acc, by, bz, row);
   uint32_t done = 0;
   for (int it = 0; it < kUmmaWaitIters && !done; ++it) {
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -139,8 +143,6 @@ __global__ void __launch_bounds__(128) umma_gemm(GemmA A, GemmB B, Epi epi, int*
   if (!done && lane == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (done) {
-    const int row = row0 + warp * 32 + lane;
-    typename Epi::Acc acc;
     epi.begin(acc, by, bz, row);
 #pragma unroll 1
     for (int c0 = 0; c0 < N; c0 += 16) {
