@@ -13,8 +13,9 @@
 //   G3 mixing     per mode: [state] x [(c,re/im)] -> (o,re/im)   N = 64, K = 64 (complex as
 //                 the real 2x2 block form of the C x C mode matrix)
 //   G4 inv. y-DFT [(o,kx)] x [(ky,re/im)] -> (y, re/im)          N = 2 Mp (chunks of 256), K = 48
-//   G5 inv. x-DFT [(o,y)]  x [(kx,re/im)] -> x, Hermitian weights and 1/Mp^2   N = Mp, K = 32
-//   G6 pointwise  [pixel]  x [c]          -> o, epilogue adds bias, the G5 result, ReLU
+//   G5 inv. x-DFT [pixel: x] x [(kx,re/im) of (o,y)] -> o, Hermitian weights and 1/Mp^2,
+//      + pointwise [pixel] x [c] -> o, both into one accumulator (K = 32 each); the
+//                 epilogue adds the bias and applies ReLU
 //   P  projection [pixel]  x [c]          -> hidden, epilogue ReLU . w2 + b2, residual
 // Each epilogue writes the K-contiguous layout the next GEMM reads, so no transposes run
 // between them.  The DFT matrices are exact transforms (not learned) stored in BF16.
@@ -44,7 +45,7 @@ struct PinoRes {
   int Mp = 0, cap = 0, st_cap = 0;
   bf16 *Ex = nullptr, *Ey = nullptr, *Eyi = nullptr, *Exi = nullptr;
   bf16 *act_cp = nullptr, *act_pc = nullptr, *X1 = nullptr, *X2 = nullptr, *Y = nullptr, *Z1 = nullptr;
-  float *spec = nullptr, *wout = nullptr, *ump = nullptr;
+  float *wout = nullptr, *ump = nullptr;
   PinoState* st = nullptr;
 };
 
@@ -125,7 +126,7 @@ static int build_dft(bs_pino* net, PinoRes& R) {
 
 static void free_res(PinoRes& R) {
   void* ptrs[] = {R.Ex, R.Ey, R.Eyi, R.Exi, R.act_cp, R.act_pc, R.X1, R.X2, R.Y, R.Z1,
-                  R.spec, R.wout, R.ump, R.st};
+                  R.wout, R.ump, R.st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   R = PinoRes();
@@ -165,7 +166,6 @@ static int ensure_res(bs_pino* net, int Mp, int B, int nst, PinoRes** out) {
       (rc = dev_alloc((void**)&R.X2, MY * mx * Bn * C * 2 * sizeof(bf16))) ||
       (rc = dev_alloc((void**)&R.Y, Bn * C * mx * MY * 2 * sizeof(bf16))) ||
       (rc = dev_alloc((void**)&R.Z1, Bn * C * Mp * mx * 2 * sizeof(bf16))) ||
-      (rc = dev_alloc((void**)&R.spec, Bn * C * P * sizeof(float))) ||
       (rc = dev_alloc((void**)&R.wout, Bn * P * sizeof(float))) ||
       (rc = dev_alloc((void**)&R.ump, Bn * P * sizeof(float))) ||
       (rc = dev_alloc((void**)&R.st, (size_t)(nst > B ? nst : B) * sizeof(PinoState))))
@@ -253,38 +253,44 @@ struct EpiZ {    // G4 (blockIdx.z = 256-column chunk): rows (o, kx), cols (y, r
   }
 };
 
-struct EpiSpec { // G5: rows (o, y), cols x -> spec[b][o][y][x] (FP32)
-  typedef NoAcc Acc;
-  float* spec; int Mp, C;
-  __device__ void prefetch(Acc&, int, int, int) const {}
-  __device__ void begin(Acc&, int, int, int) const {}
-  __device__ void end(Acc&, int, int, int) const {}
-  __device__ void chunk(Acc&, int b, int, int row, int c0, const float* v) const {
-    if (row >= C * Mp) return;
-    float4* dst = reinterpret_cast<float4*>(spec + ((size_t)b * C * Mp + row) * Mp + c0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+// G5: one tile = 128 pixels of one state (a row y of the network grid, or half of one at
+// Mp = 256).  A1 = the inverse x-DFT matrix rows of the tile's x, B1 = the state's inverse
+// y-DFT output Z1[o][y][(kx, re/im)] (24 columns, zero-padded to 32); A2 = the tile's
+// activations [pixel][c], B2 = the pointwise weights W[o][c].
+template <int Mp>
+struct PwOps {
+  const bf16 *Exi, *Z1, *act_pc, *W;
+  __device__ void load(bf16* sA1, bf16* sB1, bf16* sA2, bf16* sB2) const {
+    constexpr int C = 32, P = Mp * Mp, KZ = 24;
+    const int tid = threadIdx.x, b = blockIdx.y;
+    const int row0 = blockIdx.x * 128, y = row0 / Mp, x0 = row0 - y * Mp;
+    for (int e = tid; e < 128 * 4; e += 128) {
+      const int r = e >> 2, kv = e & 3;
+      cp_async_16(sA1 + canon_idx(r, kv * 8, 32), Exi + (size_t)(x0 + r) * 32 + kv * 8, true);
+      cp_async_16(sA2 + canon_idx(r, kv * 8, 32), act_pc + ((size_t)b * P + row0 + r) * C + kv * 8, true);
+    }
+    for (int e = tid; e < C * 4; e += 128) {
+      const int o = e >> 2, kv = e & 3;
+      const bool ok = kv * 8 < KZ;
+      cp_async_16(sB1 + canon_idx(o, kv * 8, 32), ok ? Z1 + (((size_t)b * C + o) * Mp + y) * KZ + kv * 8 : Z1, ok);
+      cp_async_16(sB2 + canon_idx(o, kv * 8, 32), W + (size_t)o * C + kv * 8, true);
+    }
   }
 };
 
-struct SpecAcc { float s[32]; };
-struct EpiAct {  // G6: rows pixels, cols o -> ReLU(W v + b + spec) into both activation layouts
-  typedef SpecAcc Acc;   // the pixel's spectral outputs, loaded while the product runs (C = 32)
-  bf16 *act_cp, *act_pc; const float* spec; const float* bias; int P, C;
-  __device__ void prefetch(Acc& a, int b, int, int p) const {
-    if (p >= P) return;
-#pragma unroll
-    for (int o = 0; o < 32; ++o) a.s[o] = spec[((size_t)b * C + o) * P + p];
-  }
+struct EpiAct {  // G5: rows pixels, cols o -> ReLU(spectral + W v + b) into both activation layouts
+  typedef NoAcc Acc;
+  bf16 *act_cp, *act_pc; const float* bias; int P, C;
+  __device__ void prefetch(Acc&, int, int, int) const {}
   __device__ void begin(Acc&, int, int, int) const {}
   __device__ void end(Acc&, int, int, int) const {}
-  __device__ void chunk(Acc& a, int b, int, int p, int c0, const float* v) const {
+  __device__ void chunk(Acc&, int b, int, int p, int c0, const float* v) const {
     if (p >= P) return;
     __align__(16) bf16 h[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int o = c0 + q;
-      const float x = fmaxf(v[q] + bias[o] + a.s[o], 0.f);
+      const float x = fmaxf(v[q] + bias[o], 0.f);
       h[q] = __float2bfloat16(x);
       act_cp[((size_t)b * C + o) * P + p] = h[q];
     }
@@ -481,13 +487,10 @@ static int pino_network(bs_pino* net, PinoRes& R, const PinoState* st, int B, cu
     BS_TRY_LAUNCH((launch_umma<256, 48>(dim3((C * mx + 127) / 128, B, (2 * Mp) / 256),
                                         GemmA{R.Y, (long long)C * mx * MY * 2, MY * 2, C * mx, MY * 2},
                                         GemmB{R.Eyi, 0, 256 * 48}, EpiZ{R.Z1, Mp, mx, C}, net->err, s)));
-    // G5
-    BS_TRY_LAUNCH((launch_umma<Mp, 32>(dim3(C * Mp / 128, B), GemmA{R.Z1, (long long)C * Mp * mx * 2, mx * 2, C * Mp, mx * 2},
-                                       GemmB{R.Exi, 0, 0}, EpiSpec{R.spec, Mp, C}, net->err, s)));
-    // G6
-    BS_TRY_LAUNCH((launch_umma<32, 32>(dim3(P / 128, B), GemmA{R.act_pc, (long long)P * C, C, P, C},
-                                       GemmB{net->Wpw + (size_t)l * C * C, 0, 0},
-                                       EpiAct{R.act_cp, R.act_pc, R.spec, net->pw_b + l * C, P, C}, net->err, s)));
+    // G5: inverse x-DFT and the pointwise product into one accumulator
+    BS_TRY_LAUNCH((launch_umma2<32, 32, 32>(dim3(P / 128, B),
+                                            PwOps<Mp>{R.Exi, R.Z1, R.act_pc, net->Wpw + (size_t)l * C * C},
+                                            EpiAct{R.act_cp, R.act_pc, net->pw_b + l * C, P, C}, net->err, s)));
   }
   BS_TRY_LAUNCH((launch_umma<128, 32>(dim3(P / 128, B), GemmA{R.act_pc, (long long)P * C, C, P, C},
                                       GemmB{net->W1, 0, 0}, EpiProj{R.wout, net->b1, net->w2, net->b2, P},
@@ -616,8 +619,8 @@ size_t pino_partials_bytes(int M, int N) {
   return (size_t)(N + 1) * nblocks * 2 * sizeof(double);
 }
 
-// kernels per network step: restrict, lift, 6 per layer, projection, apply
-int pino_launches_per_step(const bs_pino* net) { return 3 + 6 * net->L + 1; }
+// kernels per network step: restrict, lift, 5 per layer, projection, apply
+int pino_launches_per_step(const bs_pino* net) { return 3 + 5 * net->L + 1; }
 
 int pino_error_flag(const bs_pino* net, int* flag) {
   BS_CUDA_TRY(cudaMemcpy(flag, net->err, sizeof(int), cudaMemcpyDeviceToHost));
