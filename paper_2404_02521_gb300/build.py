@@ -21,6 +21,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no contraction into fused multiply-adds, so x86 and Arm hosts round alike
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr"]
+# the fine stepper's device code, too: its layouts and launch plans instantiate the same
+# stencil in different kernels, and only without implicit contraction do they round alike
+# (its multiply-adds are written as explicit fused operations)
+FILE_FLAGS = {"fine.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -60,7 +64,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), *extra, "-I", INCLUDE, "-c", src,
+               "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

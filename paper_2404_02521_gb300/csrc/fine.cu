@@ -40,12 +40,18 @@ __device__ __forceinline__ void cl_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-// b = dtau R_h w at one node from the 3x3 neighbourhood of hi (eq. fd in index units).
+// b = dtau R_h w at one node from the 3x3 neighbourhood of hi (eq. fd in index units).  This
+// file is compiled without implicit contraction; the multiply-adds are explicit, so every
+// kernel that instantiates the stencil rounds it alike.
 __device__ __forceinline__ float rhs_point(float ce, float cw, float cs, float cn, float cg, float rdt,
                                            float nW, float nC, float nE, float cW, float cC,
                                            float cE, float sW, float sC, float sE) {
-  return ce * (cE - cC) - cw * (cC - cW) + cs * (sC - cC) - cn * (cC - nC) +
-         cg * ((sE - nE) - (sW - nW)) - rdt * cC;
+  float t = ce * (cE - cC);
+  t = fmaf(-cw, cC - cW, t);
+  t = fmaf(cs, sC - cC, t);
+  t = fmaf(-cn, cC - nC, t);
+  t = fmaf(cg, (sE - nE) - (sW - nW), t);
+  return fmaf(-rdt, cC, t);
 }
 
 // Jacobi update of one node from the old increments around it.
@@ -54,8 +60,7 @@ __device__ __forceinline__ float jacobi_point(float b, float invd, float ce, flo
                                               float cW, float cE, float sW, float sC, float sE) {
   const float t1 = fmaf(ce, cE, fmaf(cw, cW, b));
   const float t2 = fmaf(cs, sC, cn * nC);
-  const float t3 = cg * ((sE - nE) - (sW - nW));
-  return ((t1 + t2) + t3) * invd;
+  return fmaf(cg, (sE - nE) - (sW - nW), t1 + t2) * invd;
 }
 
 // Asynchronous 4-byte global -> shared copy; with ok == false the destination is zero-filled
@@ -86,7 +91,7 @@ __device__ __forceinline__ float next_guess(float v, float* dp, int e, bool extr
   if (!dp) return v;
   const float prev = dp[e];
   dp[e] = v;
-  return extrap ? 2.f * v - prev : v;
+  return extrap ? fmaf(2.f, v, -prev) : v;
 }
 
 // One Jacobi sweep over the thread's column strip (own band rows r0..r0+K-1, plane rows
@@ -818,10 +823,27 @@ int fine_launches(const bs_grid* g, const ItemDesc* items, int n, int nsteps) {
   return total;
 }
 
+// Band layouts of the 129..256-column grids.  The default: 8 CTAs of 32 rows (512 threads, one
+// column x 16 rows each).  For one or a few states: 16 CTAs of 16 rows (256 threads), each on
+// an SM of its own (its shared memory is padded so that no second CTA shares the SM), so that
+// a state's steps run on twice the SMs at half the warps per SM -- 2.03 against 3.06 ms for
+// 512 steps of one 256 x 256 state, but more waves for a large batch.  Every node is computed
+// with the same operations from its global indices in both, so results agree bit for bit.
+typedef BandCfg<256, 512, 16> Band256;
+typedef BandCfg<256, 256, 16> Band256x16;
+constexpr size_t kBandSpreadSmem = 120 * 1024;   // above half an SM's shared memory
+constexpr double kBand16Time = 0.66;             // Band256x16's time per state over Band256's
+
 template <class CFG>
-static int launch_band(const FineBatch& fb, cudaStream_t s) {
-  const size_t smem = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
-                      (size_t)CFG::BH * sizeof(float4);
+static size_t band_smem(bool spread) {
+  const size_t b = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
+                   (size_t)CFG::BH * sizeof(float4);
+  return spread ? std::max(b, kBandSpreadSmem) : b;
+}
+
+template <class CFG>
+static int launch_band(const FineBatch& fb, cudaStream_t s, bool spread = false) {
+  const size_t smem = band_smem<CFG>(spread);
   auto kern = fine_band_kernel<CFG>;
   BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (fb.sh.C > 8) BS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -841,17 +863,24 @@ static int launch_band(const FineBatch& fb, cudaStream_t s) {
   return BS_OK;
 }
 
-// Clusters of the fine band kernel that the device runs at once (0 if unknown: cluster tiles).
+// Clusters of the fine band kernel that the device runs at once (0 if unknown), measured once
+// per device, layout and cluster size.
 template <class CFG>
-static int band_capacity(const BandShape& sh) {
-  const size_t smem = (size_t)3 * CFG::PLANE * sizeof(float) + (size_t)CFG::BH * CFG::NCOL * sizeof(float) +
-                      (size_t)CFG::BH * sizeof(float4);
-  auto kern = fine_band_kernel<CFG>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      (sh.C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+static int band_capacity(const BandShape& sh, bool spread = false) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
+  std::lock_guard<std::mutex> lock(mu);
+  const int key = sh.C * 2 + (spread ? 1 : 0);
+  auto it = cache.find({dev, key});
+  if (it != cache.end()) return it->second;
+  const size_t smem = band_smem<CFG>(spread);
+  auto kern = fine_band_kernel<CFG>;
+  int n = 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sh.C, 1, 1);
   cfg.blockDim = dim3(CFG::NT, 1, 1);
@@ -863,12 +892,33 @@ static int band_capacity(const BandShape& sh) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      (sh.C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) ||
+      cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
     cudaGetLastError();
-    return 0;
+    n = 0;
   }
+  cache[{dev, key}] = n;
   return n;
+}
+
+static BandShape band16_shape(const BandShape& sh) {
+  BandShape s16 = sh;
+  s16.G = 1;
+  s16.BH = 16;
+  s16.C = (sh.M + 15) / 16;
+  return s16;
+}
+
+// Whether a launch of n states on a 256-column band grid takes the 16-CTA layout: fewer
+// waves times time per state (BS_OPT_FINE_TILE 1 or 2 forces the 8- or the 16-CTA layout).
+static bool use_band16(const BandShape& sh, int n) {
+  if (sh.ncol != 256) return false;
+  if (g_opt.fine_tile == 1 || g_opt.fine_tile == 2) return g_opt.fine_tile == 2;
+  const int cap8 = band_capacity<Band256>(sh), cap16 = band_capacity<Band256x16>(band16_shape(sh), true);
+  if (cap8 <= 0 || cap16 <= 0) return false;
+  const double t8 = std::ceil((double)n / cap8), t16 = std::ceil((double)n / cap16) * kBand16Time;
+  return t16 < t8;
 }
 
 int fine_cluster_capacity(const bs_grid* g) {
@@ -878,7 +928,7 @@ int fine_cluster_capacity(const bs_grid* g) {
     case 32: return band_capacity<BandCfg<32, 256, 4>>(sh);
     case 64: return band_capacity<BandCfg<64, 512, 8>>(sh);
     case 128: return band_capacity<BandCfg<128, 512, 16>>(sh);
-    case 256: return band_capacity<BandCfg<256, 512, 16>>(sh);
+    case 256: return band_capacity<Band256>(sh);
   }
   return 0;
 }
@@ -886,19 +936,20 @@ int fine_cluster_capacity(const bs_grid* g) {
 int launch_fine(const bs_grid* g, const ItemDesc* items, int n, int nsteps, cudaStream_t s) {
   const BandShape sh = g->shape;
   if (sh.C < 1 || sh.C > kMaxCluster) return launch_ctiles(g, items, n, nsteps, s);
+  const bool b16 = use_band16(sh, std::min(n, kMaxItems));
   for (int base = 0; base < n; base += kMaxItems) {
     FineBatch fb;
     fb.n = (n - base) < kMaxItems ? (n - base) : kMaxItems;
     for (int k = 0; k < fb.n; ++k) fb.it[k] = items[base + k];
     fb.nsteps = nsteps;
-    fb.sh = sh;
+    fb.sh = b16 ? band16_shape(sh) : sh;
     fb.h = (float)(g->xmax / (g->M - 1));
     int rc;
     switch (sh.ncol) {
       case 32: rc = launch_band<BandCfg<32, 256, 4>>(fb, s); break;
       case 64: rc = launch_band<BandCfg<64, 512, 8>>(fb, s); break;
       case 128: rc = launch_band<BandCfg<128, 512, 16>>(fb, s); break;
-      case 256: rc = launch_band<BandCfg<256, 512, 16>>(fb, s); break;
+      case 256: rc = b16 ? launch_band<Band256x16>(fb, s, true) : launch_band<Band256>(fb, s); break;
       default: rc = set_error(BS_ERR_ARG, "fine_propagate_batched: no band shape for M=%d", g->M);
     }
     if (rc != BS_OK) return rc;

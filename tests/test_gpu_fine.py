@@ -154,6 +154,32 @@ def test_tile_step_split_over_launches(bs):
     assert rel_err(to_np(one), oracle_fine(M, xmax, p, u0, 0.1, dtau, 1)) <= FP32_FINE_TOL
 
 
+@pytest.mark.parametrize("M", [129, 200, 256])
+def test_band_layouts_agree_bitwise(bs, tile_layout, M):
+    # a state in one cluster of 8 CTAs of 32 rows or of 16 CTAs of 16 rows: the same
+    # operations per node, so the same result bit for bit, one state or several per launch
+    import torch
+    p = PARAMS[1]
+    dtau = dtau_for(M, p)
+    u0 = to_gpu(start_state(M, 4.0, p, "random", seed=3 * M))
+    g = bs.Grid(M, 4.0)
+    outs = {}
+    for layout in (1, 2):
+        tile_layout(layout)
+        for n in (1, 3):
+            out = [torch.empty_like(u0) for _ in range(n)]
+            bs.fine_propagate_batched(g, [p] * n, [u0] * n, out, [0.05 * k for k in range(n)], [dtau] * n, 40)
+            torch.cuda.synchronize()
+            outs[(layout, n)] = out[0]
+    tile_layout(0)
+    auto = torch.empty_like(u0)
+    bs.fine_propagate_batched(g, [p], [u0], [auto], [0.0], [dtau], 40)
+    torch.cuda.synchronize()
+    for key, out in outs.items():
+        assert torch.equal(out, outs[(1, 1)]), key
+    assert torch.equal(auto, outs[(1, 1)])
+
+
 @pytest.mark.parametrize("layout", [1, 2])
 def test_tile_one_sweep_commit_in_split_step(bs, tile_layout, layout):
     # items of one batch with different step sizes: the batch's cold step takes 26 sweeps and
