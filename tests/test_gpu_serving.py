@@ -55,6 +55,25 @@ def plain(bs, reqs, fine_steps):
     return outs
 
 
+def test_mix_switches_fine_layouts_bitwise(bs):
+    # two 256^2 requests with the same parameters share their F launches in the mix (16
+    # states: the 8-CTA band layout) but not alone (8 states: the 16-CTA layout), and a 512^2
+    # request's F runs as cluster tiles; every result is the same bit for bit either way
+    import torch
+    from paper_2404_02521_gb300 import serving
+    p = wl.exchange_cfg2(0.7).params
+    reqs = [wl.Problem("s256a", 256, 4.0, 8, 0, 1, p), wl.Problem("s256b", 256, 4.0, 8, 0, 1, p),
+            wl.Problem("s512", 512, 4.0, 4, 0, 1, wl.basket_cfg1().params)]
+    outs = [torch.zeros((r.M, r.M), device="cuda") for r in reqs]
+    sv = bs.Server(1 << 31, 4)
+    res, _ = serving.replay(sv, reqs, [0.0, 0.0, 0.0], outs)
+    sv.close()
+    assert all(r["status"] == 0 for r in res), res
+    assert torch.equal(outs[0], outs[1])
+    for r, a, b in zip(reqs, outs, alone(bs, reqs)):
+        assert torch.equal(a, b), r.name
+
+
 def test_mix_equals_alone_bitwise(bs):
     import torch
     from paper_2404_02521_gb300 import serving
