@@ -467,19 +467,22 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
   // the own rows of the previous increment and of lo: asynchronous copies, all in flight at
   // once, zero-filled outside the domain (with VEC = 4 a chunk lies wholly inside or outside:
   // M and the region origin are multiples of 4).
+  // The second increment plane needs only its halo rows: the launch's first sweep reads the
+  // first plane and writes every own row of the second before anything reads it.
   for (int e = tid * VEC; e < PLANE; e += CFG::NT * VEC) {
     const int pr = e / NCOL, c = e % NCOL;
     const int j = jb + pr - 1, i = ix0 + c;
     const bool in = (i >= 0 && i < M && j >= 0 && j < M);
     const size_t gi = in ? (size_t)j * M + i : 0;
+    const bool halo = pr == 0 || pr == BH + 1;
     if constexpr (VEC == 4) {
       cp_async16(hi + e, hi_g + gi, in);
       cp_async16(dA + e, dv_g + gi, in && !first);
-      cp_async16(dB + e, dv_g + gi, in && !first);
+      if (halo) cp_async16(dB + e, dv_g + gi, in && !first);
     } else {
       cp_async4(hi + e, hi_g + gi, in);
       cp_async4(dA + e, dv_g + gi, in && !first);
-      cp_async4(dB + e, dv_g + gi, in && !first);
+      if (halo) cp_async4(dB + e, dv_g + gi, in && !first);
     }
   }
   for (int e = tid * VEC; e < BH * NCOL; e += CFG::NT * VEC) {
