@@ -350,7 +350,7 @@ int coarse_propagate_batched(const bs_grid* g, int kind, const bs_pino* net, con
   if (kind == BS_COARSE_PINO) {
     std::vector<ItemDesc> items((size_t)B);
     for (int b = 0; b < B; ++b) items[(size_t)b] = make_item(p[b], tau0[b], dtau_slice);
-    gm->n_coarse += ((B + 127) / 128) * pino_launches_per_step(const_cast<bs_pino*>(net));
+    gm->n_coarse += ((B + 127) / 128) * pino_launches_per_step(const_cast<bs_pino*>(net), gm->M);
     return pino_propagate_batched(const_cast<bs_pino*>(net), g, items.data(), u_in, u_out, B, s);
   }
   if (kind != BS_COARSE_NUM) return set_error(BS_ERR_ARG, "coarse_propagate_batched: unknown kind %d", kind);
@@ -657,7 +657,7 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
       g->n_coarse += 1;
       return launch_sweep(g, d, sa, s);
     }
-    const int per_slice = pino_launches_per_step(pnet);
+    const int per_slice = pino_launches_per_step(pnet, g->M);
     for (int n = sa.n_first; n < sa.N; ++n)
       g->n_coarse += (sa.mode == SWEEP_ITER && n == sa.n_first) ? 1 : per_slice;
     g->n_coarse += 1;

@@ -329,5 +329,5 @@ int pino_sweep(bs_pino* net, const bs_grid* g, const ItemDesc& d, const SweepArg
                double* partials, cudaStream_t s);
 size_t pino_partials_bytes(int M, int N);
 int pino_error_flag(const bs_pino* net, int* flag);
-int pino_launches_per_step(const bs_pino* net);
+int pino_launches_per_step(const bs_pino* net, int M);
 }  // namespace bsp

@@ -16,6 +16,9 @@
 //   G5 inv. x-DFT [pixel: x] x [(kx,re/im) of (o,y)] -> o, Hermitian weights and 1/Mp^2,
 //      + pointwise [pixel] x [c] -> o, both into one accumulator (K = 32 each); the
 //                 epilogue adds the bias and applies ReLU
+//      At Mp = 128 a tile is one row of pixels; before the last layer the same kernel then
+//      runs the next layer's G1 on the row (pino_pointwise_xdft_kernel), so only the first
+//      layer launches G1 on its own.
 //   P  projection [pixel]  x [c]          -> hidden, epilogue ReLU . w2 + b2, residual
 // Each epilogue writes the K-contiguous layout the next GEMM reads, so no transposes run
 // between them.  The DFT matrices are exact transforms (not learned) stored in BF16.
@@ -300,6 +303,84 @@ struct EpiAct {  // G5: rows pixels, cols o -> ReLU(spectral + W v + b) into bot
   }
 };
 
+// Mp = 128: the two-product stage of a layer and, in the same kernel, the next layer's x-DFT
+// of the tile's row (a tile is one row y of 128 pixels).  The tile's new activations go to
+// shared memory as the B operand [o][x] of a third product D3[(kx, re/im)][o] = Ex act^T
+// (accumulator columns 32..63), whose rows 0..23 are the x-DFT output of the row; the
+// channel-major copy of the activations, which only the x-DFT read, is not written.
+constexpr size_t kPwxSmem = 2 * ((size_t)2 * (128 + 32) * 32 + 128 * 128 + 32 * 128) + 64;
+
+__global__ void __launch_bounds__(128) pino_pointwise_xdft_kernel(PwOps<128> ops, const bf16* __restrict__ Ex,
+                                                                  const float* __restrict__ bias, bf16* act_pc,
+                                                                  bf16* X1, int* err) {
+  constexpr int Mp = 128, C = 32, P = Mp * Mp, mx = 12;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  bf16* sA1 = reinterpret_cast<bf16*>(smem);
+  bf16* sB1 = sA1 + 128 * 32;
+  bf16* sA2 = sB1 + 32 * 32;
+  bf16* sB2 = sA2 + 128 * 32;
+  bf16* sA3 = sB2 + 32 * 32;    // x-DFT matrix rows (kx, re/im), K = x, zero below row 32
+  bf16* sB3 = sA3 + 128 * 128;  // the tile's activations [o][x]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB3 + 32 * 128);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.y, y = blockIdx.x, x = tid;
+  ops.load(sA1, sB1, sA2, sB2);
+  for (int e = tid; e < 128 * 16; e += 128) {
+    const int r = e >> 4, kv = e & 15;
+    const bool ok = r < 32;
+    cp_async_16(sA3 + canon_idx(r, kv * 8, 128), ok ? Ex + (size_t)r * Mp + kv * 8 : Ex, ok);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  const uint32_t tmem = umma_setup<64>(tslot, mbar);
+  if (tid == 0) {
+    umma_issue<32>(tmem, smem_u32(sA1), smem_u32(sB1), 32, false);
+    umma_issue<32>(tmem, smem_u32(sA2), smem_u32(sB2), 32, true);
+    umma_commit(mbar);
+  }
+  const size_t p = (size_t)y * Mp + x;
+  if (umma_wait(mbar, err, 0)) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < C; c0 += 16) {
+      float v[16];
+      umma_ld16(tmem, c0, v);
+      __align__(16) bf16 h[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int o = c0 + q;
+        h[q] = __float2bfloat16(fmaxf(v[q] + bias[o], 0.f));
+        sB3[canon_idx(o, x, 128)] = h[q];
+      }
+      uint4* dst = reinterpret_cast<uint4*>(act_pc + ((size_t)b * P + p) * C + c0);
+      dst[0] = reinterpret_cast<const uint4*>(h)[0];
+      dst[1] = reinterpret_cast<const uint4*>(h)[1];
+    }
+  }
+  // the activations, written by the threads, become the tensor cores' operand
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (tid == 0) {
+    umma_issue<32>(tmem + 32, smem_u32(sA3), smem_u32(sB3), 128, false);
+    umma_commit(mbar);
+  }
+  if (umma_wait(mbar, err, 1) && warp == 0) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < C; c0 += 16) {
+      float v[16];
+      umma_ld16(tmem + 32, c0, v);   // lane = row (kx, re/im)
+      if (lane < 2 * mx) {
+        const int kx = lane >> 1, ri = lane & 1;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          X1[(((size_t)b * C + c0 + q) * mx + kx) * (2 * Mp) + 2 * y + ri] = __float2bfloat16(v[q]);
+      }
+    }
+  }
+  umma_teardown<64>(tmem);
+}
+
 struct ProjAcc { float s; };
 struct EpiProj { // P: rows pixels, cols hidden -> w = sum_h ReLU(v + b1) w2[h] + b2
   typedef ProjAcc Acc;
@@ -472,9 +553,10 @@ static int pino_network(bs_pino* net, PinoRes& R, const PinoState* st, int B, cu
   BS_CUDA_TRY(cudaGetLastError());
   const int modes = MY * mx;
   for (int l = 0; l < net->L; ++l) {
-    // G1
-    BS_TRY_LAUNCH((launch_umma<32, Mp>(dim3(C * Mp / 128, B), GemmA{R.act_cp, (long long)C * P, Mp, C * Mp, Mp},
-                                       GemmB{R.Ex, 0, 0}, EpiX1{R.X1, Mp, mx, C}, net->err, s)));
+    // G1 (at Mp = 128 after the first layer it ran inside the previous layer's last stage)
+    if (Mp != 128 || l == 0)
+      BS_TRY_LAUNCH((launch_umma<32, Mp>(dim3(C * Mp / 128, B), GemmA{R.act_cp, (long long)C * P, Mp, C * Mp, Mp},
+                                         GemmB{R.Ex, 0, 0}, EpiX1{R.X1, Mp, mx, C}, net->err, s)));
     // G2
     BS_TRY_LAUNCH((launch_umma<64, 2 * Mp>(dim3((C * mx + 127) / 128, B),
                                            GemmA{R.X1, (long long)C * mx * 2 * Mp, 2 * Mp, C * mx, 2 * Mp},
@@ -487,10 +569,25 @@ static int pino_network(bs_pino* net, PinoRes& R, const PinoState* st, int B, cu
     BS_TRY_LAUNCH((launch_umma<256, 48>(dim3((C * mx + 127) / 128, B, (2 * Mp) / 256),
                                         GemmA{R.Y, (long long)C * mx * MY * 2, MY * 2, C * mx, MY * 2},
                                         GemmB{R.Eyi, 0, 256 * 48}, EpiZ{R.Z1, Mp, mx, C}, net->err, s)));
-    // G5: inverse x-DFT and the pointwise product into one accumulator
-    BS_TRY_LAUNCH((launch_umma2<32, 32, 32>(dim3(P / 128, B),
-                                            PwOps<Mp>{R.Exi, R.Z1, R.act_pc, net->Wpw + (size_t)l * C * C},
-                                            EpiAct{R.act_cp, R.act_pc, net->pw_b + l * C, P, C}, net->err, s)));
+    // G5: inverse x-DFT and the pointwise product into one accumulator (at Mp = 128, before
+    // the last layer, with the next layer's x-DFT of the row)
+    const PwOps<Mp> pw{R.Exi, R.Z1, R.act_pc, net->Wpw + (size_t)l * C * C};
+    if constexpr (Mp == 128) {
+      if (l + 1 < net->L) {
+        static bool attr_set = false;
+        if (!attr_set) {
+          BS_CUDA_TRY(cudaFuncSetAttribute(pino_pointwise_xdft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kPwxSmem));
+          attr_set = true;
+        }
+        pino_pointwise_xdft_kernel<<<dim3(Mp, B), 128, kPwxSmem, s>>>(pw, R.Ex, net->pw_b + l * C, R.act_pc, R.X1,
+                                                                      net->err);
+        BS_CUDA_TRY(cudaGetLastError());
+        continue;
+      }
+    }
+    BS_TRY_LAUNCH((launch_umma2<32, 32, 32>(dim3(P / 128, B), pw, EpiAct{R.act_cp, R.act_pc, net->pw_b + l * C, P, C},
+                                            net->err, s)));
   }
   BS_TRY_LAUNCH((launch_umma<128, 32>(dim3(P / 128, B), GemmA{R.act_pc, (long long)P * C, C, P, C},
                                       GemmB{net->W1, 0, 0}, EpiProj{R.wout, net->b1, net->w2, net->b2, P},
@@ -619,8 +716,11 @@ size_t pino_partials_bytes(int M, int N) {
   return (size_t)(N + 1) * nblocks * 2 * sizeof(double);
 }
 
-// kernels per network step: restrict, lift, 5 per layer, projection, apply
-int pino_launches_per_step(const bs_pino* net) { return 3 + 5 * net->L + 1; }
+// kernels per network step on an M x M state: restrict, lift, 5 per layer (4 after the first
+// at Mp = 128), projection, apply
+int pino_launches_per_step(const bs_pino* net, int M) {
+  return network_grid(M) == 128 ? 5 + 4 * net->L : 4 + 5 * net->L;
+}
 
 int pino_error_flag(const bs_pino* net, int* flag) {
   BS_CUDA_TRY(cudaMemcpy(flag, net->err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -158,7 +158,7 @@ static int request_sweep(bs_server* sv, Slot& sl, const ItemDesc& dc, const Swee
     cudaEvent_t e1 = batch_event(sv);
     BS_CUDA_TRY(cudaEventRecord(e1, sv->pino_stream));
     BS_CUDA_TRY(cudaStreamWaitEvent(sl.st, e1, 0));
-    sv->launches += (long long)(a.N - a.n_first) * pino_launches_per_step(r.net) + 1;
+    sv->launches += (long long)(a.N - a.n_first) * pino_launches_per_step(r.net, r.M) + 1;
   } else if (sl.g->coarse_M > 0) {
     if ((rc = resampled_sweep(sl.g, dc, a, sl.st))) return rc;
     sv->launches += (long long)(a.N - a.n_first) * resampled_launches_per_slice() + 1;

@@ -118,37 +118,43 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(mbar)));
 }
 
-// Bounded wait for the products (records an error flag on time-out).
-__device__ __forceinline__ bool umma_wait(uint64_t* mbar, int* err) {
+// Bounded wait for the products committed to mbar's phase of the given parity (0 for the
+// first commit, 1 for the second); records an error flag on time-out.
+__device__ __forceinline__ bool umma_wait(uint64_t* mbar, int* err, uint32_t parity = 0) {
   uint32_t done = 0;
   for (int it = 0; it < kUmmaWaitIters && !done; ++it) {
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done) : "r"(smem_u32(mbar)), "r"(0u) : "memory");
+                 : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
   }
   if (!done && (threadIdx.x & 31) == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   return done != 0;
 }
 
+// 16 accumulator columns from column c0 of the warp's 32 lanes (warp w reads lanes 32w..32w+31).
+__device__ __forceinline__ void umma_ld16(uint32_t tmem, int c0, float (&v)[16]) {
+  const int warp = threadIdx.x >> 5;
+  uint32_t r[16];
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                 "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 // Each warp reads its 32 accumulator rows, 16 columns at a time, into the epilogue.
 template <int N, class Epi>
 __device__ __forceinline__ void umma_readback(uint32_t tmem, const Epi& epi, typename Epi::Acc& acc, int by,
                                               int bz, int row) {
-  const int warp = threadIdx.x >> 5;
   epi.begin(acc, by, bz, row);
 #pragma unroll 1
   for (int c0 = 0; c0 < N; c0 += 16) {
-    uint32_t r[16];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
     float v[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+    umma_ld16(tmem, c0, v);
     epi.chunk(acc, by, bz, row, c0, v);
   }
   epi.end(acc, by, bz, row);
