@@ -581,27 +581,37 @@ def exchange_arm(args, local):
     }
 
 
+SERVE_COARSE_M = 256   # serving: grids above this run the numerical G on this coarse grid
+
+
 def serving_run(args):
     """Serving sample: the first args.serve_requests requests of the seeded serving trace
     (seed 12345: basket/exchange 50/50, sigma ~ U[0.1,0.5], rho ~ U[-0.7,0.7],
     r ~ U[0,0.08], T ~ U[0.25,2], M in {64,128,256,512}, N in {16,32,64}; fine steps per slice
-    64 doubled until the Jacobi bound is <= 0.7, one coarse step per slice, tol 1e-4).
-    Poisson arrivals at args.serve_load x the measured one-at-a-time capacity (above 1 the
-    queue grows, so the solves/s show what batching and overlap add)."""
+    64 doubled until the Jacobi bound is <= 0.7, one coarse step per slice, tol 1e-4; the
+    numerical G on the request's grid, on 256 x 256 for the 512 x 512 requests as in the
+    large solve).  Poisson arrivals at args.serve_load x the measured one-at-a-time capacity
+    (above 1 the queue grows, so the solves/s show what batching and overlap add)."""
+    import types
+
     import numpy as np
     import torch
 
     import paper_2404_02521_gb300 as bs
     from paper_2404_02521_gb300 import serving
 
+    def with_coarse(r):
+        f = {k.name: getattr(r, k.name) for k in dataclasses.fields(r)}
+        return types.SimpleNamespace(**f, coarse_M=SERVE_COARSE_M if r.M > SERVE_COARSE_M else 0)
+
     n = args.serve_requests
-    reqs = [t.problem for t in wl.serving_trace(n, 0.0)]
+    reqs = [with_coarse(t.problem) for t in wl.serving_trace(n, 0.0)]
     fs = [bs.bs_fine_steps_for(r.M, r.params, r.N) for r in reqs]
     # warm-up: one small request per grid size (autotuner, allocations, module loads)
     seen = {}
     for i, r in enumerate(reqs):
         seen.setdefault(r.M, i)
-    warm = [wl.Problem("w", reqs[i].M, reqs[i].xmax, 16, 0, 1, dataclasses.replace(reqs[i].params, T=0.25))
+    warm = [with_coarse(wl.Problem("w", reqs[i].M, reqs[i].xmax, 16, 0, 1, dataclasses.replace(reqs[i].params, T=0.25)))
             for i in seen.values()]
     wfs = [bs.bs_fine_steps_for(r.M, r.params, r.N) for r in warm]
     serving.service_times(warm, wfs, [torch.empty((r.M, r.M), device="cuda") for r in warm])
@@ -625,6 +635,7 @@ def serving_run(args):
     diff = max(float((a - b).abs().max() / b.abs().max()) for a, b in zip(outs, alone))
     return {
         "requests": n, "sample": f"first {n} requests of the seeded serving trace (seed 12345)",
+        "coarse": f"numerical G on the request's grid, on {SERVE_COARSE_M}x{SERVE_COARSE_M} for larger grids",
         "grids": sorted({r.M for r in reqs}), "arrival_rate_per_s": rate,
         "load": args.serve_load, "one_at_a_time_capacity_per_s": capacity,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
