@@ -12,7 +12,7 @@
 //   G2 y-DFT      [(c,kx)] x [(y,re/im)]  -> (ky mode, re/im)    N = 64 (48 used),  K = 2 Mp
 //   G3 mixing     per mode: [state] x [(c,re/im)] -> (o,re/im)   N = 64, K = 64 (complex as
 //                 the real 2x2 block form of the C x C mode matrix)
-//   G4 inv. y-DFT [(o,kx)] x [(ky,re/im)] -> (y, re/im)          N = 2 Mp (chunks of 256), K = 48
+//   G4 inv. y-DFT [(o,kx)] x [(ky,re/im)] -> (y, re/im)          N = 2 Mp (chunks of 128), K = 48
 //   G5 inv. x-DFT [pixel: x] x [(kx,re/im) of (o,y)] -> o, Hermitian weights and 1/Mp^2,
 //      + pointwise [pixel] x [c] -> o, both into one accumulator (K = 32 each); the
 //                 epilogue adds the bias and applies ReLU
@@ -239,7 +239,8 @@ struct EpiY {    // G3 (blockIdx.y = mode): rows b, cols (o, re/im) -> Y[b][o][k
   }
 };
 
-struct EpiZ {    // G4 (blockIdx.z = 256-column chunk): rows (o, kx), cols (y, re/im) -> Z1[b][o][y][kx][re/im]
+constexpr int kG4Chunk = 128;   // G4 columns per CTA: more CTAs, and shorter epilogues, at one state
+struct EpiZ {    // G4 (blockIdx.z = column chunk): rows (o, kx), cols (y, re/im) -> Z1[b][o][y][kx][re/im]
   typedef NoAcc Acc;
   bf16* Z1; int Mp, mx, C;
   __device__ void prefetch(Acc&, int, int, int) const {}
@@ -250,7 +251,7 @@ struct EpiZ {    // G4 (blockIdx.z = 256-column chunk): rows (o, kx), cols (y, r
     const int o = row / mx, kx = row - (row / mx) * mx;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int col = z * 256 + c0 + q, y = col >> 1;
+      const int col = z * kG4Chunk + c0 + q, y = col >> 1;
       Z1[((((size_t)b * C + o) * Mp + y) * mx + kx) * 2 + (col & 1)] = __float2bfloat16(v[q]);
     }
   }
@@ -565,10 +566,10 @@ static int pino_network(bs_pino* net, PinoRes& R, const PinoState* st, int B, cu
     BS_TRY_LAUNCH((launch_umma<64, 64>(dim3(1, modes), GemmA{R.X2, (long long)B * C * 2, 64, B, 64},
                                        GemmB{net->R + (size_t)l * modes * 64 * 64, 64 * 64, 0},
                                        EpiY{R.Y, mx, MY, C, B}, net->err, s)));
-    // G4 (blockIdx.z = 256-column chunk of (y, re/im))
-    BS_TRY_LAUNCH((launch_umma<256, 48>(dim3((C * mx + 127) / 128, B, (2 * Mp) / 256),
-                                        GemmA{R.Y, (long long)C * mx * MY * 2, MY * 2, C * mx, MY * 2},
-                                        GemmB{R.Eyi, 0, 256 * 48}, EpiZ{R.Z1, Mp, mx, C}, net->err, s)));
+    // G4 (blockIdx.z = kG4Chunk-column chunk of (y, re/im))
+    BS_TRY_LAUNCH((launch_umma<kG4Chunk, 48>(dim3((C * mx + 127) / 128, B, (2 * Mp) / kG4Chunk),
+                                             GemmA{R.Y, (long long)C * mx * MY * 2, MY * 2, C * mx, MY * 2},
+                                             GemmB{R.Eyi, 0, kG4Chunk * 48}, EpiZ{R.Z1, Mp, mx, C}, net->err, s)));
     // G5: inverse x-DFT and the pointwise product into one accumulator (at Mp = 128, before
     // the last layer, with the next layer's x-DFT of the row)
     const PwOps<Mp> pw{R.Exi, R.Z1, R.act_pc, net->Wpw + (size_t)l * C * C};
