@@ -12,7 +12,7 @@
 //   G2 y-DFT      [(c,kx)] x [(y,re/im)]  -> (ky mode, re/im)    N = 64 (48 used),  K = 2 Mp
 //   G3 mixing     per mode: [state] x [(c,re/im)] -> (o,re/im)   N = 64, K = 64 (complex as
 //                 the real 2x2 block form of the C x C mode matrix)
-//   G4 inv. y-DFT [(o,kx)] x [(ky,re/im)] -> (y, re/im)          N = 2 Mp (chunks of 128), K = 48
+//   G4 inv. y-DFT [(o,kx)] x [(ky,re/im)] -> (y, re/im)          N = 2 Mp (chunks of 64), K = 48
 //   G5 inv. x-DFT [pixel: x] x [(kx,re/im) of (o,y)] -> o, Hermitian weights and 1/Mp^2,
 //      + pointwise [pixel] x [c] -> o, both into one accumulator (K = 32 each); the
 //                 epilogue adds the bias and applies ReLU
@@ -239,7 +239,7 @@ struct EpiY {    // G3 (blockIdx.y = mode): rows b, cols (o, re/im) -> Y[b][o][k
   }
 };
 
-constexpr int kG4Chunk = 128;   // G4 columns per CTA: more CTAs, and shorter epilogues, at one state
+constexpr int kG4Chunk = 64;    // G4 columns per CTA: more CTAs, and shorter epilogues, at one state
 struct EpiZ {    // G4 (blockIdx.z = column chunk): rows (o, kx), cols (y, re/im) -> Z1[b][o][y][kx][re/im]
   typedef NoAcc Acc;
   bf16* Z1; int Mp, mx, C;
