@@ -94,6 +94,17 @@ __device__ __forceinline__ float next_guess(float v, float* dp, int e, bool extr
   return extrap ? fmaf(2.f, v, -prev) : v;
 }
 
+// next_guess with the mode fixed at compile time, so that the sweeps carry no per-node select:
+// XM = 0 no history (guess = v), 1 history kept (guess = v), 2 history kept and the guess
+// extrapolated.
+template <int XM>
+__device__ __forceinline__ float next_guess_x(float v, float* dp, int e) {
+  if (XM == 0) return v;
+  const float prev = dp[e];
+  dp[e] = v;
+  return XM == 2 ? fmaf(2.f, v, -prev) : v;
+}
+
 // One Jacobi sweep over the thread's column strip (own band rows r0..r0+K-1, plane rows
 // r0+1..r0+K).  Strip rows 1..K-2 read only rows of the strip itself, written by this CTA
 // in the previous sweep; they are updated before the cluster wait.  The two end rows read
@@ -102,10 +113,14 @@ __device__ __forceinline__ float next_guess(float v, float* dp, int e, bool extr
 // The thread's own column of the old increment is in dv[]; lo[k] is the compensation word of
 // strip row k (registers, or shared memory through StripLo).  FIRST also evaluates
 // b = dtau R_h w from hi; LAST also applies the increment to (hi, lo) of the PDE nodes and
-// leaves the next step's initial guess (next_guess) in wr and dv[].  Nodes that are not PDE
-// rows have invd = 0 and write a zero increment; LAST leaves their hi (Dirichlet data) to the
-// far-field update, which may follow it directly.
-template <class CFG, bool FIRST, bool LAST, class LoT>
+// leaves the next step's initial guess (next_guess_x<XM>, history in dp) in wr and dv[].  Nodes
+// that are not PDE rows have invd = 0 and write a zero increment; LAST leaves their hi
+// (Dirichlet data) to the far-field update, which may follow it directly, unless UNCOND: then
+// every node takes the compensated update, which leaves hi as it is where v = 0 and lo = 0 (a
+// kernel may choose this only where each far-field value is written by the thread that owns
+// the node, after its sweep).  The plane rows are addressed from per-thread base pointers at
+// the row north of the strip, so every access in the unrolled rows is a constant offset.
+template <class CFG, bool FIRST, bool LAST, class LoT, int XM = 0, bool UNCOND = false>
 __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* __restrict__ wr,
                                            float* hi, const HaloPush& wr_push,
                                            const HaloPush& hi_push, const float4* __restrict__ rowc,
@@ -113,80 +128,90 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ rd, float* 
                                            const float (&invd)[CFG::K], LoT& lo,
                                            int col, int il, int ir, int r0, float ce, float cw,
                                            float cgi, float rdt, bool clustered,
-                                           float* dp = nullptr, bool extrap = false) {
+                                           float* dp = nullptr) {
   constexpr int NCOL = CFG::NCOL, K = CFG::K;
   static_assert(K >= 4, "strip needs interior rows");
   const int p0 = r0 + 1;
-  // rows 0 and 1 of the strip
-  const float r0W = rd[p0 * NCOL + il], r0E = rd[p0 * NCOL + ir];
-  const float r1W = rd[(p0 + 1) * NCOL + il], r1E = rd[(p0 + 1) * NCOL + ir];
+  // base pointers at plane row p0 - 1 = r0 (the row north of the strip)
+  const float* rW = rd + r0 * NCOL + il;
+  const float* rC = rd + r0 * NCOL + col;
+  const float* rE = rd + r0 * NCOL + ir;
+  const float* hW = hi + r0 * NCOL + il;
+  const float* hC = hi + r0 * NCOL + col;
+  const float* hE = hi + r0 * NCOL + ir;
+  float* hO = hi + r0 * NCOL + col;
+  float* wO = wr + r0 * NCOL + col;
+  float* dO = dp ? dp + r0 * NCOL + col : nullptr;   // own row k at dO[k * NCOL]
+  const float4* rcs = rowc + r0;
+  // rows 0 and 1 of the strip (plane rows p0, p0 + 1 at offsets 1, 2)
+  const float r0W = rW[NCOL], r0E = rE[NCOL];
+  const float r1W = rW[2 * NCOL], r1E = rE[2 * NCOL];
   const float dv1_old = dv[1];
   float nW = r0W, nC = dv[0], nE = r0E;
   float cW = r1W, cE = r1E;
   float h0W = 0.f, h0C = 0.f, h0E = 0.f, h1W = 0.f, h1C = 0.f, h1E = 0.f;
   float hnW = 0.f, hnC = 0.f, hnE = 0.f, hcW = 0.f, hcC = 0.f, hcE = 0.f;
   if (FIRST) {
-    h0W = hi[p0 * NCOL + il]; h0C = hi[p0 * NCOL + col]; h0E = hi[p0 * NCOL + ir];
-    h1W = hi[(p0 + 1) * NCOL + il]; h1C = hi[(p0 + 1) * NCOL + col]; h1E = hi[(p0 + 1) * NCOL + ir];
+    h0W = hW[NCOL]; h0C = hC[NCOL]; h0E = hE[NCOL];
+    h1W = hW[2 * NCOL]; h1C = hC[2 * NCOL]; h1E = hE[2 * NCOL];
     hnW = h0W; hnC = h0C; hnE = h0E;
     hcW = h1W; hcC = h1C; hcE = h1E;
   }
 #pragma unroll
   for (int k = 1; k <= K - 2; ++k) {
-    const int p = p0 + k;
-    const float sW = rd[(p + 1) * NCOL + il], sE = rd[(p + 1) * NCOL + ir];
+    const float sW = rW[(k + 2) * NCOL], sE = rE[(k + 2) * NCOL];
     const float sC = dv[k + 1];
-    const float4 rc = rowc[p - 1];
+    const float4 rc = rcs[k];
     const float cg = cgi * rc.z;
     if (FIRST) {
-      const float hsW = hi[(p + 1) * NCOL + il], hsC = hi[(p + 1) * NCOL + col],
-                  hsE = hi[(p + 1) * NCOL + ir];
+      const float hsW = hW[(k + 2) * NCOL], hsC = hC[(k + 2) * NCOL], hsE = hE[(k + 2) * NCOL];
       b[k] = rhs_point(ce, cw, rc.x, rc.y, cg, rdt, hnW, hnC, hnE, hcW, hcC, hcE, hsW, hsC, hsE);
       hnW = hcW; hnC = hcC; hnE = hcE;
       hcW = hsW; hcC = hsC; hcE = hsE;
     }
     const float v = jacobi_point(b[k], invd[k], ce, cw, rc.x, rc.y, cg, nW, nC, nE, cW, cE, sW, sC, sE);
-    const float g = LAST ? next_guess(v, dp, (r0 + k) * NCOL + col, extrap) : v;
-    wr[p * NCOL + col] = g;
+    const float g = LAST ? next_guess_x<XM>(v, dO, k * NCOL) : v;
+    wO[(k + 1) * NCOL] = g;
     nC = dv[k];
     dv[k] = g;
     nW = cW; nE = cE;
     cW = sW; cE = sE;
-    if (LAST && invd[k] != 0.f) hi[p * NCOL + col] = two_sum_update(hi[p * NCOL + col], v, lo[k]);
+    if (LAST && (UNCOND || invd[k] != 0.f)) hO[(k + 1) * NCOL] = two_sum_update(hO[(k + 1) * NCOL], v, lo[k]);
   }
   if (clustered) cl_wait();
   {  // last strip row: north = old row K-2 (window), south = plane row p0+K
-    const int k = K - 1, p = p0 + k;
-    const float sW = rd[(p + 1) * NCOL + il], sC = rd[(p + 1) * NCOL + col], sE = rd[(p + 1) * NCOL + ir];
-    const float4 rc = rowc[p - 1];
+    constexpr int k = K - 1;
+    const int p = p0 + k;
+    const float sW = rW[(k + 2) * NCOL], sC = rC[(k + 2) * NCOL], sE = rE[(k + 2) * NCOL];
+    const float4 rc = rcs[k];
     const float cg = cgi * rc.z;
     if (FIRST) {
-      const float hsW = hi[(p + 1) * NCOL + il], hsC = hi[(p + 1) * NCOL + col],
-                  hsE = hi[(p + 1) * NCOL + ir];
+      const float hsW = hW[(k + 2) * NCOL], hsC = hC[(k + 2) * NCOL], hsE = hE[(k + 2) * NCOL];
       b[k] = rhs_point(ce, cw, rc.x, rc.y, cg, rdt, hnW, hnC, hnE, hcW, hcC, hcE, hsW, hsC, hsE);
     }
     const float v = jacobi_point(b[k], invd[k], ce, cw, rc.x, rc.y, cg, nW, nC, nE, cW, cE, sW, sC, sE);
-    const float g = LAST ? next_guess(v, dp, (r0 + k) * NCOL + col, extrap) : v;
+    const float g = LAST ? next_guess_x<XM>(v, dO, k * NCOL) : v;
     band_store<CFG>(wr, wr_push, p - 1, col, g);
     dv[k] = g;
-    if (LAST && invd[k] != 0.f) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[k]));
+    if (LAST && (UNCOND || invd[k] != 0.f))
+      band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hO[(k + 1) * NCOL], v, lo[k]));
   }
   {  // first strip row: north = plane row p0-1, south = old row 1
     const int p = p0;
-    const float qW = rd[(p - 1) * NCOL + il], qC = rd[(p - 1) * NCOL + col], qE = rd[(p - 1) * NCOL + ir];
-    const float4 rc = rowc[p - 1];
+    const float qW = rW[0], qC = rC[0], qE = rE[0];
+    const float4 rc = rcs[0];
     const float cg = cgi * rc.z;
     if (FIRST) {
-      const float hqW = hi[(p - 1) * NCOL + il], hqC = hi[(p - 1) * NCOL + col],
-                  hqE = hi[(p - 1) * NCOL + ir];
+      const float hqW = hW[0], hqC = hC[0], hqE = hE[0];
       b[0] = rhs_point(ce, cw, rc.x, rc.y, cg, rdt, hqW, hqC, hqE, h0W, h0C, h0E, h1W, h1C, h1E);
     }
     const float v = jacobi_point(b[0], invd[0], ce, cw, rc.x, rc.y, cg, qW, qC, qE, r0W, r0E, r1W,
                                  dv1_old, r1E);
-    const float g = LAST ? next_guess(v, dp, r0 * NCOL + col, extrap) : v;
+    const float g = LAST ? next_guess_x<XM>(v, dO, 0) : v;
     band_store<CFG>(wr, wr_push, p - 1, col, g);
     dv[0] = g;
-    if (LAST && invd[0] != 0.f) band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hi[p * NCOL + col], v, lo[0]));
+    if (LAST && (UNCOND || invd[0] != 0.f))
+      band_store<CFG>(hi, hi_push, p - 1, col, two_sum_update(hO[NCOL], v, lo[0]));
   }
 }
 
@@ -291,9 +316,14 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_band_kernel(const __grid_cons
       if (s == 0)
         fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0,
                                      ce, cw, cgi, rdt, clustered);
-      else if (s == m - 1)
-        fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0,
-                                     ce, cw, cgi, rdt, clustered, DP, step + 1 >= d.xstart);
+      else if (s == m - 1) {
+        if (step + 1 >= d.xstart)
+          fine_sweep<CFG, false, true, decltype(lo), 2>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir,
+                                                        r0, ce, cw, cgi, rdt, clustered, DP);
+        else
+          fine_sweep<CFG, false, true, decltype(lo), 1>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir,
+                                                        r0, ce, cw, cgi, rdt, clustered, DP);
+      }
       else
         fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir,
                                       r0, ce, cw, cgi, rdt, clustered);
@@ -571,9 +601,15 @@ __global__ void __launch_bounds__(CFG::NT, 1) fine_ctile_kernel(const __grid_con
       } else if (fst)
         fine_sweep<CFG, true, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
                                      cgi, rdt, true);
-      else if (lst)
-        fine_sweep<CFG, false, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
-                                     cgi, rdt, true, DP, extrap);
+      else if (lst) {
+        // unconditional commit: the far-field data are set by the owning thread after the sweep
+        if (extrap)
+          fine_sweep<CFG, false, true, decltype(lo), 2, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col,
+                                                              il, ir, r0, ce, cw, cgi, rdt, true, DP);
+        else
+          fine_sweep<CFG, false, true, decltype(lo), 1, true>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col,
+                                                              il, ir, r0, ce, cw, cgi, rdt, true, DP);
+      }
       else
         fine_sweep<CFG, false, false>(rd, wr, hi, wp, hi_push, rowc, dv, b, invd, lo, col, il, ir, r0, ce, cw,
                                       cgi, rdt, true);
