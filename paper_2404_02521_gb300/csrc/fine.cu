@@ -54,13 +54,13 @@ __device__ __forceinline__ float rhs_point(float ce, float cw, float cs, float c
   return fmaf(-rdt, cC, t);
 }
 
-// Jacobi update of one node from the old increments around it.
+// Jacobi update of one node from the old increments around it: the four axis neighbours join
+// b in one chain of fused multiply-adds, then the mixed term, then the diagonal scale.
 __device__ __forceinline__ float jacobi_point(float b, float invd, float ce, float cw, float cs,
                                               float cn, float cg, float nW, float nC, float nE,
                                               float cW, float cE, float sW, float sC, float sE) {
-  const float t1 = fmaf(ce, cE, fmaf(cw, cW, b));
-  const float t2 = fmaf(cs, sC, cn * nC);
-  return fmaf(cg, (sE - nE) - (sW - nW), t1 + t2) * invd;
+  const float t = fmaf(cn, nC, fmaf(cs, sC, fmaf(ce, cE, fmaf(cw, cW, b))));
+  return fmaf(cg, (sE - nE) - (sW - nW), t) * invd;
 }
 
 // Asynchronous 4-byte global -> shared copy; with ok == false the destination is zero-filled
