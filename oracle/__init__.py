@@ -14,6 +14,8 @@ Modules
   resample      bilinear resampling; the numerical coarse model on a coarser grid (Sec. 4.4)
   fd_nd         eq. (bse_general) for n assets discretised like eq. (fd) (19-point stencil
                 at n = 3), implicit Euler by sparse LU
+  physics       the PDE term of the PINO training loss (Sec. 3.5, eq. bs_totalloss) and its
+                gradient
 
 Pinning: every function is checked by ``tests/test_oracle_*.py`` against facts
 the mathematics fixes (exactness of centred differences on x^a y^b, a, b <= 2,
