@@ -205,6 +205,25 @@ int coarse_propagate_batched(const bs_grid* g, int kind, const bs_pino* net, con
 int pino_load(const char* path, bs_pino** net);
 int pino_destroy(bs_pino* net);
 
+/* PDE term of the PINO training loss (Sec. 3.5, eq. bs_totalloss, MSE_f) for B predicted
+ * slices on the device.  A prediction u_pred[b] of u(tau + dtau[b]) from u_prev[b] = u(tau) is
+ * scored at the collocation points that carry a PDE row, 0 <= i, j <= M-2 (the far edges hold
+ * Dirichlet data), by the residual of eq. (bse_change_variable) discretised by eq. (fd) with
+ * the slice as one implicit-Euler step:
+ *   r = (u_pred - u_prev) / dtau - R_h u_pred,     loss[b] = sum r^2 / (M-1)^2,
+ * and, where grad is given, grad[b] = d loss[b] / d u_pred[b] on every node (the adjoint of the
+ * residual: 2/(M-1)^2 (r / dtau - R_h^T r)), so that a training loop can back-propagate it.
+ *  p[B], dtau[B]          host arrays (per-item parameters and slice lengths, dtau > 0)
+ *  u_pred[B], u_prev[B]   host arrays of device pointers to float[M*M] (read only)
+ *  loss                   device double[B], overwritten (FP64 sums of FP32 residuals; the
+ *                         order of the block sums may vary, so the last bits may too)
+ *  grad                   NULL, or a host array of B device pointers to float[M*M] (written;
+ *                         must not alias u_pred or u_prev)
+ * Asynchronous.  Errors: BS_ERR_ARG (NULL, B < 1, dtau <= 0, bad parameters), BS_ERR_CUDA. */
+int pino_physics_loss(const bs_grid* g, const bs_params* p, const float* const* u_pred,
+                      const float* const* u_prev, const double* dtau, int B, double* loss,
+                      float* const* grad, bs_stream stream);
+
 /* Parareal, eq. (parareal): u_{n+1}^{k+1} = G(u_n^{k+1}) + F(u_n^k) - G(u_n^k) on N slices
  * of [0, p->T], starting from the payoff and one serial coarse sweep.  F takes fine_steps
  * implicit-Euler steps per slice; G is the numerical model with coarse_steps steps per slice

@@ -25,7 +25,8 @@ EXPORTS = ["bs_last_error", "bs_grid_create", "bs_grid_destroy", "bs_payoff",
            "parareal_solve", "bs_fine_sweeps", "bs_set_option", "bs_grid_stats", "bs_phase_stats", "parareal_solve_noalloc",
            "bs_coarse_variant", "bs_coarse_variant_info", "bs_payoff3", "fine_propagate3", "coarse_propagate3", "parareal_solve3", "bs_server_create", "bs_server_submit", "bs_server_progress",
            "bs_server_poll", "bs_server_stats", "bs_server_destroy", "bs_fine_steps_for",
-           "bs_grid_set_coarse", "bs_device_allocations", "parareal_sweep_range", "coarse_propagate_batched"]
+           "bs_grid_set_coarse", "bs_device_allocations", "parareal_sweep_range", "coarse_propagate_batched",
+           "pino_physics_loss"]
 OPT_FINE_SWEEPS, OPT_JACOBI_TARGET, OPT_KRYLOV_TOL, OPT_KRYLOV_MAXIT, OPT_PHASE_TIMING = 0, 1, 2, 3, 4
 OPT_JACOBI_TARGET_COLD = 5
 OPT_COARSE_VARIANT = 6
@@ -104,6 +105,7 @@ def load(path: Optional[str] = None):
     lib.fine_propagate_batched.argtypes = [vp, P(bs_params), P(vp), P(vp), P(d), P(d), i, i, vp]
     lib.coarse_propagate.argtypes = [vp, i, vp, P(bs_params), vp, vp, d, d, i, vp]
     lib.pino_load.argtypes = [C.c_char_p, P(vp)]
+    lib.pino_physics_loss.argtypes = [vp, P(bs_params), P(vp), P(vp), P(d), i, vp, P(vp), vp]
     lib.pino_destroy.argtypes = [vp]
     lib.parareal_solve.argtypes = [vp, P(bs_params), i, i, i, i, vp, d, i, vp, P(i), P(d), vp]
     lib.bs_fine_sweeps.argtypes = [vp, P(bs_params), d, i]
@@ -214,6 +216,19 @@ def fine_propagate_batched(g: Grid, params: Sequence, u_in: Sequence, u_out: Seq
     dt = (C.c_double * B)(*[float(t) for t in dtau])
     return check(load().fine_propagate_batched(g.h, P, pin, pout, t0, dt, int(nsteps), B,
                                                _stream(stream)))
+
+
+def pino_physics_loss(g: Grid, params: Sequence, u_pred: Sequence, u_prev: Sequence,
+                      dtau: Sequence[float], loss, grad: Optional[Sequence] = None, stream=None):
+    """PDE term of the PINO training loss (Sec. 3.5): loss[b] (a device float64 tensor of
+    len(u_pred)) and, with grad, d loss[b] / d u_pred[b] into grad[b]."""
+    B = len(u_pred)
+    P = (bs_params * B)(*[to_params(p) for p in params])
+    pp = (C.c_void_p * B)(*[_ptr(x) for x in u_pred])
+    pv = (C.c_void_p * B)(*[_ptr(x) for x in u_prev])
+    dt = (C.c_double * B)(*[float(t) for t in dtau])
+    pg = (C.c_void_p * B)(*[_ptr(x) for x in grad]) if grad is not None else None
+    return check(load().pino_physics_loss(g.h, P, pp, pv, dt, B, _ptr(loss), pg, _stream(stream)))
 
 
 def bs_payoff3(M: int, xmax: float, p, u, stream=None):

@@ -190,6 +190,12 @@ int launch_krylov_fine(bs_grid* g, const ItemDesc* items, int n, int nsteps, cud
 
 using namespace bsp;
 
+namespace bsp {
+int launch_physics_loss(const bs_grid* g, const bs_params* p, const float* const* u_pred,
+                        const float* const* u_prev, const double* dtau, int B, double* loss,
+                        float* const* grad, cudaStream_t s);
+}  // namespace bsp
+
 extern "C" {
 
 const char* bs_last_error(void) { return g_err; }
@@ -763,6 +769,24 @@ int parareal_solve(const bs_grid* gc, const bs_params* p, int N, int fine_steps,
   if (status == BS_ERR_MAXITER && k < N)
     return set_error(BS_ERR_MAXITER, "parareal_solve: tol %g not met after %d iterations", tol, k);
   return BS_OK;
+}
+
+int pino_physics_loss(const bs_grid* g, const bs_params* p, const float* const* u_pred,
+                      const float* const* u_prev, const double* dtau, int B, double* loss,
+                      float* const* grad, bs_stream stream) {
+  if (!g || !p || !u_pred || !u_prev || !dtau || !loss)
+    return set_error(BS_ERR_ARG, "pino_physics_loss: NULL argument");
+  if (B < 1) return set_error(BS_ERR_ARG, "pino_physics_loss: B=%d", B);
+  for (int b = 0; b < B; ++b) {
+    int rc = check_params(&p[b]);
+    if (rc) return rc;
+    if (!u_pred[b] || !u_prev[b] || (grad && !grad[b]))
+      return set_error(BS_ERR_ARG, "pino_physics_loss: NULL state %d", b);
+    if (grad && (grad[b] == u_pred[b] || grad[b] == u_prev[b]))
+      return set_error(BS_ERR_ARG, "pino_physics_loss: grad[%d] aliases an input", b);
+    if (!(dtau[b] > 0.0)) return set_error(BS_ERR_ARG, "pino_physics_loss: dtau[%d] <= 0", b);
+  }
+  return launch_physics_loss(g, p, u_pred, u_prev, dtau, B, loss, grad, (cudaStream_t)stream);
 }
 
 }  // extern "C"

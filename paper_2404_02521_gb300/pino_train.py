@@ -10,8 +10,10 @@ pointwise layers, ReLU, projection) predicts the increment u(tau_n + dtau) - u(t
 
 Loss (Sec. 3.5, eq. bs_totalloss, adapted to a slice map): mean squared error against the
 fine solution, plus a physics term -- the residual of eq. (bse_change_variable) of the
-prediction, with centred differences and the slice as one implicit step -- and a boundary
-term on the far edges.  Adam, learning rate 1e-3 decayed by 0.96 at fixed intervals.
+prediction at the collocation points, discretised by eq. (fd) with the slice as one implicit
+step -- and a boundary term on the far edges.  The physics term and its gradient are the
+library's kernel (pino_physics_loss); the network's forward and backward passes are PyTorch.
+Adam, learning rate 1e-3 decayed by 0.96 at fixed intervals.
 
 Usage (on a GPU machine):
     python -m paper_2404_02521_gb300.pino_train --out weights.bin [--problems 256] [--iters 6000] [--slices 12,64]
@@ -86,23 +88,31 @@ class FNO(torch.nn.Module):
                               self.p1.out_features)
 
 
-def pde_residual(u_new, u_old, dtau, prm, h):
-    """(u_new - u_old)/dtau - R_h u_new on interior nodes (eq. fd with one step per slice)."""
-    s1, s2, rho, r = [prm[:, k].view(-1, 1, 1) for k in range(4)]
-    M = u_new.shape[-1]
-    x = torch.arange(M, device=u_new.device, dtype=u_new.dtype) * h
-    X = x.view(1, 1, M)
-    Y = x.view(1, M, 1)
-    c = u_new[:, 1:-1, 1:-1]
-    uxx = (u_new[:, 1:-1, 2:] - 2 * c + u_new[:, 1:-1, :-2]) / h ** 2
-    uyy = (u_new[:, 2:, 1:-1] - 2 * c + u_new[:, :-2, 1:-1]) / h ** 2
-    uxy = (u_new[:, 2:, 2:] + u_new[:, :-2, :-2] - u_new[:, :-2, 2:] - u_new[:, 2:, :-2]) / (4 * h * h)
-    ux = (u_new[:, 1:-1, 2:] - u_new[:, 1:-1, :-2]) / (2 * h)
-    uy = (u_new[:, 2:, 1:-1] - u_new[:, :-2, 1:-1]) / (2 * h)
-    Xi, Yi = X[:, :, 1:-1], Y[:, 1:-1, :]
-    Ru = (0.5 * s1 ** 2 * Xi ** 2 * uxx + 0.5 * s2 ** 2 * Yi ** 2 * uyy + rho * s1 * s2 * Xi * Yi * uxy
-          + r * Xi * ux + r * Yi * uy - r * c)
-    return (c - u_old[:, 1:-1, 1:-1]) / dtau - Ru
+class PhysicsLoss(torch.autograd.Function):
+    """Per-sample PDE term of the loss, eq. bs_totalloss's MSE_f, on the device: the mean
+    square of the residual of eq. (bse_change_variable) over the collocation points, from
+    the library (forward and gradient in one kernel launch)."""
+
+    @staticmethod
+    def forward(ctx, pred, u_prev, params, dtau, grid):
+        pred = pred.detach().contiguous()
+        u_prev = u_prev.detach().contiguous()
+        B = pred.shape[0]
+        loss = torch.empty(B, dtype=torch.float64, device=pred.device)
+        grad = torch.empty_like(pred)
+        bs.pino_physics_loss(grid, params, list(pred), list(u_prev), [dtau] * B, loss, list(grad))
+        ctx.save_for_backward(grad)
+        return loss.to(pred.dtype)
+
+    @staticmethod
+    def backward(ctx, g_loss):
+        (grad,) = ctx.saved_tensors
+        return g_loss.view(-1, 1, 1) * grad, None, None, None, None
+
+
+def sample_params(prm):
+    """bs_params of the samples of a batch (the residual needs sigma1, sigma2, rho, r only)."""
+    return [wl.Params(float(a), float(b), float(c), float(d)) for a, b, c, d in prm.tolist()]
 
 
 def generate(M, N, fine_steps, n_problems, seed, device, rough=0.0):
@@ -188,6 +198,7 @@ def main():
         print(f"data: {args.problems} trajectories x {N} slices of {fine} fine steps "
               f"({time.time() - t0:.1f} s)", flush=True)
     h = 4.0 / (M - 1)
+    grid = bs.Grid(M, 4.0)
     x = torch.arange(M, device=dev, dtype=torch.float32) * h
     Xg, Yg = x.view(1, M).expand(M, M), x.view(M, 1).expand(M, M)
     model = FNO().to(dev)
@@ -220,7 +231,7 @@ def main():
         inc2 = torch.mean((u1[:, :-1, :-1] - u0[:, :-1, :-1]) ** 2, dim=(1, 2)) + 1e-12
         data = torch.mean(torch.mean((pred[:, :-1, :-1] - u1[:, :-1, :-1]) ** 2, dim=(1, 2)) / inc2) * 1e-4
         bnd = torch.mean((pred[:, -1, :] - u1[:, -1, :]) ** 2) + torch.mean((pred[:, :, -1] - u1[:, :, -1]) ** 2)
-        phys = torch.mean(pde_residual(pred, u0, dtau, p, h) ** 2) * dtau ** 2
+        phys = torch.mean(PhysicsLoss.apply(pred, u0, sample_params(p), dtau, grid)) * dtau ** 2
         loss = data + 0.1 * bnd + args.physics_weight * phys
         opt.zero_grad(set_to_none=True)
         loss.backward()

@@ -55,6 +55,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.coarse_propagate(None, 0, None, C.byref(p), None, None, 0.0, 0.1, 1, None) == _lib.BS_ERR_ARG
     k = C.c_int()
     assert lib.parareal_solve(None, C.byref(p), 8, 16, 0, 4, None, 1e-4, 8, None, C.byref(k), None, None) == _lib.BS_ERR_ARG
+    assert lib.pino_physics_loss(None, C.byref(p), None, None, None, 1, None, None, None) == _lib.BS_ERR_ARG
     assert lib.bs_grid_destroy(None) == _lib.BS_OK
 
 
