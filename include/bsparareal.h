@@ -316,12 +316,13 @@ int bs_fine_sweeps(const bs_grid* g, const bs_params* p, double dtau, int first_
  *                        the same systems to the same Krylov tolerance).
  *  BS_OPT_FINE_TILE      layout of the fine stepper: 0 (default) per launch, the one with less
  *                        work counted in waves of co-resident clusters; 1 or 2 forces one.
- *                        Grids with M > 256 run as overlapping cluster tiles: 1 regions of
- *                        256 x 256 nodes (8 CTAs, up to 24 sweeps per launch), 2 regions of
- *                        288 x 288 (9 CTAs, up to 16 sweeps).  Grids with 128 < M <= 256 keep a
- *                        state in one cluster: 1 of 8 CTAs of 32 rows, 2 of 16 CTAs of 16 rows
- *                        (one CTA per SM; faster for one or a few states).  Smaller grids have
- *                        one layout.  All layouts give the same result bit for bit.
+ *                        Grids with M > 256 run as overlapping cluster tiles: layout 1 on
+ *                        regions of 256 x 256 nodes (8 CTAs, up to 24 sweeps per launch),
+ *                        layout 2 on regions of 288 x 288 (9 CTAs, up to 16 sweeps).  Grids
+ *                        with 128 < M <= 256 keep a state in one cluster: layout 1 on 8 CTAs
+ *                        of 32 rows, layout 2 on 16 CTAs of 16 rows (one CTA per SM; faster
+ *                        for one or a few states).  Smaller grids have one layout.  All
+ *                        layouts give the same result bit for bit.
  * Returns BS_OK or BS_ERR_ARG for an unknown option or an out-of-range value. */
 enum { BS_OPT_FINE_SWEEPS = 0, BS_OPT_JACOBI_TARGET = 1, BS_OPT_KRYLOV_TOL = 2,
        BS_OPT_KRYLOV_MAXIT = 3, BS_OPT_PHASE_TIMING = 4, BS_OPT_JACOBI_TARGET_COLD = 5,
