@@ -119,3 +119,33 @@ def test_trainer_backpropagates_the_physics_term(bs):
         want_g = wgt * physics.loss_grad(pred[b].astype(np.float64), prev[b].astype(np.float64), dt, w)
         got_g = t_pred.grad[b].detach().cpu().double().numpy()
         assert np.max(np.abs(got_g - want_g)) <= PHYS_REL_TOL * np.max(np.abs(want_g))
+
+
+def test_pino_training_runs_end_to_end(bs, tmp_path):
+    # a few iterations of the trainer (data from the library's F, the physics term from the
+    # library's kernel): it finishes, and the network it writes loads and runs as G
+    import re
+    import subprocess
+    import sys
+
+    import torch
+    out = str(tmp_path / "w.bin")
+    cmd = [sys.executable, "-m", "paper_2404_02521_gb300.pino_train", "--out", out, "--M", "64",
+           "--slices", "8", "--fine-dtau", str(1.0 / 2048), "--problems", "8", "--iters", "30",
+           "--batch", "4"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    errs = [float(v) for v in re.findall(r"N=8: ([0-9.eE+-]+|nan|inf)", r.stdout)]
+    assert errs and all(np.isfinite(errs)), r.stdout[-2000:]
+    net = bs.Pino(out)
+    try:
+        M, p = 64, PARAMS[0]
+        g = bs.Grid(M, 4.0)
+        X, Y = fd.mesh(M, 4.0)
+        u0 = to_gpu(fd.payoff(p, X, Y))
+        u1 = torch.empty_like(u0)
+        bs.coarse_propagate(g, bs.COARSE_PINO, net, p, u0, u1, 0.0, 1.0 / 8, 1)
+        torch.cuda.synchronize()
+        assert torch.isfinite(u1).all()
+    finally:
+        net.close()
