@@ -149,3 +149,24 @@ def test_pino_training_runs_end_to_end(bs, tmp_path):
         assert torch.isfinite(u1).all()
     finally:
         net.close()
+
+
+def test_physics_loss_of_a_large_batch(bs):
+    # more samples than one launch carries: the library splits the batch
+    import torch
+    M, B = 24, 40
+    rng = np.random.default_rng(9)
+    g = bs.Grid(M, 4.0)
+    ps = [PARAMS[b % 3] for b in range(B)]
+    dts = [0.01 * (1 + b % 5) for b in range(B)]
+    prev = [np.asarray(wl.random_field(rng, M), dtype=np.float32) for _ in range(B)]
+    pred = [np.asarray(a + 0.01 * wl.random_field(rng, M), dtype=np.float32) for a in prev]
+    loss = torch.empty(B, dtype=torch.float64, device="cuda")
+    bs.pino_physics_loss(g, ps, [to_gpu(a) for a in pred], [to_gpu(a) for a in prev], dts, loss)
+    torch.cuda.synchronize()
+    got = loss.cpu().numpy()
+    for b in range(B):
+        p = ps[b]
+        w = fd.stencil_weights(M, 4.0, p.sigma1, p.sigma2, p.rho, p.r)
+        want = physics.loss(pred[b].astype(np.float64), prev[b].astype(np.float64), dts[b], w)
+        assert abs(got[b] - want) <= PHYS_REL_TOL * want, b
