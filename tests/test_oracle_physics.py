@@ -60,3 +60,43 @@ def test_gradient_matches_finite_differences(M):
     np.testing.assert_allclose(g, fdg, rtol=1e-6, atol=1e-6 * np.max(np.abs(fdg)))
     # the far edges hold no collocation point but are read by their neighbours' rows
     assert np.all(g[M - 1, :] != 0.0) and np.all(g[:, M - 1] != 0.0)
+
+
+def _fd_gradient(loss_fn, u_pred, eps=1e-6):
+    M = u_pred.shape[0]
+    out = np.zeros((M, M))
+    for j in range(M):
+        for i in range(M):
+            up = u_pred.copy(); up[j, i] += eps
+            um = u_pred.copy(); um[j, i] -= eps
+            out[j, i] = (loss_fn(up) - loss_fn(um)) / (2 * eps)
+    return out
+
+
+@pytest.mark.parametrize("kind", ["offset_sign", "missing_diag", "no_dtau"])
+def test_planted_gradient_mistakes_fail_the_finite_difference_pin(kind):
+    # plausible slips in writing the adjoint (the scatter to the negated offset, the
+    # dropped 1/dtau identity part, a factor dtau too many) must disagree with the
+    # finite differences that pin the correct gradient
+    M, dtau = 6, 0.02
+    rng = np.random.default_rng(4)
+    p = _params(rho=0.6)
+    w = fd.stencil_weights(M, 4.0, p.sigma1, p.sigma2, p.rho, p.r)
+    u_pred = rng.standard_normal((M, M))
+    u_prev = rng.standard_normal((M, M))
+    n = M - 1
+    r = physics.residual(u_pred, u_prev, dtau, w)
+    c = 2.0 * r / (n * n)
+    g = np.zeros((M, M))
+    if kind != "missing_diag":
+        g[:n, :n] += c / dtau * (dtau if kind == "no_dtau" else 1.0)
+    J, I = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for (di, dj), wt in w.items():
+        sgn = -1 if kind == "offset_sign" else 1
+        tj, ti = J + sgn * dj, I + sgn * di
+        ok = (tj >= 0) & (ti >= 0) & (tj < M) & (ti < M)
+        np.add.at(g, (tj[ok], ti[ok]), -(c * wt[:n, :n])[ok])
+    want = _fd_gradient(lambda u: physics.loss(u, u_prev, dtau, w), u_pred)
+    assert np.max(np.abs(g - want)) > 1e-3 * np.max(np.abs(want))
+    np.testing.assert_allclose(physics.loss_grad(u_pred, u_prev, dtau, w), want, rtol=1e-6,
+                               atol=1e-6 * np.max(np.abs(want)))
